@@ -1,0 +1,195 @@
+"""Pins of the oracle's multilevel machinery: level bands (Eqs. def:qlevels,
+decomposition), level selection (Theorem levels, Eq. costrecurrence, the top-level
+sample constraint of Section 3.2.1), sample allocation (Eqs. optSamples, optMu,
+totalCost) and the multilevel estimator (Eq. multiEstimator)."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from paper_2103_10516_gb300 import synth
+
+
+def test_bands_sum_to_quadratic_form(O):
+    m = synth.grid_laplacian_2d(10, shift=0.1)
+    n = 40
+    c = O.cheb_coeffs("log", 0.1, 8.1, n)
+    mu = O.moments(m, 0.1, 8.1, 0, 0, [n] * 3)
+    for levels in ([n], [0, n], [3, 9, 27, n], list(range(0, n + 1))):
+        lo = -1
+        tot = np.zeros(3)
+        for hi in levels:
+            tot += O.band(c, mu, lo, hi)
+            lo = hi
+        assert np.allclose(tot, mu @ c, rtol=0, atol=1e-12 * np.sum(np.abs(c)) * 100)
+
+
+def test_band_means_exact_under_exhaustive_signs(O):
+    # E[Q_{l'l}] = sum_{j=l'+1..l} c_j tr T_j(At): exact over all 2^d sign vectors
+    d = 9
+    m = synth.random_symmetric(d, 0.5, seed=2, diag_shift=2.0)
+    lam = np.linalg.eigvalsh(m.to_dense())
+    a, b = lam[0] - 0.3, lam[-1] + 0.3
+    n = 10
+    c = O.cheb_coeffs("exp", a, b, n)
+    Z = np.array(list(itertools.product([-1.0, 1.0], repeat=d)))
+    mu = O.moments_z(m, a, b, Z, n)
+    th = np.arccos((2 * lam - (a + b)) / (b - a))
+    tr = [np.sum(np.cos(j * th)) for j in range(n + 1)]
+    for lo, hi in ((-1, 2), (2, 5), (5, 10), (-1, 10)):
+        exact = sum(c[j] * tr[j] for j in range(lo + 1, hi + 1))
+        assert abs(O.band(c, mu, lo, hi).mean() - exact) < 1e-11 * d * np.sum(np.abs(c))
+
+
+def _path_cost(V, levels, model):
+    prev = [0] + levels[:-1]
+    return sum(math.sqrt(V[lp, l] * O_cost(l, model)) for lp, l in zip(prev, levels))
+
+
+def O_cost(l, model):
+    return float(l) if model == "linear" else float((l + 1) // 2)
+
+
+def _random_V(n, rng):
+    # a plausible variance table: V[l', l] from random per-term spreads and
+    # correlations, so that it is a genuine covariance-derived table
+    terms = rng.standard_normal((25, n + 1)) * np.exp(-0.3 * np.arange(n + 1))[None, :]
+    V = np.zeros((n + 1, n + 1))
+    for lo in range(n):
+        for hi in range(lo + 1, n + 1):
+            V[lo, hi] = np.var(terms[:, lo + 1: hi + 1].sum(axis=1), ddof=1)
+    return V
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("model", ["symmetric", "linear"])
+def test_level_dp_matches_brute_force(O, seed, model):
+    rng = np.random.default_rng(seed)
+    n = 9
+    V = _random_V(n, rng)
+    levels = O.select_levels(V, model, m_pilot=0)
+    best = min(_path_cost(V, list(s) + [n], model)
+               for r in range(n) for s in itertools.combinations(range(1, n), r))
+    assert levels[-1] == n and levels == sorted(set(levels))
+    assert abs(_path_cost(V, levels, model) - best) < 1e-12 * best
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("max_levels", [0, 2, 3])
+def test_constrained_dp_matches_brute_force(O, seed, max_levels):
+    # the top-level constraint m_L = mu sqrt(V_L / C_L) >= m_pilot, budget mode,
+    # mu = budget / sum sqrt(V_k C_k); optionally at most max_levels levels
+    rng = np.random.default_rng(100 + seed)
+    n = 9
+    V = _random_V(n, rng)
+    budget = float(rng.uniform(20, 400))
+    m_pilot = 5
+    levels = O.select_levels(V, "symmetric", m_pilot=m_pilot, mode="budget", target=budget,
+                             max_levels=max_levels)
+    cands = []
+    for r in range(n):
+        for s in itertools.combinations(range(1, n), r):
+            lv = list(s) + [n]
+            if max_levels and len(lv) > max_levels:
+                continue
+            S = _path_cost(V, lv, "symmetric")
+            lp = lv[-2] if len(lv) > 1 else 0
+            mL = budget / S * math.sqrt(V[lp, n] / O_cost(n, "symmetric"))
+            if mL >= m_pilot:
+                cands.append((S, lv))
+    if not cands:
+        assert levels == [n]
+    else:
+        best = min(S for S, _ in cands)
+        assert abs(_path_cost(V, levels, "symmetric") - best) < 1e-12 * best
+
+
+def test_allocation_is_kkt_optimal(O):
+    # m_k = mu sqrt(V_k / C_k) minimises sum V_k / m_k subject to sum m_k C_k = C
+    rng = np.random.default_rng(0)
+    n = 30
+    V = _random_V(n, rng)
+    levels = [2, 7, 15, n]
+    budget = 5000.0
+    prev = [0] + levels[:-1]
+    Vk = np.array([V[lp, l] for lp, l in zip(prev, levels)])
+    Ck = np.array([O_cost(l, "symmetric") for l in levels])
+    S = np.sum(np.sqrt(Vk * Ck))
+    mstar = budget / S * np.sqrt(Vk / Ck)
+    assert abs(np.sum(mstar * Ck) - budget) < 1e-9 * budget
+    # total-cost identity (Eq. totalCost): variance eps^2 = S^2 / C at the optimum
+    assert abs(np.sum(Vk / mstar) - S * S / budget) < 1e-12 * S * S / budget
+    f0 = np.sum(Vk / mstar)
+    for _ in range(200):
+        dm = rng.standard_normal(len(levels))
+        dm -= Ck * (dm @ Ck) / (Ck @ Ck)          # stay on the budget plane
+        m2 = mstar + 0.05 * mstar.min() * dm / np.max(np.abs(dm))
+        assert np.sum(Vk / m2) >= f0 * (1 - 1e-12)
+    got = O.allocate(levels, V, "symmetric", "budget", budget)
+    assert got == [max(1, math.ceil(v)) for v in mstar]
+    # variance mode: mu = eps^-2 S gives variance sum V_k/m_k = eps^2
+    eps2 = 1e-3 * S * S / budget
+    mv = S / eps2 * np.sqrt(Vk / Ck)
+    assert abs(np.sum(Vk / mv) - eps2) < 1e-12 * eps2
+    assert O.allocate(levels, V, "symmetric", "variance", eps2) == \
+        [max(1, math.ceil(v)) for v in mv]
+
+
+def test_paper_level_table_arithmetic():
+    # Table level_example: 18 levels of a typical nuclear-norm trial; with the
+    # cost l per sample the samples add to 15,048 matvecs (caption: 15,070 for a
+    # budget of 15,000), consistent with counts rounded up and the top level
+    # holding at least m_pilot = 10 samples.
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "level_example.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    levels = [int(r[0]) for r in rows]
+    samples = [int(r[1]) for r in rows]
+    assert len(levels) == 18 and levels[-1] == 300
+    assert sum(l * m for l, m in zip(levels, samples)) == 15048
+    assert samples[-1] >= 10
+
+
+def _c1_logdet_closed_form():
+    # eigenvalues of the 64x64 Dirichlet 5-point Laplacian + 0.1 I
+    k = np.arange(1, 65)
+    e = 2.0 - 2.0 * np.cos(k * np.pi / 65.0)
+    lam = (e[:, None] + e[None, :]).ravel() + 0.1
+    return lam
+
+
+def test_c1_closed_form_and_estimate(O):
+    m = synth.grid_laplacian_2d(64, shift=0.1)
+    assert m.nnz == 20224
+    lo, hi = O.gershgorin(m)
+    assert abs(lo - 0.1) < 1e-12 and abs(hi - 8.1) < 1e-12
+    lam = _c1_logdet_closed_form()
+    logdet = float(np.sum(np.log(lam)))
+    assert abs(logdet - 5018.30909251356) < 1e-8
+    sign, ld = np.linalg.slogdet(m.to_dense())
+    assert sign == 1.0 and abs(ld - logdet) < 1e-9 * logdet
+    n = 128
+    c = O.cheb_coeffs("log", 0.1, 8.1, n)
+    trp = float(np.sum(O.cheb_eval(c, (2 * lam - 8.2) / 8.0)))
+    assert abs(trp - logdet) < 1e-3            # interpolation error of p_128
+    out = O.mlmc_fixed(m, "log", 0.1, 8.1, n, [8, 32, 128], [256, 64, 16], seed=0)
+    assert out["m"] == [256, 64, 16]
+    assert abs(out["estimate"] - trp) < 5 * out["stderr"]
+    # level means telescope to the estimate
+    assert abs(sum(out["level_mean"]) - out["estimate"]) < 1e-9
+
+
+def test_auto_mlmc_consistent(O):
+    m = synth.grid_laplacian_2d(16, shift=0.1)
+    n = 40
+    out = O.mlmc_auto(m, "log", 0.1, 8.1, n, seed=1, m_pilot=10, mode="budget", target=4000.0)
+    assert out["levels"][-1] == n
+    assert out["m"][-1] >= 10
+    spent = sum(mk * O_cost(l, "symmetric") for mk, l in zip(out["m"], out["levels"]))
+    assert spent >= 4000.0 - 1e-9 and spent <= 4000.0 + sum(O_cost(l, "symmetric")
+                                                             for l in out["levels"])
+    lam = np.linalg.eigvalsh(m.to_dense())
+    c = O.cheb_coeffs("log", 0.1, 8.1, n)
+    trp = float(np.sum(O.cheb_eval(c, (2 * lam - 8.2) / 8.0)))
+    assert abs(out["estimate"] - trp) < 5 * out["stderr"]
