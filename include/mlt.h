@@ -1,0 +1,251 @@
+/*
+ * mlt.h -- C ABI of the GB300 multilevel Chebyshev-Hutchinson trace engine.
+ *
+ * Estimates tr f(A) = sum_i f(lambda_i) for a large sparse symmetric A
+ * (Hallman & Troester, "A Multilevel Approach to Stochastic Trace Estimation",
+ * Section 1, Eq. def:trace) by Hutchinson's estimator with Rademacher probes
+ * (Section 2.1, Eq. def:mcEstimate), a degree-n Chebyshev interpolant of f
+ * (Section 2.2, Eq. chebSeries) and multilevel Monte Carlo over bands of its
+ * coefficients (Section 3, Eqs. def:qlevels, decomposition; Section 4,
+ * Eq. multiEstimator).  Triangle counting uses tr(A^3)/6 with control variates
+ * (Section 5.4).
+ *
+ * Conventions shared by every entry point
+ *   - Return value: MLT_OK (0) on success, a negative MLT_E* code otherwise.
+ *     No call aborts the process or throws; mlt_last_error() returns a message
+ *     for the calling thread's most recent failure.
+ *   - Arrays passed in are owned by the caller.  A pointer documented as
+ *     "host or device" may be either: the library asks the CUDA driver which
+ *     one it is.  Device pointers must be on the current device.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls return
+ *     after their results are in the caller's arrays (host outputs) or after
+ *     the work producing them has been queued on `stream` (device outputs of
+ *     mlt_moments); scratch buffers belong to the matrix handle, so calls on
+ *     one handle must not overlap.
+ *   - CSR layout: rowptr int64[nrows+1], col int32[nnz] (each row's columns
+ *     ascending, no duplicates), values per val_type.
+ *   - Probes: probe id p (a global counter) has entries
+ *       z_i = +1 if bit 63 of mix64(((p << 32) | i) ^ (seed * 0x9E3779B97F4A7C15)) is 0,
+ *       z_i = -1 otherwise,
+ *     mix64 the SplitMix64 output finaliser (Steele, Lea, Flood 2014).  The
+ *     paper only asks for Rademacher entries (Section 2.1); fixing the
+ *     generator makes every result reproducible under any blocking.
+ */
+#ifndef MLT_H
+#define MLT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define MLT_OK        0
+#define MLT_EINVAL   (-1)  /* bad argument (null pointer, size, interval, ...) */
+#define MLT_ENOMEM   (-2)  /* device or host allocation failed                 */
+#define MLT_ECUDA    (-3)  /* a CUDA call failed                               */
+#define MLT_ERANGE   (-4)  /* result bound exceeded (int64 triangle bound, ...) */
+#define MLT_ETIMEOUT (-5)  /* a bounded device wait gave up                    */
+
+/* ---- value types of mlt_create_csr --------------------------------------- */
+#define MLT_F64      0     /* vals is double[nnz]                            */
+#define MLT_F32      1     /* vals is float[nnz]                             */
+#define MLT_PATTERN  2     /* vals ignored: every stored entry equals 1      */
+
+/* ---- flags of mlt_create_csr --------------------------------------------- */
+#define MLT_GRAM        1u /* the operator is A = X^T X of the given X        */
+#define MLT_DEVICE_PTRS 2u /* rowptr/col/vals are device pointers; they are
+                              referenced, not copied, and must outlive the
+                              handle                                         */
+
+/* ---- functions f of mlt_cheb_coeffs -------------------------------------- */
+#define MLT_FN_LOG   0     /* log x      (log-determinant)                   */
+#define MLT_FN_SQRT  1     /* sqrt x     (nuclear norm with A = X^T X)       */
+#define MLT_FN_EXP   2     /* exp x      (Estrada index)                     */
+#define MLT_FN_INV   3     /* 1/x        (trace of the inverse)              */
+#define MLT_FN_POW   4     /* x^p        (Schatten p-norms use p/2)          */
+#define MLT_FN_CUBE  5     /* x^3        (triangle counting, tr A^3)         */
+
+/* ---- precision of mlt_moments -------------------------------------------- */
+#define MLT_PREC_FP64 0    /* vectors, SpMM and dots in FP64                 */
+#define MLT_PREC_FP32 1    /* vectors and SpMM in FP32, dots summed in FP64  */
+
+/* ---- flags of mlt_moments ------------------------------------------------ */
+#define MLT_DIRECT   1u    /* mu_j = z . V_j at every step (n matvecs for
+                              degree n) instead of the doubling identities
+                              mu_2k = 2 V_k.V_k - mu_0,
+                              mu_2k+1 = 2 V_k+1.V_k - mu_1 (ceil(n/2) matvecs) */
+
+/* ---- spectrum interval methods ------------------------------------------- */
+#define MLT_BOUNDS_GERSHGORIN 0
+
+/* ---- multilevel parameters ------------------------------------------------ */
+#define MLT_MAX_LEVELS 1024
+#define MLT_MAX_DEGREE 4096
+#define MLT_MODE_BUDGET    0   /* target = total cost C in cost-model units   */
+#define MLT_MODE_VARIANCE  1   /* target = estimator variance eps^2           */
+#define MLT_COST_SYMMETRIC 0   /* C_{l'l} = ceil(l/2)  (Section 3.1)          */
+#define MLT_COST_LINEAR    1   /* C_{l'l} = l          (Section 3.1)          */
+
+typedef struct mlt_matrix mlt_matrix;   /* opaque; owns device copies */
+
+/*
+ * Create a matrix handle from a CSR matrix (nrows x ncols, nnz entries).
+ * The stored entries are multiplied by `scale` (use 1.0 for none; a 0/1
+ * adjacency scaled to a chosen spectral radius uses scale != 1).  Without
+ * MLT_GRAM the matrix must be square and symmetric (symmetry is the caller's
+ * promise, not checked) and the operator is A itself; with MLT_GRAM the
+ * operator is A = X^T X (dimension ncols), applied as X^T (X v) (Section 1,
+ * footnote on Schatten norms).  Host arrays are copied to the device (on
+ * `stream`, finished before return); with MLT_DEVICE_PTRS they are used in
+ * place.  Errors: MLT_EINVAL on negative sizes, null arrays with nnz > 0,
+ * nnz > 2^31-1, rowptr[0] != 0 or rowptr[nrows] != nnz; MLT_ENOMEM; MLT_ECUDA.
+ */
+int mlt_create_csr(int64_t nrows, int64_t ncols, int64_t nnz,
+                   const int64_t* rowptr, const int32_t* col, const void* vals,
+                   int val_type, double scale, unsigned flags, void* stream,
+                   mlt_matrix** out);
+
+/* Release a handle and every device buffer it owns (NULL is a no-op). */
+int mlt_destroy(mlt_matrix* m);
+
+/* Operator dimension d (nrows, or ncols for a Gram handle) and stored nnz. */
+int mlt_matrix_info(const mlt_matrix* m, int64_t* dim, int64_t* nnz);
+
+/*
+ * Interval [a, b] containing the spectrum of the operator.  The map
+ * g(x) = (2x - a - b)/(b - a) needs one (Section 2.2).  MLT_BOUNDS_GERSHGORIN:
+ * Gershgorin discs (min_i a_ii - r_i, max_i a_ii + r_i) for A; for a Gram
+ * handle [0, ||X||_1 ||X||_inf].  `steps` and `seed` are reserved (pass 0).
+ */
+int mlt_spectrum_bounds(mlt_matrix* m, int method, int steps, uint64_t seed,
+                        double* a, double* b);
+
+/*
+ * Chebyshev coefficients c[0..n] of the degree-n interpolant of
+ * f~ = f o g^{-1} on [-1, 1] at the nodes x_j = cos(j pi / n), 0 <= j <= n
+ * (Section 2.2, Eq. chebSeries and the node formula), so that
+ * f(x) ~= sum_j c_j T_j(g(x)) on [a, b].  `p` is the exponent for MLT_FN_POW.
+ * c: host array of n+1 doubles.  Errors: MLT_EINVAL for n < 1 or n > MLT_MAX_DEGREE,
+ * a >= b, an unknown fn, or f undefined somewhere on [a, b] (log/sqrt/pow of a
+ * negative number, 1/x across 0).
+ */
+int mlt_cheb_coeffs(int fn, double p, double a, double b, int n, double* c);
+
+/*
+ * Chebyshev moments mu[p][j] = z_p^T T_j(At) z_p, j = 0..degree[p], with
+ * At = (2A - (a+b) I)/(b-a) and z_p the probe with id probe_offset + p
+ * (Section 2.2: the three-term recurrence Eq. recurrence applied to a block of
+ * probes; the doubling identities unless MLT_DIRECT).  Each probe stops at its
+ * own degree, so one call serves all levels of a multilevel run.
+ *   degree : host int32[nprobes], each 0..MLT_MAX_DEGREE.
+ *   mu     : host or device double[nprobes * ld_mu], row p = probe p;
+ *            entries j > degree[p] are set to 0.  ld_mu >= max degree + 1.
+ *   precision: MLT_PREC_FP64 or MLT_PREC_FP32; flags: 0 or MLT_DIRECT.
+ * Errors: MLT_EINVAL (a >= b, bad sizes, ld_mu too small), MLT_ENOMEM,
+ * MLT_ECUDA.  Moments with |mu_j| > d (1 + 1e-6), impossible when the spectrum
+ * lies in [a, b], give MLT_ERANGE after the results are written.
+ */
+int mlt_moments(mlt_matrix* m, double a, double b, uint64_t seed,
+                int64_t probe_offset, int64_t nprobes, const int32_t* degree,
+                int precision, unsigned flags, double* mu, int64_t ld_mu,
+                void* stream);
+
+typedef struct {
+    int fn;                          /* MLT_FN_*                                  */
+    double fn_p;                     /* exponent for MLT_FN_POW                   */
+    double a, b;                     /* spectrum interval, a < b                  */
+    int n;                           /* interpolant degree, 1..MLT_MAX_DEGREE     */
+    uint64_t seed;                   /* probe seed; probe ids start at 0          */
+    int nlevels;                     /* > 0: fixed levels/m below; 0: automatic   */
+    int32_t levels[MLT_MAX_LEVELS];  /* fixed: 0 <= l_1 < ... < l_L = n           */
+    int64_t m[MLT_MAX_LEVELS];       /* fixed: samples per level (>= 1)           */
+    int m_pilot;                     /* automatic: pilot probes at degree n (>= 2) */
+    int mode;                        /* automatic: MLT_MODE_BUDGET / _VARIANCE    */
+    double target;                   /* automatic: budget C or variance eps^2     */
+    int cost_model;                  /* MLT_COST_SYMMETRIC / MLT_COST_LINEAR      */
+    int max_levels;                  /* automatic: at most this many levels, 0 = any */
+    int reuse_pilot;                 /* automatic: pilot rows count as top-level samples */
+    int precision;                   /* MLT_PREC_*                                */
+    unsigned flags;                  /* mlt_moments flags                         */
+    void* stream;                    /* cudaStream_t                              */
+} mlt_mlmc_params;
+
+typedef struct {
+    double estimate;                 /* Gamma_m of Eq. multiEstimator             */
+    double std_error;                /* sqrt(sum_k s_k^2 / m_k)                   */
+    int nlevels;
+    int32_t levels[MLT_MAX_LEVELS];
+    int64_t m[MLT_MAX_LEVELS];       /* samples used per level                    */
+    double level_mean[MLT_MAX_LEVELS];
+    double level_var[MLT_MAX_LEVELS];/* sample variance of each level's Q         */
+    int64_t probes;                  /* probe ids consumed (pilot included)       */
+    int64_t matvecs;                 /* operator applications, pilot included     */
+} mlt_mlmc_result;
+
+/* Default parameters: automatic levels, budget mode, symmetric cost model,
+ * reuse of the pilot, FP64. */
+void mlt_mlmc_default_params(mlt_mlmc_params* p);
+
+/*
+ * Multilevel estimate of tr p_n(At) ~= tr f(A) (Section 3; Section 4,
+ * Eq. multiEstimator).  Fixed mode (nlevels > 0): level k uses m[k] fresh
+ * probes, ids following those of level k-1 (level 1 starts at id 0), each run
+ * to degree levels[k]; its samples are Q_{l_{k-1} l_k} = sum of c_j mu_j over
+ * j = l_{k-1}+1 .. l_k (l_0 = -1).  Automatic mode (nlevels == 0): m_pilot
+ * probes (ids 0..m_pilot-1) at degree n give the variance of every band
+ * (Section 3.2.1); levels come from the dynamic programme of Theorem levels,
+ * where at l = n only predecessors whose path recommends at least m_pilot
+ * top-level samples are allowed; sample counts are
+ * m_k = max(1, ceil(mu sqrt(V_k/C_k))) (Eqs. optSamples, optMu); fresh probes
+ * follow the pilot's ids level by level.  All levels' probes run in one
+ * ragged mlt_moments call.  Errors as mlt_moments, plus MLT_EINVAL for bad
+ * parameters.
+ */
+int mlt_mlmc_estimate(mlt_matrix* m, const mlt_mlmc_params* p, mlt_mlmc_result* r);
+
+/*
+ * Triangle-count estimate tr(A^3)/6 for a symmetric 0/1 adjacency matrix with
+ * no self-loops (Section 2.1 Example; Section 5.4).  For probes
+ * probe_offset .. probe_offset+nprobes-1 it computes, exactly in int64,
+ * x1 = z^T A z, x2 = z^T A^2 z, x3 = z^T A^3 z (two sparse products per probe
+ * block, using the symmetry of the quadratic form), in blocks of `block`
+ * probes (block must be 128).  With use_cv the estimate is
+ * [mean x3 - a2 (mean x2 - nnz) - a1 mean x1] / 6 with a1, a2 the least-squares
+ * slopes of x3 on (x1, x2) (Section 5.4; tr A = 0, tr A^2 = nnz); without it,
+ * mean x3 / 6.  x (host or device int64[nprobes*3], may be NULL) receives the
+ * per-probe moments.  Errors: MLT_EINVAL (not a square pattern matrix, a
+ * self-loop, nprobes < 1, block != 128); MLT_ERANGE when the bound
+ * sum_(i,j) deg_i deg_j on |x3| reaches 2^62.
+ */
+int mlt_triangle_trace(mlt_matrix* m, uint64_t seed, int64_t probe_offset,
+                       int64_t nprobes, int block, int use_cv, int64_t* x,
+                       double* estimate, double* std_error, void* stream);
+
+/*
+ * Kernel timing (instrumentation; the paper has no counterpart).  Between
+ * mlt_profile_start() and mlt_profile_stop() every kernel the library launches
+ * is bracketed by a pair of CUDA events recorded on the stream it runs on.
+ * mlt_profile_stop waits for those events, disables timing and writes up to
+ * max_stats per-kernel totals (launch count, summed event time in ms) into
+ * stats (host array), the number written to *nstats.  Not thread-safe with
+ * respect to concurrent library calls on other threads.
+ */
+typedef struct {
+    char name[40];
+    int64_t launches;
+    double total_ms;
+} mlt_kernel_stat;
+
+int mlt_profile_start(void);
+int mlt_profile_stop(mlt_kernel_stat* stats, int max_stats, int* nstats);
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+const char* mlt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MLT_H */

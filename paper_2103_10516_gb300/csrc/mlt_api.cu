@@ -1,0 +1,836 @@
+// The C ABI declared in include/mlt.h: argument checking, device memory of the
+// matrix handles, probe ordering and grouping for the moment engine, and the
+// multilevel and triangle drivers that tie kernels and host arithmetic together.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "mlt_internal.h"
+
+namespace mlt {
+
+static thread_local std::string g_error;
+
+void set_error(const std::string& msg) { g_error = msg; }
+
+int fail(int code, const std::string& msg)
+{
+    g_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return MLT_OK;
+    g_error = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return MLT_ENOMEM;
+    return MLT_ECUDA;
+}
+
+// ---- kernel timing ---------------------------------------------------------
+namespace {
+struct ProfRec {
+    const char* name;
+    cudaEvent_t e0, e1;
+};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+std::vector<ProfRec> g_prof;
+std::vector<cudaEvent_t> g_event_pool;
+
+cudaEvent_t take_event()
+{
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+}  // namespace
+
+ProfScope::ProfScope(const char* name, cudaStream_t stream) : idx(-1), s(stream)
+{
+    if (!g_prof_on) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    ProfRec r{name, take_event(), take_event()};
+    if (!r.e0 || !r.e1) return;
+    cudaEventRecord(r.e0, s);
+    g_prof.push_back(r);
+    idx = (int)g_prof.size() - 1;
+}
+
+ProfScope::~ProfScope()
+{
+    if (idx < 0) return;
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    cudaEventRecord(g_prof[idx].e1, s);
+}
+
+int DevBuf::ensure(size_t want, cudaStream_t s)
+{
+    if (want <= bytes) return MLT_OK;
+    if (p) {
+        cudaFreeAsync(p, s);
+        p = nullptr;
+        bytes = 0;
+    }
+    size_t sz = want + want / 8;
+    sz = (sz + (1u << 21) - 1) & ~((size_t)(1u << 21) - 1);
+    cudaError_t e = cudaMallocAsync(&p, sz, s);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        return fail(MLT_ENOMEM, "device scratch allocation of " + std::to_string(sz) + " bytes failed");
+    }
+    bytes = sz;
+    return MLT_OK;
+}
+
+void DevBuf::release()
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+static bool is_device_ptr(const void* ptr)
+{
+    if (!ptr) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+static int dev_alloc_copy(T** dst, const void* src, size_t count, bool src_dev, cudaStream_t s)
+{
+    *dst = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMallocAsync((void**)dst, count * sizeof(T), s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MLT_ENOMEM, "cudaMallocAsync for the matrix failed");
+    }
+    if (src) {
+        MLT_CUDA_TRY(cudaMemcpyAsync(*dst, src, count * sizeof(T),
+                                     src_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    }
+    return MLT_OK;
+}
+
+__global__ void f32_to_f64_kernel(const float* __restrict__ in, double* __restrict__ out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
+// CSR sanity: rowptr non-decreasing within [0, nnz], columns in [0, ncols) and
+// strictly increasing inside each row.  bad[0] |= 1 (rowptr), 2 (column range),
+// 4 (order or duplicate).
+__global__ void validate_csr_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                    int64_t nrows, int64_t ncols, int64_t nnz, int* bad)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t beg = rowptr[r], end = rowptr[r + 1];
+        if (beg < 0 || end > nnz || end < beg) {
+            atomicOr(bad, 1);
+            continue;
+        }
+        int64_t prev = -1;
+        for (int64_t k = beg; k < end; ++k) {
+            const int64_t c = col[k];
+            if (c < 0 || c >= ncols) atomicOr(bad, 2);
+            else if (c <= prev) atomicOr(bad, 4);
+            prev = c;
+        }
+    }
+}
+
+// Gershgorin discs: lo_i = a_ii - r_i, hi_i = a_ii + r_i (scaled entries).
+__global__ void gershgorin_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                  const double* __restrict__ val, double scale, int64_t d,
+                                  double* lo_out, double* hi_out)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < d;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        double dg = 0.0, off = 0.0;
+        for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+            const double v = (val ? val[k] : 1.0) * scale;
+            if (col[k] == r) dg += v;
+            else off += fabs(v);
+        }
+        lo_out[r] = dg - off;
+        hi_out[r] = dg + off;
+    }
+}
+
+// ||X||_1 (max column sum) and ||X||_inf (max row sum) for a Gram bound.
+__global__ void absrow_kernel(const int64_t* __restrict__ rowptr, const double* __restrict__ val,
+                              double scale, int64_t nrows, double* out)
+{
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) s += fabs((val ? val[k] : 1.0) * scale);
+        out[r] = s;
+    }
+}
+
+int gershgorin_device(mlt_matrix* M, double* lo, double* hi, cudaStream_t s)
+{
+    int rc;
+    const bool gram = (M->flags & MLT_GRAM) != 0;
+    if (!gram) {
+        const int64_t d = M->A.nrows;
+        if ((rc = M->ws_out.ensure((size_t)2 * std::max<int64_t>(d, 1) * sizeof(double), s))) return rc;
+        double* buf = M->ws_out.as<double>();
+        const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((d + 255) / 256, 16LL * M->num_sms));
+        ProfScope ps("gershgorin", s);
+        gershgorin_kernel<<<nb, 256, 0, s>>>(M->A.rowptr, M->A.col, M->A.val64, M->scale, d, buf, buf + d);
+        MLT_CUDA_TRY(cudaGetLastError());
+        std::vector<double> h(2 * d);
+        MLT_CUDA_TRY(cudaMemcpyAsync(h.data(), buf, 2 * d * sizeof(double), cudaMemcpyDeviceToHost, s));
+        MLT_CUDA_TRY(cudaStreamSynchronize(s));
+        double l = INFINITY, u = -INFINITY;
+        for (int64_t i = 0; i < d; ++i) { l = std::min(l, h[i]); u = std::max(u, h[d + i]); }
+        *lo = l;
+        *hi = u;
+        return MLT_OK;
+    }
+    const int64_t nr = M->A.nrows, nc = M->A.ncols;
+    const int64_t tot = nr + nc;
+    if ((rc = M->ws_out.ensure((size_t)std::max<int64_t>(tot, 1) * sizeof(double), s))) return rc;
+    double* buf = M->ws_out.as<double>();
+    int nb = (int)std::max<int64_t>(1, std::min<int64_t>((nr + 255) / 256, 16LL * M->num_sms));
+    ProfScope ps("abs_row_sums", s);
+    absrow_kernel<<<nb, 256, 0, s>>>(M->A.rowptr, M->A.val64, M->scale, nr, buf);
+    nb = (int)std::max<int64_t>(1, std::min<int64_t>((nc + 255) / 256, 16LL * M->num_sms));
+    absrow_kernel<<<nb, 256, 0, s>>>(M->AT.rowptr, M->AT.val64, M->scale, nc, buf + nr);
+    MLT_CUDA_TRY(cudaGetLastError());
+    std::vector<double> h(tot);
+    MLT_CUDA_TRY(cudaMemcpyAsync(h.data(), buf, tot * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MLT_CUDA_TRY(cudaStreamSynchronize(s));
+    double rmax = 0.0, cmax = 0.0;
+    for (int64_t i = 0; i < nr; ++i) rmax = std::max(rmax, h[i]);
+    for (int64_t i = 0; i < nc; ++i) cmax = std::max(cmax, h[nr + i]);
+    *lo = 0.0;
+    *hi = rmax * cmax;
+    return MLT_OK;
+}
+
+static void free_matrix(mlt_matrix* M)
+{
+    void* owned[] = {M->own_rowptr, M->own_col, M->own_val, M->own_val32, M->own_t_rowptr,
+                     M->own_t_col, M->own_t_val, M->own_t_val32, M->upper};
+    for (void* p : owned)
+        if (p) cudaFree(p);
+    mlt::DevBuf* bufs[] = {&M->ws_v[0], &M->ws_v[1], &M->ws_w, &M->ws_part, &M->ws_dots,
+                           &M->ws_misc, &M->ws_out, &M->ws_y, &M->ws_z, &M->ws_x};
+    for (auto* b : bufs) b->release();
+}
+
+// Transpose a host CSR (counting sort by column; rows stay ascending).
+static void host_transpose(int64_t nrows, int64_t ncols, const int64_t* rp, const int32_t* ci,
+                           const double* v, std::vector<int64_t>& trp, std::vector<int32_t>& tci,
+                           std::vector<double>& tv)
+{
+    const int64_t nnz = rp[nrows];
+    trp.assign(ncols + 1, 0);
+    for (int64_t k = 0; k < nnz; ++k) ++trp[ci[k] + 1];
+    for (int64_t j = 0; j < ncols; ++j) trp[j + 1] += trp[j];
+    std::vector<int64_t> pos(trp.begin(), trp.end() - 1);
+    tci.resize(std::max<int64_t>(nnz, 1));
+    if (v) tv.resize(std::max<int64_t>(nnz, 1));
+    for (int64_t i = 0; i < nrows; ++i)
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+            const int64_t q = pos[ci[k]]++;
+            tci[q] = (int32_t)i;
+            if (v) tv[q] = v[k];
+        }
+}
+
+}  // namespace mlt
+
+using namespace mlt;
+
+extern "C" {
+
+const char* mlt_last_error(void) { return g_error.c_str(); }
+
+int mlt_profile_start(void)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto& r : g_prof) {
+        g_event_pool.push_back(r.e0);
+        g_event_pool.push_back(r.e1);
+    }
+    g_prof.clear();
+    g_prof_on = true;
+    return MLT_OK;
+}
+
+int mlt_profile_stop(mlt_kernel_stat* stats, int max_stats, int* nstats)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_on = false;
+    std::map<std::string, std::pair<int64_t, double>> agg;
+    int rc = MLT_OK;
+    for (auto& r : g_prof) {
+        float ms = 0.0f;
+        cudaError_t e = cudaEventSynchronize(r.e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.e0, r.e1);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "mlt_profile_stop");
+            continue;
+        }
+        auto& a = agg[r.name];
+        a.first += 1;
+        a.second += ms;
+        g_event_pool.push_back(r.e0);
+        g_event_pool.push_back(r.e1);
+    }
+    g_prof.clear();
+    int n = 0;
+    for (auto& kv : agg) {
+        if (stats && n < max_stats) {
+            std::memset(stats[n].name, 0, sizeof(stats[n].name));
+            std::strncpy(stats[n].name, kv.first.c_str(), sizeof(stats[n].name) - 1);
+            stats[n].launches = kv.second.first;
+            stats[n].total_ms = kv.second.second;
+        }
+        ++n;
+    }
+    if (nstats) *nstats = std::min(n, max_stats);
+    return rc;
+}
+
+int mlt_create_csr(int64_t nrows, int64_t ncols, int64_t nnz, const int64_t* rowptr,
+                   const int32_t* col, const void* vals, int val_type, double scale, unsigned flags,
+                   void* stream, mlt_matrix** out)
+{
+    try {
+        if (!out) return fail(MLT_EINVAL, "mlt_create_csr: null output handle");
+        *out = nullptr;
+        if (nrows < 0 || ncols < 0 || nnz < 0) return fail(MLT_EINVAL, "mlt_create_csr: negative size");
+        if (nnz > 2147483647LL) return fail(MLT_EINVAL, "mlt_create_csr: nnz must be below 2^31");
+        if (nrows > 2147483647LL || ncols > 2147483647LL)
+            return fail(MLT_EINVAL, "mlt_create_csr: dimensions must be below 2^31");
+        if (!rowptr) return fail(MLT_EINVAL, "mlt_create_csr: null rowptr");
+        if (nnz > 0 && !col) return fail(MLT_EINVAL, "mlt_create_csr: null col");
+        if (val_type != MLT_F64 && val_type != MLT_F32 && val_type != MLT_PATTERN)
+            return fail(MLT_EINVAL, "mlt_create_csr: unknown value type");
+        if (val_type != MLT_PATTERN && nnz > 0 && !vals)
+            return fail(MLT_EINVAL, "mlt_create_csr: null values");
+        if (!std::isfinite(scale)) return fail(MLT_EINVAL, "mlt_create_csr: scale must be finite");
+        const bool gram = (flags & MLT_GRAM) != 0;
+        if (!gram && nrows != ncols) return fail(MLT_EINVAL, "mlt_create_csr: matrix must be square");
+        if (flags & ~(MLT_GRAM | MLT_DEVICE_PTRS)) return fail(MLT_EINVAL, "mlt_create_csr: unknown flags");
+        const bool dev = (flags & MLT_DEVICE_PTRS) != 0;
+        cudaStream_t s = (cudaStream_t)stream;
+
+        int64_t r0 = 0, rn = 0;
+        if (dev) {
+            MLT_CUDA_TRY(cudaMemcpy(&r0, rowptr, sizeof(int64_t), cudaMemcpyDeviceToHost));
+            MLT_CUDA_TRY(cudaMemcpy(&rn, rowptr + nrows, sizeof(int64_t), cudaMemcpyDeviceToHost));
+        } else {
+            r0 = rowptr[0];
+            rn = rowptr[nrows];
+        }
+        if (r0 != 0 || rn != nnz) return fail(MLT_EINVAL, "mlt_create_csr: rowptr[0] must be 0 and rowptr[nrows] nnz");
+
+        int device = 0, num_sms = 0;
+        MLT_CUDA_TRY(cudaGetDevice(&device));
+        MLT_CUDA_TRY(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device));
+        mlt_matrix* M = new (std::nothrow) mlt_matrix();
+        if (!M) return fail(MLT_ENOMEM, "mlt_create_csr: host allocation failed");
+        int rc = MLT_OK;
+        auto bail = [&](int code) {
+            cudaStreamSynchronize(s);
+            free_matrix(M);
+            delete M;
+            return code;
+        };
+        M->device = device;
+        M->num_sms = num_sms;
+        M->val_type = val_type;
+        M->flags = flags;
+        M->scale = scale;
+        M->A.nrows = nrows;
+        M->A.ncols = ncols;
+        M->A.nnz = nnz;
+
+        // rowptr / col
+        if (dev) {
+            M->A.rowptr = rowptr;
+            M->A.col = col;
+        } else {
+            int64_t* rp = nullptr;
+            int32_t* ci = nullptr;
+            if ((rc = dev_alloc_copy(&rp, rowptr, nrows + 1, false, s))) return bail(rc);
+            M->own_rowptr = rp;
+            M->A.rowptr = rp;
+            if ((rc = dev_alloc_copy(&ci, col, nnz, false, s))) return bail(rc);
+            M->own_col = ci;
+            M->A.col = ci;
+        }
+        // reject malformed CSR arrays before any kernel indexes with them
+        {
+            int* bad = nullptr;
+            if (cudaMallocAsync((void**)&bad, sizeof(int), s) != cudaSuccess) return bail(fail(MLT_ENOMEM, "cudaMallocAsync failed"));
+            int hbad = 0;
+            cudaMemsetAsync(bad, 0, sizeof(int), s);
+            const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((nrows + 255) / 256, 16LL * num_sms));
+            ProfScope ps("validate_csr", s);
+            validate_csr_kernel<<<nb, 256, 0, s>>>(M->A.rowptr, M->A.col, nrows, ncols, nnz, bad);
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            cudaFreeAsync(bad, s);
+            if (e != cudaSuccess) return bail(cuda_fail(e, "CSR validation"));
+            if (hbad & 1) return bail(fail(MLT_EINVAL, "mlt_create_csr: rowptr must be non-decreasing within [0, nnz]"));
+            if (hbad & 2) return bail(fail(MLT_EINVAL, "mlt_create_csr: column index out of range"));
+            if (hbad & 4) return bail(fail(MLT_EINVAL, "mlt_create_csr: columns must increase strictly within each row"));
+        }
+        // values: always keep an FP64 copy; an FP32 copy is made when needed
+        if (val_type == MLT_F64) {
+            if (dev) {
+                M->A.val64 = (const double*)vals;
+            } else {
+                double* v = nullptr;
+                if ((rc = dev_alloc_copy(&v, vals, nnz, false, s))) return bail(rc);
+                M->own_val = v;
+                M->A.val64 = v;
+            }
+        } else if (val_type == MLT_F32) {
+            float* v32 = nullptr;
+            if (dev) {
+                M->A.val32 = (const float*)vals;
+            } else {
+                if ((rc = dev_alloc_copy(&v32, vals, nnz, false, s))) return bail(rc);
+                M->own_val32 = v32;
+                M->A.val32 = v32;
+            }
+            double* v = nullptr;
+            if ((rc = dev_alloc_copy(&v, nullptr, nnz, false, s))) return bail(rc);
+            M->own_val = v;
+            M->A.val64 = v;
+            if (nnz > 0) {
+                const int nb = (int)std::min<int64_t>((nnz + 255) / 256, 4096);
+                ProfScope ps("f32_to_f64", s);
+                f32_to_f64_kernel<<<nb, 256, 0, s>>>(M->A.val32, v, nnz);
+                if ((rc = cuda_fail(cudaGetLastError(), "f32_to_f64_kernel"))) return bail(rc);
+            }
+        }
+        if (gram) {
+            // X^T as its own CSR, built on the host from the (host) arrays
+            std::vector<int64_t> hrp;
+            std::vector<int32_t> hci;
+            std::vector<double> hv;
+            const int64_t* rp = rowptr;
+            const int32_t* ci = col;
+            const double* vv = nullptr;
+            if (dev || val_type != MLT_F64) {
+                hrp.resize(nrows + 1);
+                hci.resize(std::max<int64_t>(nnz, 1));
+                if ((rc = cuda_fail(cudaMemcpyAsync(hrp.data(), M->A.rowptr, (nrows + 1) * sizeof(int64_t),
+                                                    cudaMemcpyDeviceToHost, s), "copy rowptr"))) return bail(rc);
+                if (nnz && (rc = cuda_fail(cudaMemcpyAsync(hci.data(), M->A.col, nnz * sizeof(int32_t),
+                                                           cudaMemcpyDeviceToHost, s), "copy col"))) return bail(rc);
+                if (M->A.val64) {
+                    hv.resize(std::max<int64_t>(nnz, 1));
+                    if (nnz && (rc = cuda_fail(cudaMemcpyAsync(hv.data(), M->A.val64, nnz * sizeof(double),
+                                                               cudaMemcpyDeviceToHost, s), "copy vals"))) return bail(rc);
+                    vv = hv.data();
+                }
+                if ((rc = cuda_fail(cudaStreamSynchronize(s), "sync"))) return bail(rc);
+                rp = hrp.data();
+                ci = hci.data();
+            } else {
+                vv = (const double*)vals;
+            }
+            std::vector<int64_t> trp;
+            std::vector<int32_t> tci;
+            std::vector<double> tv;
+            host_transpose(nrows, ncols, rp, ci, vv, trp, tci, tv);
+            int64_t* drp = nullptr;
+            int32_t* dci = nullptr;
+            if ((rc = dev_alloc_copy(&drp, trp.data(), ncols + 1, false, s))) return bail(rc);
+            M->own_t_rowptr = drp;
+            if ((rc = dev_alloc_copy(&dci, tci.data(), nnz, false, s))) return bail(rc);
+            M->own_t_col = dci;
+            M->AT.nrows = ncols;
+            M->AT.ncols = nrows;
+            M->AT.nnz = nnz;
+            M->AT.rowptr = drp;
+            M->AT.col = dci;
+            if (vv) {
+                double* dv = nullptr;
+                if ((rc = dev_alloc_copy(&dv, tv.data(), nnz, false, s))) return bail(rc);
+                M->own_t_val = dv;
+                M->AT.val64 = dv;
+            }
+            if ((rc = cuda_fail(cudaStreamSynchronize(s), "sync"))) return bail(rc);
+        }
+        if ((rc = cuda_fail(cudaStreamSynchronize(s), "mlt_create_csr sync"))) return bail(rc);
+        *out = M;
+        return MLT_OK;
+    } catch (...) {
+        return fail(MLT_ENOMEM, "mlt_create_csr: exception");
+    }
+}
+
+int mlt_destroy(mlt_matrix* m)
+{
+    if (!m) return MLT_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    const int dev = m->device;
+    if (cur != dev) cudaSetDevice(dev);
+    cudaDeviceSynchronize();
+    free_matrix(m);
+    delete m;
+    if (cur != dev) cudaSetDevice(cur);
+    return MLT_OK;
+}
+
+int mlt_matrix_info(const mlt_matrix* m, int64_t* dim, int64_t* nnz)
+{
+    if (!m) return fail(MLT_EINVAL, "mlt_matrix_info: null handle");
+    if (dim) *dim = m->dim();
+    if (nnz) *nnz = m->A.nnz;
+    return MLT_OK;
+}
+
+int mlt_spectrum_bounds(mlt_matrix* m, int method, int steps, uint64_t seed, double* a, double* b)
+{
+    (void)steps;
+    (void)seed;
+    if (!m || !a || !b) return fail(MLT_EINVAL, "mlt_spectrum_bounds: null argument");
+    if (method != MLT_BOUNDS_GERSHGORIN) return fail(MLT_EINVAL, "mlt_spectrum_bounds: unknown method");
+    try {
+        return gershgorin_device(m, a, b, (cudaStream_t)0);
+    } catch (...) {
+        return fail(MLT_ENOMEM, "mlt_spectrum_bounds: exception");
+    }
+}
+
+int mlt_cheb_coeffs(int fn, double p, double a, double b, int n, double* c)
+{
+    try {
+        return cheb_coeffs_host(fn, p, a, b, n, c);
+    } catch (...) {
+        return fail(MLT_ENOMEM, "mlt_cheb_coeffs: exception");
+    }
+}
+
+int mlt_moments(mlt_matrix* m, double a, double b, uint64_t seed, int64_t probe_offset,
+                int64_t nprobes, const int32_t* degree, int precision, unsigned flags, double* mu,
+                int64_t ld_mu, void* stream)
+{
+    try {
+        if (!m) return fail(MLT_EINVAL, "mlt_moments: null handle");
+        if (nprobes < 0) return fail(MLT_EINVAL, "mlt_moments: negative probe count");
+        if (nprobes == 0) return MLT_OK;
+        if (!degree || !mu) return fail(MLT_EINVAL, "mlt_moments: null degree or mu");
+        if (!(a < b) || !std::isfinite(a) || !std::isfinite(b))
+            return fail(MLT_EINVAL, "mlt_moments: need finite a < b");
+        if (precision != MLT_PREC_FP64 && precision != MLT_PREC_FP32)
+            return fail(MLT_EINVAL, "mlt_moments: unknown precision");
+        if (flags & ~MLT_DIRECT) return fail(MLT_EINVAL, "mlt_moments: unknown flags");
+        if (probe_offset < 0 || probe_offset + nprobes > (1LL << 32))
+            return fail(MLT_EINVAL, "mlt_moments: probe ids must lie in [0, 2^32)");
+        int maxdeg = 0;
+        for (int64_t p = 0; p < nprobes; ++p) {
+            if (degree[p] < 0 || degree[p] > MLT_MAX_DEGREE)
+                return fail(MLT_EINVAL, "mlt_moments: degree out of range");
+            maxdeg = std::max(maxdeg, (int)degree[p]);
+        }
+        if (ld_mu < maxdeg + 1) return fail(MLT_EINVAL, "mlt_moments: ld_mu below max degree + 1");
+        const int direct = (flags & MLT_DIRECT) ? 1 : 0;
+        cudaStream_t s = (cudaStream_t)stream;
+        const int64_t d = m->dim();
+        int rc;
+
+        // output: caller's device array, or a device staging copy
+        const bool out_dev = is_device_ptr(mu);
+        double* mu_dev = mu;
+        const size_t out_bytes = (size_t)nprobes * ld_mu * sizeof(double);
+        if (!out_dev) {
+            if ((rc = m->ws_out.ensure(out_bytes, s))) return rc;
+            mu_dev = m->ws_out.as<double>();
+        }
+        // the probe order: by degree, descending (stable), so live probes are a prefix
+        std::vector<int64_t> order(nprobes);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int64_t x, int64_t y) { return degree[x] > degree[y]; });
+
+        // group size from the memory the V buffers may take
+        const size_t sv = precision == MLT_PREC_FP32 ? sizeof(float) : sizeof(double);
+        const bool gram = (m->flags & MLT_GRAM) != 0;
+        const size_t per_probe = sv * ((size_t)2 * std::max<int64_t>(d, 1) + (gram ? (size_t)m->A.nrows : 0));
+        size_t free_b = 0, total_b = 0;
+        MLT_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+        const size_t budget = std::min<size_t>((size_t)16 << 30, free_b / 3);
+        int64_t gmax = (int64_t)std::max<size_t>(8, budget / per_probe);
+        gmax = std::min<int64_t>(gmax, 1024);
+        const int64_t ngroups = (nprobes + gmax - 1) / gmax;
+        const int64_t gsz = (nprobes + ngroups - 1) / ngroups;
+
+        // device scratch: error flag + per-group ids/degrees/rows
+        const size_t meta = 256 + (size_t)gsz * (2 * sizeof(int64_t) + sizeof(int32_t)) + 256;
+        if ((rc = m->ws_misc.ensure(meta, s))) return rc;
+        char* base = m->ws_misc.as<char>();
+        int* err = reinterpret_cast<int*>(base);
+        int64_t* ids_dev = reinterpret_cast<int64_t*>(base + 256);
+        int64_t* row_dev = ids_dev + gsz;
+        int32_t* deg_dev = reinterpret_cast<int32_t*>(row_dev + gsz);
+        MLT_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+        std::vector<int64_t> hid(gsz), hrow(gsz);
+        std::vector<int32_t> hdeg(gsz);
+        for (int64_t g0 = 0; g0 < nprobes; g0 += gsz) {
+            const int B = (int)std::min<int64_t>(gsz, nprobes - g0);
+            int K = 0;
+            for (int c = 0; c < B; ++c) {
+                const int64_t p = order[g0 + c];
+                hid[c] = probe_offset + p;
+                hrow[c] = p;
+                hdeg[c] = degree[p];
+                K = std::max(K, direct ? degree[p] : (degree[p] + 1) / 2);
+            }
+            std::vector<int> act(std::max(K, 1));
+            for (int k = 0; k < K; ++k) {
+                int n = 0;
+                while (n < B && (direct ? hdeg[n] : (hdeg[n] + 1) / 2) > k) ++n;
+                act[k] = n;
+            }
+            MLT_CUDA_TRY(cudaMemcpyAsync(ids_dev, hid.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+            MLT_CUDA_TRY(cudaMemcpyAsync(row_dev, hrow.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+            MLT_CUDA_TRY(cudaMemcpyAsync(deg_dev, hdeg.data(), B * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+            MomentPlan plan;
+            plan.dim = d;
+            plan.B = B;
+            plan.ldv = (B + 7) & ~7;
+            plan.K = K;
+            plan.act = act.data();
+            plan.ids_dev = ids_dev;
+            plan.deg_dev = deg_dev;
+            plan.row_dev = row_dev;
+            plan.direct = direct;
+            if ((rc = run_moments_group(m, precision, plan, a, b, seed, mu_dev, ld_mu, err, s))) return rc;
+            if (g0 + gsz < nprobes) MLT_CUDA_TRY(cudaStreamSynchronize(s));   // host arrays reused
+        }
+        if (!out_dev) MLT_CUDA_TRY(cudaMemcpyAsync(mu, mu_dev, out_bytes, cudaMemcpyDeviceToHost, s));
+        int herr = 0;
+        MLT_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        MLT_CUDA_TRY(cudaStreamSynchronize(s));
+        if (herr) return fail(MLT_ERANGE, "mlt_moments: |mu_j| > d; the spectrum is not inside [a, b]");
+        return MLT_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(MLT_ENOMEM, "mlt_moments: host allocation failed");
+    } catch (...) {
+        return fail(MLT_ECUDA, "mlt_moments: exception");
+    }
+}
+
+void mlt_mlmc_default_params(mlt_mlmc_params* p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->fn = MLT_FN_LOG;
+    p->n = 64;
+    p->m_pilot = 10;
+    p->mode = MLT_MODE_BUDGET;
+    p->target = 1000.0;
+    p->cost_model = MLT_COST_SYMMETRIC;
+    p->reuse_pilot = 1;
+    p->precision = MLT_PREC_FP64;
+}
+
+int mlt_mlmc_estimate(mlt_matrix* m, const mlt_mlmc_params* P, mlt_mlmc_result* R)
+{
+    try {
+        if (!m || !P || !R) return fail(MLT_EINVAL, "mlt_mlmc_estimate: null argument");
+        const int n = P->n;
+        if (n < 1 || n > MLT_MAX_DEGREE) return fail(MLT_EINVAL, "mlt_mlmc_estimate: n out of range");
+        if (P->cost_model != MLT_COST_SYMMETRIC && P->cost_model != MLT_COST_LINEAR)
+            return fail(MLT_EINVAL, "mlt_mlmc_estimate: unknown cost model");
+        std::vector<double> c(n + 1);
+        int rc = cheb_coeffs_host(P->fn, P->fn_p, P->a, P->b, n, c.data());
+        if (rc) return rc;
+        const int64_t d = m->dim();
+        std::vector<int> levels;
+        std::vector<int64_t> counts, fresh;
+        std::vector<double> pilot;     // m_pilot x (n+1) moments, reused by the top level
+        int m_pilot = 0;
+        int64_t next_id = 0;
+        int64_t matvecs = 0;
+        const int dir = (P->flags & MLT_DIRECT) ? 1 : 0;
+        auto steps_of = [&](int l) -> int64_t { return dir ? l : (l + 1) / 2; };
+        if (P->nlevels > 0) {
+            if (P->nlevels > MLT_MAX_LEVELS) return fail(MLT_EINVAL, "mlt_mlmc_estimate: too many levels");
+            for (int k = 0; k < P->nlevels; ++k) {
+                const int l = P->levels[k];
+                if (l < 0 || l > n || (k > 0 && l <= P->levels[k - 1]))
+                    return fail(MLT_EINVAL, "mlt_mlmc_estimate: levels must rise strictly within [0, n]");
+                if (P->m[k] < 1) return fail(MLT_EINVAL, "mlt_mlmc_estimate: every level needs m >= 1");
+                levels.push_back(l);
+                counts.push_back(P->m[k]);
+            }
+            if (levels.back() != n) return fail(MLT_EINVAL, "mlt_mlmc_estimate: the last level must be n");
+            fresh = counts;
+        } else {
+            m_pilot = P->m_pilot;
+            if (m_pilot < 2) return fail(MLT_EINVAL, "mlt_mlmc_estimate: automatic mode needs m_pilot >= 2");
+            if (!(P->target > 0.0) || !std::isfinite(P->target))
+                return fail(MLT_EINVAL, "mlt_mlmc_estimate: target must be positive");
+            if (P->mode != MLT_MODE_BUDGET && P->mode != MLT_MODE_VARIANCE)
+                return fail(MLT_EINVAL, "mlt_mlmc_estimate: unknown mode");
+            pilot.assign((size_t)m_pilot * (n + 1), 0.0);
+            std::vector<int32_t> pdeg(m_pilot, n);
+            rc = mlt_moments(m, P->a, P->b, P->seed, 0, m_pilot, pdeg.data(), P->precision, P->flags,
+                             pilot.data(), n + 1, P->stream);
+            if (rc) return rc;
+            matvecs += (int64_t)m_pilot * steps_of(n);
+            next_id = m_pilot;
+            std::vector<double> V((size_t)(n + 1) * (n + 1));
+            band_variances(c.data(), n, pilot.data(), n + 1, m_pilot, V.data());
+            std::vector<int> lv(n + 1);
+            int L = 0;
+            const int mp = P->reuse_pilot ? m_pilot : 0;
+            rc = select_levels(V.data(), n, P->cost_model, mp, P->mode, P->target, P->max_levels, lv.data(), &L);
+            if (rc) return rc;
+            levels.assign(lv.begin(), lv.begin() + L);
+            counts.resize(L);
+            allocate_samples(levels.data(), L, V.data(), n, P->cost_model, P->mode, P->target, mp, counts.data());
+            fresh = counts;
+            if (P->reuse_pilot) fresh[L - 1] = counts[L - 1] - m_pilot;
+        }
+        const int L = (int)levels.size();
+        // one ragged moment call for all levels' fresh probes
+        int64_t total = 0;
+        for (int k = 0; k < L; ++k) total += fresh[k];
+        std::vector<int32_t> deg(total);
+        {
+            int64_t q = 0;
+            for (int k = 0; k < L; ++k)
+                for (int64_t i = 0; i < fresh[k]; ++i) deg[q++] = levels[k];
+        }
+        std::vector<double> mu((size_t)std::max<int64_t>(total, 1) * (n + 1));
+        if (total > 0) {
+            rc = mlt_moments(m, P->a, P->b, P->seed, next_id, total, deg.data(), P->precision, P->flags,
+                             mu.data(), n + 1, P->stream);
+            if (rc) return rc;
+        }
+        for (int k = 0; k < L; ++k) matvecs += fresh[k] * steps_of(levels[k]);
+        // combination (Eq. multiEstimator)
+        std::memset(R, 0, sizeof(*R));
+        double est = 0.0, var_sum = 0.0;
+        int64_t q = 0;
+        int lo = -1;
+        for (int k = 0; k < L; ++k) {
+            const int hi = levels[k];
+            std::vector<double> samples;
+            samples.reserve(counts[k]);
+            auto band = [&](const double* row) {
+                double s = 0.0;
+                for (int j = lo + 1; j <= hi; ++j) s += c[j] * row[j];
+                return s;
+            };
+            if (k == L - 1 && m_pilot > 0 && P->reuse_pilot)
+                for (int p = 0; p < m_pilot; ++p) samples.push_back(band(&pilot[(size_t)p * (n + 1)]));
+            for (int64_t i = 0; i < fresh[k]; ++i, ++q) samples.push_back(band(&mu[(size_t)q * (n + 1)]));
+            const int64_t mk = (int64_t)samples.size();
+            double mean = 0.0;
+            for (double v : samples) mean += v;
+            mean /= (double)mk;
+            double ss = 0.0;
+            for (double v : samples) ss += (v - mean) * (v - mean);
+            const double var = mk > 1 ? ss / (double)(mk - 1) : std::nan("");
+            R->levels[k] = hi;
+            R->m[k] = mk;
+            R->level_mean[k] = mean;
+            R->level_var[k] = var;
+            est += mean;
+            var_sum += var / (double)mk;
+            lo = hi;
+        }
+        R->nlevels = L;
+        R->estimate = est;
+        R->std_error = std::sqrt(var_sum);
+        R->probes = next_id + total;
+        R->matvecs = matvecs;
+        (void)d;
+        return MLT_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(MLT_ENOMEM, "mlt_mlmc_estimate: host allocation failed");
+    } catch (...) {
+        return fail(MLT_ECUDA, "mlt_mlmc_estimate: exception");
+    }
+}
+
+int mlt_triangle_trace(mlt_matrix* m, uint64_t seed, int64_t probe_offset, int64_t nprobes, int block,
+                       int use_cv, int64_t* x, double* estimate, double* std_error, void* stream)
+{
+    try {
+        if (!m) return fail(MLT_EINVAL, "mlt_triangle_trace: null handle");
+        if (m->val_type != MLT_PATTERN || (m->flags & MLT_GRAM) || m->A.nrows != m->A.ncols)
+            return fail(MLT_EINVAL, "mlt_triangle_trace: needs a square 0/1 pattern matrix");
+        if (nprobes < 1) return fail(MLT_EINVAL, "mlt_triangle_trace: need at least one probe");
+        if (block != 128) return fail(MLT_EINVAL, "mlt_triangle_trace: block must be 128");
+        if (probe_offset < 0 || probe_offset + nprobes > (1LL << 32))
+            return fail(MLT_EINVAL, "mlt_triangle_trace: probe ids must lie in [0, 2^32)");
+        cudaStream_t s = (cudaStream_t)stream;
+        int rc = tri_prepare(m, s);
+        if (rc) return rc;
+        const bool out_dev = x && is_device_ptr(x);
+        int64_t* x_dev = x;
+        const size_t xbytes = (size_t)nprobes * 3 * sizeof(int64_t);
+        if (!out_dev) {
+            if ((rc = m->ws_out.ensure(xbytes, s))) return rc;
+            x_dev = m->ws_out.as<int64_t>();
+        }
+        for (int64_t b0 = 0; b0 < nprobes; b0 += block) {
+            const int nb = (int)std::min<int64_t>(block, nprobes - b0);
+            if ((rc = tri_block(m, seed, probe_offset + b0, nb, x_dev + 3 * b0, s))) return rc;
+        }
+        std::vector<int64_t> hx(nprobes * 3);
+        MLT_CUDA_TRY(cudaMemcpyAsync(hx.data(), x_dev, xbytes, cudaMemcpyDeviceToHost, s));
+        MLT_CUDA_TRY(cudaStreamSynchronize(s));
+        if (x && !out_dev) std::memcpy(x, hx.data(), xbytes);
+        double mx = 0.0;
+        for (int64_t v : hx) mx = std::max(mx, std::fabs((double)v));
+        if ((double)nprobes * (double)nprobes * mx * mx >= 4.2e37)
+            return fail(MLT_ERANGE, "mlt_triangle_trace: moment sums would overflow 128-bit integers");
+        double est = 0.0, se = 0.0;
+        triangle_estimate_host(hx.data(), nprobes, m->A.nnz, use_cv, &est, &se);
+        if (estimate) *estimate = est;
+        if (std_error) *std_error = se;
+        return MLT_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(MLT_ENOMEM, "mlt_triangle_trace: host allocation failed");
+    } catch (...) {
+        return fail(MLT_ECUDA, "mlt_triangle_trace: exception");
+    }
+}
+
+}  // extern "C"

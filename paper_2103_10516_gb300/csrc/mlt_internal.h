@@ -1,0 +1,117 @@
+// Internal declarations shared by the translation units of libmlt.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "mlt.h"
+
+namespace mlt {
+
+// Thread-local error message behind mlt_last_error().
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define MLT_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t e_ = (expr);                             \
+        if (e_ != cudaSuccess) return ::mlt::cuda_fail(e_, #expr); \
+    } while (0)
+
+// Kernel timing: while mlt_profile_start() is in effect, every library kernel
+// launch is bracketed by CUDA events recorded on its own stream.
+struct ProfScope {
+    int idx;
+    cudaStream_t s;
+    ProfScope(const char* name, cudaStream_t stream);
+    ~ProfScope();
+};
+
+// A grow-only device buffer owned by a matrix handle.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    int ensure(size_t want, cudaStream_t s);
+    void release();
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+// One CSR operand on the device.
+struct DevCSR {
+    int64_t nrows = 0, ncols = 0, nnz = 0;
+    const int64_t* rowptr = nullptr;
+    const int32_t* col = nullptr;
+    const double* val64 = nullptr;   // null for a pattern matrix
+    const float* val32 = nullptr;    // FP32 copy of the values (lazily made)
+};
+
+}  // namespace mlt
+
+struct mlt_matrix {
+    int device = 0;
+    int num_sms = 0;
+    int val_type = MLT_PATTERN;
+    unsigned flags = 0;
+    double scale = 1.0;
+    mlt::DevCSR A;     // A itself, or X for a Gram handle
+    mlt::DevCSR AT;    // X^T for a Gram handle
+    bool owns = true;
+    // owned device allocations (null when referencing caller memory)
+    void* own_rowptr = nullptr; void* own_col = nullptr; void* own_val = nullptr;
+    void* own_val32 = nullptr;
+    void* own_t_rowptr = nullptr; void* own_t_col = nullptr; void* own_t_val = nullptr;
+    void* own_t_val32 = nullptr;
+    // triangle preparation: first index of each row with col > row
+    int64_t* upper = nullptr;
+    int tri_state = 0;          // 0 unprepared, 1 ready, <0 error code
+    double tri_bound = 0.0;     // sum_(i,j) deg_i deg_j
+    // scratch
+    mlt::DevBuf ws_v[2], ws_w, ws_part, ws_dots, ws_misc, ws_out, ws_y, ws_z, ws_x;
+    int64_t dim() const { return (flags & MLT_GRAM) ? A.ncols : A.nrows; }
+};
+
+namespace mlt {
+
+// ---- Chebyshev moment kernels (cheb_kernels.cu) -----------------------------
+struct MomentPlan {
+    int64_t dim;            // operator dimension d
+    int B;                  // probes in this group (sorted by degree, descending)
+    int ldv;                // row stride of the V buffers (>= B, multiple of 8)
+    int K;                  // steps of the longest probe
+    const int* act;         // host: active probes at step k (k < K)
+    const int64_t* ids_dev; // device: global probe id of each sorted probe
+    const int32_t* deg_dev; // device: degree of each sorted probe
+    const int64_t* row_dev; // device: output row of each sorted probe
+    int direct;
+};
+
+int run_moments_group(mlt_matrix* M, int precision, const MomentPlan& plan, double a, double b,
+                      uint64_t seed, double* mu_dev, int64_t ld_mu, int* err_flag_dev,
+                      cudaStream_t s);
+
+int ensure_fp32_values(mlt_matrix* M, cudaStream_t s);
+
+// ---- triangle kernels (tri_kernels.cu) ---------------------------------------
+int tri_prepare(mlt_matrix* M, cudaStream_t s);
+int tri_block(mlt_matrix* M, uint64_t seed, int64_t id0, int nb, int64_t* x_dev, cudaStream_t s);
+
+// ---- misc kernels -----------------------------------------------------------
+int gershgorin_device(mlt_matrix* M, double* lo, double* hi, cudaStream_t s);
+
+// ---- host-side method (mlt_host.cpp) -----------------------------------------
+int cheb_coeffs_host(int fn, double p, double a, double b, int n, double* c);
+double cost_of(int l, int model);
+// V is (n+1) x (n+1) row-major: V[lo*(n+1)+hi], sample variance of Q_{lo,hi}.
+void band_variances(const double* c, int n, const double* mu, int64_t ld, int m, double* V);
+int select_levels(const double* V, int n, int cost_model, int m_pilot, int mode, double target,
+                  int max_levels, int* levels_out, int* nlevels_out);
+void allocate_samples(const int* levels, int L, const double* V, int n, int cost_model, int mode,
+                      double target, int m_pilot, int64_t* m_out);
+void triangle_estimate_host(const int64_t* x, int64_t m, int64_t nnz, int use_cv, double* est,
+                            double* se);
+
+}  // namespace mlt

@@ -1,0 +1,298 @@
+"""Python binding of the C ABI in include/mlt.h (ctypes; argument marshalling only).
+
+Every computation runs in libmlt.so.  Importing this module does not need a GPU,
+but calling anything that touches the device does; there is no CPU fallback.
+If the library has not been built, ``lib()`` raises instead of degrading.
+
+Device memory and streams may come from PyTorch: any function taking an array
+accepts a numpy array (host) or a torch tensor (host or CUDA); ``stream`` is a
+cudaStream_t as an int (``torch.cuda.current_stream().cuda_stream``) or None.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmlt.so")
+
+MLT_OK, MLT_EINVAL, MLT_ENOMEM, MLT_ECUDA, MLT_ERANGE, MLT_ETIMEOUT = 0, -1, -2, -3, -4, -5
+MLT_F64, MLT_F32, MLT_PATTERN = 0, 1, 2
+MLT_GRAM, MLT_DEVICE_PTRS = 1, 2
+MLT_FN = {"log": 0, "sqrt": 1, "exp": 2, "inv": 3, "pow": 4, "cube": 5}
+MLT_PREC = {"fp64": 0, "fp32": 1}
+MLT_DIRECT = 1
+MLT_BOUNDS_GERSHGORIN = 0
+MLT_MAX_LEVELS = 1024
+MLT_MAX_DEGREE = 4096
+MLT_MODE = {"budget": 0, "variance": 1}
+MLT_COST = {"symmetric": 0, "linear": 1}
+
+EXPORTS = ["mlt_create_csr", "mlt_destroy", "mlt_matrix_info", "mlt_spectrum_bounds",
+           "mlt_cheb_coeffs", "mlt_moments", "mlt_mlmc_default_params", "mlt_mlmc_estimate",
+           "mlt_triangle_trace", "mlt_profile_start", "mlt_profile_stop", "mlt_last_error"]
+
+
+class MLTError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (code %d)" % (msg, code))
+        self.code = code
+
+
+class mlt_mlmc_params(ctypes.Structure):
+    _fields_ = [("fn", ctypes.c_int), ("fn_p", ctypes.c_double), ("a", ctypes.c_double),
+                ("b", ctypes.c_double), ("n", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("nlevels", ctypes.c_int), ("levels", ctypes.c_int32 * MLT_MAX_LEVELS),
+                ("m", ctypes.c_int64 * MLT_MAX_LEVELS), ("m_pilot", ctypes.c_int),
+                ("mode", ctypes.c_int), ("target", ctypes.c_double), ("cost_model", ctypes.c_int),
+                ("max_levels", ctypes.c_int), ("reuse_pilot", ctypes.c_int),
+                ("precision", ctypes.c_int), ("flags", ctypes.c_uint), ("stream", ctypes.c_void_p)]
+
+
+class mlt_mlmc_result(ctypes.Structure):
+    _fields_ = [("estimate", ctypes.c_double), ("std_error", ctypes.c_double),
+                ("nlevels", ctypes.c_int), ("levels", ctypes.c_int32 * MLT_MAX_LEVELS),
+                ("m", ctypes.c_int64 * MLT_MAX_LEVELS),
+                ("level_mean", ctypes.c_double * MLT_MAX_LEVELS),
+                ("level_var", ctypes.c_double * MLT_MAX_LEVELS),
+                ("probes", ctypes.c_int64), ("matvecs", ctypes.c_int64)]
+
+
+class mlt_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libmlt.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libmlt.so is not built (%s); run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, u64, dbl, ci, cu = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                      ctypes.c_uint64, ctypes.c_double, ctypes.c_int, ctypes.c_uint)
+    L.mlt_create_csr.argtypes = [i64, i64, i64, vp, vp, vp, ci, dbl, cu, vp, ctypes.POINTER(vp)]
+    L.mlt_destroy.argtypes = [vp]
+    L.mlt_matrix_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.mlt_spectrum_bounds.argtypes = [vp, ci, ci, u64, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+    L.mlt_cheb_coeffs.argtypes = [ci, dbl, dbl, dbl, ci, vp]
+    L.mlt_moments.argtypes = [vp, dbl, dbl, u64, i64, i64, vp, ci, cu, vp, i64, vp]
+    L.mlt_mlmc_default_params.argtypes = [ctypes.POINTER(mlt_mlmc_params)]
+    L.mlt_mlmc_default_params.restype = None
+    L.mlt_mlmc_estimate.argtypes = [vp, ctypes.POINTER(mlt_mlmc_params), ctypes.POINTER(mlt_mlmc_result)]
+    L.mlt_triangle_trace.argtypes = [vp, u64, i64, i64, ci, ci, vp, ctypes.POINTER(dbl),
+                                     ctypes.POINTER(dbl), vp]
+    L.mlt_profile_start.argtypes = []
+    L.mlt_profile_stop.argtypes = [ctypes.POINTER(mlt_kernel_stat), ci, ctypes.POINTER(ci)]
+    L.mlt_last_error.argtypes = []
+    L.mlt_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("mlt_mlmc_default_params", "mlt_last_error"):
+            getattr(L, name).restype = ci
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != MLT_OK:
+        raise MLTError(rc, lib().mlt_last_error().decode(errors="replace"))
+
+
+def _ptr(a):
+    """Raw address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError("expected a numpy array or torch tensor")
+
+
+def _is_cuda(a):
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _stream(stream):
+    return None if stream is None else int(stream)
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+
+def mlt_create_csr(nrows, ncols, nnz, rowptr, col, vals=None, val_type=None, scale=1.0,
+                   flags=0, stream=None):
+    """Returns an opaque handle (int).  rowptr int64, col int32, vals float64/float32."""
+    if val_type is None:
+        if vals is None:
+            val_type = MLT_PATTERN
+        else:
+            dt = str(vals.dtype)
+            val_type = MLT_F32 if dt.endswith("float32") else MLT_F64
+    if _is_cuda(rowptr):
+        flags |= MLT_DEVICE_PTRS
+    h = ctypes.c_void_p()
+    _check(lib().mlt_create_csr(nrows, ncols, nnz, _ptr(rowptr), _ptr(col), _ptr(vals), val_type,
+                                float(scale), flags, _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def mlt_destroy(handle):
+    if handle:
+        _check(lib().mlt_destroy(handle))
+
+
+def mlt_matrix_info(handle):
+    d, nnz = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().mlt_matrix_info(handle, ctypes.byref(d), ctypes.byref(nnz)))
+    return d.value, nnz.value
+
+
+def mlt_spectrum_bounds(handle, method=MLT_BOUNDS_GERSHGORIN, steps=0, seed=0):
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib().mlt_spectrum_bounds(handle, method, steps, seed, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def mlt_cheb_coeffs(fn, a, b, n, p=0.0):
+    c = np.zeros(n + 1)
+    _check(lib().mlt_cheb_coeffs(MLT_FN[fn] if isinstance(fn, str) else fn, float(p), float(a),
+                                 float(b), int(n), _ptr(c)))
+    return c
+
+
+def mlt_moments(handle, a, b, seed, probe_offset, degrees, precision="fp64", flags=0, out=None,
+                stream=None):
+    """mu[p, j] for j <= degrees[p]; `out` (nprobes x ld, float64, host or CUDA) is
+    filled in place, else a new numpy array is returned."""
+    deg = np.ascontiguousarray(degrees, dtype=np.int32)
+    if out is None:
+        ld = int(deg.max()) + 1 if deg.size else 1
+        out = np.zeros((deg.size, ld))
+    ld = out.shape[1]
+    prec = MLT_PREC[precision] if isinstance(precision, str) else precision
+    _check(lib().mlt_moments(handle, float(a), float(b), int(seed), int(probe_offset), deg.size,
+                             _ptr(deg), prec, int(flags), _ptr(out), ld, _stream(stream)))
+    return out
+
+
+def mlt_mlmc_default_params():
+    p = mlt_mlmc_params()
+    lib().mlt_mlmc_default_params(ctypes.byref(p))
+    return p
+
+
+def mlt_mlmc_estimate(handle, params):
+    r = mlt_mlmc_result()
+    _check(lib().mlt_mlmc_estimate(handle, ctypes.byref(params), ctypes.byref(r)))
+    L = r.nlevels
+    return {"estimate": r.estimate, "stderr": r.std_error, "levels": list(r.levels[:L]),
+            "m": list(r.m[:L]), "level_mean": list(r.level_mean[:L]),
+            "level_var": list(r.level_var[:L]), "probes": r.probes, "matvecs": r.matvecs}
+
+
+def mlt_triangle_trace(handle, seed, probe_offset, nprobes, block=128, use_cv=True, x=None,
+                       stream=None):
+    """Returns (estimate, stderr); per-probe (x1, x2, x3) go to `x` if given."""
+    est, se = ctypes.c_double(), ctypes.c_double()
+    _check(lib().mlt_triangle_trace(handle, int(seed), int(probe_offset), int(nprobes), int(block),
+                                    int(bool(use_cv)), _ptr(x), ctypes.byref(est), ctypes.byref(se),
+                                    _stream(stream)))
+    return est.value, se.value
+
+
+def mlt_profile_start():
+    _check(lib().mlt_profile_start())
+
+
+def mlt_profile_stop(max_stats=64):
+    """{kernel name: (launches, total ms)} of the launches since mlt_profile_start()."""
+    arr = (mlt_kernel_stat * max_stats)()
+    n = ctypes.c_int()
+    _check(lib().mlt_profile_stop(arr, max_stats, ctypes.byref(n)))
+    return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(n.value)}
+
+
+def mlt_last_error():
+    return lib().mlt_last_error().decode(errors="replace")
+
+
+# ---------------------------------------------------------------------------
+# convenience: a handle bound to a CSR (arrays from paper_2103_10516_gb300.synth)
+# ---------------------------------------------------------------------------
+
+class Matrix:
+    """Owns one mlt_matrix handle built from host CSR arrays (or CUDA tensors)."""
+
+    def __init__(self, csr, gram=False, scale=1.0, vals_dtype=None, stream=None):
+        vals = csr.val
+        if vals is not None and vals_dtype is not None:
+            vals = np.ascontiguousarray(vals, dtype=vals_dtype)
+        self._keep = (csr.rowptr, csr.col, vals)
+        self.handle = mlt_create_csr(csr.nrows, csr.ncols, csr.nnz, csr.rowptr, csr.col, vals,
+                                     scale=scale, flags=MLT_GRAM if gram else 0, stream=stream)
+        self.dim, self.nnz = mlt_matrix_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            mlt_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def moments(self, a, b, seed, probe_offset, degrees, **kw):
+        return mlt_moments(self.handle, a, b, seed, probe_offset, degrees, **kw)
+
+    def bounds(self):
+        return mlt_spectrum_bounds(self.handle)
+
+    def triangles(self, seed, probe_offset, nprobes, use_cv=True, x=None, stream=None):
+        return mlt_triangle_trace(self.handle, seed, probe_offset, nprobes, 128, use_cv, x, stream)
+
+    def mlmc(self, fn, a, b, n, seed=0, levels=None, m=None, m_pilot=10, mode="budget",
+             target=1000.0, cost_model="symmetric", max_levels=0, reuse_pilot=True,
+             precision="fp64", direct=False, p=0.0, stream=None):
+        P = mlt_mlmc_default_params()
+        P.fn = MLT_FN[fn] if isinstance(fn, str) else fn
+        P.fn_p = p
+        P.a, P.b, P.n, P.seed = float(a), float(b), int(n), int(seed)
+        if levels is not None:
+            P.nlevels = len(levels)
+            for k, (l, mk) in enumerate(zip(levels, m)):
+                P.levels[k] = int(l)
+                P.m[k] = int(mk)
+        else:
+            P.nlevels = 0
+        P.m_pilot = int(m_pilot)
+        P.mode = MLT_MODE[mode]
+        P.target = float(target)
+        P.cost_model = MLT_COST[cost_model]
+        P.max_levels = int(max_levels)
+        P.reuse_pilot = int(bool(reuse_pilot))
+        P.precision = MLT_PREC[precision]
+        P.flags = MLT_DIRECT if direct else 0
+        P.stream = _stream(stream)
+        return mlt_mlmc_estimate(self.handle, P)

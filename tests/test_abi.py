@@ -1,0 +1,87 @@
+"""The C ABI without a GPU: the library builds and loads, exports every function
+include/mlt.h declares, its structs match the ctypes mirrors byte for byte, and
+its host-only arithmetic (Chebyshev coefficients) agrees with the oracle."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mlt.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2103_10516_gb300 import build, mlt
+    build.build()
+    return mlt
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(mlt_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = _declared()
+    assert len(names) >= 10
+    lib = L.lib()
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(L.EXPORTS) == names
+    out = subprocess.run(["nm", "-D", "--defined-only", L.LIB_PATH], capture_output=True,
+                         text=True).stdout
+    for n in names:
+        assert re.search(r"\bT %s$" % n, out, flags=re.M), n
+
+
+def test_struct_layout_matches_ctypes(L, tmp_path):
+    import ctypes
+    src = tmp_path / "layout.c"
+    fields_p = [f for f, _ in L.mlt_mlmc_params._fields_]
+    fields_r = [f for f, _ in L.mlt_mlmc_result._fields_]
+    body = ['#include <stdio.h>', '#include <stddef.h>', '#include "mlt.h"', 'int main(void){',
+            'printf("%zu\\n", sizeof(mlt_mlmc_params));',
+            'printf("%zu\\n", sizeof(mlt_mlmc_result));']
+    body += ['printf("%%zu\\n", offsetof(mlt_mlmc_params, %s));' % f for f in fields_p]
+    body += ['printf("%%zu\\n", offsetof(mlt_mlmc_result, %s));' % f for f in fields_r]
+    body += ['return 0;}']
+    src.write_text("\n".join(body))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    expect = [ctypes.sizeof(L.mlt_mlmc_params), ctypes.sizeof(L.mlt_mlmc_result)]
+    expect += [getattr(L.mlt_mlmc_params, f).offset for f in fields_p]
+    expect += [getattr(L.mlt_mlmc_result, f).offset for f in fields_r]
+    assert vals == expect
+
+
+def test_constants_match_header(L):
+    txt = open(HEADER).read()
+    def val(name):
+        return int(re.search(r"#define %s\s+\(?(-?\d+)u?\)?" % name, txt).group(1))
+    assert val("MLT_EINVAL") == L.MLT_EINVAL and val("MLT_ERANGE") == L.MLT_ERANGE
+    assert val("MLT_MAX_LEVELS") == L.MLT_MAX_LEVELS and val("MLT_MAX_DEGREE") == L.MLT_MAX_DEGREE
+    assert val("MLT_GRAM") == L.MLT_GRAM and val("MLT_DEVICE_PTRS") == L.MLT_DEVICE_PTRS
+    assert val("MLT_FN_SQRT") == L.MLT_FN["sqrt"] and val("MLT_PREC_FP32") == L.MLT_PREC["fp32"]
+
+
+@pytest.mark.parametrize("fn,a,b,n", [("log", 0.1, 8.1, 128), ("sqrt", 0.0, 50.0, 512),
+                                       ("exp", -10.0, 10.0, 128), ("inv", 0.5, 3.0, 40),
+                                       ("cube", -1.0, 1.0, 9), ("pow", 0.2, 4.0, 64)])
+def test_cheb_coeffs_match_oracle(L, O, fn, a, b, n):
+    # host-only arithmetic of the library (no device work)
+    got = L.mlt_cheb_coeffs(fn, a, b, n, p=1.5)
+    ref = O.cheb_coeffs(fn, a, b, n, p=1.5)
+    assert np.max(np.abs(got - ref)) <= 1e-14 * np.sum(np.abs(ref))
+
+
+def test_cheb_coeffs_rejects_bad_input(L):
+    for args in (("log", -1.0, 2.0, 8), ("log", 1.0, 1.0, 8), ("inv", -1.0, 1.0, 8),
+                 ("exp", 0.0, 1.0, 0), ("exp", 0.0, 1.0, 5000)):
+        with pytest.raises(L.MLTError) as e:
+            L.mlt_cheb_coeffs(*args)
+        assert e.value.code == L.MLT_EINVAL

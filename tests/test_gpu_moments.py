@@ -1,0 +1,161 @@
+"""GPU parity of the Chebyshev moment engine (mlt_moments) against the CPU
+oracle on the same seeded probes.  Tolerance: |mu_gpu - mu_oracle| <= 1e-10 * d
+for FP64 (|mu_j| <= d, so this is 1e-10 relative to the largest possible
+moment); FP32 vectors use a bound derived from single-precision rounding."""
+import numpy as np
+import pytest
+
+from paper_2103_10516_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2103_10516_gb300 import build, mlt
+    build.build()
+    return mlt
+
+
+def _c1_degrees():
+    # the 64x64 log-det workload: 256 probes at degree 8, 64 at 32, 16 at 128
+    return np.array([8] * 256 + [32] * 64 + [128] * 16, dtype=np.int32)
+
+
+def test_c1_logdet_moments_fp64(L, O):
+    m = synth.grid_laplacian_2d(64, shift=0.1)
+    deg = _c1_degrees()
+    with L.Matrix(m) as M:
+        got = M.moments(0.1, 8.1, 0, 0, deg)
+    ref = O.moments(m, 0.1, 8.1, 0, 0, deg)
+    assert got.shape == ref.shape
+    err = np.max(np.abs(got - ref))
+    assert err <= TOL64 * m.nrows, err
+    assert np.all(got[:, 0] == m.nrows)
+
+
+def test_direct_mode_matches(L, O):
+    m = synth.grid_laplacian_2d(20, shift=0.1)
+    deg = np.array([0, 1, 2, 3, 17, 40, 41, 5] * 5, dtype=np.int32)
+    with L.Matrix(m) as M:
+        got = M.moments(0.1, 8.1, 7, 100, deg, flags=L.MLT_DIRECT)
+        dbl = M.moments(0.1, 8.1, 7, 100, deg)
+    ref = O.moments(m, 0.1, 8.1, 7, 100, deg)
+    assert np.max(np.abs(got - ref)) <= TOL64 * m.nrows
+    assert np.max(np.abs(dbl - ref)) <= TOL64 * m.nrows
+
+
+@pytest.mark.parametrize("nprobes", [1, 5, 37, 130])
+def test_ragged_random_degrees(L, O, nprobes):
+    rng = np.random.default_rng(nprobes)
+    m = synth.random_symmetric(300, 0.02, seed=nprobes, diag_shift=0.0)
+    lo, hi = O.gershgorin(m)
+    deg = rng.integers(0, 70, size=nprobes).astype(np.int32)
+    with L.Matrix(m) as M:
+        got = M.moments(lo, hi, 11, 3, deg)
+    ref = O.moments(m, lo, hi, 11, 3, deg)
+    assert np.max(np.abs(got - ref)) <= TOL64 * m.nrows
+
+
+def test_many_groups(L, O):
+    # more probes than one group holds: groups are formed and results land in
+    # the caller's order
+    m = synth.grid_laplacian_2d(8, shift=0.5)
+    deg = (np.arange(2100) % 23).astype(np.int32)
+    with L.Matrix(m) as M:
+        got = M.moments(0.5, 8.5, 1, 0, deg)
+    ref = O.moments(m, 0.5, 8.5, 1, 0, deg)
+    assert np.max(np.abs(got - ref)) <= TOL64 * m.nrows
+
+
+def test_gram_operator(L, O):
+    X = synth.sparse_gaussian(700, 240, 0.02, seed=3)
+    deg = np.array([64] * 20 + [9] * 13, dtype=np.int32)
+    with L.Matrix(X, gram=True) as M:
+        a, b = M.bounds()
+        assert a == 0.0 and b > 0
+        got = M.moments(a, b, 5, 0, deg)
+    ref = O.moments(X, a, b, 5, 0, deg, gram=True)
+    assert np.max(np.abs(got - ref)) <= TOL64 * 240
+
+
+def test_pattern_with_scale(L, O):
+    g = synth.rmat_adjacency(10, 8, seed=2)
+    sc = 0.05
+    with L.Matrix(g, scale=sc) as M:
+        a, b = M.bounds()
+        got = M.moments(a, b, 4, 9, [30] * 40)
+    ra, rb = O.gershgorin(g)
+    assert abs(a - ra * sc) < 1e-12 and abs(b - rb * sc) < 1e-12
+    ref = O.moments(g, a, b, 4, 9, [30] * 40, scale=sc)
+    assert np.max(np.abs(got - ref)) <= TOL64 * g.nrows
+
+
+def test_fp32_values_input(L, O):
+    m = synth.grid_laplacian_2d(12, shift=0.1)
+    with L.Matrix(m, vals_dtype=np.float32) as M:
+        got = M.moments(0.1, 8.1, 0, 0, [20] * 9)
+    # the oracle sees the FP32-rounded entries (4.1 is not exact in FP32)
+    m32 = synth.CSR(m.nrows, m.ncols, m.rowptr, m.col, m.val.astype(np.float32).astype(np.float64))
+    ref = O.moments(m32, 0.1, 8.1, 0, 0, [20] * 9)
+    assert np.max(np.abs(got - ref)) <= TOL64 * m.nrows
+
+
+def test_fp32_precision_mode(L, O):
+    # FP32 vectors: each step adds relative rounding ~2^-24 to V; the doubled
+    # moments carry |2 V_k.V_k| <= 2d, so after k steps the error stays below
+    # ~ k * 2^-24 * 2d * (a small growth factor); 64 * eps32 * d bounds degree <= 128.
+    m = synth.grid_laplacian_2d(64, shift=0.1)
+    deg = _c1_degrees()
+    with L.Matrix(m) as M:
+        got = M.moments(0.1, 8.1, 0, 0, deg, precision="fp32")
+    ref = O.moments(m, 0.1, 8.1, 0, 0, deg)
+    err = np.max(np.abs(got - ref))
+    assert err <= 64 * 2.0 ** -24 * m.nrows, err
+
+
+def test_device_output_and_extra_columns(L, O):
+    import torch
+    m = synth.grid_laplacian_2d(10, shift=0.1)
+    deg = np.array([5, 0, 9], dtype=np.int32)
+    out = torch.full((3, 14), 7.0, dtype=torch.float64, device="cuda")
+    host = np.full((3, 14), 7.0)
+    with L.Matrix(m) as M:
+        M.moments(0.1, 8.1, 2, 0, deg, out=out)
+        M.moments(0.1, 8.1, 2, 0, deg, out=host)
+    dev = out.cpu().numpy()
+    assert np.array_equal(dev, host)
+    ref = O.moments(m, 0.1, 8.1, 2, 0, deg)
+    assert np.max(np.abs(host[:, :10] - ref)) <= TOL64 * m.nrows
+    assert np.all(host[:, 10:] == 0.0) and host[1, 1] == 0.0 and host[0, 6] == 0.0
+
+
+def test_degenerate_inputs(L, O):
+    m = synth.grid_laplacian_2d(4, shift=0.1)
+    with L.Matrix(m) as M:
+        z = M.moments(0.1, 8.1, 0, 0, np.zeros(0, dtype=np.int32))
+        assert z.shape[0] == 0
+        zero = M.moments(0.1, 8.1, 0, 0, [0, 0])
+        assert np.all(zero == 16.0)
+        with pytest.raises(L.MLTError) as e:
+            M.moments(1.0, 1.0, 0, 0, [3])
+        assert e.value.code == L.MLT_EINVAL
+        with pytest.raises(L.MLTError) as e:
+            M.moments(0.1, 8.1, 0, 0, [-1])
+        assert e.value.code == L.MLT_EINVAL
+        with pytest.raises(L.MLTError) as e:     # spectrum far outside [a, b]
+            M.moments(0.1, 0.2, 0, 0, [40])
+        assert e.value.code == L.MLT_ERANGE
+    # a 1x1 matrix and a matrix with empty rows
+    one = synth.CSR(1, 1, np.array([0, 1]), np.array([0]), np.array([2.0]))
+    with L.Matrix(one) as M:
+        got = M.moments(1.0, 3.0, 0, 0, [6])
+    assert np.max(np.abs(got - O.moments(one, 1.0, 3.0, 0, 0, [6]))) <= 1e-12
+    e = synth.CSR(5, 5, np.array([0, 1, 1, 1, 2, 2]), np.array([0, 3]), np.array([1.0, 0.5]))
+    with L.Matrix(e) as M:
+        got = M.moments(-1.0, 1.5, 3, 0, [7, 3])
+    assert np.max(np.abs(got - O.moments(e, -1.0, 1.5, 3, 0, [7, 3]))) <= 1e-12

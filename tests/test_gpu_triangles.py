@@ -1,0 +1,99 @@
+"""GPU parity of the exact triangle path (mlt_triangle_trace): per-probe int64
+moments bit-exact against the oracle, and the control-variate estimate equal to
+the oracle's to the last bit (same integer sums, same double-precision steps)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2103_10516_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2103_10516_gb300 import build, mlt
+    build.build()
+    return mlt
+
+
+@pytest.mark.parametrize("d,p,nprobes", [(500, 0.03, 300), (64, 0.5, 1), (2000, 0.004, 129)])
+def test_random_graph_bit_exact(L, O, d, p, nprobes):
+    g = synth.random_graph(d, p, seed=d)
+    x = np.zeros((nprobes, 3), dtype=np.int64)
+    with L.Matrix(g) as G:
+        est, se = G.triangles(5, 17, nprobes, use_cv=True, x=x)
+        est0, se0 = G.triangles(5, 17, nprobes, use_cv=False)
+    xr = O.triangle_moments(g, 5, 17, nprobes)
+    assert np.array_equal(x, xr)
+    er, sr, _, _ = O.triangle_estimate(xr, g.nnz, True)
+    assert est == er and (se == sr or (math.isnan(se) and math.isnan(sr)))
+    er0, sr0, _, _ = O.triangle_estimate(xr, g.nnz, False)
+    assert est0 == er0 and (se0 == sr0 or (math.isnan(se0) and math.isnan(sr0)))
+
+
+def test_rmat_scale14_and_truth(L, O):
+    g = synth.rmat_adjacency(14, 16, seed=0)
+    x = np.zeros((512, 3), dtype=np.int64)
+    with L.Matrix(g) as G:
+        est, se = G.triangles(0, 0, 512, x=x)
+    assert np.array_equal(x, O.triangle_moments(g, 0, 0, 512))
+    T = O.triangle_count(g)
+    assert abs(est - T) < 5 * se
+
+
+def test_exhaustive_signs_give_exact_count(L, O):
+    # every sign vector of a 10-vertex graph: mean x3 = 6T exactly.  The probes
+    # here are the generator's, so instead check E over many ids is unbiased and
+    # the per-probe moments agree with the oracle on explicit probe ids.
+    g = synth.random_graph(10, 0.5, seed=11)
+    x = np.zeros((1024, 3), dtype=np.int64)
+    with L.Matrix(g) as G:
+        G.triangles(3, 0, 1024, x=x)
+    assert np.array_equal(x, O.triangle_moments(g, 3, 0, 1024))
+    T = O.triangle_count(g)
+    assert abs(x[:, 2].mean() - 6 * T) < 5 * x[:, 2].std() / 32
+
+
+def test_device_output(L, O):
+    import torch
+    g = synth.random_graph(300, 0.05, seed=2)
+    xd = torch.zeros((200, 3), dtype=torch.int64, device="cuda")
+    with L.Matrix(g) as G:
+        est, _ = G.triangles(1, 0, 200, x=xd)
+    assert np.array_equal(xd.cpu().numpy(), O.triangle_moments(g, 1, 0, 200))
+
+
+def test_rejects_bad_inputs(L):
+    with L.Matrix(synth.grid_laplacian_2d(5)) as M:      # has values
+        with pytest.raises(L.MLTError) as e:
+            M.triangles(0, 0, 10)
+        assert e.value.code == L.MLT_EINVAL
+    loop = synth.CSR(3, 3, np.array([0, 2, 3, 4]), np.array([0, 1, 0, 2]))
+    with L.Matrix(loop) as M:
+        with pytest.raises(L.MLTError) as e:
+            M.triangles(0, 0, 10)
+        assert e.value.code == L.MLT_EINVAL
+    g = synth.random_graph(20, 0.3, seed=0)
+    with L.Matrix(g) as M:
+        with pytest.raises(L.MLTError):
+            L.mlt_triangle_trace(M.handle, 0, 0, 10, block=64)
+        with pytest.raises(L.MLTError):
+            M.triangles(0, 0, 0)
+
+
+def test_full_size_rmat20_sampled(L, O):
+    # the R-MAT scale-20 triangle workload at full size: 1024 probes in blocks
+    # of 128; a sample of probes (first, block edges, last) against the oracle
+    g = synth.rmat_adjacency(20, 16, seed=0)
+    x = np.zeros((1024, 3), dtype=np.int64)
+    with L.Matrix(g) as G:
+        est, se = G.triangles(0, 0, 1024, x=x)
+    for p in (0, 127, 128, 1023):
+        assert np.array_equal(x[p], O.triangle_moments(g, 0, p, 1)[0]), p
+    er, sr, _, _ = O.triangle_estimate(x, g.nnz, True)   # same sums -> same bits
+    assert est == er and se == sr
+    assert np.all(x[:, 1] > 0)
