@@ -168,8 +168,8 @@ class Triangles:
         return {"workload": self.name, "graph": "R-MAT scale 20, edge factor 16, a=0.57 b=c=0.19, seed 0",
                 "d": self.d, "nnz": self.nnz, "probes": self.NPROBES, "block": self.BLOCK,
                 "control_variates": True,
-                "l2": "inputs larger than L2 (col 4*nnz = %.0f MB, y 512 B/row = %.0f MB)"
-                      % (4e-6 * self.nnz, 512e-6 * self.d)}
+                "l2": "inputs larger than L2 (col 4*nnz = %.0f MB + rowptr %.0f MB + y 128 B/row = %.0f MB)"
+                      % (4e-6 * self.nnz, 8e-6 * self.d, 128e-6 * self.d)}
 
     def kernel_bytes(self):
         """Algorithmic bytes per launch (one 128-probe block) of each kernel:
@@ -177,8 +177,8 @@ class Triangles:
         d, nnz = self.d, self.nnz
         return {
             "tri_zbits": 16 * d,
-            "tri_pass1": 8 * (d + 1) + 4 * nnz + 16 * d + 512 * d,
-            "tri_pass2": 8 * (d + 1) + 8 * d + 4 * (nnz // 2) + 512 * d,
+            "tri_pass1": 8 * (d + 1) + 4 * nnz + 16 * d + 128 * d,
+            "tri_pass2": 8 * (d + 1) + 8 * d + 4 * (nnz // 2) + 128 * d,
         }
 
     # ours

@@ -457,3 +457,55 @@ def gershgorin(m):
         lo = min(lo, dg - off)
         hi = max(hi, dg + off)
     return lo, hi
+
+
+# ---------------------------------------------------------------------------
+# Learned coarse level: a 16 -> 128 -> 128 -> 1 ReLU network trained by mean
+# squared error (a project addition; its nearest relative in the paper is the
+# regression control variate of Section 5.4).  Plain FP64 forward and
+# hand-written backward, used to check the GPU kernels' gradients.
+# ---------------------------------------------------------------------------
+
+MLP_IN, MLP_HID = 16, 128
+
+
+def mlp_init(seed=0):
+    """He-style initial weights (normal, std sqrt(2 / fan_in)); biases zero."""
+    rng = np.random.default_rng(seed)
+    return {
+        "W1": rng.standard_normal((MLP_HID, MLP_IN)) * math.sqrt(2.0 / MLP_IN),
+        "b1": np.zeros(MLP_HID),
+        "W2": rng.standard_normal((MLP_HID, MLP_HID)) * math.sqrt(2.0 / MLP_HID),
+        "b2": np.zeros(MLP_HID),
+        "w3": rng.standard_normal(MLP_HID) * math.sqrt(1.0 / MLP_HID),
+        "b3": 0.0,
+    }
+
+
+def mlp_forward(P, X):
+    """X: B x 16.  Returns (y, cache)."""
+    X = np.asarray(X, dtype=np.float64)
+    a1 = X @ P["W1"].T + P["b1"]
+    h1 = np.maximum(a1, 0.0)
+    a2 = h1 @ P["W2"].T + P["b2"]
+    h2 = np.maximum(a2, 0.0)
+    y = h2 @ P["w3"] + P["b3"]
+    return y, (X, h1, h2)
+
+
+def mlp_loss_grad(P, X, t):
+    """Loss L = mean (y - t)^2 and its gradient with respect to every parameter."""
+    y, (X, h1, h2) = mlp_forward(P, X)
+    t = np.asarray(t, dtype=np.float64)
+    B = X.shape[0]
+    r = y - t
+    L = float(np.mean(r * r))
+    dy = 2.0 * r / B
+    g = {"w3": h2.T @ dy, "b3": float(np.sum(dy))}
+    dh2 = np.outer(dy, P["w3"]) * (h2 > 0)
+    g["W2"] = dh2.T @ h1
+    g["b2"] = dh2.sum(axis=0)
+    dh1 = (dh2 @ P["W2"]) * (h1 > 0)
+    g["W1"] = dh1.T @ X
+    g["b1"] = dh1.sum(axis=0)
+    return L, g

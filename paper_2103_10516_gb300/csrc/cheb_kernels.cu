@@ -14,6 +14,14 @@
 // so degree n needs ceil(n/2) operator applications.  Direct mode keeps
 // mu_{k+1} = z . V_{k+1} (n applications).
 //
+// Work split (fixed per matrix, so every result is reproducible): rows cost
+// kRowCost units plus one per entry; the unit axis is cut into chunks of Uc
+// units.  A row of degree <= Uc belongs to the chunk holding its first unit.
+// Longer rows are cut into fixed segments of Uc entries whose partial products
+// go to a scratch table; a second kernel adds each row's segments in order and
+// applies the recurrence there.  Work items (chunks, then segments) are dealt
+// round-robin to groups of G lanes; a group always owns the same columns.
+//
 // Reductions are deterministic: each CTA writes per-column partial sums in a
 // fixed order, and a separate kernel adds the CTA partials in CTA order.
 #include <cuda_runtime.h>
@@ -30,6 +38,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kSlots = 16;          // steps whose partials are buffered before a reduction
+constexpr int64_t kRowCost = 4;     // units charged per row (the epilogue) on top of its entries
 
 template <typename T> struct Lanes;
 template <> struct Lanes<double> { static constexpr int N = 2; };   // 16-byte vectors
@@ -55,109 +64,138 @@ struct StepArgs {
     int B;                 // probes in the group (columns >= B are padding)
     uint64_t seedmix;
     const int64_t* ids;    // global id of each column's probe (direct mode)
-    double* partials;      // [gridDim.x][2][ldv]
+    double* partials;      // [gridDim.x][2][ldv] for this launch
+    // work split of this operand
+    int64_t nch, Uc, nseg;
+    int nlong;
+    const int64_t* crow;
+    const int32_t* seg_row;
+    const int64_t* seg_k0;
+    const int32_t* long_rows;
+    const int64_t* long_seg0;
+    T* segpart;            // [nseg][ldv] partial products of long-row segments
 };
 
 template <typename T, int G>
-__global__ void __launch_bounds__(kThreads) cheb_step_kernel(StepArgs<T> a)
+struct Lane {
+    static constexpr int N = Lanes<T>::N;
+    int glane;
+    unsigned gmask;
+    bool vok;
+    int c0;
+    long long gcls, ncls;   // group index within its column class, groups per class
+    bool active;
+
+    __device__ Lane(const StepArgs<T>& a)
+    {
+        const int tid = threadIdx.x;
+        const int lane = tid & 31;
+        glane = lane & (G - 1);
+        gmask = (G == 32) ? 0xFFFFFFFFu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+        const int gpb = kThreads / G;
+        const long long gg = (long long)blockIdx.x * gpb + tid / G;
+        const long long total = (long long)gridDim.x * gpb;
+        ncls = total / a.nchunks;
+        gcls = gg / a.nchunks;
+        const int chunk = (int)(gg % a.nchunks);
+        const int vidx = chunk * G + glane;
+        vok = vidx < a.nvec;
+        c0 = vidx * N;
+        active = gg < ncls * a.nchunks;
+    }
+};
+
+// acc = sum over entries [k0, k1) of a_ij * V[j, c0 .. c0+N).
+template <typename T, int G>
+__device__ __forceinline__ void row_product(const StepArgs<T>& a, const Lane<T, G>& L, int64_t k0,
+                                            int64_t k1, T (&acc)[Lanes<T>::N])
 {
     constexpr int N = Lanes<T>::N;
     using P = Pack<T, N>;
-    __shared__ double red[2][kThreads * N];
-
-    const int tid = threadIdx.x;
-    const int lane = tid & 31;
-    const int glane = lane & (G - 1);
-    const unsigned gmask = (G == 32) ? 0xFFFFFFFFu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-    const int gpb = kThreads / G;
-    const int gib = tid / G;
-    const long long gg = (long long)blockIdx.x * gpb + gib;
-    const long long total = (long long)gridDim.x * gpb;
-    const long long rstride = total / a.nchunks;
-    const int chunk = (int)(gg % a.nchunks);
-    const int vidx = chunk * G + glane;
-    const bool vok = vidx < a.nvec;
-    const int c0 = vidx * N;
-
-    double s_self[N], s_cross[N];
 #pragma unroll
-    for (int q = 0; q < N; ++q) { s_self[q] = 0.0; s_cross[q] = 0.0; }
-
-    if (gg < rstride * a.nchunks) {
-        for (long long r = gg / a.nchunks; r < a.nrows; r += rstride) {
-            const int64_t beg = a.rowptr[r];
-            const int64_t end = a.rowptr[r + 1];
-            T acc[N];
-#pragma unroll
-            for (int q = 0; q < N; ++q) acc[q] = T(0);
-            for (int64_t base = beg; base < end; base += G) {
-                const int64_t k = base + glane;
-                int cj = 0;
-                T vj = T(0);
-                if (k < end) {
-                    cj = __ldg(a.col + k);
-                    vj = a.val ? __ldg(a.val + k) : T(1);
-                }
-                const int cnt = (int)min((int64_t)G, end - base);
+    for (int q = 0; q < N; ++q) acc[q] = T(0);
+    for (int64_t base = k0; base < k1; base += G) {
+        const int64_t k = base + L.glane;
+        int cj = 0;
+        T vj = T(0);
+        if (k < k1) {
+            cj = __ldg(a.col + k);
+            vj = a.val ? __ldg(a.val + k) : T(1);
+        }
+        const int cnt = (int)min((int64_t)G, k1 - base);
 #pragma unroll 4
-                for (int t = 0; t < cnt; ++t) {
-                    const int c = __shfl_sync(gmask, cj, t, G);
-                    const T v = __shfl_sync(gmask, vj, t, G);
-                    if (vok) {
-                        const P x = *reinterpret_cast<const P*>(a.vgather + (size_t)c * a.ldv + c0);
+        for (int t = 0; t < cnt; ++t) {
+            const int c = __shfl_sync(L.gmask, cj, t, G);
+            const T v = __shfl_sync(L.gmask, vj, t, G);
+            if (L.vok) {
+                const P x = *reinterpret_cast<const P*>(a.vgather + (size_t)c * a.ldv + L.c0);
 #pragma unroll
-                        for (int q = 0; q < N; ++q) acc[q] = fma(v, x.v[q], acc[q]);
-                    }
-                }
-            }
-            if (!vok) continue;
-            const size_t off = (size_t)r * a.ldv + c0;
-            P out;
-            if (a.mode == 2) {
-#pragma unroll
-                for (int q = 0; q < N; ++q) out.v[q] = acc[q];
-                *reinterpret_cast<P*>(a.vprev_out + off) = out;
-                continue;
-            }
-            const P xc = *reinterpret_cast<const P*>(a.vcur + off);
-            if (a.mode == 0) {
-#pragma unroll
-                for (int q = 0; q < N; ++q) out.v[q] = a.alpha * acc[q] + a.beta * xc.v[q];
-            } else {
-                const P xp = *reinterpret_cast<const P*>(a.vprev_out + off);
-#pragma unroll
-                for (int q = 0; q < N; ++q)
-                    out.v[q] = T(2) * (a.alpha * acc[q] + a.beta * xc.v[q]) - xp.v[q];
-            }
-            *reinterpret_cast<P*>(a.vprev_out + off) = out;
-            if (!a.direct) {
-#pragma unroll
-                for (int q = 0; q < N; ++q) {
-                    const double o = (double)out.v[q];
-                    s_self[q] = fma(o, o, s_self[q]);
-                    s_cross[q] = fma(o, (double)xc.v[q], s_cross[q]);
-                }
-            } else {
-#pragma unroll
-                for (int q = 0; q < N; ++q) {
-                    if (c0 + q >= a.B) break;
-                    const bool neg = probe_negative(a.seedmix, (uint64_t)a.ids[c0 + q], (uint64_t)r);
-                    const double o = (double)out.v[q];
-                    s_cross[q] += neg ? -o : o;
-                }
+                for (int q = 0; q < N; ++q) acc[q] = fma(v, x.v[q], acc[q]);
             }
         }
     }
-    if (a.mode == 2) return;
+}
 
-    // CTA reduction in a fixed order: column c collects the groups of this CTA
-    // whose chunk holds it, in group order.
+// V_{k+1}[r] from acc = (A V_k)[r], and the fused dot products.
+template <typename T>
+__device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0, const T (&acc)[Lanes<T>::N],
+                                         double (&s_self)[Lanes<T>::N], double (&s_cross)[Lanes<T>::N])
+{
+    constexpr int N = Lanes<T>::N;
+    using P = Pack<T, N>;
+    const size_t off = (size_t)r * a.ldv + c0;
+    P out;
+    if (a.mode == 2) {
+#pragma unroll
+        for (int q = 0; q < N; ++q) out.v[q] = acc[q];
+        *reinterpret_cast<P*>(a.vprev_out + off) = out;
+        return;
+    }
+    const P xc = *reinterpret_cast<const P*>(a.vcur + off);
+    if (a.mode == 0) {
+#pragma unroll
+        for (int q = 0; q < N; ++q) out.v[q] = a.alpha * acc[q] + a.beta * xc.v[q];
+    } else {
+        const P xp = *reinterpret_cast<const P*>(a.vprev_out + off);
+#pragma unroll
+        for (int q = 0; q < N; ++q) out.v[q] = T(2) * (a.alpha * acc[q] + a.beta * xc.v[q]) - xp.v[q];
+    }
+    *reinterpret_cast<P*>(a.vprev_out + off) = out;
+    if (!a.direct) {
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            const double o = (double)out.v[q];
+            s_self[q] = fma(o, o, s_self[q]);
+            s_cross[q] = fma(o, (double)xc.v[q], s_cross[q]);
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            if (c0 + q >= a.B) break;
+            const bool neg = probe_negative(a.seedmix, (uint64_t)a.ids[c0 + q], (uint64_t)r);
+            const double o = (double)out.v[q];
+            s_cross[q] += neg ? -o : o;
+        }
+    }
+}
+
+// CTA reduction in a fixed order: column c collects the groups of this CTA
+// whose column chunk holds it, in group order.
+template <typename T, int G>
+__device__ __forceinline__ void cta_partials(const StepArgs<T>& a, const Lane<T, G>& L,
+                                             const double (&s_self)[Lanes<T>::N],
+                                             const double (&s_cross)[Lanes<T>::N])
+{
+    constexpr int N = Lanes<T>::N;
+    __shared__ double red[2][kThreads * N];
+    const int tid = threadIdx.x;
 #pragma unroll
     for (int q = 0; q < N; ++q) {
         red[0][tid * N + q] = s_self[q];
         red[1][tid * N + q] = s_cross[q];
     }
     __syncthreads();
+    const int gpb = kThreads / G;
     const int ncols = a.nvec * N;
     double* part = a.partials + (size_t)blockIdx.x * 2 * a.ldv;
     const long long g0 = (long long)blockIdx.x * gpb;
@@ -167,7 +205,7 @@ __global__ void __launch_bounds__(kThreads) cheb_step_kernel(StepArgs<T> a)
         double s0 = 0.0, s1 = 0.0;
         for (int g = 0; g < gpb; ++g) {
             const long long gglob = g0 + g;
-            if (gglob >= rstride * a.nchunks || (int)(gglob % a.nchunks) != ch) continue;
+            if (gglob >= L.ncls * a.nchunks || (int)(gglob % a.nchunks) != ch) continue;
             const int t = g * G + gl;
             s0 += red[0][t * N + q];
             s1 += red[1][t * N + q];
@@ -177,6 +215,78 @@ __global__ void __launch_bounds__(kThreads) cheb_step_kernel(StepArgs<T> a)
     }
 }
 
+template <typename T, int G>
+__global__ void __launch_bounds__(kThreads) cheb_step_kernel(StepArgs<T> a)
+{
+    constexpr int N = Lanes<T>::N;
+    const Lane<T, G> L(a);
+    double s_self[N], s_cross[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) { s_self[q] = 0.0; s_cross[q] = 0.0; }
+
+    if (L.active) {
+        const int64_t nitems = a.nch + a.nseg;
+        for (int64_t it = L.gcls; it < nitems; it += L.ncls) {
+            T acc[N];
+            if (it < a.nch) {
+                const int64_t u0 = it * a.Uc, u1 = u0 + a.Uc;
+                for (int64_t r = __ldg(a.crow + it); r < a.nrows; ++r) {
+                    const int64_t beg = __ldg(a.rowptr + r);
+                    const int64_t pr = beg + kRowCost * r;
+                    if (pr >= u1) break;
+                    if (pr < u0) continue;
+                    const int64_t end = __ldg(a.rowptr + r + 1);
+                    if (end - beg > a.Uc) continue;          // long row: done by segments
+                    row_product<T, G>(a, L, beg, end, acc);
+                    if (L.vok) epilogue<T>(a, r, L.c0, acc, s_self, s_cross);
+                }
+            } else {
+                const int64_t sidx = it - a.nch;
+                const int64_t r = __ldg(a.seg_row + sidx);
+                const int64_t k0 = __ldg(a.seg_k0 + sidx);
+                const int64_t k1 = min(k0 + a.Uc, __ldg(a.rowptr + r + 1));
+                row_product<T, G>(a, L, k0, k1, acc);
+                if (L.vok) {
+                    Pack<T, N> p;
+#pragma unroll
+                    for (int q = 0; q < N; ++q) p.v[q] = acc[q];
+                    *reinterpret_cast<Pack<T, N>*>(a.segpart + (size_t)sidx * a.ldv + L.c0) = p;
+                }
+            }
+        }
+    }
+    if (a.mode == 2) return;
+    cta_partials<T, G>(a, L, s_self, s_cross);
+}
+
+// Long rows: add the segment products in segment order, then the recurrence.
+template <typename T, int G>
+__global__ void __launch_bounds__(kThreads) cheb_long_kernel(StepArgs<T> a)
+{
+    constexpr int N = Lanes<T>::N;
+    using P = Pack<T, N>;
+    const Lane<T, G> L(a);
+    double s_self[N], s_cross[N];
+#pragma unroll
+    for (int q = 0; q < N; ++q) { s_self[q] = 0.0; s_cross[q] = 0.0; }
+    if (L.active) {
+        for (int64_t i = L.gcls; i < a.nlong; i += L.ncls) {
+            if (!L.vok) continue;
+            T acc[N];
+#pragma unroll
+            for (int q = 0; q < N; ++q) acc[q] = T(0);
+            for (int64_t sidx = a.long_seg0[i]; sidx < a.long_seg0[i + 1]; ++sidx) {
+                const P p = *reinterpret_cast<const P*>(a.segpart + (size_t)sidx * a.ldv + L.c0);
+#pragma unroll
+                for (int q = 0; q < N; ++q) acc[q] += p.v[q];
+            }
+            epilogue<T>(a, a.long_rows[i], L.c0, acc, s_self, s_cross);
+        }
+    }
+    if (a.mode == 2) return;
+    cta_partials<T, G>(a, L, s_self, s_cross);
+}
+
 struct ReduceArgs {
     int nslots;
     int step0;
@@ -184,19 +294,24 @@ struct ReduceArgs {
     int act[kSlots];
 };
 
+// One warp per (slot, kind, column): lane l adds CTAs l, l+32, ... in order, then
+// a fixed shuffle tree; the summation order never depends on timing.
 __global__ void reduce_partials_kernel(const double* __restrict__ part, int max_blocks, int ldv,
                                        ReduceArgs ra, double* __restrict__ dots, int B)
 {
     const int slot = blockIdx.y;
     const int act = ra.act[slot];
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int idx = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (idx >= 2 * act) return;
     const int kind = idx / act, c = idx % act;
     const double* p = part + (size_t)slot * max_blocks * 2 * ldv + (size_t)kind * ldv + c;
     double s = 0.0;
     const int nb = ra.nblocks[slot];
-    for (int b = 0; b < nb; ++b) s += p[(size_t)b * 2 * ldv];
-    dots[(size_t)(ra.step0 + slot) * 2 * B + (size_t)kind * B + c] = s;
+    for (int b = lane; b < nb; b += 32) s += p[(size_t)b * 2 * ldv];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+    if (lane == 0) dots[(size_t)(ra.step0 + slot) * 2 * B + (size_t)kind * B + c] = s;
 }
 
 template <typename T>
@@ -258,35 +373,61 @@ int pow2_at_least(int v)
     return g;
 }
 
+// Launch the step (and, with long rows, the segment kernel after it).  The
+// CTA partials of the two kernels sit next to each other in `part`.
 template <typename T, int G>
-int launch_step_g(const StepArgs<T>& a, int max_blocks, int* nblocks_out, cudaStream_t s)
+int launch_step_g(StepArgs<T> a, int max_main, int max_long, int* nblocks_out, cudaStream_t s)
 {
-    const long long items = a.nrows * (long long)a.nchunks;
     const int gpb = kThreads / G;
-    long long want = (items + gpb - 1) / gpb;
-    int nb = (int)std::max<long long>(1, std::min<long long>(want, max_blocks));
-    // every CTA must own at least one group per chunk so rstride > 0
-    const long long min_groups = a.nchunks;
-    if ((long long)nb * gpb < min_groups) nb = (int)((min_groups + gpb - 1) / gpb);
+    const long long items = (a.nch + a.nseg) * (long long)a.nchunks;
+    int nb = (int)std::max<long long>(1, std::min<long long>((items + gpb - 1) / gpb, max_main));
+    if ((long long)nb * gpb < a.nchunks) nb = (a.nchunks + gpb - 1) / gpb;
     {
         ProfScope ps(a.mode == 2 ? "gram_spmm" : "cheb_step", s);
         cheb_step_kernel<T, G><<<nb, kThreads, 0, s>>>(a);
     }
-    *nblocks_out = nb;
-    return cuda_fail(cudaGetLastError(), "cheb_step_kernel launch");
+    MLT_CUDA_TRY(cudaGetLastError());
+    int nl = 0;
+    if (a.nlong > 0) {
+        const long long litems = (long long)a.nlong * a.nchunks;
+        nl = (int)std::max<long long>(1, std::min<long long>((litems + gpb - 1) / gpb, max_long));
+        if ((long long)nl * gpb < a.nchunks) nl = (a.nchunks + gpb - 1) / gpb;
+        StepArgs<T> b = a;
+        if (b.partials) b.partials += (size_t)nb * 2 * a.ldv;
+        ProfScope ps(a.mode == 2 ? "gram_spmm_long" : "cheb_step_long", s);
+        cheb_long_kernel<T, G><<<nl, kThreads, 0, s>>>(b);
+    }
+    MLT_CUDA_TRY(cudaGetLastError());
+    *nblocks_out = nb + nl;
+    return MLT_OK;
 }
 
 template <typename T>
-int launch_step(int G, const StepArgs<T>& a, int max_blocks, int* nb, cudaStream_t s)
+int launch_step(int G, const StepArgs<T>& a, int max_main, int max_long, int* nb, cudaStream_t s)
 {
     switch (G) {
-    case 1: return launch_step_g<T, 1>(a, max_blocks, nb, s);
-    case 2: return launch_step_g<T, 2>(a, max_blocks, nb, s);
-    case 4: return launch_step_g<T, 4>(a, max_blocks, nb, s);
-    case 8: return launch_step_g<T, 8>(a, max_blocks, nb, s);
-    case 16: return launch_step_g<T, 16>(a, max_blocks, nb, s);
-    default: return launch_step_g<T, 32>(a, max_blocks, nb, s);
+    case 1: return launch_step_g<T, 1>(a, max_main, max_long, nb, s);
+    case 2: return launch_step_g<T, 2>(a, max_main, max_long, nb, s);
+    case 4: return launch_step_g<T, 4>(a, max_main, max_long, nb, s);
+    case 8: return launch_step_g<T, 8>(a, max_main, max_long, nb, s);
+    case 16: return launch_step_g<T, 16>(a, max_main, max_long, nb, s);
+    default: return launch_step_g<T, 32>(a, max_main, max_long, nb, s);
     }
+}
+
+template <typename T>
+void set_split(StepArgs<T>& a, const SpmmPlan& P, T* segpart)
+{
+    a.nch = P.nch;
+    a.Uc = P.Uc;
+    a.nseg = P.nseg;
+    a.nlong = P.nlong;
+    a.crow = P.crow;
+    a.seg_row = P.seg_row;
+    a.seg_k0 = P.seg_k0;
+    a.long_rows = P.long_rows;
+    a.long_seg0 = P.long_seg0;
+    a.segpart = segpart;
 }
 
 template <typename T>
@@ -299,6 +440,8 @@ int run_group(mlt_matrix* M, const MomentPlan& plan, double a, double b, uint64_
     const int ldv = plan.ldv;
     const size_t vbytes = (size_t)d * ldv * sizeof(T);
     int rc;
+    if ((rc = ensure_spmm_plan(M, M->A, M->plan_A, s))) return rc;
+    if (gram && (rc = ensure_spmm_plan(M, M->AT, M->plan_AT, s))) return rc;
     if ((rc = M->ws_v[0].ensure(vbytes, s)) || (rc = M->ws_v[1].ensure(vbytes, s))) return rc;
     T* V[2] = {M->ws_v[0].as<T>(), M->ws_v[1].as<T>()};
     T* W = nullptr;
@@ -306,7 +449,12 @@ int run_group(mlt_matrix* M, const MomentPlan& plan, double a, double b, uint64_
         if ((rc = M->ws_w.ensure((size_t)M->A.nrows * ldv * sizeof(T), s))) return rc;
         W = M->ws_w.as<T>();
     }
-    const int max_blocks = 8 * M->num_sms;
+    const int64_t nseg = std::max(M->plan_A.nseg, gram ? M->plan_AT.nseg : (int64_t)0);
+    if ((rc = M->ws_seg.ensure((size_t)std::max<int64_t>(nseg, 1) * ldv * sizeof(T), s))) return rc;
+    T* segpart = M->ws_seg.as<T>();
+    const int max_main = 8 * M->num_sms;
+    const int max_long = 2 * M->num_sms;
+    const int max_blocks = max_main + max_long;
     if ((rc = M->ws_part.ensure((size_t)kSlots * max_blocks * 2 * ldv * sizeof(double), s))) return rc;
     if ((rc = M->ws_dots.ensure((size_t)std::max(plan.K, 1) * 2 * plan.B * sizeof(double), s))) return rc;
     double* part = M->ws_part.as<double>();
@@ -318,8 +466,8 @@ int run_group(mlt_matrix* M, const MomentPlan& plan, double a, double b, uint64_
         const int nb = (int)std::min<int64_t>((total + 255) / 256, 16LL * M->num_sms);
         ProfScope ps("init_probes", s);
         init_probes_kernel<T><<<std::max(nb, 1), 256, 0, s>>>(V[0], d, ldv, plan.B, plan.ids_dev, seedmix);
-        MLT_CUDA_TRY(cudaGetLastError());
     }
+    MLT_CUDA_TRY(cudaGetLastError());
 
     // At = alpha A + beta I; the stored entries carry `scale` (squared for X^T X).
     const double sc = gram ? M->scale * M->scale : M->scale;
@@ -357,26 +505,29 @@ int run_group(mlt_matrix* M, const MomentPlan& plan, double a, double b, uint64_
             pa.rowptr = A.rowptr; pa.col = A.col; pa.val = valA; pa.nrows = A.nrows;
             pa.vgather = cur; pa.vcur = nullptr; pa.vprev_out = W; pa.mode = 2;
             pa.partials = nullptr;
-            if ((rc = launch_step<T>(G, pa, max_blocks, &nb, s))) return rc;
+            set_split(pa, M->plan_A, segpart);
+            if ((rc = launch_step<T>(G, pa, max_main, max_long, &nb, s))) return rc;
             sa.rowptr = AT.rowptr; sa.col = AT.col; sa.val = valAT; sa.nrows = AT.nrows;
             sa.vgather = W;
+            set_split(sa, M->plan_AT, segpart);
         } else {
             sa.rowptr = A.rowptr; sa.col = A.col; sa.val = valA; sa.nrows = A.nrows;
             sa.vgather = cur;
+            set_split(sa, M->plan_A, segpart);
         }
         sa.vcur = cur;
         sa.vprev_out = out;
         sa.mode = (k == 0) ? 0 : 1;
         const int slot = k - ra.step0;
         sa.partials = part + (size_t)slot * max_blocks * 2 * ldv;
-        if ((rc = launch_step<T>(G, sa, max_blocks, &nb, s))) return rc;
+        if ((rc = launch_step<T>(G, sa, max_main, max_long, &nb, s))) return rc;
         ra.nblocks[slot] = nb;
         ra.act[slot] = act;
         ra.nslots = slot + 1;
         if (ra.nslots == kSlots || k == plan.K - 1) {
             int amax = 0;
             for (int i = 0; i < ra.nslots; ++i) amax = std::max(amax, ra.act[i]);
-            dim3 grid((2 * amax + 127) / 128, ra.nslots);
+            dim3 grid((2 * amax + 3) / 4, ra.nslots);
             ProfScope ps("reduce_partials", s);
             reduce_partials_kernel<<<grid, 128, 0, s>>>(part, max_blocks, ldv, ra, dots, plan.B);
             MLT_CUDA_TRY(cudaGetLastError());
@@ -395,6 +546,77 @@ int run_group(mlt_matrix* M, const MomentPlan& plan, double a, double b, uint64_
 }
 
 }  // namespace
+
+// Build the fixed work split of one CSR operand (once per matrix): chunk size
+// Uc from the unit count so that there are a few dozen chunks per SM, the row
+// holding the first unit of every chunk, and the segment table of rows longer
+// than Uc.  Computed on the host from a copy of rowptr.
+int ensure_spmm_plan(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, cudaStream_t s)
+{
+    if (P.ready) return MLT_OK;
+    const int64_t n = C.nrows;
+    std::vector<int64_t> rp(n + 1);
+    MLT_CUDA_TRY(cudaMemcpyAsync(rp.data(), C.rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    MLT_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t units = C.nnz + kRowCost * n;
+    int64_t Uc = units / (16LL * M->num_sms);
+    Uc = std::max<int64_t>(64, std::min<int64_t>(4096, Uc));
+    const int64_t nch = std::max<int64_t>(1, (units + Uc - 1) / Uc);
+    std::vector<int64_t> crow(nch);
+    {
+        int64_t r = 0;
+        for (int64_t c = 0; c < nch; ++c) {
+            const int64_t u = c * Uc;
+            while (r + 1 < n && rp[r + 1] + kRowCost * (r + 1) <= u) ++r;
+            crow[c] = r;
+        }
+    }
+    std::vector<int32_t> seg_row, long_rows;
+    std::vector<int64_t> seg_k0, long_seg0;
+    for (int64_t r = 0; r < n; ++r) {
+        const int64_t deg = rp[r + 1] - rp[r];
+        if (deg <= Uc) continue;
+        long_rows.push_back((int32_t)r);
+        long_seg0.push_back((int64_t)seg_row.size());
+        for (int64_t k0 = rp[r]; k0 < rp[r + 1]; k0 += Uc) {
+            seg_row.push_back((int32_t)r);
+            seg_k0.push_back(k0);
+        }
+    }
+    long_seg0.push_back((int64_t)seg_row.size());
+    const int64_t nseg = (int64_t)seg_row.size();
+    const int nlong = (int)long_rows.size();
+    const size_t bytes = nch * sizeof(int64_t) + nseg * (sizeof(int64_t) + sizeof(int32_t)) +
+                         (nlong + 1) * sizeof(int64_t) + nlong * sizeof(int32_t) + 64;
+    char* mem = nullptr;
+    if (cudaMalloc((void**)&mem, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MLT_ENOMEM, "cudaMalloc (work split) failed");
+    }
+    P.mem = mem;
+    P.crow = reinterpret_cast<int64_t*>(mem);
+    P.seg_k0 = P.crow + nch;
+    P.long_seg0 = P.seg_k0 + nseg;
+    P.seg_row = reinterpret_cast<int32_t*>(P.long_seg0 + nlong + 1);
+    P.long_rows = P.seg_row + nseg;
+    MLT_CUDA_TRY(cudaMemcpyAsync(P.crow, crow.data(), nch * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    if (nseg) {
+        MLT_CUDA_TRY(cudaMemcpyAsync(P.seg_k0, seg_k0.data(), nseg * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        MLT_CUDA_TRY(cudaMemcpyAsync(P.seg_row, seg_row.data(), nseg * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    }
+    MLT_CUDA_TRY(cudaMemcpyAsync(P.long_seg0, long_seg0.data(), (nlong + 1) * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, s));
+    if (nlong)
+        MLT_CUDA_TRY(cudaMemcpyAsync(P.long_rows, long_rows.data(), nlong * sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, s));
+    MLT_CUDA_TRY(cudaStreamSynchronize(s));
+    P.nch = nch;
+    P.Uc = Uc;
+    P.nseg = nseg;
+    P.nlong = nlong;
+    P.ready = true;
+    return MLT_OK;
+}
 
 int ensure_fp32_values(mlt_matrix* M, cudaStream_t s)
 {

@@ -142,11 +142,13 @@ __global__ void f32_to_f64_kernel(const float* __restrict__ in, double* __restri
         out[i] = (double)in[i];
 }
 
-// CSR sanity: rowptr non-decreasing within [0, nnz], columns in [0, ncols) and
-// strictly increasing inside each row.  bad[0] |= 1 (rowptr), 2 (column range),
-// 4 (order or duplicate).
-__global__ void validate_csr_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                    int64_t nrows, int64_t ncols, int64_t nnz, int* bad)
+// CSR sanity in two fully parallel passes (no thread walks a whole row):
+// per row, rowptr must be non-decreasing within [0, nnz] and each non-empty
+// row marks its first entry in a bitmap; per entry, the column must lie in
+// [0, ncols) and exceed the previous entry's unless a row starts there.
+// bad[0] |= 1 (rowptr), 2 (column range), 4 (order or duplicate).
+__global__ void validate_rows_kernel(const int64_t* __restrict__ rowptr, int64_t nrows, int64_t nnz,
+                                     unsigned* __restrict__ starts, int* bad)
 {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows;
          r += (int64_t)gridDim.x * blockDim.x) {
@@ -155,13 +157,22 @@ __global__ void validate_csr_kernel(const int64_t* __restrict__ rowptr, const in
             atomicOr(bad, 1);
             continue;
         }
-        int64_t prev = -1;
-        for (int64_t k = beg; k < end; ++k) {
-            const int64_t c = col[k];
-            if (c < 0 || c >= ncols) atomicOr(bad, 2);
-            else if (c <= prev) atomicOr(bad, 4);
-            prev = c;
+        if (end > beg) atomicOr(starts + (beg >> 5), 1u << (beg & 31));
+    }
+}
+
+__global__ void validate_cols_kernel(const int32_t* __restrict__ col, int64_t nnz, int64_t ncols,
+                                     const unsigned* __restrict__ starts, int* bad)
+{
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = col[k];
+        if (c < 0 || c >= ncols) {
+            atomicOr(bad, 2);
+            continue;
         }
+        const bool first = (starts[k >> 5] >> (k & 31)) & 1u;
+        if (!first && (k == 0 || c <= (int64_t)col[k - 1])) atomicOr(bad, 4);
     }
 }
 
@@ -240,11 +251,12 @@ int gershgorin_device(mlt_matrix* M, double* lo, double* hi, cudaStream_t s)
 static void free_matrix(mlt_matrix* M)
 {
     void* owned[] = {M->own_rowptr, M->own_col, M->own_val, M->own_val32, M->own_t_rowptr,
-                     M->own_t_col, M->own_t_val, M->own_t_val32, M->upper};
+                     M->own_t_col, M->own_t_val, M->own_t_val32, M->plan_A.mem, M->plan_AT.mem};
     for (void* p : owned)
         if (p) cudaFree(p);
     mlt::DevBuf* bufs[] = {&M->ws_v[0], &M->ws_v[1], &M->ws_w, &M->ws_part, &M->ws_dots,
-                           &M->ws_misc, &M->ws_out, &M->ws_y, &M->ws_z, &M->ws_x};
+                           &M->ws_misc, &M->ws_out, &M->ws_y, &M->ws_y32, &M->ws_z, &M->ws_x,
+                           &M->ws_tri, &M->ws_seg};
     for (auto* b : bufs) b->release();
 }
 
@@ -394,17 +406,37 @@ int mlt_create_csr(int64_t nrows, int64_t ncols, int64_t nnz, const int64_t* row
         }
         // reject malformed CSR arrays before any kernel indexes with them
         {
-            int* bad = nullptr;
-            if (cudaMallocAsync((void**)&bad, sizeof(int), s) != cudaSuccess) return bail(fail(MLT_ENOMEM, "cudaMallocAsync failed"));
+            const size_t words = (size_t)(nnz / 32 + 1);
+            char* scratch = nullptr;
+            if (cudaMallocAsync((void**)&scratch, 256 + words * sizeof(unsigned), s) != cudaSuccess) {
+                cudaGetLastError();
+                return bail(fail(MLT_ENOMEM, "cudaMallocAsync failed"));
+            }
+            int* bad = reinterpret_cast<int*>(scratch);
+            unsigned* starts = reinterpret_cast<unsigned*>(scratch + 256);
             int hbad = 0;
-            cudaMemsetAsync(bad, 0, sizeof(int), s);
-            const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((nrows + 255) / 256, 16LL * num_sms));
-            ProfScope ps("validate_csr", s);
-            validate_csr_kernel<<<nb, 256, 0, s>>>(M->A.rowptr, M->A.col, nrows, ncols, nnz, bad);
-            cudaError_t e = cudaGetLastError();
-            if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-            cudaFreeAsync(bad, s);
+            cudaError_t e = cudaMemsetAsync(scratch, 0, 256 + words * sizeof(unsigned), s);
+            const int nbr = (int)std::max<int64_t>(1, std::min<int64_t>((nrows + 255) / 256, 16LL * num_sms));
+            const int nbc = (int)std::max<int64_t>(1, std::min<int64_t>((nnz + 255) / 256, 16LL * num_sms));
+            if (e == cudaSuccess) {
+                ProfScope ps("validate_csr", s);
+                validate_rows_kernel<<<nbr, 256, 0, s>>>(M->A.rowptr, nrows, nnz, starts, bad);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) {
+                e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            }
+            if (e == cudaSuccess && hbad == 0 && nnz > 0) {
+                {
+                    ProfScope ps("validate_csr", s);
+                    validate_cols_kernel<<<nbc, 256, 0, s>>>(M->A.col, nnz, ncols, starts, bad);
+                }
+                e = cudaGetLastError();
+                if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            }
+            cudaFreeAsync(scratch, s);
             if (e != cudaSuccess) return bail(cuda_fail(e, "CSR validation"));
             if (hbad & 1) return bail(fail(MLT_EINVAL, "mlt_create_csr: rowptr must be non-decreasing within [0, nnz]"));
             if (hbad & 2) return bail(fail(MLT_EINVAL, "mlt_create_csr: column index out of range"));

@@ -49,6 +49,20 @@ struct DevCSR {
     const float* val32 = nullptr;    // FP32 copy of the values (lazily made)
 };
 
+// Fixed work split of one CSR operand for the moment engine (see
+// cheb_kernels.cu): chunks of Uc units and segments of rows longer than Uc.
+struct SpmmPlan {
+    bool ready = false;
+    int64_t nch = 0, Uc = 0, nseg = 0;
+    int nlong = 0;
+    int64_t* crow = nullptr;       // row holding the first unit of each chunk
+    int64_t* seg_k0 = nullptr;     // first entry of each segment
+    int64_t* long_seg0 = nullptr;  // first segment of each long row (nlong + 1)
+    int32_t* seg_row = nullptr;    // row of each segment
+    int32_t* long_rows = nullptr;  // the long rows
+    void* mem = nullptr;           // one device allocation holding all of the above
+};
+
 }  // namespace mlt
 
 struct mlt_matrix {
@@ -65,12 +79,22 @@ struct mlt_matrix {
     void* own_val32 = nullptr;
     void* own_t_rowptr = nullptr; void* own_t_col = nullptr; void* own_t_val = nullptr;
     void* own_t_val32 = nullptr;
-    // triangle preparation: first index of each row with col > row
-    int64_t* upper = nullptr;
+    // triangle preparation (all inside ws_tri)
+    int64_t* upper = nullptr;   // first index of each row with col > row
+    struct {
+        int64_t* crow = nullptr;     // row holding the first unit of each work chunk
+        int32_t* bslot = nullptr;    // int32 y slot of rows with degree > 127, else -1
+        int32_t* longlist = nullptr; // rows cut across chunks (degree > long_deg)
+        unsigned long long* counters = nullptr;  // chunk counters of pass 1 and pass 2
+        int nbig = 0, nlong = 0, grid1 = 0, grid2 = 0;
+        int64_t nch = 0, long_deg = 0;
+    } tri;
     int tri_state = 0;          // 0 unprepared, 1 ready, <0 error code
     double tri_bound = 0.0;     // sum_(i,j) deg_i deg_j
     // scratch
-    mlt::DevBuf ws_v[2], ws_w, ws_part, ws_dots, ws_misc, ws_out, ws_y, ws_z, ws_x;
+    mlt::SpmmPlan plan_A, plan_AT;
+    mlt::DevBuf ws_v[2], ws_w, ws_part, ws_dots, ws_misc, ws_out, ws_y, ws_y32, ws_z, ws_x, ws_tri,
+        ws_seg;
     int64_t dim() const { return (flags & MLT_GRAM) ? A.ncols : A.nrows; }
 };
 
@@ -94,6 +118,7 @@ int run_moments_group(mlt_matrix* M, int precision, const MomentPlan& plan, doub
                       cudaStream_t s);
 
 int ensure_fp32_values(mlt_matrix* M, cudaStream_t s);
+int ensure_spmm_plan(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, cudaStream_t s);
 
 // ---- triangle kernels (tri_kernels.cu) ---------------------------------------
 int tri_prepare(mlt_matrix* M, cudaStream_t s);

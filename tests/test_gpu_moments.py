@@ -159,3 +159,38 @@ def test_degenerate_inputs(L, O):
     with L.Matrix(e) as M:
         got = M.moments(-1.0, 1.5, 3, 0, [7, 3])
     assert np.max(np.abs(got - O.moments(e, -1.0, 1.5, 3, 0, [7, 3]))) <= 1e-12
+
+
+def test_rejects_malformed_csr(L):
+    rp = np.array([0, 2, 3], dtype=np.int64)
+    for col in (np.array([0, 5, 1], dtype=np.int32),      # column out of range
+                np.array([1, 0, 1], dtype=np.int32),      # not increasing in a row
+                np.array([1, 1, 0], dtype=np.int32)):     # duplicate
+        with pytest.raises(L.MLTError) as e:
+            L.mlt_create_csr(2, 2, 3, rp, col, np.ones(3))
+        assert e.value.code == L.MLT_EINVAL
+    with pytest.raises(L.MLTError) as e:                 # rowptr not monotone
+        L.mlt_create_csr(2, 2, 3, np.array([0, 4, 3], dtype=np.int64),
+                         np.array([0, 1, 0], dtype=np.int32), np.ones(3))
+    assert e.value.code == L.MLT_EINVAL
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("fp32", 64 * 2.0 ** -24)])
+def test_long_rows_in_segments(L, O, precision, tol):
+    # every row of K_300 is longer than a work chunk: segment products are
+    # added in order by the second kernel
+    g = synth.complete_graph(300)
+    with L.Matrix(g, scale=1.0 / 300) as M:
+        a, b = M.bounds()
+        got = M.moments(a, b, 6, 0, [25, 10, 3], precision=precision)
+    ref = O.moments(g, a, b, 6, 0, [25, 10, 3], scale=1.0 / 300)
+    assert np.max(np.abs(got - ref)) <= tol * g.nrows
+
+
+def test_reproducible_bits(L):
+    g = synth.rmat_adjacency(12, 16, seed=4)
+    with L.Matrix(g, scale=0.01) as M:
+        a, b = M.bounds()
+        r1 = M.moments(a, b, 1, 0, [40] * 70)
+        r2 = M.moments(a, b, 1, 0, [40] * 70)
+    assert np.array_equal(r1, r2)

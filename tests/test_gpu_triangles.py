@@ -97,3 +97,16 @@ def test_full_size_rmat20_sampled(L, O):
     er, sr, _, _ = O.triangle_estimate(x, g.nnz, True)   # same sums -> same bits
     assert est == er and se == sr
     assert np.all(x[:, 1] > 0)
+
+
+@pytest.mark.parametrize("make", [lambda: synth.complete_graph(1500),
+                                  lambda: synth.rmat_adjacency(16, 16, seed=3)])
+def test_long_rows_split_across_chunks(L, O, make):
+    # rows longer than a work chunk are cut and their counts merged atomically
+    g = make()
+    x = np.zeros((130, 3), dtype=np.int64)
+    with L.Matrix(g) as G:
+        est, se = G.triangles(9, 1000, 130, x=x)
+    assert np.array_equal(x, O.triangle_moments(g, 9, 1000, 130))
+    er, sr, _, _ = O.triangle_estimate(x, g.nnz, True)
+    assert est == er and se == sr
