@@ -24,12 +24,13 @@
  *     one handle must not overlap.
  *   - CSR layout: rowptr int64[nrows+1], col int32[nnz] (each row's columns
  *     ascending, no duplicates), values per val_type.
- *   - Probes: probe id p (a global counter) has entries
- *       z_i = +1 if bit 63 of mix64(((p << 32) | i) ^ (seed * 0x9E3779B97F4A7C15)) is 0,
- *       z_i = -1 otherwise,
- *     mix64 the SplitMix64 output finaliser (Steele, Lea, Flood 2014).  The
- *     paper only asks for Rademacher entries (Section 2.1); fixing the
- *     generator makes every result reproducible under any blocking.
+ *   - Probes: probe id p (a global counter, p < 2^32) has entries
+ *       h   = mix64((((p / 64) << 32) | i) ^ (seed * 0x9E3779B97F4A7C15)),
+ *       z_i = -1 if bit (p mod 64) of h is set, +1 otherwise,
+ *     mix64 the SplitMix64 output finaliser (Steele, Lea, Flood 2014), so one
+ *     hash gives the signs of 64 consecutive probes at one row.  The paper
+ *     only asks for Rademacher entries (Section 2.1); fixing the generator
+ *     makes every result reproducible under any blocking.
  */
 #ifndef MLT_H
 #define MLT_H
@@ -222,6 +223,80 @@ int mlt_mlmc_estimate(mlt_matrix* m, const mlt_mlmc_params* p, mlt_mlmc_result* 
 int mlt_triangle_trace(mlt_matrix* m, uint64_t seed, int64_t probe_offset,
                        int64_t nprobes, int block, int use_cv, int64_t* x,
                        double* estimate, double* std_error, void* stream);
+
+/*
+ * Learned coarse level.  The paper has no network; this is a project addition
+ * whose nearest relative is the regression control variate of Section 5.4.  A
+ * 16 -> 128 -> 128 -> 1 ReLU network S (BF16 weights and activations, FP32
+ * accumulation on the tensor cores) maps the scaled low-degree moments
+ * (mu_0 .. mu_15) / d of a probe to an estimate of its degree-l1 quadratic
+ * form P_l1 / d.  Used as the lowest level of a multilevel estimator,
+ *   E[P_n] = E[d S] + E[P_l1 - d S] + E[P_n - P_l1],
+ * it keeps the estimate unbiased for any S; a good S only lowers the variance.
+ * Parameters (FP32, MLT_NET_NPARAMS values): W1[128][16], b1[128],
+ * W2[128][128], b2[128], w3[128], b3; y = w3 . relu(W2 relu(W1 x + b1) + b2) + b3.
+ * Feature and target arrays (x: n x 16 floats row-major, t: n floats) may be
+ * host or device memory.  Errors: MLT_EINVAL, MLT_ENOMEM, MLT_ECUDA, and
+ * MLT_ETIMEOUT if a bounded tensor-core wait gave up.
+ */
+#define MLT_NET_IN       16
+#define MLT_NET_HID      128
+#define MLT_NET_NPARAMS  18817
+
+typedef struct mlt_surrogate mlt_surrogate;   /* opaque; owns device parameters */
+
+/* New network on the current device, weights drawn from N(0, 2/fan_in) with a
+ * generator seeded by `seed` (biases 0). */
+int mlt_surrogate_create(uint64_t seed, mlt_surrogate** out);
+int mlt_surrogate_destroy(mlt_surrogate* s);
+/* Copy the FP32 parameter vector in or out (host arrays of MLT_NET_NPARAMS). */
+int mlt_surrogate_set_params(mlt_surrogate* s, const float* params);
+int mlt_surrogate_get_params(mlt_surrogate* s, float* params);
+/* Mean squared error over n samples and its gradient (host array of
+ * MLT_NET_NPARAMS, may be NULL); the parameters are not changed. */
+int mlt_surrogate_loss_grad(mlt_surrogate* s, const float* x, const float* t, int64_t n,
+                            double* loss, float* grad, void* stream);
+/* `epochs` passes of Adam (lr, beta1 0.9, beta2 0.999) over consecutive
+ * minibatches of `batch` samples (the samples are independent probes, so no
+ * shuffling); *final_loss (may be NULL) is the mean squared error of the last
+ * epoch. */
+int mlt_surrogate_train(mlt_surrogate* s, const float* x, const float* t, int64_t n, int epochs,
+                        int64_t batch, double lr, double* final_loss, void* stream);
+/* y[i] = S(x_i), n outputs (host or device). */
+int mlt_surrogate_predict(mlt_surrogate* s, const float* x, int64_t n, float* y, void* stream);
+
+typedef struct {
+    int fn;             /* MLT_FN_*                                            */
+    double fn_p;        /* exponent for MLT_FN_POW                             */
+    double a, b;        /* spectrum interval                                   */
+    int n;              /* interpolant degree                                  */
+    int l1;             /* degree of the exact level above the network (>= 15) */
+    int64_t m_net;      /* samples of d S                                      */
+    int64_t m_1;        /* samples of P_l1 - d S                               */
+    int64_t m_2;        /* samples of P_n - P_l1 (0 when l1 == n)              */
+    uint64_t seed;
+    int64_t probe_offset;  /* first probe id; ids run level by level           */
+    int precision;      /* MLT_PREC_*                                           */
+    void* stream;
+} mlt_learned_params;
+
+/*
+ * Train s on n_train probes (ids train_offset ..): features (mu_0..mu_15)/d,
+ * target P_l1/d with the Chebyshev coefficients of f (Section 2.2).  The
+ * moments come from mlt_moments at degree l1.
+ */
+int mlt_learned_train(mlt_matrix* m, mlt_surrogate* s, const mlt_learned_params* p,
+                      int64_t n_train, int64_t train_offset, int epochs, int64_t batch, double lr,
+                      double* final_loss);
+
+/*
+ * Three-level estimate of tr p_n(At) with the network as the lowest level:
+ * levels (S, P_l1 - S, P_n - P_l1) with m_net, m_1, m_2 fresh probes; the
+ * result's levels[] are {15, l1, n}.  Each level is an independent sample
+ * mean, as in Eq. multiEstimator.
+ */
+int mlt_learned_estimate(mlt_matrix* m, mlt_surrogate* s, const mlt_learned_params* p,
+                         mlt_mlmc_result* r);
 
 /*
  * Kernel timing (instrumentation; the paper has no counterpart).  Between

@@ -35,13 +35,15 @@ uint64_t orc_mix64(uint64_t x)
     return x ^ (x >> 31);
 }
 
-/* Probe entry z_i of probe p: key = (p << 32) | i, mixed with the seed's
- * golden-ratio multiple; +1 when bit 63 of the hash is clear, else -1. */
+/* Probe entry z_i of probe p: one hash serves the 64 probes 64q .. 64q+63 at
+ * row i.  key = (q << 32) | i with q = p / 64, mixed with the seed's
+ * golden-ratio multiple; z_i = -1 when bit (p mod 64) of the hash is set. */
 int orc_rademacher(uint64_t seed, uint64_t p, uint64_t i)
 {
-    uint64_t key = (p << 32) | (i & 0xffffffffULL);
+    uint64_t q = p / 64;
+    uint64_t key = (q << 32) | (i & 0xffffffffULL);
     uint64_t h = orc_mix64(key ^ (seed * 0x9e3779b97f4a7c15ULL));
-    return (h >> 63) ? -1 : 1;
+    return ((h >> (p % 64)) & 1) ? -1 : 1;
 }
 
 void orc_probe(uint64_t seed, uint64_t p, int64_t d, int8_t *z)

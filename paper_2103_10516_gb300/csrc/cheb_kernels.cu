@@ -558,9 +558,11 @@ int ensure_spmm_plan(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, cudaStream_t s
     std::vector<int64_t> rp(n + 1);
     MLT_CUDA_TRY(cudaMemcpyAsync(rp.data(), C.rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     MLT_CUDA_TRY(cudaStreamSynchronize(s));
+    // about 64 chunks per SM: small matrices get chunks of a row or two, so even
+    // a narrow probe block keeps every SM busy; large ones cap at 4096 units
     const int64_t units = C.nnz + kRowCost * n;
-    int64_t Uc = units / (16LL * M->num_sms);
-    Uc = std::max<int64_t>(64, std::min<int64_t>(4096, Uc));
+    int64_t Uc = units / (64LL * M->num_sms);
+    Uc = std::max<int64_t>(8, std::min<int64_t>(4096, Uc));
     const int64_t nch = std::max<int64_t>(1, (units + Uc - 1) / Uc);
     std::vector<int64_t> crow(nch);
     {

@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libmlt.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -82,19 +83,22 @@ struct mlt_matrix {
     // triangle preparation (all inside ws_tri)
     int64_t* upper = nullptr;   // first index of each row with col > row
     struct {
-        int64_t* crow = nullptr;     // row holding the first unit of each work chunk
+        int64_t* up_ptr = nullptr;   // row pointer of the strictly upper triangle
+        int32_t* up_col = nullptr;   // its columns
+        int64_t* crow1 = nullptr;    // row holding the first unit of each pass-1 chunk
+        int64_t* crow2 = nullptr;    // same over the upper triangle (pass 2)
         int32_t* bslot = nullptr;    // int32 y slot of rows with degree > 127, else -1
-        int32_t* longlist = nullptr; // rows cut across chunks (degree > long_deg)
+        int32_t* longlist = nullptr; // rows cut across pass-1 chunks
         unsigned long long* counters = nullptr;  // chunk counters of pass 1 and pass 2
         int nbig = 0, nlong = 0, grid1 = 0, grid2 = 0;
-        int64_t nch = 0, long_deg = 0;
+        int64_t nch1 = 0, nch2 = 0;
     } tri;
     int tri_state = 0;          // 0 unprepared, 1 ready, <0 error code
     double tri_bound = 0.0;     // sum_(i,j) deg_i deg_j
     // scratch
     mlt::SpmmPlan plan_A, plan_AT;
     mlt::DevBuf ws_v[2], ws_w, ws_part, ws_dots, ws_misc, ws_out, ws_y, ws_y32, ws_z, ws_x, ws_tri,
-        ws_seg;
+        ws_seg, ws_upcol;
     int64_t dim() const { return (flags & MLT_GRAM) ? A.ncols : A.nrows; }
 };
 
@@ -123,6 +127,37 @@ int ensure_spmm_plan(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, cudaStream_t s
 // ---- triangle kernels (tri_kernels.cu) ---------------------------------------
 int tri_prepare(mlt_matrix* M, cudaStream_t s);
 int tri_block(mlt_matrix* M, uint64_t seed, int64_t id0, int nb, int64_t* x_dev, cudaStream_t s);
+
+// ---- learned level network (mlp_kernels.cu) ---------------------------------
+// FP32 parameter vector: W1[128][16], b1[128], W2[128][128], b2[128], w3[128], b3.
+constexpr int MLP_IN = 16;
+constexpr int MLP_HID = 128;
+constexpr int MLP_OFF_W1 = 0;
+constexpr int MLP_OFF_B1 = MLP_OFF_W1 + MLP_HID * MLP_IN;
+constexpr int MLP_OFF_W2 = MLP_OFF_B1 + MLP_HID;
+constexpr int MLP_OFF_B2 = MLP_OFF_W2 + MLP_HID * MLP_HID;
+constexpr int MLP_OFF_W3 = MLP_OFF_B2 + MLP_HID;
+constexpr int MLP_OFF_B3 = MLP_OFF_W3 + MLP_HID;
+constexpr int MLP_NPARAMS = MLP_OFF_B3 + 1;
+
+struct MlpDev {
+    float* P = nullptr;            // FP32 master parameters
+    float* G = nullptr;            // gradient
+    float* M = nullptr;            // Adam first moment
+    float* V = nullptr;            // Adam second moment
+    __nv_bfloat16* W1b = nullptr;  // BF16 copies read by the tiles
+    __nv_bfloat16* W2b = nullptr;
+    __nv_bfloat16* W2Tb = nullptr;
+    float* part = nullptr;         // per-tile partial gradients
+    int64_t part_tiles = 0;
+    double* loss = nullptr;        // summed squared error of the last pass
+    int* err = nullptr;
+};
+
+size_t mlp_smem_bytes();
+int mlp_launch_tiles(const MlpDev& D, const float* X, const float* T, int64_t n, float inv_n, int train,
+                     float* y, int* err, cudaStream_t s);
+int mlp_adam(const MlpDev& D, float lr, int64_t step, int update, cudaStream_t s);
 
 // ---- misc kernels -----------------------------------------------------------
 int gershgorin_device(mlt_matrix* M, double* lo, double* hi, cudaStream_t s);

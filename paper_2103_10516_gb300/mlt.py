@@ -296,3 +296,158 @@ class Matrix:
         P.flags = MLT_DIRECT if direct else 0
         P.stream = _stream(stream)
         return mlt_mlmc_estimate(self.handle, P)
+
+
+# ---------------------------------------------------------------------------
+# learned coarse level
+# ---------------------------------------------------------------------------
+
+MLT_NET_IN, MLT_NET_HID, MLT_NET_NPARAMS = 16, 128, 18817
+NET_OFF = {"W1": (0, (128, 16)), "b1": (2048, (128,)), "W2": (2176, (128, 128)),
+           "b2": (18560, (128,)), "w3": (18688, (128,)), "b3": (18816, ())}
+
+
+class mlt_learned_params(ctypes.Structure):
+    _fields_ = [("fn", ctypes.c_int), ("fn_p", ctypes.c_double), ("a", ctypes.c_double),
+                ("b", ctypes.c_double), ("n", ctypes.c_int), ("l1", ctypes.c_int),
+                ("m_net", ctypes.c_int64), ("m_1", ctypes.c_int64), ("m_2", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("probe_offset", ctypes.c_int64),
+                ("precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+def _bind_learned(L):
+    vp, i64, u64, dbl, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int
+    L.mlt_surrogate_create.argtypes = [u64, ctypes.POINTER(vp)]
+    L.mlt_surrogate_destroy.argtypes = [vp]
+    L.mlt_surrogate_set_params.argtypes = [vp, vp]
+    L.mlt_surrogate_get_params.argtypes = [vp, vp]
+    L.mlt_surrogate_loss_grad.argtypes = [vp, vp, vp, i64, ctypes.POINTER(dbl), vp, vp]
+    L.mlt_surrogate_train.argtypes = [vp, vp, vp, i64, ci, i64, dbl, ctypes.POINTER(dbl), vp]
+    L.mlt_surrogate_predict.argtypes = [vp, vp, i64, vp, vp]
+    L.mlt_learned_train.argtypes = [vp, vp, ctypes.POINTER(mlt_learned_params), i64, i64, ci, i64, dbl,
+                                    ctypes.POINTER(dbl)]
+    L.mlt_learned_estimate.argtypes = [vp, vp, ctypes.POINTER(mlt_learned_params),
+                                       ctypes.POINTER(mlt_mlmc_result)]
+    for name in ("mlt_surrogate_create", "mlt_surrogate_destroy", "mlt_surrogate_set_params",
+                 "mlt_surrogate_get_params", "mlt_surrogate_loss_grad", "mlt_surrogate_train",
+                 "mlt_surrogate_predict", "mlt_learned_train", "mlt_learned_estimate"):
+        getattr(L, name).restype = ci
+
+
+EXPORTS += ["mlt_surrogate_create", "mlt_surrogate_destroy", "mlt_surrogate_set_params",
+            "mlt_surrogate_get_params", "mlt_surrogate_loss_grad", "mlt_surrogate_train",
+            "mlt_surrogate_predict", "mlt_learned_train", "mlt_learned_estimate"]
+
+_lib_plain = lib
+
+
+def lib():  # noqa: F811  (extends the loader with the learned-level symbols)
+    L = _lib_plain()
+    if not getattr(L, "_learned_bound", False):
+        _bind_learned(L)
+        L._learned_bound = True
+    return L
+
+
+def pack_params(P):
+    """Dict of arrays (W1, b1, W2, b2, w3, b3) -> FP32 vector of MLT_NET_NPARAMS."""
+    v = np.zeros(MLT_NET_NPARAMS, dtype=np.float32)
+    for k, (off, shape) in NET_OFF.items():
+        a = np.asarray(P[k], dtype=np.float32).ravel()
+        v[off: off + a.size] = a
+    return v
+
+
+def unpack_params(v):
+    out = {}
+    for k, (off, shape) in NET_OFF.items():
+        size = int(np.prod(shape)) if shape else 1
+        a = np.asarray(v[off: off + size], dtype=np.float64)
+        out[k] = a.reshape(shape) if shape else float(a[0])
+    return out
+
+
+class Surrogate:
+    """Owns one mlt_surrogate handle."""
+
+    def __init__(self, seed=0):
+        h = ctypes.c_void_p()
+        _check(lib().mlt_surrogate_create(int(seed), ctypes.byref(h)))
+        self.handle = h.value
+
+    def close(self):
+        if self.handle:
+            _check(lib().mlt_surrogate_destroy(self.handle))
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, P):
+        v = pack_params(P) if isinstance(P, dict) else np.ascontiguousarray(P, dtype=np.float32)
+        _check(lib().mlt_surrogate_set_params(self.handle, _ptr(v)))
+
+    def get_params(self):
+        v = np.zeros(MLT_NET_NPARAMS, dtype=np.float32)
+        _check(lib().mlt_surrogate_get_params(self.handle, _ptr(v)))
+        return v
+
+    def loss_grad(self, X, T, stream=None):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        g = np.zeros(MLT_NET_NPARAMS, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(lib().mlt_surrogate_loss_grad(self.handle, _ptr(X), _ptr(T), X.shape[0],
+                                             ctypes.byref(loss), _ptr(g), _stream(stream)))
+        return loss.value, g
+
+    def train(self, X, T, epochs, batch, lr, stream=None):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(lib().mlt_surrogate_train(self.handle, _ptr(X), _ptr(T), X.shape[0], int(epochs),
+                                         int(batch), float(lr), ctypes.byref(loss), _stream(stream)))
+        return loss.value
+
+    def predict(self, X, stream=None):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.zeros(X.shape[0], dtype=np.float32)
+        _check(lib().mlt_surrogate_predict(self.handle, _ptr(X), X.shape[0], _ptr(y), _stream(stream)))
+        return y
+
+
+def learned_params(fn, a, b, n, l1, m_net, m_1, m_2, seed=0, probe_offset=0, precision="fp64",
+                   p=0.0, stream=None):
+    P = mlt_learned_params()
+    P.fn = MLT_FN[fn] if isinstance(fn, str) else fn
+    P.fn_p, P.a, P.b, P.n, P.l1 = float(p), float(a), float(b), int(n), int(l1)
+    P.m_net, P.m_1, P.m_2 = int(m_net), int(m_1), int(m_2)
+    P.seed, P.probe_offset = int(seed), int(probe_offset)
+    P.precision = MLT_PREC[precision] if isinstance(precision, str) else precision
+    P.stream = _stream(stream)
+    return P
+
+
+def mlt_learned_train(matrix, surrogate, P, n_train, train_offset, epochs, batch, lr):
+    loss = ctypes.c_double()
+    _check(lib().mlt_learned_train(matrix, surrogate, ctypes.byref(P), int(n_train), int(train_offset),
+                                   int(epochs), int(batch), float(lr), ctypes.byref(loss)))
+    return loss.value
+
+
+def mlt_learned_estimate(matrix, surrogate, P):
+    r = mlt_mlmc_result()
+    _check(lib().mlt_learned_estimate(matrix, surrogate, ctypes.byref(P), ctypes.byref(r)))
+    L = r.nlevels
+    return {"estimate": r.estimate, "stderr": r.std_error, "levels": list(r.levels[:L]),
+            "m": list(r.m[:L]), "level_mean": list(r.level_mean[:L]),
+            "level_var": list(r.level_var[:L]), "probes": r.probes, "matvecs": r.matvecs}

@@ -41,21 +41,21 @@ def test_exports_every_declared_symbol(L):
 def test_struct_layout_matches_ctypes(L, tmp_path):
     import ctypes
     src = tmp_path / "layout.c"
-    fields_p = [f for f, _ in L.mlt_mlmc_params._fields_]
-    fields_r = [f for f, _ in L.mlt_mlmc_result._fields_]
-    body = ['#include <stdio.h>', '#include <stddef.h>', '#include "mlt.h"', 'int main(void){',
-            'printf("%zu\\n", sizeof(mlt_mlmc_params));',
-            'printf("%zu\\n", sizeof(mlt_mlmc_result));']
-    body += ['printf("%%zu\\n", offsetof(mlt_mlmc_params, %s));' % f for f in fields_p]
-    body += ['printf("%%zu\\n", offsetof(mlt_mlmc_result, %s));' % f for f in fields_r]
+    structs = [("mlt_mlmc_params", L.mlt_mlmc_params), ("mlt_mlmc_result", L.mlt_mlmc_result),
+               ("mlt_learned_params", L.mlt_learned_params), ("mlt_kernel_stat", L.mlt_kernel_stat)]
+    body = ['#include <stdio.h>', '#include <stddef.h>', '#include "mlt.h"', 'int main(void){']
+    expect = []
+    for cname, cls in structs:
+        body.append('printf("%%zu\\n", sizeof(%s));' % cname)
+        expect.append(ctypes.sizeof(cls))
+        for f, _ in cls._fields_:
+            body.append('printf("%%zu\\n", offsetof(%s, %s));' % (cname, f))
+            expect.append(getattr(cls, f).offset)
     body += ['return 0;}']
     src.write_text("\n".join(body))
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
-    expect = [ctypes.sizeof(L.mlt_mlmc_params), ctypes.sizeof(L.mlt_mlmc_result)]
-    expect += [getattr(L.mlt_mlmc_params, f).offset for f in fields_p]
-    expect += [getattr(L.mlt_mlmc_result, f).offset for f in fields_r]
     assert vals == expect
 
 
@@ -67,6 +67,7 @@ def test_constants_match_header(L):
     assert val("MLT_MAX_LEVELS") == L.MLT_MAX_LEVELS and val("MLT_MAX_DEGREE") == L.MLT_MAX_DEGREE
     assert val("MLT_GRAM") == L.MLT_GRAM and val("MLT_DEVICE_PTRS") == L.MLT_DEVICE_PTRS
     assert val("MLT_FN_SQRT") == L.MLT_FN["sqrt"] and val("MLT_PREC_FP32") == L.MLT_PREC["fp32"]
+    assert val("MLT_NET_NPARAMS") == L.MLT_NET_NPARAMS and val("MLT_NET_HID") == L.MLT_NET_HID
 
 
 @pytest.mark.parametrize("fn,a,b,n", [("log", 0.1, 8.1, 128), ("sqrt", 0.0, 50.0, 512),

@@ -110,3 +110,16 @@ def test_long_rows_split_across_chunks(L, O, make):
     assert np.array_equal(x, O.triangle_moments(g, 9, 1000, 130))
     er, sr, _, _ = O.triangle_estimate(x, g.nnz, True)
     assert est == er and se == sr
+
+
+def test_empty_and_tiny_graphs(L, O):
+    empty = synth.CSR(3, 3, np.array([0, 0, 0, 0]), np.array([], dtype=np.int32))
+    x = np.ones((5, 3), dtype=np.int64)
+    with L.Matrix(empty) as G:
+        est, se = G.triangles(0, 0, 5, x=x)
+    assert np.all(x == 0) and est == 0.0
+    tri = synth.complete_graph(3)
+    x = np.zeros((200, 3), dtype=np.int64)
+    with L.Matrix(tri) as G:
+        est, se = G.triangles(2, 64, 200, x=x)
+    assert np.array_equal(x, O.triangle_moments(tri, 2, 64, 200))

@@ -13,14 +13,23 @@ def test_splitmix64_reference_sequence(O):
 
 
 def test_rademacher_definition(O):
-    # z_i of probe p = +1 iff bit 63 of mix64(((p << 32) | i) ^ (seed * gamma)) is 0
+    # z_i of probe p = +1 iff bit (p mod 64) of mix64((((p // 64) << 32) | i) ^ (seed * gamma)) is 0
     g = 0x9E3779B97F4A7C15
     for seed in (0, 1, 12345):
-        for p in (0, 7, 2**20 + 3):
+        for p in (0, 7, 63, 64, 2**20 + 3):
             z = O.rademacher(seed, p, 64)
             for i in (0, 1, 33, 63):
-                h = O.mix64((((p << 32) | i) ^ (seed * g)) % 2**64)
-                assert z[i] == (1 if (h >> 63) == 0 else -1)
+                h = O.mix64(((((p // 64) << 32) | i) ^ (seed * g)) % 2**64)
+                assert z[i] == (1 if ((h >> (p % 64)) & 1) == 0 else -1)
+
+
+def test_probes_sharing_a_hash_are_uncorrelated(O):
+    # probes 64q .. 64q+63 take different bits of the same hash: still E[z_p z_q] = 0
+    d = 100_000
+    zs = [O.rademacher(3, p, d).astype(np.float64) for p in (128, 129, 191)]
+    for a in range(3):
+        for b in range(a + 1, 3):
+            assert abs((zs[a] * zs[b]).mean()) < 4.0 / np.sqrt(d)
 
 
 def test_rademacher_statistics(O):
