@@ -71,6 +71,12 @@ extern "C" {
 /* ---- precision of mlt_moments -------------------------------------------- */
 #define MLT_PREC_FP64 0    /* vectors, SpMM and dots in FP64                 */
 #define MLT_PREC_FP32 1    /* vectors and SpMM in FP32, dots summed in FP64  */
+#define MLT_PREC_MIXED 2   /* FP32 steps first, FP64 after: see below       */
+/* MLT_PREC_MIXED_AT(k): the first k recurrence steps (degrees up to 2k with
+ * the doubling identities, up to k in direct mode) run with FP32 vectors, the
+ * rest with FP64 vectors (the two live vectors are widened at the switch);
+ * FP32 drift grows with the degree, FP64 steps stop it from growing further. */
+#define MLT_PREC_MIXED_AT(k) (MLT_PREC_MIXED | ((k) << 8))
 
 /* ---- flags of mlt_moments ------------------------------------------------ */
 #define MLT_DIRECT   1u    /* mu_j = z . V_j at every step (n matvecs for
@@ -80,6 +86,7 @@ extern "C" {
 
 /* ---- spectrum interval methods ------------------------------------------- */
 #define MLT_BOUNDS_GERSHGORIN 0
+#define MLT_BOUNDS_LANCZOS    1
 
 /* ---- multilevel parameters ------------------------------------------------ */
 #define MLT_MAX_LEVELS 1024
@@ -118,7 +125,11 @@ int mlt_matrix_info(const mlt_matrix* m, int64_t* dim, int64_t* nnz);
  * Interval [a, b] containing the spectrum of the operator.  The map
  * g(x) = (2x - a - b)/(b - a) needs one (Section 2.2).  MLT_BOUNDS_GERSHGORIN:
  * Gershgorin discs (min_i a_ii - r_i, max_i a_ii + r_i) for A; for a Gram
- * handle [0, ||X||_1 ||X||_inf].  `steps` and `seed` are reserved (pass 0).
+ * handle [0, ||X||_1 ||X||_inf].  MLT_BOUNDS_LANCZOS: `steps` Lanczos steps
+ * (at least 2) from the Rademacher start vector of probe id 0 under `seed`;
+ * the interval is [theta_min - r_min, theta_max + r_max] (extreme Ritz values
+ * and their residual norms), widened by 1%, with the lower end at least
+ * 1e-6 b for a Gram handle.  A Lanczos interval is an estimate, not a proof.
  */
 int mlt_spectrum_bounds(mlt_matrix* m, int method, int steps, uint64_t seed,
                         double* a, double* b);

@@ -430,59 +430,32 @@ void set_split(StepArgs<T>& a, const SpmmPlan& P, T* segpart)
     a.segpart = segpart;
 }
 
+// State shared by the recurrence steps of one probe group.
+struct GroupCtx {
+    bool gram;
+    int64_t d;
+    int ldv;
+    double alpha, beta;
+    uint64_t seedmix;
+    double* part;
+    double* dots;
+    int max_main, max_long, max_blocks;
+    ReduceArgs ra;
+};
+
+// Recurrence steps k0 <= k < k1 in precision T: V[k & 1] holds V_k and
+// V[(k + 1) & 1] holds V_{k-1} on entry to step k.
 template <typename T>
-int run_group(mlt_matrix* M, const MomentPlan& plan, double a, double b, uint64_t seed,
-              double* mu_dev, int64_t ld_mu, int* err_flag, cudaStream_t s)
+int run_steps(mlt_matrix* M, const MomentPlan& plan, GroupCtx& g, int k0, int k1, T* const* V, T* W,
+              T* segpart, cudaStream_t s)
 {
     constexpr int N = Lanes<T>::N;
-    const bool gram = (M->flags & MLT_GRAM) != 0;
-    const int64_t d = plan.dim;
-    const int ldv = plan.ldv;
-    const size_t vbytes = (size_t)d * ldv * sizeof(T);
-    int rc;
-    if ((rc = ensure_spmm_plan(M, M->A, M->plan_A, s))) return rc;
-    if (gram && (rc = ensure_spmm_plan(M, M->AT, M->plan_AT, s))) return rc;
-    if ((rc = M->ws_v[0].ensure(vbytes, s)) || (rc = M->ws_v[1].ensure(vbytes, s))) return rc;
-    T* V[2] = {M->ws_v[0].as<T>(), M->ws_v[1].as<T>()};
-    T* W = nullptr;
-    if (gram) {
-        if ((rc = M->ws_w.ensure((size_t)M->A.nrows * ldv * sizeof(T), s))) return rc;
-        W = M->ws_w.as<T>();
-    }
-    const int64_t nseg = std::max(M->plan_A.nseg, gram ? M->plan_AT.nseg : (int64_t)0);
-    if ((rc = M->ws_seg.ensure((size_t)std::max<int64_t>(nseg, 1) * ldv * sizeof(T), s))) return rc;
-    T* segpart = M->ws_seg.as<T>();
-    const int max_main = 8 * M->num_sms;
-    const int max_long = 2 * M->num_sms;
-    const int max_blocks = max_main + max_long;
-    if ((rc = M->ws_part.ensure((size_t)kSlots * max_blocks * 2 * ldv * sizeof(double), s))) return rc;
-    if ((rc = M->ws_dots.ensure((size_t)std::max(plan.K, 1) * 2 * plan.B * sizeof(double), s))) return rc;
-    double* part = M->ws_part.as<double>();
-    double* dots = M->ws_dots.as<double>();
-    const uint64_t seedmix = seed * kGolden;
-
-    {
-        const int64_t total = d * (int64_t)ldv;
-        const int nb = (int)std::min<int64_t>((total + 255) / 256, 16LL * M->num_sms);
-        ProfScope ps("init_probes", s);
-        init_probes_kernel<T><<<std::max(nb, 1), 256, 0, s>>>(V[0], d, ldv, plan.B, plan.ids_dev, seedmix);
-    }
-    MLT_CUDA_TRY(cudaGetLastError());
-
-    // At = alpha A + beta I; the stored entries carry `scale` (squared for X^T X).
-    const double sc = gram ? M->scale * M->scale : M->scale;
-    const double alpha = 2.0 / (b - a) * sc;
-    const double beta = -(a + b) / (b - a);
-
     const DevCSR& A = M->A;
     const DevCSR& AT = M->AT;
     const T* valA = std::is_same<T, double>::value ? (const T*)A.val64 : (const T*)A.val32;
     const T* valAT = std::is_same<T, double>::value ? (const T*)AT.val64 : (const T*)AT.val32;
-
-    ReduceArgs ra{};
-    ra.step0 = 0;
-    ra.nslots = 0;
-    for (int k = 0; k < plan.K; ++k) {
+    int rc;
+    for (int k = k0; k < k1; ++k) {
         const int act = plan.act[k];
         const int nvec = (act + N - 1) / N;
         const int G = pow2_at_least(std::min(nvec, 32));
@@ -490,23 +463,23 @@ int run_group(mlt_matrix* M, const MomentPlan& plan, double a, double b, uint64_
         T* cur = V[k & 1];
         T* out = V[(k + 1) & 1];
         StepArgs<T> sa{};
-        sa.ldv = ldv;
+        sa.ldv = g.ldv;
         sa.nvec = nvec;
         sa.nchunks = nchunks;
-        sa.alpha = (T)alpha;
-        sa.beta = (T)beta;
+        sa.alpha = (T)g.alpha;
+        sa.beta = (T)g.beta;
         sa.direct = plan.direct;
         sa.B = plan.B;
-        sa.seedmix = seedmix;
+        sa.seedmix = g.seedmix;
         sa.ids = plan.ids_dev;
         int nb = 0;
-        if (gram) {
+        if (g.gram) {
             StepArgs<T> pa = sa;
             pa.rowptr = A.rowptr; pa.col = A.col; pa.val = valA; pa.nrows = A.nrows;
             pa.vgather = cur; pa.vcur = nullptr; pa.vprev_out = W; pa.mode = 2;
             pa.partials = nullptr;
             set_split(pa, M->plan_A, segpart);
-            if ((rc = launch_step<T>(G, pa, max_main, max_long, &nb, s))) return rc;
+            if ((rc = launch_step<T>(G, pa, g.max_main, g.max_long, &nb, s))) return rc;
             sa.rowptr = AT.rowptr; sa.col = AT.col; sa.val = valAT; sa.nrows = AT.nrows;
             sa.vgather = W;
             set_split(sa, M->plan_AT, segpart);
@@ -518,9 +491,10 @@ int run_group(mlt_matrix* M, const MomentPlan& plan, double a, double b, uint64_
         sa.vcur = cur;
         sa.vprev_out = out;
         sa.mode = (k == 0) ? 0 : 1;
+        ReduceArgs& ra = g.ra;
         const int slot = k - ra.step0;
-        sa.partials = part + (size_t)slot * max_blocks * 2 * ldv;
-        if ((rc = launch_step<T>(G, sa, max_main, max_long, &nb, s))) return rc;
+        sa.partials = g.part + (size_t)slot * g.max_blocks * 2 * g.ldv;
+        if ((rc = launch_step<T>(G, sa, g.max_main, g.max_long, &nb, s))) return rc;
         ra.nblocks[slot] = nb;
         ra.act[slot] = act;
         ra.nslots = slot + 1;
@@ -529,17 +503,97 @@ int run_group(mlt_matrix* M, const MomentPlan& plan, double a, double b, uint64_
             for (int i = 0; i < ra.nslots; ++i) amax = std::max(amax, ra.act[i]);
             dim3 grid((2 * amax + 3) / 4, ra.nslots);
             ProfScope ps("reduce_partials", s);
-            reduce_partials_kernel<<<grid, 128, 0, s>>>(part, max_blocks, ldv, ra, dots, plan.B);
+            reduce_partials_kernel<<<grid, 128, 0, s>>>(g.part, g.max_blocks, g.ldv, ra, g.dots, plan.B);
             MLT_CUDA_TRY(cudaGetLastError());
             ra.step0 = k + 1;
             ra.nslots = 0;
         }
     }
+    return MLT_OK;
+}
+
+__global__ void widen_kernel(const float* __restrict__ in, double* __restrict__ out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
+// One probe group: steps [0, ks) in FP32 (when the group starts in FP32) and
+// [ks, K) in FP64; ks = 0 is all FP64, ks >= K all FP32.  At the switch the
+// two live vectors V_k, V_{k-1} are widened to FP64 and the recurrence goes on.
+int run_group(mlt_matrix* M, const MomentPlan& plan, int ks, double a, double b, uint64_t seed,
+              double* mu_dev, int64_t ld_mu, int* err_flag, cudaStream_t s)
+{
+    GroupCtx g;
+    g.gram = (M->flags & MLT_GRAM) != 0;
+    g.d = plan.dim;
+    g.ldv = plan.ldv;
+    ks = std::max(0, std::min(ks, plan.K));
+    const bool f32 = ks > 0;
+    const bool f64 = ks < plan.K || !f32;
+    const size_t n = (size_t)g.d * g.ldv;
+    const size_t wrows = g.gram ? (size_t)M->A.nrows * g.ldv : 0;
+    int rc;
+    if ((rc = ensure_spmm_plan(M, M->A, M->plan_A, s))) return rc;
+    if (g.gram && (rc = ensure_spmm_plan(M, M->AT, M->plan_AT, s))) return rc;
+    if (f32 && (rc = ensure_fp32_values(M, s))) return rc;
+    // V buffers: FP32 pair in ws_v (when used), FP64 pair in ws_v (all-FP64) or ws_v2 (mixed)
+    float* Vf[2] = {nullptr, nullptr};
+    double* Vd[2] = {nullptr, nullptr};
+    if (f32) {
+        if ((rc = M->ws_v[0].ensure(n * sizeof(float), s)) || (rc = M->ws_v[1].ensure(n * sizeof(float), s))) return rc;
+        Vf[0] = M->ws_v[0].as<float>();
+        Vf[1] = M->ws_v[1].as<float>();
+    }
+    if (f64) {
+        DevBuf* vb = f32 ? M->ws_v2 : M->ws_v;
+        if ((rc = vb[0].ensure(n * sizeof(double), s)) || (rc = vb[1].ensure(n * sizeof(double), s))) return rc;
+        Vd[0] = vb[0].as<double>();
+        Vd[1] = vb[1].as<double>();
+    }
+    const size_t tsz = f64 ? sizeof(double) : sizeof(float);
+    if (g.gram && (rc = M->ws_w.ensure(wrows * tsz, s))) return rc;
+    const int64_t nseg = std::max(M->plan_A.nseg, g.gram ? M->plan_AT.nseg : (int64_t)0);
+    if ((rc = M->ws_seg.ensure((size_t)std::max<int64_t>(nseg, 1) * g.ldv * tsz, s))) return rc;
+    g.max_main = 8 * M->num_sms;
+    g.max_long = 2 * M->num_sms;
+    g.max_blocks = g.max_main + g.max_long;
+    if ((rc = M->ws_part.ensure((size_t)kSlots * g.max_blocks * 2 * g.ldv * sizeof(double), s))) return rc;
+    if ((rc = M->ws_dots.ensure((size_t)std::max(plan.K, 1) * 2 * plan.B * sizeof(double), s))) return rc;
+    g.part = M->ws_part.as<double>();
+    g.dots = M->ws_dots.as<double>();
+    g.seedmix = seed * kGolden;
+    g.ra = ReduceArgs{};
+    // At = alpha A + beta I; the stored entries carry `scale` (squared for X^T X).
+    const double sc = g.gram ? M->scale * M->scale : M->scale;
+    g.alpha = 2.0 / (b - a) * sc;
+    g.beta = -(a + b) / (b - a);
+    {
+        const int nb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, 16LL * M->num_sms);
+        ProfScope ps("init_probes", s);
+        if (f32) init_probes_kernel<float><<<std::max(nb, 1), 256, 0, s>>>(Vf[0], g.d, g.ldv, plan.B, plan.ids_dev, g.seedmix);
+        else init_probes_kernel<double><<<std::max(nb, 1), 256, 0, s>>>(Vd[0], g.d, g.ldv, plan.B, plan.ids_dev, g.seedmix);
+    }
+    MLT_CUDA_TRY(cudaGetLastError());
+    if (f32) {
+        if ((rc = run_steps<float>(M, plan, g, 0, ks, Vf, M->ws_w.as<float>(), M->ws_seg.as<float>(), s))) return rc;
+    }
+    if (f32 && f64 && ks < plan.K) {
+        const int nb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, 16LL * M->num_sms);
+        ProfScope ps("widen_vectors", s);
+        widen_kernel<<<std::max(nb, 1), 256, 0, s>>>(Vf[0], Vd[0], (int64_t)n);
+        widen_kernel<<<std::max(nb, 1), 256, 0, s>>>(Vf[1], Vd[1], (int64_t)n);
+        MLT_CUDA_TRY(cudaGetLastError());
+    }
+    if (f64) {
+        if ((rc = run_steps<double>(M, plan, g, f32 ? ks : 0, plan.K, Vd, M->ws_w.as<double>(),
+                                    M->ws_seg.as<double>(), s))) return rc;
+    }
     {
         dim3 grid((unsigned)std::min<int64_t>((ld_mu + 127) / 128, 64), plan.B);
         ProfScope ps("finalize_moments", s);
-        finalize_moments_kernel<<<grid, 128, 0, s>>>(dots, plan.B, plan.deg_dev, plan.row_dev, mu_dev,
-                                                     ld_mu, (double)d, plan.direct, err_flag);
+        finalize_moments_kernel<<<grid, 128, 0, s>>>(g.dots, plan.B, plan.deg_dev, plan.row_dev, mu_dev,
+                                                     ld_mu, (double)g.d, plan.direct, err_flag);
         MLT_CUDA_TRY(cudaGetLastError());
     }
     return MLT_OK;
@@ -620,6 +674,33 @@ int ensure_spmm_plan(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, cudaStream_t s
     return MLT_OK;
 }
 
+// y = C x for one FP64 vector stored with stride 2 (entry i at x[2 i], the
+// other slot zero), through the balanced product kernel; the stored values
+// are used as they are (the handle's scale is not applied).
+int spmv_f64(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, const double* x, double* y, cudaStream_t s)
+{
+    int rc;
+    if ((rc = ensure_spmm_plan(M, C, P, s))) return rc;
+    if ((rc = M->ws_seg.ensure((size_t)std::max<int64_t>(P.nseg, 1) * 2 * sizeof(double), s))) return rc;
+    StepArgs<double> a{};
+    a.rowptr = C.rowptr;
+    a.col = C.col;
+    a.val = C.val64;
+    a.nrows = C.nrows;
+    a.ldv = 2;
+    a.nvec = 1;
+    a.nchunks = 1;
+    a.vgather = x;
+    a.vcur = nullptr;
+    a.vprev_out = y;
+    a.mode = 2;
+    a.B = 1;
+    a.partials = nullptr;
+    set_split(a, P, M->ws_seg.as<double>());
+    int nb = 0;
+    return launch_step<double>(1, a, 8 * M->num_sms, 2 * M->num_sms, &nb, s);
+}
+
 int ensure_fp32_values(mlt_matrix* M, cudaStream_t s)
 {
     auto conv = [&](DevCSR& C, void*& own) -> int {
@@ -644,12 +725,11 @@ int ensure_fp32_values(mlt_matrix* M, cudaStream_t s)
 int run_moments_group(mlt_matrix* M, int precision, const MomentPlan& plan, double a, double b,
                       uint64_t seed, double* mu_dev, int64_t ld_mu, int* err_flag, cudaStream_t s)
 {
-    if (precision == MLT_PREC_FP32) {
-        int rc = ensure_fp32_values(M, s);
-        if (rc) return rc;
-        return run_group<float>(M, plan, a, b, seed, mu_dev, ld_mu, err_flag, s);
-    }
-    return run_group<double>(M, plan, a, b, seed, mu_dev, ld_mu, err_flag, s);
+    // FP64: no FP32 steps; FP32: all steps FP32; mixed: FP32 for the first k steps
+    int ks = 0;
+    if (precision == MLT_PREC_FP32) ks = plan.K;
+    else if ((precision & 0xFF) == MLT_PREC_MIXED) ks = precision >> 8;
+    return run_group(M, plan, ks, a, b, seed, mu_dev, ld_mu, err_flag, s);
 }
 
 }  // namespace mlt

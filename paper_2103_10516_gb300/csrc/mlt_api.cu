@@ -254,7 +254,7 @@ static void free_matrix(mlt_matrix* M)
                      M->own_t_col, M->own_t_val, M->own_t_val32, M->plan_A.mem, M->plan_AT.mem};
     for (void* p : owned)
         if (p) cudaFree(p);
-    mlt::DevBuf* bufs[] = {&M->ws_v[0], &M->ws_v[1], &M->ws_w, &M->ws_part, &M->ws_dots,
+    mlt::DevBuf* bufs[] = {&M->ws_v[0], &M->ws_v[1], &M->ws_v2[0], &M->ws_v2[1], &M->ws_w, &M->ws_part, &M->ws_dots,
                            &M->ws_misc, &M->ws_out, &M->ws_y, &M->ws_y32, &M->ws_z, &M->ws_x,
                            &M->ws_tri, &M->ws_seg, &M->ws_upcol};
     for (auto* b : bufs) b->release();
@@ -557,8 +557,13 @@ int mlt_spectrum_bounds(mlt_matrix* m, int method, int steps, uint64_t seed, dou
     (void)steps;
     (void)seed;
     if (!m || !a || !b) return fail(MLT_EINVAL, "mlt_spectrum_bounds: null argument");
-    if (method != MLT_BOUNDS_GERSHGORIN) return fail(MLT_EINVAL, "mlt_spectrum_bounds: unknown method");
+    if (method != MLT_BOUNDS_GERSHGORIN && method != MLT_BOUNDS_LANCZOS)
+        return fail(MLT_EINVAL, "mlt_spectrum_bounds: unknown method");
     try {
+        if (method == MLT_BOUNDS_LANCZOS) {
+            if (steps < 2) return fail(MLT_EINVAL, "mlt_spectrum_bounds: Lanczos needs steps >= 2");
+            return lanczos_bounds(m, steps, seed, a, b, (cudaStream_t)0);
+        }
         return gershgorin_device(m, a, b, (cudaStream_t)0);
     } catch (...) {
         return fail(MLT_ENOMEM, "mlt_spectrum_bounds: exception");
@@ -585,7 +590,8 @@ int mlt_moments(mlt_matrix* m, double a, double b, uint64_t seed, int64_t probe_
         if (!degree || !mu) return fail(MLT_EINVAL, "mlt_moments: null degree or mu");
         if (!(a < b) || !std::isfinite(a) || !std::isfinite(b))
             return fail(MLT_EINVAL, "mlt_moments: need finite a < b");
-        if (precision != MLT_PREC_FP64 && precision != MLT_PREC_FP32)
+        if (precision != MLT_PREC_FP64 && precision != MLT_PREC_FP32 &&
+            !((precision & 0xFF) == MLT_PREC_MIXED && precision >= 0))
             return fail(MLT_EINVAL, "mlt_moments: unknown precision");
         if (flags & ~MLT_DIRECT) return fail(MLT_EINVAL, "mlt_moments: unknown flags");
         if (probe_offset < 0 || probe_offset + nprobes > (1LL << 32))

@@ -97,7 +97,7 @@ struct mlt_matrix {
     double tri_bound = 0.0;     // sum_(i,j) deg_i deg_j
     // scratch
     mlt::SpmmPlan plan_A, plan_AT;
-    mlt::DevBuf ws_v[2], ws_w, ws_part, ws_dots, ws_misc, ws_out, ws_y, ws_y32, ws_z, ws_x, ws_tri,
+    mlt::DevBuf ws_v[2], ws_v2[2], ws_w, ws_part, ws_dots, ws_misc, ws_out, ws_y, ws_y32, ws_z, ws_x, ws_tri,
         ws_seg, ws_upcol;
     int64_t dim() const { return (flags & MLT_GRAM) ? A.ncols : A.nrows; }
 };
@@ -123,6 +123,8 @@ int run_moments_group(mlt_matrix* M, int precision, const MomentPlan& plan, doub
 
 int ensure_fp32_values(mlt_matrix* M, cudaStream_t s);
 int ensure_spmm_plan(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, cudaStream_t s);
+int spmv_f64(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, const double* x, double* y, cudaStream_t s);
+int lanczos_bounds(mlt_matrix* M, int steps, uint64_t seed, double* lo, double* hi, cudaStream_t s);
 
 // ---- triangle kernels (tri_kernels.cu) ---------------------------------------
 int tri_prepare(mlt_matrix* M, cudaStream_t s);

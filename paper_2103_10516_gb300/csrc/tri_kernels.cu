@@ -546,10 +546,20 @@ __global__ void __launch_bounds__(kTriThreads) tri_pass2_kernel(
                         const int k = base + lane;
                         const int cj = k < b ? __ldg(up_col + k) : 0;
                         const int n = min(32, b - base);
-#pragma unroll 8
-                        for (int t = 0; t < n; ++t) {
-                            const int j = __shfl_sync(kFull, cj, t);
-                            acc_y(__ldg(y8 + (size_t)j * 32 + lane), j, y32, bslot, lane, s);
+                        for (int t0 = 0; t0 < n; t0 += 8) {
+                            // 8 gathers issued before any is used: the escape branch in
+                            // acc_y would otherwise keep one load in flight per warp
+                            // (lanes past n read row 0, whose line is harmless to load)
+                            int jj[8];
+                            uint32_t w[8];
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                jj[u] = __shfl_sync(kFull, cj, t0 + u);
+                                w[u] = __ldg(y8 + (size_t)jj[u] * 32 + lane);
+                            }
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if (t0 + u < n) acc_y(w[u], jj[u], y32, bslot, lane, s);
                         }
                     }
                     finish_pass2_row(row, own, s, y32, bslot, lane, x3);

@@ -24,7 +24,7 @@ MLT_GRAM, MLT_DEVICE_PTRS = 1, 2
 MLT_FN = {"log": 0, "sqrt": 1, "exp": 2, "inv": 3, "pow": 4, "cube": 5}
 MLT_PREC = {"fp64": 0, "fp32": 1}
 MLT_DIRECT = 1
-MLT_BOUNDS_GERSHGORIN = 0
+MLT_BOUNDS_GERSHGORIN, MLT_BOUNDS_LANCZOS = 0, 1
 MLT_MAX_LEVELS = 1024
 MLT_MAX_DEGREE = 4096
 MLT_MODE = {"budget": 0, "variance": 1}
@@ -451,3 +451,8 @@ def mlt_learned_estimate(matrix, surrogate, P):
     return {"estimate": r.estimate, "stderr": r.std_error, "levels": list(r.levels[:L]),
             "m": list(r.m[:L]), "level_mean": list(r.level_mean[:L]),
             "level_var": list(r.level_var[:L]), "probes": r.probes, "matvecs": r.matvecs}
+
+
+def mixed_at(k):
+    """Precision code: the first k recurrence steps in FP32, the rest in FP64."""
+    return 2 | (int(k) << 8)

@@ -4,9 +4,12 @@ given the same BF16-rounded weights and inputs, and the three-level estimator
 against the oracle's plain multilevel estimator when the network is zero.
 
 BF16 tolerance: inputs and weights are rounded before both sides see them, so
-what remains is the BF16 rounding (unit 2^-9) of the hidden activations and
-back-propagated gradients fed to the tensor cores; through two layers of 128
-terms that stays below 2e-2 in relative Frobenius norm per parameter tensor."""
+what remains is the BF16 rounding (unit 2^-9) of the values fed to the tensor
+cores: H1 on the forward path (one rounding before the output), and dH2 then
+dH1 on the backward path (two roundings before dW1).  Gradients are sums over
+the batch of terms of both signs, so their relative error exceeds the
+per-element 2^-9 by the cancellation; the bound used is 2e-2 for the forward
+pass and 5e-2 in relative Frobenius norm per gradient tensor."""
 import numpy as np
 import pytest
 
@@ -14,6 +17,7 @@ from paper_2103_10516_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 TOL_BF16 = 2e-2
+TOL_GRAD = 5e-2
 
 
 @pytest.fixture(scope="module")
@@ -70,8 +74,8 @@ def test_gradient_matches_oracle(L, O, n):
     assert abs(loss - rl) <= TOL_BF16 * rl
     G = L.unpack_params(g)
     for k in ("W1", "b1", "W2", "b2", "w3"):
-        assert _rel(G[k], rg[k]) < TOL_BF16, k
-    assert abs(G["b3"] - rg["b3"]) <= TOL_BF16 * (abs(rg["b3"]) + 1e-3)
+        assert _rel(G[k], rg[k]) < TOL_GRAD, k
+    assert abs(G["b3"] - rg["b3"]) <= TOL_GRAD * (abs(rg["b3"]) + 1e-3)
 
 
 def test_params_roundtrip_and_training_lowers_loss(L, O):

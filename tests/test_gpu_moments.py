@@ -194,3 +194,38 @@ def test_reproducible_bits(L):
         r1 = M.moments(a, b, 1, 0, [40] * 70)
         r2 = M.moments(a, b, 1, 0, [40] * 70)
     assert np.array_equal(r1, r2)
+
+
+@pytest.mark.parametrize("make,gram,sc", [
+    (lambda: synth.grid_laplacian_2d(30, shift=0.1), False, 1.0),
+    (lambda: synth.random_symmetric(400, 0.02, seed=3), False, 1.0),
+    (lambda: synth.rmat_adjacency(11, 8, seed=2), False, 0.1),
+    (lambda: synth.sparse_gaussian(600, 200, 0.03, seed=1), True, 1.0)])
+def test_lanczos_interval_contains_spectrum(L, make, gram, sc):
+    m = make()
+    A = m.to_dense() * sc
+    if gram:
+        A = A.T @ A
+    lam = np.linalg.eigvalsh(A)
+    with L.Matrix(m, gram=gram, scale=sc) as M:
+        a, b = L.mlt_spectrum_bounds(M.handle, L.MLT_BOUNDS_LANCZOS, 60, 1)
+        ga, gb = M.bounds()
+    assert a <= lam[0] and b >= lam[-1]
+    # far tighter at the top than the Gershgorin bound
+    assert b <= lam[-1] + 0.05 * abs(lam[-1]) + 1e-9
+    assert b <= gb * (1 + 1e-12)
+
+
+def test_mixed_precision_switch(L, O):
+    # FP32 for the first 16 steps (moments up to degree 32), FP64 after
+    m = synth.grid_laplacian_2d(64, shift=0.1)
+    deg = _c1_degrees()
+    with L.Matrix(m) as M:
+        f32 = M.moments(0.1, 8.1, 0, 0, deg, precision="fp32")
+        mix = M.moments(0.1, 8.1, 0, 0, deg, precision=L.mixed_at(16))
+    ref = O.moments(m, 0.1, 8.1, 0, 0, deg)
+    assert np.array_equal(mix[:, :33], f32[:, :33])      # same FP32 steps, same bits
+    assert np.max(np.abs(mix - ref)) <= 64 * 2.0 ** -24 * m.nrows
+    # past the switch the drift no longer grows as in the all-FP32 run
+    hi = slice(100, 129)
+    assert np.max(np.abs(mix[:, hi] - ref[:, hi])) <= np.max(np.abs(f32[:, hi] - ref[:, hi])) + 1e-9
