@@ -164,6 +164,40 @@ int mlt_moments(mlt_matrix* m, double a, double b, uint64_t seed,
                 int precision, unsigned flags, double* mu, int64_t ld_mu,
                 void* stream);
 
+/*
+ * Many moment computations (each as one mlt_moments call would do it) run as
+ * a single CUDA-graph launch, one graph branch per job, so that small
+ * matrices with ragged probe blocks share the GPU instead of queueing launch
+ * after launch.  Every job must use its own matrix handle.  All device memory
+ * is reserved and all inputs are on the device before the graph is captured;
+ * the call returns when every job's results are in its mu.  group_width is the
+ * number of probes per group (0: the handle's, see mlt_autotune).  Errors as
+ * mlt_moments, plus MLT_EINVAL for a repeated handle.
+ */
+typedef struct {
+    mlt_matrix* matrix;
+    double a, b;
+    uint64_t seed;
+    int64_t probe_offset;
+    int64_t nprobes;
+    const int32_t* degree;   /* host int32[nprobes]                       */
+    double* mu;              /* host or device double[nprobes * ld_mu]    */
+    int64_t ld_mu;
+    int group_width;
+} mlt_moments_job;
+
+int mlt_moments_batched(const mlt_moments_job* jobs, int njobs, int precision, unsigned flags,
+                        void* stream);
+
+/*
+ * Choose the probe-group width (probes sharing one pass over the matrix) for
+ * this handle: each width in {8, 16, 32, 64, 128} is timed on a short trial
+ * (two groups of that width, trial_steps recurrence steps, CUDA events) and
+ * the one with the least time per probe-matvec is kept on the handle for later
+ * mlt_moments calls.  *best (may be NULL) receives it.
+ */
+int mlt_autotune(mlt_matrix* m, int precision, int trial_steps, int* best, void* stream);
+
 typedef struct {
     int fn;                          /* MLT_FN_*                                  */
     double fn_p;                     /* exponent for MLT_FN_POW                   */
@@ -294,7 +328,11 @@ typedef struct {
 /*
  * Train s on n_train probes (ids train_offset ..): features (mu_0..mu_15)/d,
  * target P_l1/d with the Chebyshev coefficients of f (Section 2.2).  The
- * moments come from mlt_moments at degree l1.
+ * moments come from mlt_moments at degree l1.  Features and target are
+ * standardised with their training mean and standard deviation (kept in s),
+ * so the network models the probe-to-probe fluctuation, which is far below
+ * the mean and would otherwise be lost to BF16 rounding; mlt_learned_estimate
+ * then uses d (mean_t + std_t S(x)) as the network's estimate of P_l1.
  */
 int mlt_learned_train(mlt_matrix* m, mlt_surrogate* s, const mlt_learned_params* p,
                       int64_t n_train, int64_t train_offset, int epochs, int64_t batch, double lr,

@@ -522,7 +522,7 @@ __global__ void widen_kernel(const float* __restrict__ in, double* __restrict__ 
 // [ks, K) in FP64; ks = 0 is all FP64, ks >= K all FP32.  At the switch the
 // two live vectors V_k, V_{k-1} are widened to FP64 and the recurrence goes on.
 int run_group(mlt_matrix* M, const MomentPlan& plan, int ks, double a, double b, uint64_t seed,
-              double* mu_dev, int64_t ld_mu, int* err_flag, cudaStream_t s)
+              double* mu_dev, int64_t ld_mu, int* err_flag, cudaStream_t s, bool alloc_only)
 {
     GroupCtx g;
     g.gram = (M->flags & MLT_GRAM) != 0;
@@ -568,6 +568,7 @@ int run_group(mlt_matrix* M, const MomentPlan& plan, int ks, double a, double b,
     const double sc = g.gram ? M->scale * M->scale : M->scale;
     g.alpha = 2.0 / (b - a) * sc;
     g.beta = -(a + b) / (b - a);
+    if (alloc_only) return MLT_OK;
     {
         const int nb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, 16LL * M->num_sms);
         ProfScope ps("init_probes", s);
@@ -723,13 +724,14 @@ int ensure_fp32_values(mlt_matrix* M, cudaStream_t s)
 }
 
 int run_moments_group(mlt_matrix* M, int precision, const MomentPlan& plan, double a, double b,
-                      uint64_t seed, double* mu_dev, int64_t ld_mu, int* err_flag, cudaStream_t s)
+                      uint64_t seed, double* mu_dev, int64_t ld_mu, int* err_flag, cudaStream_t s,
+                      bool alloc_only)
 {
     // FP64: no FP32 steps; FP32: all steps FP32; mixed: FP32 for the first k steps
     int ks = 0;
     if (precision == MLT_PREC_FP32) ks = plan.K;
     else if ((precision & 0xFF) == MLT_PREC_MIXED) ks = precision >> 8;
-    return run_group(M, plan, ks, a, b, seed, mu_dev, ld_mu, err_flag, s);
+    return run_group(M, plan, ks, a, b, seed, mu_dev, ld_mu, err_flag, s, alloc_only);
 }
 
 }  // namespace mlt

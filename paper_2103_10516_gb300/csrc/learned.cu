@@ -16,24 +16,37 @@ struct mlt_surrogate {
     int device = 0;
     mlt::MlpDev D;
     void* mem = nullptr;
-    mlt::DevBuf ws_x, ws_t, ws_y, ws_part, ws_mu, ws_c, ws_loss;
+    mlt::DevBuf ws_x, ws_t, ws_y, ws_part, ws_mu, ws_c, ws_loss, ws_norm;
     int64_t step = 0;
+    // standardisation of the learned level (set by mlt_learned_train): feature k
+    // enters as (mu_k/d - mean_k)/std_k, the network predicts (P_l1/d - tmean)/tstd
+    bool has_norm = false;
+    double norm[2 * mlt::MLP_IN + 2] = {};
 };
 
 namespace mlt {
 namespace {
 
-// X[i][k] = mu[i][k] / d (k < 16); T[i] = sum_{j <= l1} c_j mu[i][j] / d.
+// X[i][k] = mu[i][k] / d (k < 16); T[i] = sum_{j <= l1} c_j mu[i][j] / d; with
+// `norm` (means, then standard deviations of the 16 features, then of the
+// target) both are standardised, in double precision, before the rounding.
 __global__ void features_kernel(const double* __restrict__ mu, int64_t ld, int64_t n, double inv_d,
-                                const double* __restrict__ c, int l1, float* __restrict__ X, float* __restrict__ T)
+                                const double* __restrict__ c, int l1, const double* __restrict__ norm,
+                                float* __restrict__ X, float* __restrict__ T)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double* row = mu + i * ld;
-        for (int k = 0; k < MLP_IN; ++k) X[i * MLP_IN + k] = (float)(row[k] * inv_d);
+        for (int k = 0; k < MLP_IN; ++k) {
+            double v = row[k] * inv_d;
+            if (norm) v = (v - norm[k]) / norm[MLP_IN + k];
+            X[i * MLP_IN + k] = (float)v;
+        }
         if (T) {
             double s = 0.0;
             for (int j = 0; j <= l1; ++j) s += c[j] * row[j];
-            T[i] = (float)(s * inv_d);
+            double v = s * inv_d;
+            if (norm) v = (v - norm[2 * MLP_IN]) / norm[2 * MLP_IN + 1];
+            T[i] = (float)v;
         }
     }
 }
@@ -150,7 +163,7 @@ int mlt_surrogate_destroy(mlt_surrogate* S)
 {
     if (!S) return MLT_OK;
     cudaDeviceSynchronize();
-    DevBuf* bufs[] = {&S->ws_x, &S->ws_t, &S->ws_y, &S->ws_part, &S->ws_mu, &S->ws_c, &S->ws_loss};
+    DevBuf* bufs[] = {&S->ws_x, &S->ws_t, &S->ws_y, &S->ws_part, &S->ws_mu, &S->ws_c, &S->ws_loss, &S->ws_norm};
     for (auto* b : bufs) b->release();
     if (S->mem) cudaFree(S->mem);
     delete S;
@@ -292,13 +305,53 @@ int mlt_learned_train(mlt_matrix* m, mlt_surrogate* S, const mlt_learned_params*
         if (rc) return rc;
         MLT_CUDA_TRY(cudaMemcpyAsync(S->ws_c.p, c.data(), (P->n + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
         const int64_t d = m->dim();
+        // standardisation from the training moments (host, double precision)
+        {
+            std::vector<double> hm((size_t)n_train * ld);
+            MLT_CUDA_TRY(cudaMemcpyAsync(hm.data(), S->ws_mu.p, hm.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+            MLT_CUDA_TRY(cudaStreamSynchronize(s));
+            const int nf = MLP_IN + 1;
+            std::vector<double> sum(nf, 0.0), sq(nf, 0.0);
+            for (int64_t i = 0; i < n_train; ++i) {
+                const double* row = &hm[(size_t)i * ld];
+                double t = 0.0;
+                for (int j = 0; j <= P->l1; ++j) t += c[j] * row[j];
+                for (int k = 0; k < nf; ++k) {
+                    const double v = (k < MLP_IN ? row[k] : t) / (double)d;
+                    sum[k] += v;
+                }
+            }
+            for (int k = 0; k < nf; ++k) sum[k] /= (double)n_train;
+            for (int64_t i = 0; i < n_train; ++i) {
+                const double* row = &hm[(size_t)i * ld];
+                double t = 0.0;
+                for (int j = 0; j <= P->l1; ++j) t += c[j] * row[j];
+                for (int k = 0; k < nf; ++k) {
+                    const double v = (k < MLP_IN ? row[k] : t) / (double)d - sum[k];
+                    sq[k] += v * v;
+                }
+            }
+            for (int k = 0; k < nf; ++k) {
+                const double sd = n_train > 1 ? std::sqrt(sq[k] / (double)(n_train - 1)) : 0.0;
+                const double safe = sd > 1e-300 ? sd : 1.0;
+                if (k < MLP_IN) {
+                    S->norm[k] = sum[k];
+                    S->norm[MLP_IN + k] = safe;
+                } else {
+                    S->norm[2 * MLP_IN] = sum[k];
+                    S->norm[2 * MLP_IN + 1] = safe;
+                }
+            }
+            S->has_norm = true;
+            if ((rc = S->ws_norm.ensure(sizeof(S->norm), s))) return rc;
+            MLT_CUDA_TRY(cudaMemcpyAsync(S->ws_norm.p, S->norm, sizeof(S->norm), cudaMemcpyHostToDevice, s));
+        }
         {
             ProfScope ps("learned_features", s);
             features_kernel<<<(unsigned)std::min<int64_t>((n_train + 255) / 256, 4096), 256, 0, s>>>(
                 S->ws_mu.as<double>(), ld, n_train, 1.0 / (double)d, S->ws_c.as<double>(), P->l1,
-                S->ws_x.as<float>(), S->ws_t.as<float>());
+                S->ws_norm.as<double>(), S->ws_x.as<float>(), S->ws_t.as<float>());
         }
-        MLT_CUDA_TRY(cudaGetLastError());
         return mlt_surrogate_train(S, S->ws_x.as<float>(), S->ws_t.as<float>(), n_train, epochs, batch, lr,
                                    final_loss, P->stream);
     } catch (...) {
@@ -336,7 +389,8 @@ int mlt_learned_estimate(mlt_matrix* m, mlt_surrogate* S, const mlt_learned_para
         {
             ProfScope ps("learned_features", s);
             features_kernel<<<(unsigned)std::min<int64_t>((nn + 255) / 256, 4096), 256, 0, s>>>(
-                S->ws_mu.as<double>(), ld, nn, 1.0 / (double)d, nullptr, 0, S->ws_x.as<float>(), nullptr);
+                S->ws_mu.as<double>(), ld, nn, 1.0 / (double)d, nullptr, 0,
+                S->has_norm ? S->ws_norm.as<double>() : nullptr, S->ws_x.as<float>(), nullptr);
         }
         MLT_CUDA_TRY(cudaGetLastError());
         if ((rc = ensure_part(S, 128, s))) return rc;
@@ -353,13 +407,18 @@ int mlt_learned_estimate(mlt_matrix* m, mlt_surrogate* S, const mlt_learned_para
             for (int j = lo + 1; j <= hi; ++j) acc += c[j] * row[j];
             return acc;
         };
+        // the network's estimate of P_l1: d (tmean + tstd y), or d y without standardisation
+        auto net = [&](int64_t i) {
+            const double v = S->has_norm ? S->norm[2 * MLP_IN] + S->norm[2 * MLP_IN + 1] * (double)y[i] : (double)y[i];
+            return (double)d * v;
+        };
         std::vector<std::vector<double>> lv(3);
         for (int64_t i = 0; i < total; ++i) {
             const double* row = &mu[(size_t)i * ld];
             if (i < P->m_net) {
-                lv[0].push_back((double)d * (double)y[i]);
+                lv[0].push_back(net(i));
             } else if (i < nn) {
-                lv[1].push_back(band(row, -1, P->l1) - (double)d * (double)y[i]);
+                lv[1].push_back(band(row, -1, P->l1) - net(i));
             } else {
                 lv[2].push_back(band(row, P->l1, n));
             }

@@ -62,9 +62,13 @@ cudaEvent_t take_event()
 }
 }  // namespace
 
+static thread_local int g_prof_paused = 0;
+ProfPause::ProfPause() { ++g_prof_paused; }
+ProfPause::~ProfPause() { --g_prof_paused; }
+
 ProfScope::ProfScope(const char* name, cudaStream_t stream) : idx(-1), s(stream)
 {
-    if (!g_prof_on) return;
+    if (!g_prof_on || g_prof_paused) return;
     std::lock_guard<std::mutex> lk(g_prof_mu);
     ProfRec r{name, take_event(), take_event()};
     if (!r.e0 || !r.e1) return;
@@ -278,6 +282,140 @@ static void host_transpose(int64_t nrows, int64_t ncols, const int64_t* rp, cons
             tci[q] = (int32_t)i;
             if (v) tv[q] = v[k];
         }
+}
+
+
+// ---- moment jobs: prepare (validation, probe order, groups, device metadata,
+// every allocation), enqueue (kernels only: no host sync, no allocation, so a
+// job can be captured in a graph), finish (results to the caller, checks) ----
+
+int prepare_moment_job(mlt_matrix* m, double a, double b, uint64_t seed, int64_t probe_offset, int64_t nprobes,
+                       const int32_t* degree, int precision, unsigned flags, double* mu, int64_t ld_mu,
+                       int group_width, MomentJob& J, cudaStream_t s)
+{
+    if (!m) return fail(MLT_EINVAL, "mlt_moments: null handle");
+    if (nprobes < 0) return fail(MLT_EINVAL, "mlt_moments: negative probe count");
+    if (nprobes > 0 && (!degree || !mu)) return fail(MLT_EINVAL, "mlt_moments: null degree or mu");
+    if (!(a < b) || !std::isfinite(a) || !std::isfinite(b))
+        return fail(MLT_EINVAL, "mlt_moments: need finite a < b");
+    if (precision != MLT_PREC_FP64 && precision != MLT_PREC_FP32 &&
+        !((precision & 0xFF) == MLT_PREC_MIXED && precision >= 0))
+        return fail(MLT_EINVAL, "mlt_moments: unknown precision");
+    if (flags & ~MLT_DIRECT) return fail(MLT_EINVAL, "mlt_moments: unknown flags");
+    if (probe_offset < 0 || probe_offset + nprobes > (1LL << 32))
+        return fail(MLT_EINVAL, "mlt_moments: probe ids must lie in [0, 2^32)");
+    if (group_width < 0) return fail(MLT_EINVAL, "mlt_moments: negative group width");
+    int maxdeg = 0;
+    for (int64_t p = 0; p < nprobes; ++p) {
+        if (degree[p] < 0 || degree[p] > MLT_MAX_DEGREE) return fail(MLT_EINVAL, "mlt_moments: degree out of range");
+        maxdeg = std::max(maxdeg, (int)degree[p]);
+    }
+    if (nprobes > 0 && ld_mu < maxdeg + 1) return fail(MLT_EINVAL, "mlt_moments: ld_mu below max degree + 1");
+    J = MomentJob();
+    J.m = m;
+    J.a = a;
+    J.b = b;
+    J.seed = seed;
+    J.precision = precision;
+    J.direct = (flags & MLT_DIRECT) ? 1 : 0;
+    J.mu_user = mu;
+    J.ld_mu = ld_mu;
+    J.nprobes = nprobes;
+    if (nprobes == 0) return MLT_OK;
+    const int64_t d = m->dim();
+    int rc;
+    J.out_dev = is_device_ptr(mu);
+    J.out_bytes = (size_t)nprobes * ld_mu * sizeof(double);
+    J.mu_dev = mu;
+    if (!J.out_dev) {
+        if ((rc = m->ws_out.ensure(J.out_bytes, s))) return rc;
+        J.mu_dev = m->ws_out.as<double>();
+    }
+    // probe order: by degree, descending (stable), so live probes are a prefix
+    std::vector<int64_t> order(nprobes);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) { return degree[x] > degree[y]; });
+    // group width: the caller's, else m->group_width (autotuned), else from memory
+    int64_t gmax = group_width > 0 ? group_width : m->group_width;
+    if (gmax <= 0) {
+        const size_t sv = precision == MLT_PREC_FP32 ? sizeof(float) : sizeof(double);
+        const bool gram = (m->flags & MLT_GRAM) != 0;
+        const size_t per_probe = sv * ((size_t)2 * std::max<int64_t>(d, 1) + (gram ? (size_t)m->A.nrows : 0));
+        size_t free_b = 0, total_b = 0;
+        MLT_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+        const size_t budget = std::min<size_t>((size_t)16 << 30, free_b / 3);
+        gmax = (int64_t)std::max<size_t>(8, budget / per_probe);
+    }
+    gmax = std::min<int64_t>(gmax, 1024);
+    const int64_t ngroups = (nprobes + gmax - 1) / gmax;
+    const int64_t gsz = (nprobes + ngroups - 1) / ngroups;
+    // device metadata for every group at once: error flag, then ids, rows, degrees
+    const size_t meta = 256 + (size_t)nprobes * (2 * sizeof(int64_t) + sizeof(int32_t)) + 256;
+    if ((rc = m->ws_misc.ensure(meta, s))) return rc;
+    char* base = m->ws_misc.as<char>();
+    J.err = reinterpret_cast<int*>(base);
+    int64_t* ids_dev = reinterpret_cast<int64_t*>(base + 256);
+    int64_t* row_dev = ids_dev + nprobes;
+    int32_t* deg_dev = reinterpret_cast<int32_t*>(row_dev + nprobes);
+    std::vector<int64_t> hid(nprobes), hrow(nprobes);
+    std::vector<int32_t> hdeg(nprobes);
+    for (int64_t c = 0; c < nprobes; ++c) {
+        hid[c] = probe_offset + order[c];
+        hrow[c] = order[c];
+        hdeg[c] = degree[order[c]];
+    }
+    MLT_CUDA_TRY(cudaMemsetAsync(J.err, 0, sizeof(int), s));
+    MLT_CUDA_TRY(cudaMemcpyAsync(ids_dev, hid.data(), nprobes * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    MLT_CUDA_TRY(cudaMemcpyAsync(row_dev, hrow.data(), nprobes * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    MLT_CUDA_TRY(cudaMemcpyAsync(deg_dev, hdeg.data(), nprobes * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    for (int64_t g0 = 0; g0 < nprobes; g0 += gsz) {
+        const int B = (int)std::min<int64_t>(gsz, nprobes - g0);
+        int K = 0;
+        for (int c = 0; c < B; ++c) K = std::max(K, J.direct ? hdeg[g0 + c] : (hdeg[g0 + c] + 1) / 2);
+        std::vector<int> act(std::max(K, 1));
+        for (int k = 0; k < K; ++k) {
+            int n = 0;
+            while (n < B && (J.direct ? hdeg[g0 + n] : (hdeg[g0 + n] + 1) / 2) > k) ++n;
+            act[k] = n;
+        }
+        J.acts.push_back(std::move(act));
+        MomentPlan plan;
+        plan.dim = d;
+        plan.B = B;
+        plan.ldv = (B + 7) & ~7;
+        plan.K = K;
+        plan.act = nullptr;
+        plan.ids_dev = ids_dev + g0;
+        plan.deg_dev = deg_dev + g0;
+        plan.row_dev = row_dev + g0;
+        plan.direct = J.direct;
+        J.groups.push_back(plan);
+    }
+    for (size_t i = 0; i < J.groups.size(); ++i) J.groups[i].act = J.acts[i].data();
+    // every device buffer the kernels will use, sized now
+    for (auto& plan : J.groups)
+        if ((rc = run_moments_group(m, precision, plan, a, b, seed, J.mu_dev, ld_mu, J.err, s, true))) return rc;
+    return MLT_OK;
+}
+
+int enqueue_moment_job(MomentJob& J, cudaStream_t s)
+{
+    for (auto& plan : J.groups) {
+        int rc = run_moments_group(J.m, J.precision, plan, J.a, J.b, J.seed, J.mu_dev, J.ld_mu, J.err, s, false);
+        if (rc) return rc;
+    }
+    return MLT_OK;
+}
+
+int finish_moment_job(MomentJob& J, cudaStream_t s)
+{
+    if (J.nprobes == 0) return MLT_OK;
+    if (!J.out_dev) MLT_CUDA_TRY(cudaMemcpyAsync(J.mu_user, J.mu_dev, J.out_bytes, cudaMemcpyDeviceToHost, s));
+    int herr = 0;
+    MLT_CUDA_TRY(cudaMemcpyAsync(&herr, J.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MLT_CUDA_TRY(cudaStreamSynchronize(s));
+    if (herr) return fail(MLT_ERANGE, "mlt_moments: |mu_j| > d; the spectrum is not inside [a, b]");
+    return MLT_OK;
 }
 
 }  // namespace mlt
@@ -584,109 +722,138 @@ int mlt_moments(mlt_matrix* m, double a, double b, uint64_t seed, int64_t probe_
                 int64_t ld_mu, void* stream)
 {
     try {
-        if (!m) return fail(MLT_EINVAL, "mlt_moments: null handle");
-        if (nprobes < 0) return fail(MLT_EINVAL, "mlt_moments: negative probe count");
-        if (nprobes == 0) return MLT_OK;
-        if (!degree || !mu) return fail(MLT_EINVAL, "mlt_moments: null degree or mu");
-        if (!(a < b) || !std::isfinite(a) || !std::isfinite(b))
-            return fail(MLT_EINVAL, "mlt_moments: need finite a < b");
-        if (precision != MLT_PREC_FP64 && precision != MLT_PREC_FP32 &&
-            !((precision & 0xFF) == MLT_PREC_MIXED && precision >= 0))
-            return fail(MLT_EINVAL, "mlt_moments: unknown precision");
-        if (flags & ~MLT_DIRECT) return fail(MLT_EINVAL, "mlt_moments: unknown flags");
-        if (probe_offset < 0 || probe_offset + nprobes > (1LL << 32))
-            return fail(MLT_EINVAL, "mlt_moments: probe ids must lie in [0, 2^32)");
-        int maxdeg = 0;
-        for (int64_t p = 0; p < nprobes; ++p) {
-            if (degree[p] < 0 || degree[p] > MLT_MAX_DEGREE)
-                return fail(MLT_EINVAL, "mlt_moments: degree out of range");
-            maxdeg = std::max(maxdeg, (int)degree[p]);
-        }
-        if (ld_mu < maxdeg + 1) return fail(MLT_EINVAL, "mlt_moments: ld_mu below max degree + 1");
-        const int direct = (flags & MLT_DIRECT) ? 1 : 0;
+        if (nprobes == 0 && m) return MLT_OK;
         cudaStream_t s = (cudaStream_t)stream;
-        const int64_t d = m->dim();
-        int rc;
-
-        // output: caller's device array, or a device staging copy
-        const bool out_dev = is_device_ptr(mu);
-        double* mu_dev = mu;
-        const size_t out_bytes = (size_t)nprobes * ld_mu * sizeof(double);
-        if (!out_dev) {
-            if ((rc = m->ws_out.ensure(out_bytes, s))) return rc;
-            mu_dev = m->ws_out.as<double>();
-        }
-        // the probe order: by degree, descending (stable), so live probes are a prefix
-        std::vector<int64_t> order(nprobes);
-        std::iota(order.begin(), order.end(), 0);
-        std::stable_sort(order.begin(), order.end(),
-                         [&](int64_t x, int64_t y) { return degree[x] > degree[y]; });
-
-        // group size from the memory the V buffers may take
-        const size_t sv = precision == MLT_PREC_FP32 ? sizeof(float) : sizeof(double);
-        const bool gram = (m->flags & MLT_GRAM) != 0;
-        const size_t per_probe = sv * ((size_t)2 * std::max<int64_t>(d, 1) + (gram ? (size_t)m->A.nrows : 0));
-        size_t free_b = 0, total_b = 0;
-        MLT_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-        const size_t budget = std::min<size_t>((size_t)16 << 30, free_b / 3);
-        int64_t gmax = (int64_t)std::max<size_t>(8, budget / per_probe);
-        gmax = std::min<int64_t>(gmax, 1024);
-        const int64_t ngroups = (nprobes + gmax - 1) / gmax;
-        const int64_t gsz = (nprobes + ngroups - 1) / ngroups;
-
-        // device scratch: error flag + per-group ids/degrees/rows
-        const size_t meta = 256 + (size_t)gsz * (2 * sizeof(int64_t) + sizeof(int32_t)) + 256;
-        if ((rc = m->ws_misc.ensure(meta, s))) return rc;
-        char* base = m->ws_misc.as<char>();
-        int* err = reinterpret_cast<int*>(base);
-        int64_t* ids_dev = reinterpret_cast<int64_t*>(base + 256);
-        int64_t* row_dev = ids_dev + gsz;
-        int32_t* deg_dev = reinterpret_cast<int32_t*>(row_dev + gsz);
-        MLT_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-        std::vector<int64_t> hid(gsz), hrow(gsz);
-        std::vector<int32_t> hdeg(gsz);
-        for (int64_t g0 = 0; g0 < nprobes; g0 += gsz) {
-            const int B = (int)std::min<int64_t>(gsz, nprobes - g0);
-            int K = 0;
-            for (int c = 0; c < B; ++c) {
-                const int64_t p = order[g0 + c];
-                hid[c] = probe_offset + p;
-                hrow[c] = p;
-                hdeg[c] = degree[p];
-                K = std::max(K, direct ? degree[p] : (degree[p] + 1) / 2);
-            }
-            std::vector<int> act(std::max(K, 1));
-            for (int k = 0; k < K; ++k) {
-                int n = 0;
-                while (n < B && (direct ? hdeg[n] : (hdeg[n] + 1) / 2) > k) ++n;
-                act[k] = n;
-            }
-            MLT_CUDA_TRY(cudaMemcpyAsync(ids_dev, hid.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-            MLT_CUDA_TRY(cudaMemcpyAsync(row_dev, hrow.data(), B * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-            MLT_CUDA_TRY(cudaMemcpyAsync(deg_dev, hdeg.data(), B * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-            MomentPlan plan;
-            plan.dim = d;
-            plan.B = B;
-            plan.ldv = (B + 7) & ~7;
-            plan.K = K;
-            plan.act = act.data();
-            plan.ids_dev = ids_dev;
-            plan.deg_dev = deg_dev;
-            plan.row_dev = row_dev;
-            plan.direct = direct;
-            if ((rc = run_moments_group(m, precision, plan, a, b, seed, mu_dev, ld_mu, err, s))) return rc;
-            if (g0 + gsz < nprobes) MLT_CUDA_TRY(cudaStreamSynchronize(s));   // host arrays reused
-        }
-        if (!out_dev) MLT_CUDA_TRY(cudaMemcpyAsync(mu, mu_dev, out_bytes, cudaMemcpyDeviceToHost, s));
-        int herr = 0;
-        MLT_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
-        MLT_CUDA_TRY(cudaStreamSynchronize(s));
-        if (herr) return fail(MLT_ERANGE, "mlt_moments: |mu_j| > d; the spectrum is not inside [a, b]");
-        return MLT_OK;
+        MomentJob J;
+        int rc = prepare_moment_job(m, a, b, seed, probe_offset, nprobes, degree, precision, flags, mu, ld_mu,
+                                    0, J, s);
+        if (rc) return rc;
+        if ((rc = enqueue_moment_job(J, s))) return rc;
+        return finish_moment_job(J, s);
     } catch (const std::bad_alloc&) {
         return fail(MLT_ENOMEM, "mlt_moments: host allocation failed");
     } catch (...) {
         return fail(MLT_ECUDA, "mlt_moments: exception");
+    }
+}
+
+int mlt_moments_batched(const mlt_moments_job* jobs, int njobs, int precision, unsigned flags, void* stream)
+{
+    try {
+        if (njobs < 0 || (njobs > 0 && !jobs)) return fail(MLT_EINVAL, "mlt_moments_batched: bad job list");
+        if (njobs == 0) return MLT_OK;
+        for (int i = 0; i < njobs; ++i)
+            for (int k = 0; k < i; ++k)
+                if (jobs[i].matrix == jobs[k].matrix)
+                    return fail(MLT_EINVAL, "mlt_moments_batched: each job needs its own matrix handle");
+        cudaStream_t s = (cudaStream_t)stream;
+        std::vector<MomentJob> J(njobs);
+        int rc;
+        for (int i = 0; i < njobs; ++i) {
+            const mlt_moments_job& q = jobs[i];
+            if ((rc = prepare_moment_job(q.matrix, q.a, q.b, q.seed, q.probe_offset, q.nprobes, q.degree, precision,
+                                         flags, q.mu, q.ld_mu, q.group_width, J[i], s)))
+                return rc;
+        }
+        MLT_CUDA_TRY(cudaStreamSynchronize(s));
+        // one graph: a branch per job on its own stream, forked from and joined to cs
+        cudaStream_t cs = nullptr;
+        MLT_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        std::vector<cudaStream_t> br(std::min(njobs, 64), nullptr);
+        std::vector<cudaEvent_t> ev(njobs + 1, nullptr);
+        auto cleanup = [&]() {
+            for (auto& x : br) if (x) cudaStreamDestroy(x);
+            for (auto& e : ev) if (e) cudaEventDestroy(e);
+            if (cs) cudaStreamDestroy(cs);
+        };
+        for (auto& x : br)
+            if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) { cleanup(); return cuda_fail(cudaGetLastError(), "stream"); }
+        for (auto& e : ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) { cleanup(); return cuda_fail(cudaGetLastError(), "event"); }
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        ProfPause pause;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[njobs], cs);
+        for (int i = 0; i < njobs && e == cudaSuccess; ++i) {
+            cudaStream_t si = br[i % br.size()];
+            e = cudaStreamWaitEvent(si, ev[njobs], 0);
+            if (e == cudaSuccess && (rc = enqueue_moment_job(J[i], si))) e = cudaErrorUnknown;
+            if (e == cudaSuccess) e = cudaEventRecord(ev[i], si);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[i], 0);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e == cudaSuccess) {
+            ProfScope ps("moments_graph", s);
+            e = cudaGraphLaunch(exec, s);
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cleanup();
+        if (e != cudaSuccess) return rc ? rc : cuda_fail(e, "mlt_moments_batched graph");
+        for (int i = 0; i < njobs; ++i)
+            if ((rc = finish_moment_job(J[i], s))) return rc;
+        return MLT_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(MLT_ENOMEM, "mlt_moments_batched: host allocation failed");
+    } catch (...) {
+        return fail(MLT_ECUDA, "mlt_moments_batched: exception");
+    }
+}
+
+int mlt_autotune(mlt_matrix* m, int precision, int trial_steps, int* best, void* stream)
+{
+    try {
+        if (!m) return fail(MLT_EINVAL, "mlt_autotune: null handle");
+        if (trial_steps < 1 || trial_steps > MLT_MAX_DEGREE / 2) return fail(MLT_EINVAL, "mlt_autotune: bad trial length");
+        cudaStream_t s = (cudaStream_t)stream;
+        double a = 0.0, b = 0.0;
+        int rc = gershgorin_device(m, &a, &b, s);
+        if (rc) return rc;
+        if (!(a < b)) b = a + 1.0;
+        const int widths[] = {8, 16, 32, 64, 128};
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        MLT_CUDA_TRY(cudaEventCreate(&e0));
+        MLT_CUDA_TRY(cudaEventCreate(&e1));
+        int bestw = 0;
+        double bestt = 0.0;
+        const int deg = 2 * trial_steps;
+        const int saved = m->group_width;
+        for (int w : widths) {
+            const int np = 2 * w;
+            std::vector<int32_t> dg(np, deg);
+            // output to a device scratch buffer; nothing is copied back
+            if ((rc = m->ws_out.ensure((size_t)np * (deg + 1) * sizeof(double), s))) break;
+            MomentJob J;
+            rc = prepare_moment_job(m, a, b, 0, 0, np, dg.data(), precision, 0, m->ws_out.as<double>(), deg + 1,
+                                    w, J, s);
+            if (rc) break;
+            if ((rc = enqueue_moment_job(J, s))) break;            // warm-up
+            MLT_CUDA_TRY(cudaEventRecord(e0, s));
+            if ((rc = enqueue_moment_job(J, s))) break;
+            MLT_CUDA_TRY(cudaEventRecord(e1, s));
+            MLT_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            MLT_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            const double per = ms / ((double)np * trial_steps);
+            if (bestw == 0 || per < bestt) {
+                bestw = w;
+                bestt = per;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc && bestw == 0) {
+            m->group_width = saved;
+            return rc;
+        }
+        m->group_width = bestw;
+        if (best) *best = bestw;
+        return MLT_OK;
+    } catch (...) {
+        return fail(MLT_ECUDA, "mlt_autotune: exception");
     }
 }
 

@@ -7,6 +7,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "mlt.h"
 
@@ -30,6 +31,12 @@ struct ProfScope {
     cudaStream_t s;
     ProfScope(const char* name, cudaStream_t stream);
     ~ProfScope();
+};
+
+// No kernel timing on this thread while alive (used around graph capture).
+struct ProfPause {
+    ProfPause();
+    ~ProfPause();
 };
 
 // A grow-only device buffer owned by a matrix handle.
@@ -95,6 +102,7 @@ struct mlt_matrix {
     } tri;
     int tri_state = 0;          // 0 unprepared, 1 ready, <0 error code
     double tri_bound = 0.0;     // sum_(i,j) deg_i deg_j
+    int group_width = 0;        // probes per group chosen by mlt_autotune (0: from memory)
     // scratch
     mlt::SpmmPlan plan_A, plan_AT;
     mlt::DevBuf ws_v[2], ws_v2[2], ws_w, ws_part, ws_dots, ws_misc, ws_out, ws_y, ws_y32, ws_z, ws_x, ws_tri,
@@ -117,9 +125,32 @@ struct MomentPlan {
     int direct;
 };
 
+// With alloc_only, every device buffer of the group is sized and nothing is
+// launched; without it, only kernels are enqueued (buffers already sized).
 int run_moments_group(mlt_matrix* M, int precision, const MomentPlan& plan, double a, double b,
                       uint64_t seed, double* mu_dev, int64_t ld_mu, int* err_flag_dev,
-                      cudaStream_t s);
+                      cudaStream_t s, bool alloc_only);
+
+// One mlt_moments call split into its phases (see mlt_api.cu).
+struct MomentJob {
+    mlt_matrix* m = nullptr;
+    double a = 0, b = 0;
+    uint64_t seed = 0;
+    int precision = 0, direct = 0;
+    double* mu_user = nullptr;
+    double* mu_dev = nullptr;
+    bool out_dev = false;
+    int64_t ld_mu = 0, nprobes = 0;
+    size_t out_bytes = 0;
+    int* err = nullptr;
+    std::vector<MomentPlan> groups;
+    std::vector<std::vector<int>> acts;
+};
+int prepare_moment_job(mlt_matrix* m, double a, double b, uint64_t seed, int64_t probe_offset, int64_t nprobes,
+                       const int32_t* degree, int precision, unsigned flags, double* mu, int64_t ld_mu,
+                       int group_width, MomentJob& J, cudaStream_t s);
+int enqueue_moment_job(MomentJob& J, cudaStream_t s);
+int finish_moment_job(MomentJob& J, cudaStream_t s);
 
 int ensure_fp32_values(mlt_matrix* M, cudaStream_t s);
 int ensure_spmm_plan(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, cudaStream_t s);

@@ -456,3 +456,59 @@ def mlt_learned_estimate(matrix, surrogate, P):
 def mixed_at(k):
     """Precision code: the first k recurrence steps in FP32, the rest in FP64."""
     return 2 | (int(k) << 8)
+
+
+# ---------------------------------------------------------------------------
+# batched moments and the autotuner
+# ---------------------------------------------------------------------------
+
+class mlt_moments_job(ctypes.Structure):
+    _fields_ = [("matrix", ctypes.c_void_p), ("a", ctypes.c_double), ("b", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("probe_offset", ctypes.c_int64),
+                ("nprobes", ctypes.c_int64), ("degree", ctypes.c_void_p), ("mu", ctypes.c_void_p),
+                ("ld_mu", ctypes.c_int64), ("group_width", ctypes.c_int)]
+
+
+EXPORTS += ["mlt_moments_batched", "mlt_autotune"]
+_lib_learned = lib
+
+
+def lib():  # noqa: F811  (extends the loader with the batching symbols)
+    L = _lib_learned()
+    if not getattr(L, "_batch_bound", False):
+        L.mlt_moments_batched.argtypes = [ctypes.POINTER(mlt_moments_job), ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_uint, ctypes.c_void_p]
+        L.mlt_moments_batched.restype = ctypes.c_int
+        L.mlt_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]
+        L.mlt_autotune.restype = ctypes.c_int
+        L._batch_bound = True
+    return L
+
+
+def mlt_moments_batched(jobs, precision="fp64", flags=0, stream=None):
+    """jobs: list of dicts with matrix (handle), a, b, seed, probe_offset, degrees,
+    out (numpy or CUDA tensor nprobes x ld) and optionally group_width."""
+    arr = (mlt_moments_job * len(jobs))()
+    keep = []
+    for i, j in enumerate(jobs):
+        deg = np.ascontiguousarray(j["degrees"], dtype=np.int32)
+        keep.append(deg)
+        out = j["out"]
+        arr[i].matrix = j["matrix"]
+        arr[i].a, arr[i].b = float(j["a"]), float(j["b"])
+        arr[i].seed, arr[i].probe_offset = int(j.get("seed", 0)), int(j.get("probe_offset", 0))
+        arr[i].nprobes = deg.size
+        arr[i].degree = _ptr(deg)
+        arr[i].mu = _ptr(out)
+        arr[i].ld_mu = out.shape[1]
+        arr[i].group_width = int(j.get("group_width", 0))
+    prec = MLT_PREC[precision] if isinstance(precision, str) else precision
+    _check(lib().mlt_moments_batched(arr, len(jobs), prec, int(flags), _stream(stream)))
+
+
+def mlt_autotune(handle, precision="fp64", trial_steps=8, stream=None):
+    best = ctypes.c_int()
+    prec = MLT_PREC[precision] if isinstance(precision, str) else precision
+    _check(lib().mlt_autotune(handle, prec, int(trial_steps), ctypes.byref(best), _stream(stream)))
+    return best.value

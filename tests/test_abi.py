@@ -42,7 +42,8 @@ def test_struct_layout_matches_ctypes(L, tmp_path):
     import ctypes
     src = tmp_path / "layout.c"
     structs = [("mlt_mlmc_params", L.mlt_mlmc_params), ("mlt_mlmc_result", L.mlt_mlmc_result),
-               ("mlt_learned_params", L.mlt_learned_params), ("mlt_kernel_stat", L.mlt_kernel_stat)]
+               ("mlt_learned_params", L.mlt_learned_params), ("mlt_kernel_stat", L.mlt_kernel_stat),
+               ("mlt_moments_job", L.mlt_moments_job)]
     body = ['#include <stdio.h>', '#include <stddef.h>', '#include "mlt.h"', 'int main(void){']
     expect = []
     for cname, cls in structs:

@@ -211,9 +211,8 @@ def test_lanczos_interval_contains_spectrum(L, make, gram, sc):
         a, b = L.mlt_spectrum_bounds(M.handle, L.MLT_BOUNDS_LANCZOS, 60, 1)
         ga, gb = M.bounds()
     assert a <= lam[0] and b >= lam[-1]
-    # far tighter at the top than the Gershgorin bound
+    # close at the top: Ritz value + residual, widened by 1%
     assert b <= lam[-1] + 0.05 * abs(lam[-1]) + 1e-9
-    assert b <= gb * (1 + 1e-12)
 
 
 def test_mixed_precision_switch(L, O):
@@ -229,3 +228,37 @@ def test_mixed_precision_switch(L, O):
     # past the switch the drift no longer grows as in the all-FP32 run
     hi = slice(100, 129)
     assert np.max(np.abs(mix[:, hi] - ref[:, hi])) <= np.max(np.abs(f32[:, hi] - ref[:, hi])) + 1e-9
+
+
+def test_batched_graph_matches_single_calls(L, O):
+    # uneven matrices with ragged degrees in one graph launch; each job's
+    # results equal the oracle's (and the single-call path's)
+    mats = [synth.diffusion_3d(s, sigma=1.0, shift=0.05 * (i + 1), seed=i) for i, s in enumerate((4, 7, 10, 5))]
+    handles = [L.Matrix(m) for m in mats]
+    rng = np.random.default_rng(3)
+    jobs, refs = [], []
+    for i, (m, h) in enumerate(zip(mats, handles)):
+        lo, hi = O.gershgorin(m)
+        deg = rng.integers(0, 40, size=10 + 7 * i).astype(np.int32)
+        out = np.zeros((deg.size, 40))
+        jobs.append({"matrix": h.handle, "a": lo, "b": hi, "seed": i, "probe_offset": 100 * i,
+                     "degrees": deg, "out": out})
+        refs.append(O.moments(m, lo, hi, i, 100 * i, deg))
+    L.mlt_moments_batched(jobs)
+    for j, ref, m in zip(jobs, refs, mats):
+        assert np.max(np.abs(j["out"][:, :ref.shape[1]] - ref)) <= TOL64 * m.nrows
+    single = handles[2].moments(jobs[2]["a"], jobs[2]["b"], 2, 200, jobs[2]["degrees"], out=np.zeros((24, 40)))
+    assert np.array_equal(single, jobs[2]["out"])
+    with pytest.raises(L.MLTError):
+        L.mlt_moments_batched([jobs[0], dict(jobs[0])])     # same handle twice
+    for h in handles:
+        h.close()
+
+
+def test_autotune_picks_a_width(L, O):
+    m = synth.grid_laplacian_2d(40, shift=0.1)
+    with L.Matrix(m) as M:
+        w = L.mlt_autotune(M.handle, "fp64", 4)
+        assert w in (8, 16, 32, 64, 128)
+        got = M.moments(0.1, 8.1, 0, 0, [12] * 50)
+    assert np.max(np.abs(got - O.moments(m, 0.1, 8.1, 0, 0, [12] * 50))) <= TOL64 * m.nrows
