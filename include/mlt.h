@@ -348,6 +348,36 @@ int mlt_learned_estimate(mlt_matrix* m, mlt_surrogate* s, const mlt_learned_para
                          mlt_mlmc_result* r);
 
 /*
+ * Chebyshev moments with no device allocation at all (the paper has no
+ * counterpart).  For callers that cannot call cudaMalloc: code running inside
+ * a stream capture it does not own, loops that cannot absorb the device-wide
+ * synchronisation an allocation may cause, and hosts whose memory pool has
+ * claimed the device memory.  It computes what mlt_moments computes with
+ * MLT_PREC_FP64 and the doubling identities, for a CSR matrix given directly
+ * by device arrays (d x d, symmetric: rowptr int64[d+1], col int32[nnz],
+ * vals double[nnz] or NULL for a 0/1 pattern, every entry times `scale`), and
+ * writes mu (device double[nprobes * ld_mu]).  degree is a host array of
+ * nprobes (at most 512) degrees.  Working memory is one fixed 32 MiB device
+ * array inside the library, held by every GPU that loads it until the process
+ * exits: the call fails with MLT_ERANGE when 2 d ldv plus its small tables
+ * exceed 4,194,304 doubles (ldv = nprobes rounded up to 32).  All calls share
+ * that array and it keeps the last call's contents, so calls that overlap on
+ * the GPU race (a captured graph holding a call included); order them.  The
+ * first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make it before any stream
+ * capture (during capture that first call fails with MLT_EINVAL).  Later
+ * calls may be captured: they then copy nothing from host memory and do not
+ * synchronise, and CSR entries out of range turn the probes' mu rows into NaN
+ * when the graph runs.  Outside a capture the call returns after mu is
+ * written.  Errors: MLT_EINVAL (bad sizes, pointers, interval, CSR entries out
+ * of range outside a capture), MLT_ERANGE, MLT_ECUDA.
+ */
+int mlt_moments_noalloc(int64_t d, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                        const double* vals, double scale, double a, double b, uint64_t seed,
+                        int64_t probe_offset, int nprobes, const int32_t* degree, double* mu,
+                        int64_t ld_mu, void* stream);
+
+/*
  * Kernel timing (instrumentation; the paper has no counterpart).  Between
  * mlt_profile_start() and mlt_profile_stop() every kernel the library launches
  * is bracketed by a pair of CUDA events recorded on the stream it runs on.

@@ -512,3 +512,33 @@ def mlt_autotune(handle, precision="fp64", trial_steps=8, stream=None):
     prec = MLT_PREC[precision] if isinstance(precision, str) else precision
     _check(lib().mlt_autotune(handle, prec, int(trial_steps), ctypes.byref(best), _stream(stream)))
     return best.value
+
+
+# ---------------------------------------------------------------------------
+# moments without device allocation (fixed 32 MiB array inside the library)
+# ---------------------------------------------------------------------------
+
+EXPORTS += ["mlt_moments_noalloc"]
+_lib_batch = lib
+
+
+def lib():  # noqa: F811  (extends the loader with the no-allocation symbol)
+    L = _lib_batch()
+    if not getattr(L, "_noalloc_bound", False):
+        vp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+        L.mlt_moments_noalloc.argtypes = [i64, i64, vp, vp, vp, dbl, dbl, dbl, ctypes.c_uint64, i64,
+                                          ctypes.c_int, vp, vp, i64, vp]
+        L.mlt_moments_noalloc.restype = ctypes.c_int
+        L._noalloc_bound = True
+    return L
+
+
+def mlt_moments_noalloc(d, nnz, rowptr, col, vals, scale, a, b, seed, probe_offset, degrees, mu,
+                        stream=None):
+    """All array arguments but `degrees` are CUDA tensors the caller owns; mu is
+    nprobes x ld and is written in place."""
+    deg = np.ascontiguousarray(degrees, dtype=np.int32)
+    _check(lib().mlt_moments_noalloc(int(d), int(nnz), _ptr(rowptr), _ptr(col), _ptr(vals), float(scale),
+                                     float(a), float(b), int(seed), int(probe_offset), deg.size, _ptr(deg),
+                                     _ptr(mu), mu.shape[1], _stream(stream)))
+    return mu
