@@ -185,20 +185,25 @@ class Triangles:
 
     def kernel_bytes(self, launches_per_step):
         """Algorithmic bytes per launch (one 128-probe block) of each kernel:
-        every array touched once, gathered rows assumed cached.  Pass 1 reads
-        rowptr, col and the sign bits and writes int8 y; pass 2 reads the
-        upper-triangle row pointer and columns (nnz/2) and int8 y."""
+        every array touched once, gathered rows assumed cached.  y of a row
+        takes 128 B (degree <= 127, int8), 256 B (<= 32767, int16) or 512 B
+        (int32).  Pass 1 reads rowptr, col and the sign bits and writes y;
+        pass 2 reads the out-list pointers, columns (nnz/2), small-section
+        lengths and slots, and y of every row with an edge once."""
         d, nnz = self.d, self.nnz
+        deg = np.diff(self.csr.rowptr)
+        ybytes = int(128 * np.sum((deg > 0) & (deg <= 127)) + 256 * np.sum((deg > 127) & (deg <= 32767))
+                     + 512 * np.sum(deg > 32767))
         return {
             "tri_zbits": 16 * d,
-            "tri_pass1": 8 * (d + 1) + 4 * nnz + 16 * d + 128 * d,
-            "tri_pass2": 8 * (d + 1) + 4 * (nnz // 2) + 128 * d,
+            "tri_pass1": 8 * (d + 1) + 4 * nnz + 16 * d + ybytes,
+            "tri_pass2": 8 * (d + 1) + 4 * (nnz // 2) + 8 * d + ybytes,
         }
 
-    # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-    # an ncu --set full capture of this workload; to be re-measured whenever
-    # the kernel changes
-    TRAFFIC = {"tri_pass1": 230.935e6, "tri_pass2": 204.829e6}
+    # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    # from an ncu capture of this workload, per kernel; empty until the
+    # current kernels have been captured
+    TRAFFIC = {}
 
     # ours
     def setup(self, mlt, torch, rank):

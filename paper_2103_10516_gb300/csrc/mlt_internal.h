@@ -87,14 +87,16 @@ struct mlt_matrix {
     void* own_val32 = nullptr;
     void* own_t_rowptr = nullptr; void* own_t_col = nullptr; void* own_t_val = nullptr;
     void* own_t_val32 = nullptr;
-    // triangle preparation (all inside ws_tri)
-    int64_t* upper = nullptr;   // first index of each row with col > row
+    // triangle preparation (inside ws_tri; out_col and pairs inside ws_upcol)
     struct {
-        int64_t* up_ptr = nullptr;   // row pointer of the strictly upper triangle
-        int32_t* up_col = nullptr;   // its columns
+        int64_t* out_ptr = nullptr;  // row pointer of the degree-oriented out-lists
+        int32_t* out_col = nullptr;  // per row: small targets (rows), then mid targets (y16 slots)
+        int32_t* nsmall = nullptr;   // length of each out-list's small section
+        int4* pairs = nullptr;       // edges into rows of degree > 32767
+        int64_t npairs = 0;
         int64_t* crow1 = nullptr;    // row holding the first unit of each pass-1 chunk
-        int64_t* crow2 = nullptr;    // same over the upper triangle (pass 2)
-        int32_t* bslot = nullptr;    // int32 y slot of rows with degree > 127, else -1
+        int64_t* crow2 = nullptr;    // same over the out-lists (pass 2)
+        int32_t* bslot = nullptr;    // y16 / y32 slot of rows with degree > 127, else -1
         int32_t* longlist = nullptr; // rows cut across pass-1 chunks
         unsigned long long* counters = nullptr;  // chunk counters of pass 1 and pass 2
         int nbig = 0, nlong = 0, grid1 = 0, grid2 = 0;
@@ -105,7 +107,7 @@ struct mlt_matrix {
     int group_width = 0;        // probes per group chosen by mlt_autotune (0: from memory)
     // scratch
     mlt::SpmmPlan plan_A, plan_AT;
-    mlt::DevBuf ws_v[2], ws_v2[2], ws_w, ws_part, ws_dots, ws_misc, ws_out, ws_y, ws_y32, ws_z, ws_x, ws_tri,
+    mlt::DevBuf ws_v[2], ws_v2[2], ws_w, ws_part, ws_dots, ws_misc, ws_out, ws_y, ws_y16, ws_y32, ws_z, ws_x, ws_tri,
         ws_seg, ws_upcol;
     int64_t dim() const { return (flags & MLT_GRAM) ? A.ncols : A.nrows; }
 };

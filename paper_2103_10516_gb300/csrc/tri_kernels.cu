@@ -4,24 +4,38 @@
 // with no self-loops, per probe:
 //   y  = A z                      (pass 1; |y_i| <= deg_i)
 //   x1 = z . y = z^T A z,  x2 = y . y = z^T A^2 z
-//   x3 = y^T A y = z^T A^3 z = 2 sum_i y_i sum_{j in N(i), j > i} y_j   (pass 2)
-// Pass 2 walks only the upper triangle: the quadratic form is symmetric, so the
-// two products of the paper's footnote suffice and half the gathers are saved.
+//   x3 = y^T A y = z^T A^3 z = 2 sum over edges {i,j} of y_i y_j      (pass 2)
+// Pass 2 visits every undirected edge once, so the two products of the
+// paper's footnote suffice and half the gathers are saved.  Each edge is
+// oriented from the endpoint of lower (degree, index) to the higher one: a
+// row's out-list then holds at most sqrt(2 nnz) entries, and the gathered
+// rows y_j concentrate on the high-degree vertices, a set small enough to stay
+// in L2.
+//
+// Row classes by degree (|y_i| <= deg_i makes each storage exact):
+//   small  deg <= 127    : y in y8, 128 x int8 per row (one 128-byte line)
+//   mid    deg <= 32767  : y in y16, 128 x int16 per row, slot bslot[i]
+//   huge   deg >  32767  : y in y32, 128 x int32 per row, slot bslot[i]
+// Each out-list is stored as [small targets (column index) | mid targets (y16
+// slot)], so the inner loops need no escape test.  Edges into huge rows (a
+// handful of vertices) go to a separate pair list with its own kernel.
 //
 // Layout (device):
-//   zb     : 4 x uint32 per row, bit t of word w = 1 when z_i of probe 32w+t is -1
-//   y8     : 128 x int8 per row (one 128-byte line); the byte -128 is an escape
-//            meaning "look in y32", used only where |y_i| > 127
-//   y32    : 128 x int32 per "big" row (degree > 127), slot bslot[i]
-//   up_ptr : row pointer of the strictly upper triangle, its columns in up_col
+//   zb      : 4 x uint32 per row; bit t + 8q of word w = 1 when z_i of probe
+//             32w + 4t + q is -1, so lane l (probes 4l..4l+3) reads its four
+//             signs one byte apart from word l/8 shifted right by l%8
+//   y32     : also the pass-1 accumulator of rows longer than a chunk
+//   out_ptr : row pointer of the oriented out-lists, out_col their entries,
+//             nsmall the length of each list's small section
+//   pairs   : (class of i, row or slot of i, y32 slot of the huge target)
 // Work split: every row costs kRowCost "units" plus one per entry (all entries
-// in pass 1, upper entries in pass 2); the unit axis is cut into chunks of
+// in pass 1, out-entries in pass 2); the unit axis is cut into chunks of
 // kChunk units that warps of a persistent grid take from an atomic counter.
 // A row of degree <= kChunk is handled whole by the chunk holding its first
-// unit; consecutive such rows are walked as one stream of entries, with the
-// row ends of 32 rows at a time held in lanes.  Longer rows are cut at chunk
-// edges: pass-1 counts are merged with integer atomics in y32 and finished by
-// a per-row kernel; pass 2 is linear in the row sums, so a cut needs no merge.
+// unit; consecutive such rows are walked with the row ends of 32 rows at a
+// time held in lanes.  Longer rows are cut at chunk edges: pass-1 counts are
+// merged with integer atomics in y32 and finished by a per-row kernel; pass 2
+// is linear in the row sums, so a cut needs no merge.
 // All sums are integers (exact, independent of order).
 #include <cuda_runtime.h>
 
@@ -35,14 +49,39 @@ namespace {
 
 constexpr int kTriThreads = 256;
 constexpr int kProbes = 128;
-constexpr int kBigDeg = 127;          // rows above this degree get an int32 slot
+constexpr int kSmallDeg = 127;        // y of rows up to this degree fits int8
+constexpr int kMidDeg = 32767;        // ... int16; rows above it keep int32
 constexpr int64_t kRowCost = 4;       // units charged per row on top of its entries
 constexpr int64_t kChunk = 1024;      // units per dynamically scheduled chunk
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kScanBlock = 1024;      // elements per CTA of the prefix scan
+static_assert(kChunk <= kMidDeg, "rows handled whole by pass 1 must be small or mid");
 
-// zb[i * 4 + w] bit t = 1 when z_i of probe (id0 + 32 w + t) is -1 (0 for
-// t >= nb - 32 w).  The 32 bits come from one or two 64-probe hash words.
+enum RowClass { kClassSmall = 0, kClassMid = 1, kClassHuge = 2 };
+
+__host__ __device__ __forceinline__ int row_class(int64_t deg)
+{
+    return deg <= kSmallDeg ? kClassSmall : (deg <= kMidDeg ? kClassMid : kClassHuge);
+}
+
+// Bit 4t + q of x moved to bit t + 8q (an 8 x 4 bit transpose).
+__device__ __forceinline__ uint32_t interleave_bytes(uint32_t x)
+{
+    uint32_t out = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t m = (x >> q) & 0x11111111u;   // bits 4t
+        m = (m | (m >> 3)) & 0x03030303u;      // pairs of t
+        m = (m | (m >> 6)) & 0x000F000Fu;      // quads of t
+        m = (m | (m >> 12)) & 0xFFu;           // t = 0..7 in bits 0..7
+        out |= m << (8 * q);
+    }
+    return out;
+}
+
+// zb[i * 4 + w]: the signs of probes id0 + 32 w .. + 31 at row i in the
+// byte-interleaved order above (0 for probes past nb).  The 32 bits come from
+// one or two 64-probe hash words.
 __global__ void zbits_kernel(int64_t d, uint64_t seedmix, int64_t id0, int nb, uint32_t* __restrict__ zb)
 {
     const int64_t total = d * 4;
@@ -60,18 +99,29 @@ __global__ void zbits_kernel(int64_t d, uint64_t seedmix, int64_t id0, int nb, u
             bits = (uint32_t)v;
             if (valid < 32) bits &= (1u << valid) - 1u;
         }
-        zb[e] = bits;
+        zb[e] = interleave_bytes(bits);
     }
 }
 
-// Per row: first index with col > row, its count of upper entries (into
-// upcnt, scanned later into up_ptr), self-loop detection, the bound
-// sum_j deg_i deg_j certifying that x3 fits in int64, and slots for big rows
-// and long rows (slot order is irrelevant to every result).
+// ---- preparation: orientation, classes, slots -------------------------------
+
+// Neighbour c (degree dc) of row r (degree deg) is an out-target of r when its
+// (degree, index) key is larger.
+__device__ __forceinline__ bool is_target(int64_t r, int64_t deg, int c, int64_t dc)
+{
+    return dc > deg || (dc == deg && c > r);
+}
+
+// Rows of degree <= kChunk, a warp each: out-list lengths by class into
+// outcnt (later scanned into out_ptr) and nsmall, the pair count, self-loop
+// detection, and the bound sum_j deg_i deg_j certifying that x3 fits in int64.
+// Every row gets its slot here (rows above kSmallDeg) and longer rows are
+// listed for tri_prepare_long_kernel.  Slot order is irrelevant to every result.
 __global__ void tri_prepare_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                   int64_t d, int64_t* __restrict__ upper, int64_t* __restrict__ upcnt,
+                                   int64_t d, int64_t* __restrict__ outcnt, int32_t* __restrict__ nsmall,
                                    int32_t* __restrict__ bslot, int32_t* __restrict__ longlist,
-                                   int* counters /* [0] nbig, [1] nlong, [2] selfloop */, double* bound)
+                                   int* counters /* [0] nbig, [1] nlong, [2] selfloop, [3] npairs */,
+                                   double* bound)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -79,32 +129,90 @@ __global__ void tri_prepare_kernel(const int64_t* __restrict__ rowptr, const int
     double wsum = 0.0;
     for (int64_t r = warp; r < d; r += nwarps) {
         const int64_t beg = rowptr[r], end = rowptr[r + 1];
-        int64_t first = end;
+        const int64_t deg = end - beg;
+        if (lane == 0) {
+            bslot[r] = deg > kSmallDeg ? atomicAdd(counters + 0, 1) : -1;
+            if (deg > kChunk) longlist[atomicAdd(counters + 1, 1)] = (int32_t)r;
+        }
+        if (deg > kChunk) continue;
+        int ns = 0, nm = 0, nh = 0;
         double dsum = 0.0;
         for (int64_t base = beg; base < end; base += 32) {
             const int64_t k = base + lane;
-            int c = -1;
+            bool t = false;
+            int64_t dc = 0;
             if (k < end) {
-                c = col[k];
-                dsum += (double)(rowptr[c + 1] - rowptr[c]);
+                const int c = col[k];
+                dc = rowptr[c + 1] - rowptr[c];
+                dsum += (double)dc;
                 if (c == r) atomicOr(counters + 2, 1);
+                t = is_target(r, deg, c, dc);
             }
-            const unsigned above = __ballot_sync(kFull, k < end && c > r);
-            if (above && first == end) first = base + __ffs(above) - 1;
+            ns += __popc(__ballot_sync(kFull, t && dc <= kSmallDeg));
+            nm += __popc(__ballot_sync(kFull, t && dc > kSmallDeg && dc <= kMidDeg));
+            nh += __popc(__ballot_sync(kFull, t && dc > kMidDeg));
         }
         for (int o = 16; o; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
         if (lane == 0) {
-            const int64_t deg = end - beg;
-            upper[r] = first;
-            upcnt[r] = end - first;
+            outcnt[r] = ns + nm;
+            nsmall[r] = ns;
+            if (nh) atomicAdd(counters + 3, nh);
             wsum += dsum * (double)deg;
-            int32_t s = -1;
-            if (deg > kBigDeg) s = atomicAdd(counters + 0, 1);
-            bslot[r] = s;
-            if (deg > kChunk) longlist[atomicAdd(counters + 1, 1)] = (int32_t)r;
         }
     }
     if (lane == 0 && wsum != 0.0) atomicAdd(bound, wsum);
+}
+
+// The same for the rows listed by tri_prepare_kernel, a CTA each.
+__global__ void __launch_bounds__(kTriThreads) tri_prepare_long_kernel(
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ longlist,
+    int64_t* __restrict__ outcnt, int32_t* __restrict__ nsmall, int* counters, double* bound)
+{
+    __shared__ int cnt[3];
+    __shared__ double dsh;
+    const int nlong = *(volatile int*)(counters + 1);
+    for (int i = blockIdx.x; i < nlong; i += gridDim.x) {
+        const int64_t r = longlist[i];
+        const int64_t beg = rowptr[r], end = rowptr[r + 1];
+        const int64_t deg = end - beg;
+        if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
+        if (threadIdx.x == 0) dsh = 0.0;
+        __syncthreads();
+        int ns = 0, nm = 0, nh = 0;
+        double dsum = 0.0;
+        for (int64_t k = beg + threadIdx.x; k < end; k += blockDim.x) {
+            const int c = col[k];
+            const int64_t dc = rowptr[c + 1] - rowptr[c];
+            dsum += (double)dc;
+            if (c == r) atomicOr(counters + 2, 1);
+            if (is_target(r, deg, c, dc)) {
+                const int cl = row_class(dc);
+                ns += cl == kClassSmall;
+                nm += cl == kClassMid;
+                nh += cl == kClassHuge;
+            }
+        }
+        for (int o = 16; o; o >>= 1) {
+            ns += __shfl_xor_sync(kFull, ns, o);
+            nm += __shfl_xor_sync(kFull, nm, o);
+            nh += __shfl_xor_sync(kFull, nh, o);
+            dsum += __shfl_xor_sync(kFull, dsum, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicAdd(cnt + 0, ns);
+            atomicAdd(cnt + 1, nm);
+            atomicAdd(cnt + 2, nh);
+            atomicAdd(&dsh, dsum);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            outcnt[r] = cnt[0] + cnt[1];
+            nsmall[r] = cnt[0];
+            if (cnt[2]) atomicAdd(counters + 3, cnt[2]);
+            atomicAdd(bound, dsh * (double)deg);
+        }
+        __syncthreads();
+    }
 }
 
 // ---- exclusive prefix scan of int64 counts, in place (three passes) --------
@@ -182,17 +290,106 @@ __global__ void scan_apply_kernel(int64_t* __restrict__ x, int64_t n, const int6
     }
 }
 
-// up_col[up_ptr[r] ...] = the columns of row r above the diagonal.
-__global__ void fill_upper_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                  const int64_t* __restrict__ upper, const int64_t* __restrict__ up_ptr,
-                                  int64_t d, int32_t* __restrict__ up_col)
+// ---- out-lists -------------------------------------------------------------
+
+// One pair of the huge-target list: how to read y_i, and the target's slot.
+__device__ __forceinline__ int4 make_pair(int64_t r, int64_t deg, const int32_t* __restrict__ bslot,
+                                          int target_slot)
+{
+    const int cl = row_class(deg);
+    return make_int4(cl, cl == kClassSmall ? (int)r : bslot[r], target_slot, 0);
+}
+
+// Rows of degree <= kChunk, a warp each: the out-list of row r in neighbour
+// order, small targets (their row) before mid targets (their slot); targets of
+// class huge are appended to the pair list.
+__global__ void fill_out_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, int64_t d,
+                                const int64_t* __restrict__ out_ptr, const int32_t* __restrict__ nsmall,
+                                const int32_t* __restrict__ bslot, int32_t* __restrict__ out_col,
+                                int4* __restrict__ pairs, int npairs, int* pair_ctr)
 {
     const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = warp; r < d; r += nwarps) {
-        const int64_t a = upper[r], b = rowptr[r + 1], o = up_ptr[r];
-        for (int64_t k = a + lane; k < b; k += 32) up_col[o + (k - a)] = col[k];
+        const int64_t beg = rowptr[r], end = rowptr[r + 1];
+        const int64_t deg = end - beg;
+        if (deg > kChunk) continue;
+        const int64_t os = out_ptr[r], om = os + nsmall[r];
+        int64_t cs = 0, cm = 0;
+        for (int64_t base = beg; base < end; base += 32) {
+            const int64_t k = base + lane;
+            int c = 0, cl = -1;
+            if (k < end) {
+                c = col[k];
+                const int64_t dc = rowptr[c + 1] - rowptr[c];
+                if (is_target(r, deg, c, dc)) cl = row_class(dc);
+            }
+            const unsigned ms = __ballot_sync(kFull, cl == kClassSmall);
+            const unsigned mm = __ballot_sync(kFull, cl == kClassMid);
+            if (cl == kClassSmall) out_col[os + cs + __popc(ms & below)] = c;
+            if (cl == kClassMid) out_col[om + cm + __popc(mm & below)] = bslot[c];
+            if (cl == kClassHuge) {
+                const int at = atomicAdd(pair_ctr, 1);
+                if (at < npairs) pairs[at] = make_pair(r, deg, bslot, bslot[c]);   // at < npairs by construction
+            }
+            cs += __popc(ms);
+            cm += __popc(mm);
+        }
+    }
+}
+
+// The same for rows longer than kChunk, a CTA each (order kept across warps).
+__global__ void __launch_bounds__(kTriThreads) fill_out_long_kernel(
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ longlist,
+    int nlong, const int64_t* __restrict__ out_ptr, const int32_t* __restrict__ nsmall,
+    const int32_t* __restrict__ bslot, int32_t* __restrict__ out_col, int4* __restrict__ pairs, int npairs,
+    int* pair_ctr)
+{
+    __shared__ int ws[kTriThreads / 32], wm[kTriThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    for (int i = blockIdx.x; i < nlong; i += gridDim.x) {
+        const int64_t r = longlist[i];
+        const int64_t beg = rowptr[r], end = rowptr[r + 1];
+        const int64_t deg = end - beg;
+        const int64_t os = out_ptr[r], om = os + nsmall[r];
+        int64_t cs = 0, cm = 0;
+        for (int64_t base = beg; base < end; base += blockDim.x) {
+            const int64_t k = base + threadIdx.x;
+            int c = 0, cl = -1;
+            if (k < end) {
+                c = col[k];
+                const int64_t dc = rowptr[c + 1] - rowptr[c];
+                if (is_target(r, deg, c, dc)) cl = row_class(dc);
+            }
+            const unsigned ms = __ballot_sync(kFull, cl == kClassSmall);
+            const unsigned mm = __ballot_sync(kFull, cl == kClassMid);
+            if (lane == 0) {
+                ws[wid] = __popc(ms);
+                wm[wid] = __popc(mm);
+            }
+            __syncthreads();
+            int ps = 0, pm = 0, ts = 0, tm = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                if (w < wid) {
+                    ps += ws[w];
+                    pm += wm[w];
+                }
+                ts += ws[w];
+                tm += wm[w];
+            }
+            if (cl == kClassSmall) out_col[os + cs + ps + __popc(ms & below)] = c;
+            if (cl == kClassMid) out_col[om + cm + pm + __popc(mm & below)] = bslot[c];
+            if (cl == kClassHuge) {
+                const int at = atomicAdd(pair_ctr, 1);
+                if (at < npairs) pairs[at] = make_pair(r, deg, bslot, bslot[c]);   // at < npairs by construction
+            }
+            cs += ts;
+            cm += tm;
+            __syncthreads();
+        }
     }
 }
 
@@ -232,10 +429,12 @@ __global__ void zero_long_rows_kernel(const int32_t* __restrict__ longlist, int 
     }
 }
 
-// The 4 sign bits of probes 4*lane .. 4*lane+3 at row j.
-__device__ __forceinline__ uint32_t sign_nibble(const uint32_t* __restrict__ zb, int64_t j, int lane)
+// ---- pass 1 ------------------------------------------------------------------
+
+// The sign bits of probes 4*lane + q at row j, in bit 8q (q = 0..3).
+__device__ __forceinline__ uint32_t sign_bytes(const uint32_t* __restrict__ zb, int64_t j, int lane)
 {
-    return (__ldg(zb + (size_t)j * 4 + (lane >> 3)) >> ((lane & 7) * 4)) & 0xFu;
+    return (__ldg(zb + (size_t)j * 4 + (lane >> 3)) >> (lane & 7)) & 0x01010101u;
 }
 
 // Byte q of `packed` counts sign bit q; folded into int counters before it can wrap.
@@ -259,39 +458,43 @@ __device__ __forceinline__ void count_negatives(const int32_t* __restrict__ col,
         const int n = (int)min((int64_t)32, b - base);
 #pragma unroll 8
         for (int t = 0; t < n; ++t)
-            packed += (sign_nibble(zb, __shfl_sync(kFull, cj, t), lane) * 0x00204081u) & 0x01010101u;
+            packed += sign_bytes(zb, __shfl_sync(kFull, cj, t), lane);
         fold(packed, cnt);
     }
 }
 
-// Store y for probes 4*lane .. 4*lane+3 of row r and add its x1, x2 terms.
-__device__ __forceinline__ void store_row(int64_t r, const int yv[4], uint32_t own, int32_t slot,
-                                          uint32_t* __restrict__ y8, int32_t* __restrict__ y32, int lane,
-                                          long long x1[4], long long x2[4])
+// Store y for probes 4*lane .. 4*lane+3 of row r (degree deg, slot if deg >
+// kSmallDeg) in its class's array, and add its x1, x2 terms.
+__device__ __forceinline__ void store_row(int64_t r, int64_t deg, const int yv[4], uint32_t own, int32_t slot,
+                                          uint32_t* __restrict__ y8, uint2* __restrict__ y16,
+                                          int32_t* __restrict__ y32, int lane, long long x1[4], long long x2[4])
 {
-    uint32_t packed = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const int v = yv[q];
-        const uint32_t byte = (v >= -127 && v <= 127) ? (uint32_t)(v & 0xFF) : 0x80u;
-        packed |= byte << (8 * q);
-        const long long yq = v;
-        x1[q] += ((own >> q) & 1u) ? -yq : yq;
+        const long long yq = yv[q];
+        x1[q] += ((own >> (8 * q)) & 1u) ? -yq : yq;
         x2[q] += yq * yq;
     }
-    y8[(size_t)r * 32 + lane] = packed;
-    if (slot >= 0) *reinterpret_cast<int4*>(y32 + (size_t)slot * kProbes + 4 * lane) =
-        make_int4(yv[0], yv[1], yv[2], yv[3]);
+    const int cl = row_class(deg);
+    if (cl == kClassSmall) {
+        y8[(size_t)r * 32 + lane] = (uint32_t)(yv[0] & 0xFF) | ((uint32_t)(yv[1] & 0xFF) << 8) |
+                                    ((uint32_t)(yv[2] & 0xFF) << 16) | ((uint32_t)(yv[3] & 0xFF) << 24);
+    } else if (cl == kClassMid) {
+        y16[(size_t)slot * 32 + lane] = make_uint2((uint32_t)(yv[0] & 0xFFFF) | ((uint32_t)yv[1] << 16),
+                                                   (uint32_t)(yv[2] & 0xFFFF) | ((uint32_t)yv[3] << 16));
+    } else {
+        *reinterpret_cast<int4*>(y32 + (size_t)slot * kProbes + 4 * lane) = make_int4(yv[0], yv[1], yv[2], yv[3]);
+    }
 }
 
 __device__ __forceinline__ void finish_pass1_row(int64_t r, int deg, int cnt[4], uint32_t own,
                                                  const int32_t* __restrict__ bslot, uint32_t* __restrict__ y8,
-                                                 int32_t* __restrict__ y32, int lane, long long x1[4],
-                                                 long long x2[4])
+                                                 uint2* __restrict__ y16, int32_t* __restrict__ y32, int lane,
+                                                 long long x1[4], long long x2[4])
 {
     if (deg > 0) {
         const int yv[4] = {deg - 2 * cnt[0], deg - 2 * cnt[1], deg - 2 * cnt[2], deg - 2 * cnt[3]};
-        store_row(r, yv, own, deg > kBigDeg ? __ldg(bslot + r) : -1, y8, y32, lane, x1, x2);
+        store_row(r, deg, yv, own, deg > kSmallDeg ? __ldg(bslot + r) : -1, y8, y16, y32, lane, x1, x2);
     }
     cnt[0] = cnt[1] = cnt[2] = cnt[3] = 0;
 }
@@ -308,8 +511,8 @@ __device__ __forceinline__ void flush_x(long long (*sx)[kProbes], int which, con
 __global__ void __launch_bounds__(kTriThreads) tri_pass1_kernel(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, int64_t d, int64_t nch,
     const int64_t* __restrict__ crow, const int32_t* __restrict__ bslot,
-    const uint32_t* __restrict__ zb, uint32_t* __restrict__ y8, int32_t* __restrict__ y32,
-    unsigned long long* __restrict__ xacc, unsigned long long* __restrict__ counter)
+    const uint32_t* __restrict__ zb, uint32_t* __restrict__ y8, uint2* __restrict__ y16,
+    int32_t* __restrict__ y32, unsigned long long* __restrict__ xacc, unsigned long long* __restrict__ counter)
 {
     __shared__ long long sx[2][kProbes];
     for (int t = threadIdx.x; t < 2 * kProbes; t += blockDim.x) (&sx[0][0])[t] = 0;
@@ -364,7 +567,7 @@ __global__ void __launch_bounds__(kTriThreads) tri_pass1_kernel(
                     const int b = __shfl_sync(kFull, a1, cur);
                     if (a == b) continue;
                     const int64_t row = r + cur;
-                    const uint32_t own = sign_nibble(zb, row, lane);   // fetched before the entries
+                    const uint32_t own = sign_bytes(zb, row, lane);   // fetched before the entries
                     int cnt[4] = {0, 0, 0, 0};
                     uint32_t packed = 0;
                     for (int base = a; base < b; base += 32) {
@@ -373,10 +576,10 @@ __global__ void __launch_bounds__(kTriThreads) tri_pass1_kernel(
                         const int n = min(32, b - base);
 #pragma unroll 8
                         for (int t = 0; t < n; ++t)
-                            packed += (sign_nibble(zb, __shfl_sync(kFull, cj, t), lane) * 0x00204081u) & 0x01010101u;
+                            packed += sign_bytes(zb, __shfl_sync(kFull, cj, t), lane);
                         fold(packed, cnt);
                     }
-                    finish_pass1_row(row, b - a, cnt, own, bslot, y8, y32, lane, x1, x2);
+                    finish_pass1_row(row, b - a, cnt, own, bslot, y8, y16, y32, lane, x1, x2);
                 }
                 r += f;
                 if (f < 32) break;
@@ -392,11 +595,12 @@ __global__ void __launch_bounds__(kTriThreads) tri_pass1_kernel(
     }
 }
 
-// Finish long rows: counts -> y, the int8 escapes, and their x1, x2 terms.
+// Finish long rows: counts -> y in the row's class array, and their x1, x2
+// terms (a huge row's y replaces its counts in y32, lane by lane).
 __global__ void __launch_bounds__(kTriThreads) tri_long_rows_kernel(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ longlist, int nlong,
     const int32_t* __restrict__ bslot, const uint32_t* __restrict__ zb, uint32_t* __restrict__ y8,
-    int32_t* __restrict__ y32, unsigned long long* __restrict__ xacc)
+    uint2* __restrict__ y16, int32_t* __restrict__ y32, unsigned long long* __restrict__ xacc)
 {
     __shared__ long long sx[2][kProbes];
     for (int t = threadIdx.x; t < 2 * kProbes; t += blockDim.x) (&sx[0][0])[t] = 0;
@@ -407,11 +611,12 @@ __global__ void __launch_bounds__(kTriThreads) tri_long_rows_kernel(
     long long x1[4] = {0, 0, 0, 0}, x2[4] = {0, 0, 0, 0};
     for (int64_t i = warp; i < nlong; i += nwarps) {
         const int64_t r = longlist[i];
-        const int deg = (int)(rowptr[r + 1] - rowptr[r]);
+        const int64_t deg = rowptr[r + 1] - rowptr[r];
         const int32_t slot = bslot[r];
         const int4 c = *reinterpret_cast<const int4*>(y32 + (size_t)slot * kProbes + 4 * lane);
-        const int yv[4] = {deg - 2 * c.x, deg - 2 * c.y, deg - 2 * c.z, deg - 2 * c.w};
-        store_row(r, yv, sign_nibble(zb, r, lane), slot, y8, y32, lane, x1, x2);
+        const int dg = (int)deg;
+        const int yv[4] = {dg - 2 * c.x, dg - 2 * c.y, dg - 2 * c.z, dg - 2 * c.w};
+        store_row(r, deg, yv, sign_bytes(zb, r, lane), slot, y8, y16, y32, lane, x1, x2);
     }
     flush_x(sx, 0, x1, lane);
     flush_x(sx, 1, x2, lane);
@@ -422,54 +627,88 @@ __global__ void __launch_bounds__(kTriThreads) tri_long_rows_kernel(
     }
 }
 
-// Add y of row j (this lane's 4 probes) into s: the int8 bytes are summed
-// with dp4a against unit vectors; an escape byte sends the lane to y32.
-__device__ __forceinline__ void add_y(int64_t j, const uint32_t* __restrict__ y8,
-                                      const int32_t* __restrict__ y32, const int32_t* __restrict__ bslot,
-                                      int lane, int s[4])
+// ---- pass 2 ------------------------------------------------------------------
+
+// s += y of the small targets (rows) listed in col[a, b), this lane's 4
+// probes; y8l = y8 + lane.  Eight gathers are in flight before the first is
+// used; lanes past the end load nothing and add zero.
+__device__ __forceinline__ void sum_small(const int32_t* __restrict__ col, int64_t a, int64_t b,
+                                          const uint32_t* __restrict__ y8l, int lane, int s[4])
 {
-    const uint32_t w = __ldg(y8 + (size_t)j * 32 + lane);
-    const uint32_t v = w ^ 0x80808080u;
-    if ((v - 0x01010101u) & ~v & 0x80808080u) {
-        const int4 t = __ldg(reinterpret_cast<const int4*>(y32 + (size_t)__ldg(bslot + j) * kProbes) + lane);
-        s[0] += t.x;
-        s[1] += t.y;
-        s[2] += t.z;
-        s[3] += t.w;
-        return;
+    for (int64_t base = a; base < b; base += 32) {
+        const int64_t k = base + lane;
+        const int cj = k < b ? __ldg(col + k) : 0;
+        const int n = (int)min((int64_t)32, b - base);
+        for (int t0 = 0; t0 < n; t0 += 8) {
+            uint32_t w[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = __shfl_sync(kFull, cj, t0 + u);
+                w[u] = t0 + u < n ? __ldg(y8l + (size_t)j * 32) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                s[0] = __dp4a((int)w[u], 0x00000001, s[0]);
+                s[1] = __dp4a((int)w[u], 0x00000100, s[1]);
+                s[2] = __dp4a((int)w[u], 0x00010000, s[2]);
+                s[3] = __dp4a((int)w[u], 0x01000000, s[3]);
+            }
+        }
     }
-    s[0] = __dp4a((int)w, 0x00000001, s[0]);
-    s[1] = __dp4a((int)w, 0x00000100, s[1]);
-    s[2] = __dp4a((int)w, 0x00010000, s[2]);
-    s[3] = __dp4a((int)w, 0x01000000, s[3]);
 }
 
-// Add an already loaded y8 word of row j into s (escape bytes go to y32).
-__device__ __forceinline__ void acc_y(uint32_t w, int64_t j, const int32_t* __restrict__ y32,
-                                      const int32_t* __restrict__ bslot, int lane, int s[4])
+// s += y of the mid targets (y16 slots) listed in col[a, b); y16l = y16 + lane.
+__device__ __forceinline__ void sum_mid(const int32_t* __restrict__ col, int64_t a, int64_t b,
+                                        const uint2* __restrict__ y16l, int lane, int s[4])
 {
-    const uint32_t v = w ^ 0x80808080u;
-    if ((v - 0x01010101u) & ~v & 0x80808080u) {
-        const int4 t = __ldg(reinterpret_cast<const int4*>(y32 + (size_t)__ldg(bslot + j) * kProbes) + lane);
-        s[0] += t.x;
-        s[1] += t.y;
-        s[2] += t.z;
-        s[3] += t.w;
-        return;
+    for (int64_t base = a; base < b; base += 32) {
+        const int64_t k = base + lane;
+        const int cj = k < b ? __ldg(col + k) : 0;
+        const int n = (int)min((int64_t)32, b - base);
+        for (int t0 = 0; t0 < n; t0 += 8) {
+            uint2 w[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = __shfl_sync(kFull, cj, t0 + u);
+                w[u] = t0 + u < n ? __ldg(y16l + (size_t)j * 32) : make_uint2(0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                s[0] = __dp2a_lo((int)w[u].x, 0x0001, s[0]);
+                s[1] = __dp2a_lo((int)w[u].x, 0x0100, s[1]);
+                s[2] = __dp2a_lo((int)w[u].y, 0x0001, s[2]);
+                s[3] = __dp2a_lo((int)w[u].y, 0x0100, s[3]);
+            }
+        }
     }
-    s[0] = __dp4a((int)w, 0x00000001, s[0]);
-    s[1] = __dp4a((int)w, 0x00000100, s[1]);
-    s[2] = __dp4a((int)w, 0x00010000, s[2]);
-    s[3] = __dp4a((int)w, 0x01000000, s[3]);
 }
 
-// x3 += y_r * s for row r (own = its y8 word), then s = 0.
-__device__ __forceinline__ void finish_pass2_row(int64_t r, uint32_t own, int s[4],
-                                                 const int32_t* __restrict__ y32,
-                                                 const int32_t* __restrict__ bslot, int lane, long long x3[4])
+// y of a small or mid row, this lane's 4 probes, from its raw words (a huge
+// row has no out-entries: every neighbour above it is huge too).
+__device__ __forceinline__ uint2 load_own(int64_t row, int32_t slot, const uint32_t* __restrict__ y8l,
+                                          const uint2* __restrict__ y16l)
 {
-    int yi[4] = {0, 0, 0, 0};
-    acc_y(own, r, y32, bslot, lane, yi);
+    return slot < 0 ? make_uint2(__ldg(y8l + (size_t)row * 32), 0u) : __ldg(y16l + (size_t)slot * 32);
+}
+
+__device__ __forceinline__ void unpack_own(uint2 w, int32_t slot, int yi[4])
+{
+    if (slot < 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) yi[q] = (int)(int8_t)(w.x >> (8 * q));
+    } else {
+        yi[0] = (int)(int16_t)(w.x & 0xFFFF);
+        yi[1] = (int)w.x >> 16;
+        yi[2] = (int)(int16_t)(w.y & 0xFFFF);
+        yi[3] = (int)w.y >> 16;
+    }
+}
+
+// x3 += y_i * s, then s = 0.
+__device__ __forceinline__ void finish_pass2_row(uint2 own, int32_t slot, int s[4], long long x3[4])
+{
+    int yi[4];
+    unpack_own(own, slot, yi);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         x3[q] += (long long)yi[q] * s[q];
@@ -477,11 +716,13 @@ __device__ __forceinline__ void finish_pass2_row(int64_t r, uint32_t own, int s[
     }
 }
 
-// Pass 2: x3 = 2 sum_i y_i sum_{j in N(i), j > i} y_j over the upper CSR.
+// Pass 2: x3 = 2 sum_i y_i sum_{j in out(i)} y_j over the oriented out-lists
+// (|s| <= kChunk * kMidDeg < 2^31: a row part never holds more than kChunk
+// entries and every main target is small or mid).
 __global__ void __launch_bounds__(kTriThreads) tri_pass2_kernel(
-    const int64_t* __restrict__ up_ptr, const int32_t* __restrict__ up_col, int64_t d, int64_t nch,
-    const int64_t* __restrict__ crow, const int32_t* __restrict__ bslot,
-    const uint32_t* __restrict__ y8, const int32_t* __restrict__ y32,
+    const int64_t* __restrict__ out_ptr, const int32_t* __restrict__ out_col, const int32_t* __restrict__ nsmall,
+    const int32_t* __restrict__ bslot, int64_t d, int64_t nch, const int64_t* __restrict__ crow,
+    const uint32_t* __restrict__ y8, const uint2* __restrict__ y16,
     unsigned long long* __restrict__ xacc, unsigned long long* __restrict__ counter)
 {
     __shared__ long long sx[kProbes];
@@ -489,30 +730,30 @@ __global__ void __launch_bounds__(kTriThreads) tri_pass2_kernel(
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
+    const uint32_t* y8l = y8 + lane;
+    const uint2* y16l = y16 + lane;
     long long x3[4] = {0, 0, 0, 0};
+    int s[4] = {0, 0, 0, 0};
     for (int64_t c = next_chunk(counter, lane); c < nch; c = next_chunk(counter, lane)) {
         const int64_t u0 = c * kChunk, u1 = u0 + kChunk;
         int64_t r = crow[c];
         while (r < d) {
-            const int64_t beg = __ldg(up_ptr + r);
+            const int64_t beg = __ldg(out_ptr + r);
             const int64_t pr = beg + kRowCost * r;
             if (pr >= u1) break;
-            const int64_t end = __ldg(up_ptr + r + 1);
+            const int64_t end = __ldg(out_ptr + r + 1);
             const int64_t deg = end - beg;
-            if (deg > kChunk) {                             // long row: this chunk's part
+            if (deg > kChunk) {                             // long out-list: this chunk's part
                 const int64_t e0 = pr + kRowCost;
                 const int64_t a = beg + max((int64_t)0, u0 - e0);
                 const int64_t b = beg + min(deg, u1 - e0);
                 if (a < b) {
-                    int s[4] = {0, 0, 0, 0};
-                    for (int64_t base = a; base < b; base += 32) {
-                        const int64_t k = base + lane;
-                        const int cj = k < b ? __ldg(up_col + k) : 0;
-                        const int n = (int)min((int64_t)32, b - base);
-#pragma unroll 8
-                        for (int t = 0; t < n; ++t) add_y(__shfl_sync(kFull, cj, t), y8, y32, bslot, lane, s);
-                    }
-                    finish_pass2_row(r, __ldg(y8 + (size_t)r * 32 + lane), s, y32, bslot, lane, x3);
+                    const int64_t mid = beg + __ldg(nsmall + r);
+                    const int32_t slot = __ldg(bslot + r);
+                    const uint2 own = load_own(r, slot, y8l, y16l);
+                    sum_small(out_col, a, min(b, mid), y8l, lane, s);
+                    sum_mid(out_col, max(a, mid), b, y16l, lane, s);
+                    finish_pass2_row(own, slot, s, x3);
                 }
                 ++r;
                 continue;
@@ -521,17 +762,21 @@ __global__ void __launch_bounds__(kTriThreads) tri_pass2_kernel(
                 ++r;
                 continue;
             }
-            // rows owned by this chunk: row ends of 32 rows at a time in lanes,
-            // then each row's entries with an unrolled loop (no boundary tests)
+            // rows owned by this chunk: row ends, small-section lengths and
+            // slots of 32 rows at a time in lanes
             for (;;) {
                 const int64_t rr = r + lane;
-                int a0 = 0, a1 = 0;
+                int a0 = 0, a1 = 0, ns = 0, sl = -1;
                 bool ok = false;
                 if (rr < d) {
-                    const int64_t s0 = __ldg(up_ptr + rr), e0 = __ldg(up_ptr + rr + 1);
+                    const int64_t s0 = __ldg(out_ptr + rr), e0 = __ldg(out_ptr + rr + 1);
                     a0 = (int)s0;
                     a1 = (int)e0;
                     ok = (s0 + kRowCost * rr < u1) && (e0 - s0 <= kChunk);
+                    if (ok && e0 > s0) {
+                        ns = __ldg(nsmall + rr);
+                        sl = __ldg(bslot + rr);
+                    }
                 }
                 const unsigned okm = __ballot_sync(kFull, ok);
                 const int f = (okm == kFull) ? 32 : (__ffs(~okm) - 1);
@@ -539,35 +784,56 @@ __global__ void __launch_bounds__(kTriThreads) tri_pass2_kernel(
                     const int a = __shfl_sync(kFull, a0, cur);
                     const int b = __shfl_sync(kFull, a1, cur);
                     if (a == b) continue;
-                    const int64_t row = r + cur;
-                    const uint32_t own = __ldg(y8 + (size_t)row * 32 + lane);   // fetched before the entries
-                    int s[4] = {0, 0, 0, 0};
-                    for (int base = a; base < b; base += 32) {
-                        const int k = base + lane;
-                        const int cj = k < b ? __ldg(up_col + k) : 0;
-                        const int n = min(32, b - base);
-                        for (int t0 = 0; t0 < n; t0 += 8) {
-                            // 8 gathers issued before any is used: the escape branch in
-                            // acc_y would otherwise keep one load in flight per warp
-                            // (lanes past n read row 0, whose line is harmless to load)
-                            int jj[8];
-                            uint32_t w[8];
-#pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                jj[u] = __shfl_sync(kFull, cj, t0 + u);
-                                w[u] = __ldg(y8 + (size_t)jj[u] * 32 + lane);
-                            }
-#pragma unroll
-                            for (int u = 0; u < 8; ++u)
-                                if (t0 + u < n) acc_y(w[u], jj[u], y32, bslot, lane, s);
-                        }
-                    }
-                    finish_pass2_row(row, own, s, y32, bslot, lane, x3);
+                    const int m = a + __shfl_sync(kFull, ns, cur);
+                    const int32_t slot = __shfl_sync(kFull, sl, cur);
+                    const uint2 own = load_own(r + cur, slot, y8l, y16l);   // fetched before the entries
+                    sum_small(out_col, a, m, y8l, lane, s);
+                    sum_mid(out_col, m, b, y16l, lane, s);
+                    finish_pass2_row(own, slot, s, x3);
                 }
                 r += f;
                 if (f < 32) break;
             }
         }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (x3[q]) atomicAdd((unsigned long long*)&sx[4 * lane + q], (unsigned long long)(2 * x3[q]));
+    __syncthreads();
+    for (int t = threadIdx.x; t < kProbes; t += blockDim.x)
+        if (sx[t]) atomicAdd(xacc + 3 * t + 2, (unsigned long long)sx[t]);
+}
+
+// Pass 2 for the edges into huge rows: x3 += 2 y_i y_h per pair, a warp per pair.
+__global__ void __launch_bounds__(kTriThreads) tri_pairs_kernel(
+    const int4* __restrict__ pairs, int64_t npairs, const uint32_t* __restrict__ y8, const uint2* __restrict__ y16,
+    const int32_t* __restrict__ y32, unsigned long long* __restrict__ xacc)
+{
+    __shared__ long long sx[kProbes];
+    for (int t = threadIdx.x; t < kProbes; t += blockDim.x) sx[t] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    long long x3[4] = {0, 0, 0, 0};
+    for (int64_t p = warp; p < npairs; p += nwarps) {
+        const int4 pr = pairs[p];
+        int yi[4];
+        if (pr.x == kClassHuge) {
+            const int4 t = *reinterpret_cast<const int4*>(y32 + (size_t)pr.y * kProbes + 4 * lane);
+            yi[0] = t.x;
+            yi[1] = t.y;
+            yi[2] = t.z;
+            yi[3] = t.w;
+        } else {
+            const int32_t slot = pr.x == kClassSmall ? -1 : pr.y;
+            unpack_own(load_own(pr.y, slot, y8 + lane, y16 + lane), slot, yi);
+        }
+        const int4 h = *reinterpret_cast<const int4*>(y32 + (size_t)pr.z * kProbes + 4 * lane);
+        x3[0] += (long long)yi[0] * h.x;
+        x3[1] += (long long)yi[1] * h.y;
+        x3[2] += (long long)yi[2] * h.z;
+        x3[3] += (long long)yi[3] * h.w;
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q)
@@ -598,42 +864,47 @@ int tri_prepare(mlt_matrix* M, cudaStream_t s)
     const size_t dd = (size_t)std::max<int64_t>(d, 1);
     const int64_t nsb = (d + kScanBlock - 1) / kScanBlock;
     int rc;
-    // upper[d], up_ptr[d+1], crow1[nch1], crow2[nch1], scan sums[nsb], bslot[d], longlist[d], counters
-    if ((rc = M->ws_tri.ensure(dd * 8 + (dd + 1) * 8 + 2 * (size_t)nch1 * 8 + (size_t)(nsb + 1) * 8 +
-                               dd * 4 * 2 + 1024, s))) return rc;
+    // out_ptr[d+1], crow1[nch1], crow2[nch1], scan sums[nsb], nsmall[d], bslot[d], longlist[d], counters
+    if ((rc = M->ws_tri.ensure((dd + 1) * 8 + 2 * (size_t)nch1 * 8 + (size_t)(nsb + 1) * 8 + dd * 4 * 3 + 1024,
+                               s)))
+        return rc;
     char* base = M->ws_tri.as<char>();
-    int64_t* upper = reinterpret_cast<int64_t*>(base);
-    int64_t* up_ptr = upper + dd;
-    int64_t* crow1 = up_ptr + dd + 1;
+    int64_t* out_ptr = reinterpret_cast<int64_t*>(base);
+    int64_t* crow1 = out_ptr + dd + 1;
     int64_t* crow2 = crow1 + nch1;
     int64_t* bsum = crow2 + nch1;
-    int32_t* bslot = reinterpret_cast<int32_t*>(bsum + nsb + 1);
+    int32_t* nsmall = reinterpret_cast<int32_t*>(bsum + nsb + 1);
+    int32_t* bslot = nsmall + dd;
     int32_t* longlist = bslot + dd;
-    int* counters = reinterpret_cast<int*>(longlist + dd);
-    double* bound = reinterpret_cast<double*>(counters + 4);
+    // nbig, nlong, selfloop, npairs, pair cursor, then the bound and the chunk
+    // counters (16-byte aligned: the int32 arrays before it may end anywhere)
+    int* counters = reinterpret_cast<int*>((reinterpret_cast<uintptr_t>(longlist + dd) + 15) & ~(uintptr_t)15);
+    double* bound = reinterpret_cast<double*>(counters + 6);
     unsigned long long* chunk_ctr = reinterpret_cast<unsigned long long*>(bound + 1);
-    MLT_CUDA_TRY(cudaMemsetAsync(counters, 0, 4 * sizeof(int) + sizeof(double), s));
+    MLT_CUDA_TRY(cudaMemsetAsync(counters, 0, 6 * sizeof(int) + sizeof(double), s));
     {
         ProfScope ps("tri_prepare", s);
         tri_prepare_kernel<<<grid_for(M->num_sms, d), kTriThreads, 0, s>>>(
-            M->A.rowptr, M->A.col, d, upper, up_ptr, bslot, longlist, counters, bound);
+            M->A.rowptr, M->A.col, d, out_ptr, nsmall, bslot, longlist, counters, bound);
+        tri_prepare_long_kernel<<<2 * M->num_sms, kTriThreads, 0, s>>>(M->A.rowptr, M->A.col, longlist, out_ptr,
+                                                                       nsmall, counters, bound);
     }
     MLT_CUDA_TRY(cudaGetLastError());
     if (d > 0) {
         ProfScope ps("tri_scan", s);
-        scan_sums_kernel<<<(unsigned)nsb, 256, 0, s>>>(up_ptr, d, bsum);
-        scan_offsets_kernel<<<1, 1024, 0, s>>>(bsum, nsb, up_ptr + d);
-        scan_apply_kernel<<<(unsigned)nsb, 256, 0, s>>>(up_ptr, d, bsum);
+        scan_sums_kernel<<<(unsigned)nsb, 256, 0, s>>>(out_ptr, d, bsum);
+        scan_offsets_kernel<<<1, 1024, 0, s>>>(bsum, nsb, out_ptr + d);
+        scan_apply_kernel<<<(unsigned)nsb, 256, 0, s>>>(out_ptr, d, bsum);
     } else {
-        MLT_CUDA_TRY(cudaMemsetAsync(up_ptr, 0, sizeof(int64_t), s));
+        MLT_CUDA_TRY(cudaMemsetAsync(out_ptr, 0, sizeof(int64_t), s));
     }
     MLT_CUDA_TRY(cudaGetLastError());
     int hc[4] = {0, 0, 0, 0};
     double hb = 0.0;
-    int64_t nnz_up = 0;
+    int64_t nnz_out = 0;
     MLT_CUDA_TRY(cudaMemcpyAsync(hc, counters, sizeof(hc), cudaMemcpyDeviceToHost, s));
     MLT_CUDA_TRY(cudaMemcpyAsync(&hb, bound, sizeof(double), cudaMemcpyDeviceToHost, s));
-    MLT_CUDA_TRY(cudaMemcpyAsync(&nnz_up, up_ptr + d, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    MLT_CUDA_TRY(cudaMemcpyAsync(&nnz_out, out_ptr + d, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     MLT_CUDA_TRY(cudaStreamSynchronize(s));
     M->tri_bound = hb;
     if (hc[2]) {
@@ -644,13 +915,20 @@ int tri_prepare(mlt_matrix* M, cudaStream_t s)
         M->tri_state = MLT_ERANGE;
         return fail(MLT_ERANGE, "sum of deg_i*deg_j over edges reaches 2^62: x3 may overflow int64");
     }
-    if ((rc = M->ws_upcol.ensure((size_t)std::max<int64_t>(nnz_up, 1) * sizeof(int32_t), s))) return rc;
-    int32_t* up_col = M->ws_upcol.as<int32_t>();
-    const int64_t nch2 = std::max<int64_t>(1, (nnz_up + kRowCost * d + kChunk - 1) / kChunk);
+    const int64_t npairs = hc[3];
+    // out_col (16-byte aligned end) then the pair list
+    const size_t col_bytes = ((size_t)std::max<int64_t>(nnz_out, 1) * sizeof(int32_t) + 15) & ~(size_t)15;
+    if ((rc = M->ws_upcol.ensure(col_bytes + (size_t)std::max<int64_t>(npairs, 1) * sizeof(int4), s))) return rc;
+    int32_t* out_col = M->ws_upcol.as<int32_t>();
+    int4* pairs = reinterpret_cast<int4*>(M->ws_upcol.as<char>() + col_bytes);
+    const int64_t nch2 = std::max<int64_t>(1, (nnz_out + kRowCost * d + kChunk - 1) / kChunk);
     {
-        ProfScope ps("tri_fill_upper", s);
-        fill_upper_kernel<<<grid_for(M->num_sms, d), kTriThreads, 0, s>>>(M->A.rowptr, M->A.col, upper,
-                                                                          up_ptr, d, up_col);
+        ProfScope ps("tri_fill_out", s);
+        fill_out_kernel<<<grid_for(M->num_sms, d), kTriThreads, 0, s>>>(M->A.rowptr, M->A.col, d, out_ptr, nsmall,
+                                                                        bslot, out_col, pairs, hc[3], counters + 4);
+        if (hc[1] > 0)
+            fill_out_long_kernel<<<(unsigned)std::min<int64_t>(hc[1], 2LL * M->num_sms), kTriThreads, 0, s>>>(
+                M->A.rowptr, M->A.col, longlist, hc[1], out_ptr, nsmall, bslot, out_col, pairs, hc[3], counters + 4);
     }
     MLT_CUDA_TRY(cudaGetLastError());
     {
@@ -658,12 +936,14 @@ int tri_prepare(mlt_matrix* M, cudaStream_t s)
         const int g1 = (int)std::min<int64_t>((nch1 + 255) / 256, 16LL * M->num_sms);
         chunk_rows_kernel<<<std::max(g1, 1), 256, 0, s>>>(M->A.rowptr, d, nch1, crow1);
         const int g2 = (int)std::min<int64_t>((nch2 + 255) / 256, 16LL * M->num_sms);
-        chunk_rows_kernel<<<std::max(g2, 1), 256, 0, s>>>(up_ptr, d, nch2, crow2);
+        chunk_rows_kernel<<<std::max(g2, 1), 256, 0, s>>>(out_ptr, d, nch2, crow2);
     }
     MLT_CUDA_TRY(cudaGetLastError());
-    M->upper = upper;
-    M->tri.up_ptr = up_ptr;
-    M->tri.up_col = up_col;
+    M->tri.out_ptr = out_ptr;
+    M->tri.out_col = out_col;
+    M->tri.nsmall = nsmall;
+    M->tri.pairs = pairs;
+    M->tri.npairs = npairs;
     M->tri.crow1 = crow1;
     M->tri.crow2 = crow2;
     M->tri.bslot = bslot;
@@ -685,12 +965,15 @@ int tri_block(mlt_matrix* M, uint64_t seed, int64_t id0, int nb, int64_t* x_dev,
     const auto& T = M->tri;
     int rc;
     const size_t dd = (size_t)std::max<int64_t>(d, 1);
+    const size_t nbig = (size_t)std::max(T.nbig, 1);
     if ((rc = M->ws_z.ensure(dd * 4 * sizeof(uint32_t), s))) return rc;
     if ((rc = M->ws_y.ensure(dd * kProbes, s))) return rc;
-    if ((rc = M->ws_y32.ensure((size_t)std::max(T.nbig, 1) * kProbes * sizeof(int32_t), s))) return rc;
+    if ((rc = M->ws_y16.ensure(nbig * kProbes * sizeof(int16_t), s))) return rc;
+    if ((rc = M->ws_y32.ensure(nbig * kProbes * sizeof(int32_t), s))) return rc;
     if ((rc = M->ws_x.ensure((size_t)kProbes * 3 * sizeof(unsigned long long), s))) return rc;
     uint32_t* zb = M->ws_z.as<uint32_t>();
     uint32_t* y8 = M->ws_y.as<uint32_t>();
+    uint2* y16 = M->ws_y16.as<uint2>();
     int32_t* y32 = M->ws_y32.as<int32_t>();
     unsigned long long* xacc = M->ws_x.as<unsigned long long>();
     MLT_CUDA_TRY(cudaMemsetAsync(xacc, 0, (size_t)kProbes * 3 * sizeof(unsigned long long), s));
@@ -711,7 +994,7 @@ int tri_block(mlt_matrix* M, uint64_t seed, int64_t id0, int nb, int64_t* x_dev,
     {
         ProfScope ps("tri_pass1", s);
         tri_pass1_kernel<<<T.grid1, kTriThreads, 0, s>>>(M->A.rowptr, M->A.col, d, T.nch1, T.crow1, T.bslot,
-                                                         zb, y8, y32, xacc, T.counters);
+                                                         zb, y8, y16, y32, xacc, T.counters);
     }
     MLT_CUDA_TRY(cudaGetLastError());
     if (T.nlong > 0) {
@@ -719,13 +1002,19 @@ int tri_block(mlt_matrix* M, uint64_t seed, int64_t id0, int nb, int64_t* x_dev,
                                              4LL * M->num_sms);
         ProfScope ps("tri_long_rows", s);
         tri_long_rows_kernel<<<std::max(g, 1), kTriThreads, 0, s>>>(M->A.rowptr, T.longlist, T.nlong,
-                                                                    T.bslot, zb, y8, y32, xacc);
+                                                                    T.bslot, zb, y8, y16, y32, xacc);
     }
     MLT_CUDA_TRY(cudaGetLastError());
     {
         ProfScope ps("tri_pass2", s);
-        tri_pass2_kernel<<<T.grid2, kTriThreads, 0, s>>>(T.up_ptr, T.up_col, d, T.nch2, T.crow2, T.bslot,
-                                                         y8, y32, xacc, T.counters + 1);
+        tri_pass2_kernel<<<T.grid2, kTriThreads, 0, s>>>(T.out_ptr, T.out_col, T.nsmall, T.bslot, d, T.nch2,
+                                                         T.crow2, y8, y16, xacc, T.counters + 1);
+    }
+    MLT_CUDA_TRY(cudaGetLastError());
+    if (T.npairs > 0) {
+        const int g = (int)std::min<int64_t>((T.npairs * 32 + kTriThreads - 1) / kTriThreads, 4LL * M->num_sms);
+        ProfScope ps("tri_pairs", s);
+        tri_pairs_kernel<<<std::max(g, 1), kTriThreads, 0, s>>>(T.pairs, T.npairs, y8, y16, y32, xacc);
     }
     MLT_CUDA_TRY(cudaGetLastError());
     MLT_CUDA_TRY(cudaMemcpyAsync(x_dev, xacc, (size_t)nb * 3 * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));

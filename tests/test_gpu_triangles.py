@@ -123,3 +123,37 @@ def test_empty_and_tiny_graphs(L, O):
     with L.Matrix(tri) as G:
         est, se = G.triangles(2, 64, 200, x=x)
     assert np.array_equal(x, O.triangle_moments(tri, 2, 64, 200))
+
+
+def _undirected(d, u, v):
+    """Symmetric 0/1 CSR from undirected edges (u, v), duplicates and loops dropped."""
+    u, v = np.asarray(u, dtype=np.int64), np.asarray(v, dtype=np.int64)
+    keep = u != v
+    a, b = np.minimum(u, v)[keep], np.maximum(u, v)[keep]
+    key = np.unique(a * d + b)
+    a, b = key // d, key % d
+    return synth._from_coo(d, d, np.concatenate([a, b]), np.concatenate([b, a]), None)
+
+
+def test_degree_classes_and_huge_rows(L, O):
+    # every storage class of y in one graph: two adjacent hubs of degree
+    # > 32767 (int32 rows, edges into them on the pair list, one hub-to-hub
+    # pair), a 300-clique (int16 rows) and sparse leaves (int8 rows)
+    rng = np.random.default_rng(7)
+    d = 40_002
+    h1, h2 = d - 2, d - 1
+    l1 = rng.choice(40_000, 34_000, replace=False)
+    l2 = rng.choice(40_000, 34_000, replace=False)
+    clique = rng.choice(40_000, 300, replace=False)
+    cu, cv = np.triu_indices(300, 1)
+    su, sv = rng.integers(0, 40_000, 60_000), rng.integers(0, 40_000, 60_000)
+    g = _undirected(d, np.concatenate([[h1], np.full(l1.size, h1), np.full(l2.size, h2), clique[cu], su]),
+                    np.concatenate([[h2], l1, l2, clique[cv], sv]))
+    deg = np.diff(g.rowptr)
+    assert deg[h1] > 32767 and deg[h2] > 32767 and deg.max() > 127 and np.sum((deg > 127) & (deg <= 32767)) >= 300
+    x = np.zeros((160, 3), dtype=np.int64)
+    with L.Matrix(g) as G:
+        est, se = G.triangles(4, 250, 160, x=x)
+    assert np.array_equal(x, O.triangle_moments(g, 4, 250, 160))
+    er, sr, _, _ = O.triangle_estimate(x, g.nnz, True)
+    assert est == er and se == sr
