@@ -30,10 +30,11 @@
 //   pairs   : (class of i, row or slot of i, y32 slot of the huge target)
 // Work split: every row costs kRowCost "units" plus one per entry (all entries
 // in pass 1, out-entries in pass 2); the unit axis is cut into chunks of
-// kChunk units that warps of a persistent grid take from an atomic counter.
-// A row of degree <= kChunk is handled whole by the chunk holding its first
-// unit; consecutive such rows are walked with the row ends of 32 rows at a
-// time held in lanes.  Longer rows are cut at chunk edges: pass-1 counts are
+// kChunk units that warps of a persistent grid take from an atomic counter
+// (small chunks, so the last ones to finish leave little idle time).  A row of
+// degree <= kLongRow is handled whole by the chunk holding its first unit;
+// consecutive such rows are walked with the row ends of 32 rows at a time held
+// in lanes.  Longer rows are cut at chunk edges: pass-1 counts are
 // merged with integer atomics in y32 and finished by a per-row kernel; pass 2
 // is linear in the row sums, so a cut needs no merge.
 // All sums are integers (exact, independent of order).
@@ -52,10 +53,13 @@ constexpr int kProbes = 128;
 constexpr int kSmallDeg = 127;        // y of rows up to this degree fits int8
 constexpr int kMidDeg = 32767;        // ... int16; rows above it keep int32
 constexpr int64_t kRowCost = 4;       // units charged per row on top of its entries
-constexpr int64_t kChunk = 1024;      // units per dynamically scheduled chunk
+constexpr int64_t kChunk = 256;       // units per dynamically scheduled chunk
+constexpr int64_t kLongRow = 1024;    // rows above this degree are cut at chunk edges
+constexpr int kGather = 8;            // gathers each lane keeps in flight (divides 32)
 constexpr unsigned kFull = 0xFFFFFFFFu;
+static_assert(32 % kGather == 0, "a gather batch never crosses a 32-entry column block");
 constexpr int kScanBlock = 1024;      // elements per CTA of the prefix scan
-static_assert(kChunk <= kMidDeg, "rows handled whole by pass 1 must be small or mid");
+static_assert(kLongRow <= kMidDeg && kChunk <= kLongRow, "rows handled whole by pass 1 must be small or mid");
 
 enum RowClass { kClassSmall = 0, kClassMid = 1, kClassHuge = 2 };
 
@@ -112,7 +116,7 @@ __device__ __forceinline__ bool is_target(int64_t r, int64_t deg, int c, int64_t
     return dc > deg || (dc == deg && c > r);
 }
 
-// Rows of degree <= kChunk, a warp each: out-list lengths by class into
+// Rows of degree <= kLongRow, a warp each: out-list lengths by class into
 // outcnt (later scanned into out_ptr) and nsmall, the pair count, self-loop
 // detection, and the bound sum_j deg_i deg_j certifying that x3 fits in int64.
 // Every row gets its slot here (rows above kSmallDeg) and longer rows are
@@ -132,9 +136,9 @@ __global__ void tri_prepare_kernel(const int64_t* __restrict__ rowptr, const int
         const int64_t deg = end - beg;
         if (lane == 0) {
             bslot[r] = deg > kSmallDeg ? atomicAdd(counters + 0, 1) : -1;
-            if (deg > kChunk) longlist[atomicAdd(counters + 1, 1)] = (int32_t)r;
+            if (deg > kLongRow) longlist[atomicAdd(counters + 1, 1)] = (int32_t)r;
         }
-        if (deg > kChunk) continue;
+        if (deg > kLongRow) continue;
         int ns = 0, nm = 0, nh = 0;
         double dsum = 0.0;
         for (int64_t base = beg; base < end; base += 32) {
@@ -300,7 +304,7 @@ __device__ __forceinline__ int4 make_pair(int64_t r, int64_t deg, const int32_t*
     return make_int4(cl, cl == kClassSmall ? (int)r : bslot[r], target_slot, 0);
 }
 
-// Rows of degree <= kChunk, a warp each: the out-list of row r in neighbour
+// Rows of degree <= kLongRow, a warp each: the out-list of row r in neighbour
 // order, small targets (their row) before mid targets (their slot); targets of
 // class huge are appended to the pair list.
 __global__ void fill_out_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, int64_t d,
@@ -315,7 +319,7 @@ __global__ void fill_out_kernel(const int64_t* __restrict__ rowptr, const int32_
     for (int64_t r = warp; r < d; r += nwarps) {
         const int64_t beg = rowptr[r], end = rowptr[r + 1];
         const int64_t deg = end - beg;
-        if (deg > kChunk) continue;
+        if (deg > kLongRow) continue;
         const int64_t os = out_ptr[r], om = os + nsmall[r];
         int64_t cs = 0, cm = 0;
         for (int64_t base = beg; base < end; base += 32) {
@@ -340,7 +344,7 @@ __global__ void fill_out_kernel(const int64_t* __restrict__ rowptr, const int32_
     }
 }
 
-// The same for rows longer than kChunk, a CTA each (order kept across warps).
+// The same for rows longer than kLongRow, a CTA each (order kept across warps).
 __global__ void __launch_bounds__(kTriThreads) fill_out_long_kernel(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ longlist,
     int nlong, const int64_t* __restrict__ out_ptr, const int32_t* __restrict__ nsmall,
@@ -447,18 +451,29 @@ __device__ __forceinline__ void fold(uint32_t& packed, int cnt[4])
     packed = 0;
 }
 
-// Negative-sign counts over entries [a, b) of one row, for this lane's 4 probes.
+// Negative-sign counts over entries [a, b) of one row, for this lane's 4
+// probes.  kGather gathers are in flight before the first is used; lanes
+// past the end load nothing and add zero.
 __device__ __forceinline__ void count_negatives(const int32_t* __restrict__ col, int64_t a, int64_t b,
                                                 const uint32_t* __restrict__ zb, int lane, int cnt[4])
 {
+    const uint32_t* zbl = zb + (lane >> 3);
+    const int sh = lane & 7;
     uint32_t packed = 0;
     for (int64_t base = a; base < b; base += 32) {
         const int64_t k = base + lane;
         const int cj = k < b ? __ldg(col + k) : 0;
         const int n = (int)min((int64_t)32, b - base);
-#pragma unroll 8
-        for (int t = 0; t < n; ++t)
-            packed += sign_bytes(zb, __shfl_sync(kFull, cj, t), lane);
+        for (int t0 = 0; t0 < n; t0 += kGather) {
+            uint32_t w[kGather];
+#pragma unroll
+            for (int u = 0; u < kGather; ++u) {
+                const int j = __shfl_sync(kFull, cj, t0 + u);
+                w[u] = t0 + u < n ? __ldg(zbl + (size_t)j * 4) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < kGather; ++u) packed += (w[u] >> sh) & 0x01010101u;
+        }
         fold(packed, cnt);
     }
 }
@@ -507,7 +522,7 @@ __device__ __forceinline__ void flush_x(long long (*sx)[kProbes], int which, con
 }
 
 // Pass 1: y = A z for 128 probes, plus x1 = z.y and x2 = y.y (rows of degree
-// <= kChunk; longer rows only accumulate their counts here).
+// <= kLongRow; longer rows only accumulate their counts here).
 __global__ void __launch_bounds__(kTriThreads) tri_pass1_kernel(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, int64_t d, int64_t nch,
     const int64_t* __restrict__ crow, const int32_t* __restrict__ bslot,
@@ -529,7 +544,7 @@ __global__ void __launch_bounds__(kTriThreads) tri_pass1_kernel(
             if (pr >= u1) break;
             const int64_t end = __ldg(rowptr + r + 1);
             const int64_t deg = end - beg;
-            if (deg > kChunk) {                             // long row: this chunk's part
+            if (deg > kLongRow) {                           // long row: this chunk's part
                 const int64_t e0 = pr + kRowCost;
                 const int64_t a = beg + max((int64_t)0, u0 - e0);
                 const int64_t b = beg + min(deg, u1 - e0);
@@ -558,7 +573,7 @@ __global__ void __launch_bounds__(kTriThreads) tri_pass1_kernel(
                     const int64_t s0 = __ldg(rowptr + rr), e0 = __ldg(rowptr + rr + 1);
                     a0 = (int)s0;
                     a1 = (int)e0;
-                    ok = (s0 + kRowCost * rr < u1) && (e0 - s0 <= kChunk);
+                    ok = (s0 + kRowCost * rr < u1) && (e0 - s0 <= kLongRow);
                 }
                 const unsigned okm = __ballot_sync(kFull, ok);
                 const int f = (okm == kFull) ? 32 : (__ffs(~okm) - 1);
@@ -569,16 +584,7 @@ __global__ void __launch_bounds__(kTriThreads) tri_pass1_kernel(
                     const int64_t row = r + cur;
                     const uint32_t own = sign_bytes(zb, row, lane);   // fetched before the entries
                     int cnt[4] = {0, 0, 0, 0};
-                    uint32_t packed = 0;
-                    for (int base = a; base < b; base += 32) {
-                        const int k = base + lane;
-                        const int cj = k < b ? __ldg(col + k) : 0;
-                        const int n = min(32, b - base);
-#pragma unroll 8
-                        for (int t = 0; t < n; ++t)
-                            packed += sign_bytes(zb, __shfl_sync(kFull, cj, t), lane);
-                        fold(packed, cnt);
-                    }
+                    count_negatives(col, a, b, zb, lane, cnt);
                     finish_pass1_row(row, b - a, cnt, own, bslot, y8, y16, y32, lane, x1, x2);
                 }
                 r += f;
@@ -630,8 +636,8 @@ __global__ void __launch_bounds__(kTriThreads) tri_long_rows_kernel(
 // ---- pass 2 ------------------------------------------------------------------
 
 // s += y of the small targets (rows) listed in col[a, b), this lane's 4
-// probes; y8l = y8 + lane.  Eight gathers are in flight before the first is
-// used; lanes past the end load nothing and add zero.
+// probes; y8l = y8 + lane.  kGather gathers are in flight before the first
+// is used; lanes past the end load nothing and add zero.
 __device__ __forceinline__ void sum_small(const int32_t* __restrict__ col, int64_t a, int64_t b,
                                           const uint32_t* __restrict__ y8l, int lane, int s[4])
 {
@@ -639,15 +645,15 @@ __device__ __forceinline__ void sum_small(const int32_t* __restrict__ col, int64
         const int64_t k = base + lane;
         const int cj = k < b ? __ldg(col + k) : 0;
         const int n = (int)min((int64_t)32, b - base);
-        for (int t0 = 0; t0 < n; t0 += 8) {
-            uint32_t w[8];
+        for (int t0 = 0; t0 < n; t0 += kGather) {
+            uint32_t w[kGather];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < kGather; ++u) {
                 const int j = __shfl_sync(kFull, cj, t0 + u);
                 w[u] = t0 + u < n ? __ldg(y8l + (size_t)j * 32) : 0u;
             }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < kGather; ++u) {
                 s[0] = __dp4a((int)w[u], 0x00000001, s[0]);
                 s[1] = __dp4a((int)w[u], 0x00000100, s[1]);
                 s[2] = __dp4a((int)w[u], 0x00010000, s[2]);
@@ -665,15 +671,15 @@ __device__ __forceinline__ void sum_mid(const int32_t* __restrict__ col, int64_t
         const int64_t k = base + lane;
         const int cj = k < b ? __ldg(col + k) : 0;
         const int n = (int)min((int64_t)32, b - base);
-        for (int t0 = 0; t0 < n; t0 += 8) {
-            uint2 w[8];
+        for (int t0 = 0; t0 < n; t0 += kGather) {
+            uint2 w[kGather];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < kGather; ++u) {
                 const int j = __shfl_sync(kFull, cj, t0 + u);
                 w[u] = t0 + u < n ? __ldg(y16l + (size_t)j * 32) : make_uint2(0u, 0u);
             }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < kGather; ++u) {
                 s[0] = __dp2a_lo((int)w[u].x, 0x0001, s[0]);
                 s[1] = __dp2a_lo((int)w[u].x, 0x0100, s[1]);
                 s[2] = __dp2a_lo((int)w[u].y, 0x0001, s[2]);
@@ -717,8 +723,8 @@ __device__ __forceinline__ void finish_pass2_row(uint2 own, int32_t slot, int s[
 }
 
 // Pass 2: x3 = 2 sum_i y_i sum_{j in out(i)} y_j over the oriented out-lists
-// (|s| <= kChunk * kMidDeg < 2^31: a row part never holds more than kChunk
-// entries and every main target is small or mid).
+// (|s| <= kLongRow * kMidDeg < 2^31: a row part never holds more than
+// kLongRow entries and every main target is small or mid).
 __global__ void __launch_bounds__(kTriThreads) tri_pass2_kernel(
     const int64_t* __restrict__ out_ptr, const int32_t* __restrict__ out_col, const int32_t* __restrict__ nsmall,
     const int32_t* __restrict__ bslot, int64_t d, int64_t nch, const int64_t* __restrict__ crow,
@@ -743,7 +749,7 @@ __global__ void __launch_bounds__(kTriThreads) tri_pass2_kernel(
             if (pr >= u1) break;
             const int64_t end = __ldg(out_ptr + r + 1);
             const int64_t deg = end - beg;
-            if (deg > kChunk) {                             // long out-list: this chunk's part
+            if (deg > kLongRow) {                           // long out-list: this chunk's part
                 const int64_t e0 = pr + kRowCost;
                 const int64_t a = beg + max((int64_t)0, u0 - e0);
                 const int64_t b = beg + min(deg, u1 - e0);
@@ -772,7 +778,7 @@ __global__ void __launch_bounds__(kTriThreads) tri_pass2_kernel(
                     const int64_t s0 = __ldg(out_ptr + rr), e0 = __ldg(out_ptr + rr + 1);
                     a0 = (int)s0;
                     a1 = (int)e0;
-                    ok = (s0 + kRowCost * rr < u1) && (e0 - s0 <= kChunk);
+                    ok = (s0 + kRowCost * rr < u1) && (e0 - s0 <= kLongRow);
                     if (ok && e0 > s0) {
                         ns = __ldg(nsmall + rr);
                         sl = __ldg(bslot + rr);

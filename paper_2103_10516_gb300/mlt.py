@@ -32,7 +32,11 @@ MLT_COST = {"symmetric": 0, "linear": 1}
 
 EXPORTS = ["mlt_create_csr", "mlt_destroy", "mlt_matrix_info", "mlt_spectrum_bounds",
            "mlt_cheb_coeffs", "mlt_moments", "mlt_mlmc_default_params", "mlt_mlmc_estimate",
-           "mlt_triangle_trace", "mlt_profile_start", "mlt_profile_stop", "mlt_last_error"]
+           "mlt_triangle_trace", "mlt_profile_start", "mlt_profile_stop", "mlt_last_error",
+           "mlt_surrogate_create", "mlt_surrogate_destroy", "mlt_surrogate_set_params",
+           "mlt_surrogate_get_params", "mlt_surrogate_loss_grad", "mlt_surrogate_train",
+           "mlt_surrogate_predict", "mlt_learned_train", "mlt_learned_estimate",
+           "mlt_moments_batched", "mlt_autotune", "mlt_moments_noalloc"]
 
 
 class MLTError(RuntimeError):
@@ -94,6 +98,9 @@ def lib():
     L.mlt_profile_stop.argtypes = [ctypes.POINTER(mlt_kernel_stat), ci, ctypes.POINTER(ci)]
     L.mlt_last_error.argtypes = []
     L.mlt_last_error.restype = ctypes.c_char_p
+    _bind_learned(L)
+    _bind_batch(L)
+    _bind_noalloc(L)
     for name in EXPORTS:
         if name not in ("mlt_mlmc_default_params", "mlt_last_error"):
             getattr(L, name).restype = ci
@@ -328,25 +335,6 @@ def _bind_learned(L):
                                     ctypes.POINTER(dbl)]
     L.mlt_learned_estimate.argtypes = [vp, vp, ctypes.POINTER(mlt_learned_params),
                                        ctypes.POINTER(mlt_mlmc_result)]
-    for name in ("mlt_surrogate_create", "mlt_surrogate_destroy", "mlt_surrogate_set_params",
-                 "mlt_surrogate_get_params", "mlt_surrogate_loss_grad", "mlt_surrogate_train",
-                 "mlt_surrogate_predict", "mlt_learned_train", "mlt_learned_estimate"):
-        getattr(L, name).restype = ci
-
-
-EXPORTS += ["mlt_surrogate_create", "mlt_surrogate_destroy", "mlt_surrogate_set_params",
-            "mlt_surrogate_get_params", "mlt_surrogate_loss_grad", "mlt_surrogate_train",
-            "mlt_surrogate_predict", "mlt_learned_train", "mlt_learned_estimate"]
-
-_lib_plain = lib
-
-
-def lib():  # noqa: F811  (extends the loader with the learned-level symbols)
-    L = _lib_plain()
-    if not getattr(L, "_learned_bound", False):
-        _bind_learned(L)
-        L._learned_bound = True
-    return L
 
 
 def pack_params(P):
@@ -469,21 +457,11 @@ class mlt_moments_job(ctypes.Structure):
                 ("ld_mu", ctypes.c_int64), ("group_width", ctypes.c_int)]
 
 
-EXPORTS += ["mlt_moments_batched", "mlt_autotune"]
-_lib_learned = lib
-
-
-def lib():  # noqa: F811  (extends the loader with the batching symbols)
-    L = _lib_learned()
-    if not getattr(L, "_batch_bound", False):
-        L.mlt_moments_batched.argtypes = [ctypes.POINTER(mlt_moments_job), ctypes.c_int, ctypes.c_int,
-                                          ctypes.c_uint, ctypes.c_void_p]
-        L.mlt_moments_batched.restype = ctypes.c_int
-        L.mlt_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
-                                   ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]
-        L.mlt_autotune.restype = ctypes.c_int
-        L._batch_bound = True
-    return L
+def _bind_batch(L):
+    L.mlt_moments_batched.argtypes = [ctypes.POINTER(mlt_moments_job), ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_uint, ctypes.c_void_p]
+    L.mlt_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                               ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]
 
 
 def mlt_moments_batched(jobs, precision="fp64", flags=0, stream=None):
@@ -518,19 +496,10 @@ def mlt_autotune(handle, precision="fp64", trial_steps=8, stream=None):
 # moments without device allocation (fixed 32 MiB array inside the library)
 # ---------------------------------------------------------------------------
 
-EXPORTS += ["mlt_moments_noalloc"]
-_lib_batch = lib
-
-
-def lib():  # noqa: F811  (extends the loader with the no-allocation symbol)
-    L = _lib_batch()
-    if not getattr(L, "_noalloc_bound", False):
-        vp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
-        L.mlt_moments_noalloc.argtypes = [i64, i64, vp, vp, vp, dbl, dbl, dbl, ctypes.c_uint64, i64,
-                                          ctypes.c_int, vp, vp, i64, vp]
-        L.mlt_moments_noalloc.restype = ctypes.c_int
-        L._noalloc_bound = True
-    return L
+def _bind_noalloc(L):
+    vp, i64, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+    L.mlt_moments_noalloc.argtypes = [i64, i64, vp, vp, vp, dbl, dbl, dbl, ctypes.c_uint64, i64,
+                                      ctypes.c_int, vp, vp, i64, vp]
 
 
 def mlt_moments_noalloc(d, nnz, rowptr, col, vals, scale, a, b, seed, probe_offset, degrees, mu,
