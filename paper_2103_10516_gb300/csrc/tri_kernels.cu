@@ -478,6 +478,61 @@ __device__ __forceinline__ void count_negatives(const int32_t* __restrict__ col,
     }
 }
 
+// The same counts, bit-sliced, for spans of at least kSliceMin entries (and
+// at most kLongRow).  Lane l takes entry l/4 of every batch of 8 entries and
+// sign word l%4 of it (32 probes), and counts each of the 32 bit positions in
+// eight bit planes: bit t of c[p] is bit p of position t's count (a lane sees
+// at most kLongRow/8 = 128 words, so eight planes never overflow).  Adding a
+// word is a ripple-carry increment, 16 bitwise operations for 32 probes.
+// The eight entry slots are then summed lane against lane with a bit-sliced
+// adder (totals <= 1024 need 11 planes), and each lane reads its own four
+// probes out of the planes of word l/8.
+constexpr int kSliceMin = 16;
+static_assert(kLongRow / 8 <= 255 && kLongRow <= 2047, "plane counts of the sliced counter");
+
+__device__ __forceinline__ void count_negatives_sliced(const int32_t* __restrict__ col, int64_t a, int64_t b,
+                                                       const uint32_t* __restrict__ zb, int lane, int cnt[4])
+{
+    uint32_t c[11];
+#pragma unroll
+    for (int p = 0; p < 11; ++p) c[p] = 0u;
+    const int slot = lane >> 2, w = lane & 3;
+    for (int64_t base = a; base < b; base += 8) {
+        const int64_t k = base + slot;
+        uint32_t x = 0u;
+        if (k < b) x = __ldg(zb + (size_t)__ldg(col + k) * 4 + w);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            const uint32_t t = c[p] & x;
+            c[p] ^= x;
+            x = t;
+        }
+    }
+#pragma unroll
+    for (int m = 4; m <= 16; m <<= 1) {
+        uint32_t carry = 0u;
+#pragma unroll
+        for (int p = 0; p < 11; ++p) {
+            const uint32_t o = __shfl_xor_sync(kFull, c[p], m);
+            const uint32_t sum = c[p] ^ o ^ carry;
+            carry = (c[p] & o) | (carry & (c[p] ^ o));
+            c[p] = sum;
+        }
+    }
+    const int src = lane >> 3, sh = lane & 7;
+    uint32_t lo = 0u, hi = 0u;   // 16-bit lanes: probes q = 0, 2 and q = 1, 3
+#pragma unroll
+    for (int p = 0; p < 11; ++p) {
+        const uint32_t t = (__shfl_sync(kFull, c[p], src) >> sh) & 0x01010101u;
+        lo += (t & 0x00010001u) << p;
+        hi += ((t >> 8) & 0x00010001u) << p;
+    }
+    cnt[0] += (int)(lo & 0xFFFFu);
+    cnt[1] += (int)(hi & 0xFFFFu);
+    cnt[2] += (int)(lo >> 16);
+    cnt[3] += (int)(hi >> 16);
+}
+
 // Store y for probes 4*lane .. 4*lane+3 of row r (degree deg, slot if deg >
 // kSmallDeg) in its class's array, and add its x1, x2 terms.
 __device__ __forceinline__ void store_row(int64_t r, int64_t deg, const int yv[4], uint32_t own, int32_t slot,
@@ -550,7 +605,8 @@ __global__ void __launch_bounds__(kTriThreads) tri_pass1_kernel(
                 const int64_t b = beg + min(deg, u1 - e0);
                 if (a < b) {
                     int cnt[4] = {0, 0, 0, 0};
-                    count_negatives(col, a, b, zb, lane, cnt);
+                    if (b - a >= kSliceMin) count_negatives_sliced(col, a, b, zb, lane, cnt);
+                    else count_negatives(col, a, b, zb, lane, cnt);
                     int32_t* acc = y32 + (size_t)__ldg(bslot + r) * kProbes + 4 * lane;
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
@@ -584,7 +640,8 @@ __global__ void __launch_bounds__(kTriThreads) tri_pass1_kernel(
                     const int64_t row = r + cur;
                     const uint32_t own = sign_bytes(zb, row, lane);   // fetched before the entries
                     int cnt[4] = {0, 0, 0, 0};
-                    count_negatives(col, a, b, zb, lane, cnt);
+                    if (b - a >= kSliceMin) count_negatives_sliced(col, a, b, zb, lane, cnt);
+                    else count_negatives(col, a, b, zb, lane, cnt);
                     finish_pass1_row(row, b - a, cnt, own, bslot, y8, y16, y32, lane, x1, x2);
                 }
                 r += f;
