@@ -2,7 +2,9 @@
 """Throughput benchmark of the multilevel Chebyshev-Hutchinson engine on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload rmat20_triangles|logdet64|estrada_rmat22]
+                    [--workload rmat20_triangles|logdet64|estrada_rmat22|diffusion64_batched|
+                                nuclear_gram|stencil3d|estrada_learned]
+                    [--precision fp32|fp64|mixed] [--scale S]
 
 One step is one pass of the whole hot path over one batch of synthetic input:
 
@@ -16,6 +18,18 @@ One step is one pass of the whole hot path over one batch of synthetic input:
   estrada_rmat22: FP32 Chebyshev moments of the scale-22 R-MAT adjacency
       scaled to spectral radius <= 10 (interval [-10, 10]), 256 probes to
       degree 128.  Units: probe-matvecs (64 per probe).
+  diffusion64_batched: FP64 log-det level moments of 64 3D diffusion
+      operators (10^3 .. 100^3 grids) in one CUDA-graph launch.  Units:
+      probe-matvecs summed over the matrices.
+  nuclear_gram: moments of X^T X (X 2^18 x 2^16, density 1e-4) for the
+      nuclear norm, 512 probes to degree 512, in the --precision given.
+      Units: probe-matvecs (X then X^T).
+  stencil3d: moments of the 7-point 3D diffusion operator on a 100^3 grid,
+      128 probes to degree 128, in the --precision given (fp32 default): the
+      streaming case of the fused step.
+  estrada_learned: the learned coarse level (BF16 network, FP32 moments)
+      against plain FP64 MLMC at equal standard error on the Estrada index of
+      an R-MAT graph (scale 22 unless --scale); the comparison is in config.
 
 Under torchrun every rank runs its own probes (disjoint probe ids): weak
 scaling with no collective on the data path; the timing is the max over ranks.
@@ -39,6 +53,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# FP64 (non-tensor) rate of a GB300, nominal: the denominator of the FP64
+# recurrence, which is bound by FP64 arithmetic on this part, not by HBM
+FP64_TFLOPS_NOMINAL = 1.25
+
+
+def step_flops(d, nnz, probe_matvecs):
+    """Algorithmic FP64 flops of a step's recurrence: 2 per stored entry (one
+    FMA) and 8 per vector entry (the update and both dot products) per
+    probe-matvec."""
+    return probe_matvecs * (2 * nnz + 8 * d)
 
 
 def load_peaks():
@@ -260,6 +284,10 @@ class LogDet64:
     def kernel_bytes(self, launches_per_step):
         return step_bytes(self.d, self.nnz, 12, 8, self.units(), launches_per_step)
 
+    def kernel_flops(self, launches_per_step):
+        n = launches_per_step.get("cheb_step")
+        return {"cheb_step": step_flops(self.d, self.nnz, self.units()) / n} if n else {}
+
     def setup(self, mlt, torch, rank):
         self.M = mlt.Matrix(self.csr)
         self.flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
@@ -361,12 +389,463 @@ class EstradaRmat22:
 
     def cpu_sample(self, oracle, nprobes, offset):
         if self.scale is None:
-            self.scale = 10.0 / oracle.gershgorin(self.csr)[1]
+            self.scale = 10.0 / gershgorin_upper(self.csr)
         deg = np.full(nprobes, 16, dtype=np.int32)
         oracle.moments(self.csr, -10.0, 10.0, 0, offset, deg, scale=self.scale)
         return nprobes * 16      # the oracle runs direct: one matvec per degree
 
-WORKLOADS = {c.name: c for c in (Triangles, LogDet64, EstradaRmat22)}
+def gershgorin_upper(c):
+    """max_i (a_ii + sum_{j != i} |a_ij|): an upper bound on the spectrum of a
+    symmetric CSR (the CPU arms' interval; the GPU arm asks the library)."""
+    rows = np.repeat(np.arange(c.nrows), np.diff(c.rowptr))
+    v = np.ones(c.nnz) if c.val is None else np.asarray(c.val, dtype=np.float64)
+    diag = rows == c.col
+    r = np.bincount(rows, weights=np.where(diag, v, np.abs(v)), minlength=c.nrows)
+    return float(r.max())
+
+
+def gram_upper(x):
+    """||X||_1 ||X||_inf >= ||X^T X||_2."""
+    v = np.abs(np.asarray(x.val, dtype=np.float64))
+    rows = np.repeat(np.arange(x.nrows), np.diff(x.rowptr))
+    return float(np.bincount(rows, weights=v, minlength=x.nrows).max() *
+                 np.bincount(x.col, weights=v, minlength=x.ncols).max())
+
+
+class Diffusion64Batched:
+    """64 log-det moment jobs in one CUDA-graph launch (mlt_moments_batched).
+
+    Matrix i is the 7-point 3D diffusion operator on an s_i^3 grid, s_i =
+    round(10 * 10^(i/63)) (10 .. 100), lognormal cell coefficients (seed i)
+    and a diagonal shift drawn from U[0.01, 1]; interval [shift, Gershgorin
+    upper bound]; f = log.  Even i: levels {16, 64, 256} with {64, 16, 4}
+    probes; odd i: {16, 48, 128, 256} with {64, 32, 8, 4}.  FP64."""
+    name = "diffusion64_batched"
+    unit = "probe-matvecs/s"
+    dtype = "f64"
+    NMAT = 64
+
+    def __init__(self):
+        from paper_2103_10516_gb300 import synth
+        self.mats, self.shift, self.deg = [], [], []
+        for i in range(self.NMAT):
+            side = int(round(10 * 10 ** (i / 63)))
+            sh = float(np.random.default_rng(1000 + i).uniform(0.01, 1.0))
+            self.mats.append(synth.diffusion_3d(side, sigma=1.0, shift=sh, seed=i))
+            self.shift.append(sh)
+            lv, m = ([16, 64, 256], [64, 16, 4]) if i % 2 == 0 else ([16, 48, 128, 256], [64, 32, 8, 4])
+            self.deg.append(np.repeat(np.array(lv, dtype=np.int32), m))
+        self.d = sum(c.nrows for c in self.mats)
+        self.nnz = sum(c.nnz for c in self.mats)
+        self.widths = [0] * self.NMAT
+        self.seq_ms = None
+
+    def units(self):
+        return int(sum(int(np.sum((dg + 1) // 2)) for dg in self.deg))
+
+    def config(self):
+        return {"workload": self.name, "matrices": self.NMAT,
+                "grid_sides": [self.mats[0].nrows and round(self.mats[0].nrows ** (1 / 3)),
+                               round(self.mats[-1].nrows ** (1 / 3))],
+                "sum_d": self.d, "sum_nnz": self.nnz, "f": "log",
+                "probes_per_matrix": [int(self.deg[0].size), int(self.deg[1].size)],
+                "group_widths": sorted(set(self.widths)),
+                "sequential_ms_per_step": self.seq_ms,
+                "l2": "inputs larger than L2 (sum of matrices %.0f MB)" % ((12 * self.nnz + 8 * self.d) * 1e-6)}
+
+    def _launches(self, dg, width):
+        """Recurrence launches of one job: probes sorted by degree, cut into
+        equal groups of at most `width`, each running to its top degree."""
+        dg = np.sort(dg)[::-1]
+        ng = -(-dg.size // width)
+        gs = -(-dg.size // ng)
+        return int(sum((int(dg[g0]) + 1) // 2 for g0 in range(0, dg.size, gs)))
+
+    def kernel_bytes(self, launches_per_step):
+        return {}
+
+    def graph_step(self):
+        """(algorithmic bytes, kernel launches) of one step's graph: per job,
+        the recurrence launches stream the matrix once each and every live
+        probe's V rows (3 x 8 B); per probe group there is also one probe
+        initialisation, one finalisation and a reduction every 16 steps."""
+        byt, launches = 0, 0
+        for c, dg, w in zip(self.mats, self.deg, self.widths):
+            L = self._launches(dg, w if w > 0 else 1024)
+            byt += L * (12 * c.nnz + 8 * (c.nrows + 1)) + 24 * c.nrows * int(np.sum((dg + 1) // 2))
+            d = np.sort(dg)[::-1]
+            width = w if w > 0 else 1024
+            ng = -(-d.size // width)
+            gs = -(-d.size // ng)
+            for g0 in range(0, d.size, gs):
+                K = (int(d[g0]) + 1) // 2
+                launches += K + 2 + -(-K // 16)
+        return byt, launches
+
+    def graph_flops(self):
+        return sum(step_flops(c.nrows, c.nnz, int(np.sum((dg + 1) // 2))) for c, dg in zip(self.mats, self.deg))
+
+    def _jobs(self, handles, outs, i):
+        return [{"matrix": h.handle, "a": self.shift[k], "b": self.b[k], "seed": 7, "probe_offset": i * 128,
+                 "degrees": self.deg[k], "out": outs[k], "group_width": self.widths[k]}
+                for k, h in enumerate(handles)]
+
+    def setup(self, mlt, torch, rank):
+        self.M = [mlt.Matrix(c) for c in self.mats]
+        self.b = [M.bounds()[1] for M in self.M]
+        self.widths = [mlt.mlt_autotune(M.handle, "fp64", 4) for M in self.M]
+        self.out = [torch.empty((dg.size, 257), dtype=torch.float64, device="cuda") for dg in self.deg]
+        self.base = rank * (1 << 20)
+        # the same 64 jobs as separate calls, for comparison (untimed setup)
+        stream = torch.cuda.current_stream()
+        for rep in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k, M in enumerate(self.M):
+                mlt.mlt_moments(M.handle, self.shift[k], self.b[k], 7, (self.base + rep) * 128, self.deg[k],
+                                out=self.out[k], stream=stream.cuda_stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            self.seq_ms = round(e0.elapsed_time(e1), 3)
+
+    def step(self, mlt, stream, i):
+        mlt.mlt_moments_batched(self._jobs(self.M, self.out, self.base + i % 4096), "fp64", stream=stream)
+
+    def e2e_setup(self, torch):
+        self.h = [(torch.from_numpy(c.rowptr).pin_memory(), torch.from_numpy(c.col).pin_memory(),
+                   torch.from_numpy(c.val).pin_memory()) for c in self.mats]
+        self.h_out = [torch.empty((dg.size, 257), dtype=torch.float64).pin_memory() for dg in self.deg]
+        h2d = sum(r.numel() * 8 + c.numel() * 4 + v.numel() * 8 for r, c, v in self.h)
+        return h2d, sum(o.numel() * 8 for o in self.h_out)
+
+    def e2e_step(self, mlt, stream, i):
+        hs = [mlt.mlt_create_csr(c.nrows, c.nrows, c.nnz, r, col, v, stream=stream)
+              for c, (r, col, v) in zip(self.mats, self.h)]
+        try:
+            jobs = [{"matrix": h, "a": self.shift[k], "b": self.b[k], "seed": 7, "probe_offset": i * 128,
+                     "degrees": self.deg[k], "out": self.h_out[k], "group_width": self.widths[k]}
+                    for k, h in enumerate(hs)]
+            mlt.mlt_moments_batched(jobs, "fp64", stream=stream)
+        finally:
+            for h in hs:
+                mlt.mlt_destroy(h)
+
+    def cpu_sample(self, oracle, nprobes, offset):
+        # every matrix, nprobes probes to degree 8 each (the oracle runs the
+        # direct recurrence: one matvec per degree)
+        if not hasattr(self, "b_cpu"):
+            self.b_cpu = [gershgorin_upper(c) for c in self.mats]
+        deg = np.full(nprobes, 8, dtype=np.int32)
+        for c, sh, b in zip(self.mats, self.shift, self.b_cpu):
+            oracle.moments(c, sh, b, 7, offset, deg)
+        return self.NMAT * int(np.sum(deg))
+
+
+class NuclearGram:
+    """Chebyshev moments of A = X^T X for the nuclear norm (f = sqrt):
+    X has 2^18 rows and 2^16 columns, each entry nonzero with probability
+    1e-4, N(0,1) values (seed 0); the interval comes from 50 Lanczos steps on
+    X^T X; 512 probes to degree 512.  A probe-matvec applies X and then X^T.
+    Precision: fp32 (vectors FP32, dots FP64; default), fp64, or mixed
+    (FP32 for the first 128 steps, then FP64)."""
+    name = "nuclear_gram"
+    unit = "probe-matvecs/s"
+    NPROBES = 512
+    DEG = 512
+
+    def __init__(self, precision=None):
+        from paper_2103_10516_gb300 import synth
+        self.X = synth.sparse_gaussian(1 << 18, 1 << 16, 1e-4, seed=0)
+        self.d = self.X.ncols
+        self.nnz = self.X.nnz
+        self.precision = precision or "fp32"
+        self.dtype = {"fp32": "f32", "fp64": "f64", "mixed": "f32+f64"}[self.precision]
+        self.drift = None
+
+    def _prec(self, mlt):
+        return mlt.mixed_at(128) if self.precision == "mixed" else self.precision
+
+    def units(self):
+        return self.NPROBES * ((self.DEG + 1) // 2)
+
+    def config(self):
+        return {"workload": self.name, "X": "2^18 x 2^16, density 1e-4, N(0,1) values, seed 0",
+                "nnz": self.nnz, "operator": "X^T X (two SpMMs per step)", "f": "sqrt",
+                "probes": self.NPROBES, "degree": self.DEG, "precision": self.precision,
+                "interval": getattr(self, "ab", None), "group_width": getattr(self, "group_width", None),
+                "max_abs_dmu_vs_fp64_over_d": self.drift,
+                "l2": "inputs larger than L2 per step (V blocks 2 x %.0f MB, X and X^T %.0f MB)"
+                      % (self.d * self.NPROBES * (8 if self.precision == "fp64" else 4) * 1e-6,
+                         2 * 12 * self.nnz * 1e-6)}
+
+    def kernel_bytes(self, launches_per_step):
+        """Per launch of each SpMM: its matrix once, and per live probe the
+        gathered vector read once and the output written (X V -> W: V read, W
+        written; X^T W -> V_{k+1}: W, V_k and V_{k-1} read, V_{k+1} written)."""
+        sv = 8 if self.precision == "fp64" else 4
+        m, n, nnz = self.X.nrows, self.X.ncols, self.nnz
+        out = {}
+        pm = self.units()
+        if launches_per_step.get("gram_spmm"):
+            L = launches_per_step["gram_spmm"]
+            out["gram_spmm"] = (12 * nnz + 8 * (m + 1)) + (n + m) * sv * pm / L
+        if launches_per_step.get("cheb_step"):
+            L = launches_per_step["cheb_step"]
+            out["cheb_step"] = (12 * nnz + 8 * (n + 1)) + (m + 3 * n) * sv * pm / L
+        return out
+
+    def setup(self, mlt, torch, rank):
+        self.M = mlt.Matrix(self.X, gram=True)
+        self.ab = [round(v, 6) for v in mlt.mlt_spectrum_bounds(self.M.handle, mlt.MLT_BOUNDS_LANCZOS, 50, 0)]
+        self.group_width = mlt.mlt_autotune(self.M.handle, "fp32" if self.precision != "fp64" else "fp64", 4)
+        self.out = torch.empty((self.NPROBES, self.DEG + 1), dtype=torch.float64, device="cuda")
+        self.deg = np.full(self.NPROBES, self.DEG, dtype=np.int32)
+        self.base = rank * (1 << 24)
+        if self.precision != "fp64":
+            # drift of this precision against FP64 on 32 probes (untimed)
+            deg = self.deg[:32]
+            lo = mlt.mlt_moments(self.M.handle, *self.ab, 0, 0, deg, precision=self._prec(mlt))
+            hi = mlt.mlt_moments(self.M.handle, *self.ab, 0, 0, deg, precision="fp64")
+            self.drift = float(np.max(np.abs(lo - hi)) / self.d)
+
+    def step(self, mlt, stream, i):
+        return mlt.mlt_moments(self.M.handle, self.ab[0], self.ab[1], 0, self.base + (i % 1024) * self.NPROBES,
+                               self.deg, precision=self._prec(mlt), out=self.out, stream=stream)
+
+    def e2e_setup(self, torch):
+        self.h = (torch.from_numpy(self.X.rowptr).pin_memory(), torch.from_numpy(self.X.col).pin_memory(),
+                  torch.from_numpy(self.X.val).pin_memory())
+        self.h_out = torch.empty((self.NPROBES, self.DEG + 1), dtype=torch.float64).pin_memory()
+        return (sum(t.numel() * t.element_size() for t in self.h), self.h_out.numel() * 8)
+
+    def e2e_step(self, mlt, stream, i):
+        r, c, v = self.h
+        h = mlt.mlt_create_csr(self.X.nrows, self.X.ncols, self.nnz, r, c, v, flags=mlt.MLT_GRAM, stream=stream)
+        try:
+            mlt.mlt_moments(h, self.ab[0], self.ab[1], 0, self.base + i * self.NPROBES, self.deg,
+                            precision=self._prec(mlt), out=self.h_out, stream=stream)
+        finally:
+            mlt.mlt_destroy(h)
+
+    def cpu_sample(self, oracle, nprobes, offset):
+        if not hasattr(self, "ab"):
+            self.ab = [0.0, gram_upper(self.X)]
+        deg = np.full(nprobes, 16, dtype=np.int32)
+        oracle.moments(self.X, self.ab[0], self.ab[1], 0, offset, deg, gram=True)
+        return int(np.sum(deg))                  # direct recurrence: one probe-matvec per degree
+
+
+class Stencil3D:
+    """Chebyshev moments of one large 3D diffusion operator: the 7-point
+    operator on a 100^3 grid (d = 10^6, lognormal coefficients, seed 0, shift
+    0.1), 128 probes to degree 128, interval [0.1, Gershgorin bound], in the
+    --precision given (fp32 by default).  A streaming case for the fused step:
+    V rows of neighbouring grid cells are near each other, so the step's cost
+    is the matrix and the three V blocks it streams."""
+    name = "stencil3d"
+    unit = "probe-matvecs/s"
+    NPROBES = 128
+    DEG = 128
+
+    def __init__(self, precision=None):
+        from paper_2103_10516_gb300 import synth
+        self.csr = synth.diffusion_3d(100, sigma=1.0, shift=0.1, seed=0)
+        self.d = self.csr.nrows
+        self.nnz = self.csr.nnz
+        self.precision = precision or "fp32"
+        self.dtype = {"fp32": "f32", "fp64": "f64", "mixed": "f32+f64"}[self.precision]
+
+    def _prec(self, mlt):
+        return mlt.mixed_at(32) if self.precision == "mixed" else self.precision
+
+    def units(self):
+        return self.NPROBES * ((self.DEG + 1) // 2)
+
+    def config(self):
+        return {"workload": self.name, "matrix": "7-point 3D diffusion, 100^3 grid, lognormal kappa, shift 0.1",
+                "d": self.d, "nnz": self.nnz, "probes": self.NPROBES, "degree": self.DEG,
+                "precision": self.precision, "interval": getattr(self, "ab", None),
+                "group_width": getattr(self, "group_width", None),
+                "l2": "inputs larger than L2 (V blocks 2 x %.0f MB)"
+                      % (self.d * self.NPROBES * (8 if self.precision == "fp64" else 4) * 1e-6)}
+
+    def kernel_bytes(self, launches_per_step):
+        sv = 8 if self.precision == "fp64" else 4
+        return step_bytes(self.d, self.nnz, 4 + sv, sv, self.units(), launches_per_step)
+
+    def kernel_flops(self, launches_per_step):
+        n = launches_per_step.get("cheb_step")
+        return {"cheb_step": step_flops(self.d, self.nnz, self.units()) / n} if n else {}
+
+    def setup(self, mlt, torch, rank):
+        self.M = mlt.Matrix(self.csr)
+        self.ab = [0.1, self.M.bounds()[1]]
+        self.group_width = mlt.mlt_autotune(self.M.handle, "fp32" if self.precision != "fp64" else "fp64", 4)
+        self.out = torch.empty((self.NPROBES, self.DEG + 1), dtype=torch.float64, device="cuda")
+        self.deg = np.full(self.NPROBES, self.DEG, dtype=np.int32)
+        self.base = rank * (1 << 24)
+
+    def step(self, mlt, stream, i):
+        return mlt.mlt_moments(self.M.handle, self.ab[0], self.ab[1], 0, self.base + (i % 1024) * self.NPROBES,
+                               self.deg, precision=self._prec(mlt), out=self.out, stream=stream)
+
+    def e2e_setup(self, torch):
+        self.h = (torch.from_numpy(self.csr.rowptr).pin_memory(), torch.from_numpy(self.csr.col).pin_memory(),
+                  torch.from_numpy(self.csr.val).pin_memory())
+        self.h_out = torch.empty((self.NPROBES, self.DEG + 1), dtype=torch.float64).pin_memory()
+        return (sum(t.numel() * t.element_size() for t in self.h), self.h_out.numel() * 8)
+
+    def e2e_step(self, mlt, stream, i):
+        r, c, v = self.h
+        h = mlt.mlt_create_csr(self.d, self.d, self.nnz, r, c, v, stream=stream)
+        try:
+            mlt.mlt_moments(h, self.ab[0], self.ab[1], 0, self.base + i * self.NPROBES, self.deg,
+                            precision=self._prec(mlt), out=self.h_out, stream=stream)
+        finally:
+            mlt.mlt_destroy(h)
+
+    def cpu_sample(self, oracle, nprobes, offset):
+        if not hasattr(self, "ab"):
+            self.ab = [0.1, gershgorin_upper(self.csr)]
+        deg = np.full(nprobes, 8, dtype=np.int32)
+        oracle.moments(self.csr, self.ab[0], self.ab[1], 0, offset, deg)
+        return int(np.sum(deg))                  # direct recurrence: one probe-matvec per degree
+
+
+class EstradaLearned:
+    """The learned coarse level against the plain FP64 multilevel estimator,
+    at equal standard error, on the Estrada index tr exp(A): R-MAT adjacency
+    (edge factor 16, seed 1) scaled to Gershgorin radius 10, interval
+    [-10, 10], n = 128.
+
+    Setup (untimed, reported in config["comparison"]):
+      1. plain FP64 MLMC with levels and sample counts from a 10-probe pilot
+         under a fixed matvec budget: estimate, standard error s_p, GPU time t_p;
+      2. the BF16 network trained on 2^16 FP32 probes ((mu_0..mu_15)/d ->
+         P_64/d), GPU time of training;
+      3. a small pilot of the learned estimator gives the variances V_k of its
+         levels (S, P_64 - S, P_128 - P_64); sample counts m_k follow the
+         optimal allocation m_k = sqrt(V_k / C_k) sum_j sqrt(V_j C_j) / s_p^2
+         (C = 8, 32, 64 recurrence steps) so that its standard error matches s_p.
+    Step (timed): one learned FP32 estimate with those m_k.  The reported
+    ratio is (s^2 t)_plain / (s^2 t)_learned, the variance-per-GPU-second gain."""
+    name = "estrada_learned"
+    unit = "probe-matvecs/s"
+    dtype = "f32+bf16"
+    L1, N = 64, 128
+    COST = (8, 32, 64)
+
+    def __init__(self, scale=None):
+        from paper_2103_10516_gb300 import synth
+        self.scale_log2 = scale or 22
+        self.csr = synth.rmat_adjacency(self.scale_log2, 16, seed=1)
+        self.d = self.csr.nrows
+        self.nnz = self.csr.nnz
+        self.ntrain = 1 << 16
+        self.budget = 16384
+        self.cmp = None
+        self.m = None
+        self.scale = None
+
+    def units(self):
+        return int(sum(mk * c for mk, c in zip(self.m, self.COST)))
+
+    def config(self):
+        return {"workload": self.name, "graph": "R-MAT scale %d, edge factor 16, seed 1" % self.scale_log2,
+                "d": self.d, "nnz": self.nnz, "f": "exp", "interval": [-10.0, 10.0], "n": self.N,
+                "l1": self.L1, "train_probes": self.ntrain, "m": self.m, "comparison": self.cmp,
+                "l2": "inputs larger than L2 (V blocks of 4 B x d per probe)"}
+
+    def kernel_bytes(self, launches_per_step):
+        return step_bytes(self.d, self.nnz, 4, 4, self.units(), launches_per_step)
+
+    def _timed(self, torch, fn):
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        out = fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / 1e3
+
+    def setup(self, mlt, torch, rank):
+        sp = torch.cuda.current_stream().cuda_stream
+        M0 = mlt.Matrix(self.csr)
+        self.scale = 10.0 / M0.bounds()[1]
+        M0.close()
+        self.M = mlt.Matrix(self.csr, scale=self.scale)
+        self.group_width = mlt.mlt_autotune(self.M.handle, "fp32", 4)
+        base = rank << 30
+        plain, t_p = self._timed(torch, lambda: self.M.mlmc(
+            "exp", -10.0, 10.0, self.N, seed=3, m_pilot=10, mode="budget", target=self.budget,
+            precision="fp64", stream=sp))
+        self.S = mlt.Surrogate(5)
+        P = mlt.learned_params("exp", -10.0, 10.0, self.N, self.L1, 1, 1, 1, seed=7, probe_offset=base + (1 << 24),
+                               precision="fp32", stream=sp)
+        loss, t_train = self._timed(torch, lambda: mlt.mlt_learned_train(
+            self.M.handle, self.S.handle, P, self.ntrain, base + (1 << 20), 40, 2048, 2e-3))
+        pil = mlt.learned_params("exp", -10.0, 10.0, self.N, self.L1, 512, 128, 32, seed=11,
+                                 probe_offset=base + (1 << 26), precision="fp32", stream=sp)
+        pilot, t_pil = self._timed(torch, lambda: mlt.mlt_learned_estimate(self.M.handle, self.S.handle, pil))
+        V = [max(v, 1e-300) for v in pilot["level_var"]]
+        s2 = plain["stderr"] ** 2
+        tot = sum(np.sqrt(v * c) for v, c in zip(V, self.COST))
+        self.m = [max(2, int(np.ceil(np.sqrt(v / c) * tot / s2))) for v, c in zip(V, self.COST)]
+        self.base = base + (1 << 28)
+        self.cmp = {"plain_fp64": {"estimate": plain["estimate"], "stderr": plain["stderr"],
+                                   "gpu_s": round(t_p, 4), "levels": plain["levels"], "m": plain["m"],
+                                   "budget_matvecs": self.budget},
+                    "learned_fp32": {"train_gpu_s": round(t_train, 3), "train_loss": loss,
+                                     "pilot_level_var": V, "pilot_gpu_s": round(t_pil, 4)}}
+        self.results = []
+
+    def step(self, mlt, stream, i):
+        P = mlt.learned_params("exp", -10.0, 10.0, self.N, self.L1, *self.m, seed=13,
+                               probe_offset=self.base + i * sum(self.m), precision="fp32", stream=stream)
+        r = mlt.mlt_learned_estimate(self.M.handle, self.S.handle, P)
+        self.results.append((r["estimate"], r["stderr"]))
+        return r
+
+    def finish(self, ms_per_step):
+        """Called after the timed steps: the comparison at the measured time."""
+        if not self.results:
+            return
+        se = float(np.sqrt(np.mean([e[1] ** 2 for e in self.results])))
+        lp = self.cmp["learned_fp32"]
+        lp.update({"estimate_first": self.results[0][0], "stderr": se, "gpu_s": round(ms_per_step / 1e3, 4),
+                   "m": self.m})
+        pl = self.cmp["plain_fp64"]
+        gain = (pl["stderr"] ** 2 * pl["gpu_s"]) / (se ** 2 * lp["gpu_s"])
+        self.cmp["variance_time_gain"] = round(gain, 3)
+        n_runs_to_amortise = lp["train_gpu_s"] / max(pl["gpu_s"] * (pl["stderr"] ** 2 / se ** 2) - lp["gpu_s"], 1e-9)
+        self.cmp["estimates_to_amortise_training"] = round(n_runs_to_amortise, 1)
+
+    def e2e_setup(self, torch):
+        self.h = (torch.from_numpy(self.csr.rowptr).pin_memory(), torch.from_numpy(self.csr.col).pin_memory())
+        return (self.h[0].numel() * 8 + self.h[1].numel() * 4, 8 * 3 * 4)
+
+    def e2e_step(self, mlt, stream, i):
+        h = mlt.mlt_create_csr(self.d, self.d, self.nnz, self.h[0], self.h[1], None, scale=self.scale,
+                               stream=stream)
+        try:
+            P = mlt.learned_params("exp", -10.0, 10.0, self.N, self.L1, *self.m, seed=17,
+                                   probe_offset=self.base + (i + 1000) * sum(self.m), precision="fp32",
+                                   stream=stream)
+            mlt.mlt_learned_estimate(h, self.S.handle, P)
+        finally:
+            mlt.mlt_destroy(h)
+
+    def cpu_sample(self, oracle, nprobes, offset):
+        if self.scale is None:
+            self.scale = 10.0 / gershgorin_upper(self.csr)
+        deg = np.full(nprobes, 16, dtype=np.int32)
+        oracle.moments(self.csr, -10.0, 10.0, 0, offset, deg, scale=self.scale)
+        return nprobes * 16
+
+
+WORKLOADS = {c.name: c for c in (Triangles, LogDet64, EstradaRmat22, Diffusion64Batched, NuclearGram,
+                                            Stencil3D, EstradaLearned)}
 
 
 # ---------------------------------------------------------------------------
@@ -403,7 +882,7 @@ def run_ours(args, dist):
 
     torch.cuda.set_device(dist.local)
     mlt.lib()
-    wl = WORKLOADS[args.workload]()
+    wl = make_workload(args)
     wl.setup(mlt, torch, dist.rank)
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
@@ -429,6 +908,8 @@ def run_ours(args, dist):
     clk = clocks.stop() if dist.rank == 0 else None
     ms = e0.elapsed_time(e1) / args.steps
     ms = dist.max(ms)
+    if hasattr(wl, "finish"):
+        wl.finish(ms)
     value = wl.units() * dist.world / (ms / 1e3)
 
     # roofline of the dominant kernel
@@ -445,7 +926,18 @@ def run_ours(args, dist):
             tot = tot + stats[companion][1]
         avg_ms = tot / n
         byt = kb.get(name)
-        if byt is not None:
+        kf = wl.kernel_flops({k: v[0] / args.steps for k, v in stats.items()}) \
+            if wl.dtype == "f64" and hasattr(wl, "kernel_flops") else {}
+        if kf.get(name) is not None:
+            ach = kf[name] / (avg_ms / 1e3) / 1e12
+            roof = {"bound": "alu", "kernel": name, "achieved": round(ach, 4), "peak": FP64_TFLOPS_NOMINAL,
+                    "unit": "TFLOP/s", "frac": round(ach / FP64_TFLOPS_NOMINAL, 4),
+                    "peak_source": "nominal FP64 rate of GB300", "avg_launch_ms": round(avg_ms, 4),
+                    "algorithmic_flops_per_launch": int(kf[name]),
+                    "hbm_gbs_on_algorithmic_bytes": round(byt / (avg_ms / 1e3) / 1e9, 1) if byt else None,
+                    "includes": companion if companion in stats else None,
+                    "traffic": getattr(wl, "TRAFFIC", {}).get(name), "share_of_step": round(tot / (ms * args.steps), 4)}
+        elif byt is not None:
             ach = byt / (avg_ms / 1e3) / 1e9
             roof = {"bound": "hbm", "kernel": name, "achieved": round(ach, 1),
                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4),
@@ -455,6 +947,19 @@ def run_ours(args, dist):
                     "traffic": getattr(wl, "TRAFFIC", {}).get(name),
                     "share_of_step": round(tot / (ms * args.steps), 4)}
     launches = int(sum(v[0] for v in stats.values()))
+    if not stats and hasattr(wl, "graph_step"):
+        # the step is one CUDA graph: its kernels are not timed one by one, so
+        # the roofline covers the whole step
+        byt, nl = wl.graph_step()
+        fl = wl.graph_flops()
+        ach = fl / (ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "moments_graph (whole step)", "achieved": round(ach, 4),
+                "peak": FP64_TFLOPS_NOMINAL, "unit": "TFLOP/s", "frac": round(ach / FP64_TFLOPS_NOMINAL, 4),
+                "peak_source": "nominal FP64 rate of GB300", "avg_launch_ms": round(ms, 4),
+                "algorithmic_flops_per_launch": int(fl),
+                "hbm_gbs_on_algorithmic_bytes": round(byt / (ms / 1e3) / 1e9, 1),
+                "includes": "every kernel of the graph", "traffic": None, "share_of_step": 1.0}
+        launches = nl * args.steps
 
     # end to end through the C ABI with pinned host buffers
     ke = max(1, min(args.steps, args.e2e_steps))
@@ -490,7 +995,7 @@ def run_reference(args, dist):
         return
     import oracle
     oracle.lib()
-    wl = WORKLOADS[args.workload]()
+    wl = make_workload(args)
     cores = os.cpu_count() or 1
     n = max(1, min(cores, 16))
     for i in range(args.warmup):
@@ -513,6 +1018,19 @@ def run_reference(args, dist):
     print(json.dumps(line))
 
 
+def make_workload(args):
+    cls = WORKLOADS[args.workload]
+    if args.scale is not None:
+        if cls is not EstradaLearned:
+            raise SystemExit("--scale applies to the estrada_learned workload only")
+        return cls(args.scale)
+    if args.precision is not None:
+        if cls not in (NuclearGram, Stencil3D):
+            raise SystemExit("--precision applies to the nuclear_gram and stencil3d workloads only")
+        return cls(args.precision)
+    return cls()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -520,6 +1038,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat20_triangles", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp64", "mixed"])
+    ap.add_argument("--scale", type=int, default=None, help="R-MAT scale of estrada_learned")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -24,6 +24,12 @@
 //
 // Reductions are deterministic: each CTA writes per-column partial sums in a
 // fixed order, and a separate kernel adds the CTA partials in CTA order.
+// Each thread's running dot products are FP64 for FP64 vectors.  For FP32
+// vectors they are compensated (Kahan) FP32 sums, whose error is at most
+// 2^-23 times the sum of |terms| (below the rounding already in the FP32
+// vectors), because FP64 arithmetic on GB300 runs at 1/64 of the FP32 rate
+// and a per-row FP64 update would cost more than streaming the vectors; the
+// sums leave each thread as FP64 and everything after that is FP64.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -45,6 +51,33 @@ template <> struct Lanes<double> { static constexpr int N = 2; };   // 16-byte v
 template <> struct Lanes<float> { static constexpr int N = 4; };
 
 template <typename T, int N> struct alignas(sizeof(T) * N) Pack { T v[N]; };
+
+// A thread's running dot product.
+template <typename T> struct DotAcc;
+template <> struct DotAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct DotAcc<float> {
+    float s = 0.0f, c = 0.0f;   // Kahan: s - c is the running sum
+    __device__ __forceinline__ void add(float x)
+    {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ void add_prod(float a, float b)
+    {
+        const float y = fmaf(a, b, -c);   // the product enters unrounded
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
 
 template <typename T>
 struct StepArgs {
@@ -139,7 +172,7 @@ __device__ __forceinline__ void row_product(const StepArgs<T>& a, const Lane<T, 
 // V_{k+1}[r] from acc = (A V_k)[r], and the fused dot products.
 template <typename T>
 __device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0, const T (&acc)[Lanes<T>::N],
-                                         double (&s_self)[Lanes<T>::N], double (&s_cross)[Lanes<T>::N])
+                                         DotAcc<T> (&s_self)[Lanes<T>::N], DotAcc<T> (&s_cross)[Lanes<T>::N])
 {
     constexpr int N = Lanes<T>::N;
     using P = Pack<T, N>;
@@ -164,17 +197,15 @@ __device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0
     if (!a.direct) {
 #pragma unroll
         for (int q = 0; q < N; ++q) {
-            const double o = (double)out.v[q];
-            s_self[q] = fma(o, o, s_self[q]);
-            s_cross[q] = fma(o, (double)xc.v[q], s_cross[q]);
+            s_self[q].add_prod(out.v[q], out.v[q]);
+            s_cross[q].add_prod(out.v[q], xc.v[q]);
         }
     } else {
 #pragma unroll
         for (int q = 0; q < N; ++q) {
             if (c0 + q >= a.B) break;
             const bool neg = probe_negative(a.seedmix, (uint64_t)a.ids[c0 + q], (uint64_t)r);
-            const double o = (double)out.v[q];
-            s_cross[q] += neg ? -o : o;
+            s_cross[q].add(neg ? -out.v[q] : out.v[q]);
         }
     }
 }
@@ -183,16 +214,16 @@ __device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0
 // whose column chunk holds it, in group order.
 template <typename T, int G>
 __device__ __forceinline__ void cta_partials(const StepArgs<T>& a, const Lane<T, G>& L,
-                                             const double (&s_self)[Lanes<T>::N],
-                                             const double (&s_cross)[Lanes<T>::N])
+                                             const DotAcc<T> (&s_self)[Lanes<T>::N],
+                                             const DotAcc<T> (&s_cross)[Lanes<T>::N])
 {
     constexpr int N = Lanes<T>::N;
     __shared__ double red[2][kThreads * N];
     const int tid = threadIdx.x;
 #pragma unroll
     for (int q = 0; q < N; ++q) {
-        red[0][tid * N + q] = s_self[q];
-        red[1][tid * N + q] = s_cross[q];
+        red[0][tid * N + q] = s_self[q].value();
+        red[1][tid * N + q] = s_cross[q].value();
     }
     __syncthreads();
     const int gpb = kThreads / G;
@@ -220,9 +251,7 @@ __global__ void __launch_bounds__(kThreads) cheb_step_kernel(StepArgs<T> a)
 {
     constexpr int N = Lanes<T>::N;
     const Lane<T, G> L(a);
-    double s_self[N], s_cross[N];
-#pragma unroll
-    for (int q = 0; q < N; ++q) { s_self[q] = 0.0; s_cross[q] = 0.0; }
+    DotAcc<T> s_self[N], s_cross[N];
 
     if (L.active) {
         const int64_t nitems = a.nch + a.nseg;
@@ -266,9 +295,7 @@ __global__ void __launch_bounds__(kThreads) cheb_long_kernel(StepArgs<T> a)
     constexpr int N = Lanes<T>::N;
     using P = Pack<T, N>;
     const Lane<T, G> L(a);
-    double s_self[N], s_cross[N];
-#pragma unroll
-    for (int q = 0; q < N; ++q) { s_self[q] = 0.0; s_cross[q] = 0.0; }
+    DotAcc<T> s_self[N], s_cross[N];
     if (L.active) {
         for (int64_t i = L.gcls; i < a.nlong; i += L.ncls) {
             if (!L.vok) continue;
