@@ -58,6 +58,16 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 FP64_TFLOPS_NOMINAL = 1.25
 
 
+# Each rank draws its probes from ids probe_base(rank) .. probe_base(rank) +
+# PROBE_SPAN of its workload: disjoint ranges, so the ranks' samples are
+# independent (and 8 ranks stay below the 2^32 probe ids of the library).
+PROBE_BASE_SHIFT = 28
+
+
+def probe_base(rank):
+    return int(rank) << PROBE_BASE_SHIFT
+
+
 def step_flops(d, nnz, probe_matvecs):
     """Algorithmic FP64 flops of a step's recurrence: 2 per stored entry (one
     FMA) and 8 per vector entry (the update and both dot products) per
@@ -190,6 +200,7 @@ class Triangles:
     dtype = "int64"
     NPROBES = 1024
     BLOCK = 128
+    PROBE_SPAN = (4096 + 64) * 1024     # timed steps cycle through 4096 blocks; e2e steps follow
 
     def __init__(self):
         from paper_2103_10516_gb300 import synth
@@ -233,7 +244,7 @@ class Triangles:
     def setup(self, mlt, torch, rank):
         self.M = mlt.Matrix(self.csr)
         self.x = torch.empty((self.NPROBES, 3), dtype=torch.int64, device="cuda")
-        self.base = rank * (1 << 24)
+        self.base = probe_base(rank)
 
     def step(self, mlt, stream, i):
         return mlt.mlt_triangle_trace(self.M.handle, 0, self.base + (i % 4096) * self.NPROBES,
@@ -249,7 +260,7 @@ class Triangles:
         h = mlt.mlt_create_csr(self.d, self.d, self.nnz, self.h_rowptr, self.h_col, None,
                                stream=stream)
         try:
-            mlt.mlt_triangle_trace(h, 0, self.base + i * self.NPROBES, self.NPROBES, self.BLOCK,
+            mlt.mlt_triangle_trace(h, 0, self.base + (4096 + i) * self.NPROBES, self.NPROBES, self.BLOCK,
                                    True, self.h_x, stream)
         finally:
             mlt.mlt_destroy(h)
@@ -264,6 +275,7 @@ class LogDet64:
     name = "logdet64"
     unit = "probe-matvecs/s"
     dtype = "f64"
+    PROBE_SPAN = 0     # probes ids restart per seed; each rank and step has its own seed
 
     def __init__(self):
         from paper_2103_10516_gb300 import synth
@@ -333,6 +345,7 @@ class EstradaRmat22:
     dtype = "f32"
     NPROBES = 256
     DEG = 128
+    PROBE_SPAN = (1024 + 64) * 256
 
     def __init__(self):
         from paper_2103_10516_gb300 import synth
@@ -366,7 +379,7 @@ class EstradaRmat22:
         self.group_width = mlt.mlt_autotune(self.M.handle, "fp32", 4)
         self.out = torch.empty((self.NPROBES, self.DEG + 1), dtype=torch.float64, device="cuda")
         self.deg = np.full(self.NPROBES, self.DEG, dtype=np.int32)
-        self.base = rank * (1 << 24)
+        self.base = probe_base(rank)
 
     def step(self, mlt, stream, i):
         return mlt.mlt_moments(self.M.handle, -10.0, 10.0, 0, self.base + (i % 1024) * self.NPROBES,
@@ -382,7 +395,7 @@ class EstradaRmat22:
         h = mlt.mlt_create_csr(self.d, self.d, self.nnz, self.h_rowptr, self.h_col, None,
                                scale=self.scale, stream=stream)
         try:
-            mlt.mlt_moments(h, -10.0, 10.0, 0, self.base + i * self.NPROBES, self.deg,
+            mlt.mlt_moments(h, -10.0, 10.0, 0, self.base + (1024 + i) * self.NPROBES, self.deg,
                             precision="fp32", out=self.h_out, stream=stream)
         finally:
             mlt.mlt_destroy(h)
@@ -424,6 +437,7 @@ class Diffusion64Batched:
     unit = "probe-matvecs/s"
     dtype = "f64"
     NMAT = 64
+    PROBE_SPAN = (4096 + 64 + 2) * 128   # every matrix draws from the same id range (its own seed stream)
 
     def __init__(self):
         from paper_2103_10516_gb300 import synth
@@ -485,8 +499,8 @@ class Diffusion64Batched:
     def graph_flops(self):
         return sum(step_flops(c.nrows, c.nnz, int(np.sum((dg + 1) // 2))) for c, dg in zip(self.mats, self.deg))
 
-    def _jobs(self, handles, outs, i):
-        return [{"matrix": h.handle, "a": self.shift[k], "b": self.b[k], "seed": 7, "probe_offset": i * 128,
+    def _jobs(self, handles, outs, off):
+        return [{"matrix": h.handle, "a": self.shift[k], "b": self.b[k], "seed": 7, "probe_offset": off,
                  "degrees": self.deg[k], "out": outs[k], "group_width": self.widths[k]}
                 for k, h in enumerate(handles)]
 
@@ -495,21 +509,21 @@ class Diffusion64Batched:
         self.b = [M.bounds()[1] for M in self.M]
         self.widths = [mlt.mlt_autotune(M.handle, "fp64", 4) for M in self.M]
         self.out = [torch.empty((dg.size, 257), dtype=torch.float64, device="cuda") for dg in self.deg]
-        self.base = rank * (1 << 20)
+        self.base = probe_base(rank)
         # the same 64 jobs as separate calls, for comparison (untimed setup)
         stream = torch.cuda.current_stream()
         for rep in range(2):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for k, M in enumerate(self.M):
-                mlt.mlt_moments(M.handle, self.shift[k], self.b[k], 7, (self.base + rep) * 128, self.deg[k],
+                mlt.mlt_moments(M.handle, self.shift[k], self.b[k], 7, self.base + (4160 + rep) * 128, self.deg[k],
                                 out=self.out[k], stream=stream.cuda_stream)
             e1.record(stream)
             torch.cuda.synchronize()
             self.seq_ms = round(e0.elapsed_time(e1), 3)
 
     def step(self, mlt, stream, i):
-        mlt.mlt_moments_batched(self._jobs(self.M, self.out, self.base + i % 4096), "fp64", stream=stream)
+        mlt.mlt_moments_batched(self._jobs(self.M, self.out, self.base + (i % 4096) * 128), "fp64", stream=stream)
 
     def e2e_setup(self, torch):
         self.h = [(torch.from_numpy(c.rowptr).pin_memory(), torch.from_numpy(c.col).pin_memory(),
@@ -522,7 +536,8 @@ class Diffusion64Batched:
         hs = [mlt.mlt_create_csr(c.nrows, c.nrows, c.nnz, r, col, v, stream=stream)
               for c, (r, col, v) in zip(self.mats, self.h)]
         try:
-            jobs = [{"matrix": h, "a": self.shift[k], "b": self.b[k], "seed": 7, "probe_offset": i * 128,
+            jobs = [{"matrix": h, "a": self.shift[k], "b": self.b[k], "seed": 7,
+                     "probe_offset": self.base + (4096 + i) * 128,
                      "degrees": self.deg[k], "out": self.h_out[k], "group_width": self.widths[k]}
                     for k, h in enumerate(hs)]
             mlt.mlt_moments_batched(jobs, "fp64", stream=stream)
@@ -552,6 +567,7 @@ class NuclearGram:
     unit = "probe-matvecs/s"
     NPROBES = 512
     DEG = 512
+    PROBE_SPAN = (1024 + 64) * 512
 
     def __init__(self, precision=None):
         from paper_2103_10516_gb300 import synth
@@ -600,7 +616,7 @@ class NuclearGram:
         self.group_width = mlt.mlt_autotune(self.M.handle, "fp32" if self.precision != "fp64" else "fp64", 4)
         self.out = torch.empty((self.NPROBES, self.DEG + 1), dtype=torch.float64, device="cuda")
         self.deg = np.full(self.NPROBES, self.DEG, dtype=np.int32)
-        self.base = rank * (1 << 24)
+        self.base = probe_base(rank)
         if self.precision != "fp64":
             # drift of this precision against FP64 on 32 probes (untimed)
             deg = self.deg[:32]
@@ -622,7 +638,7 @@ class NuclearGram:
         r, c, v = self.h
         h = mlt.mlt_create_csr(self.X.nrows, self.X.ncols, self.nnz, r, c, v, flags=mlt.MLT_GRAM, stream=stream)
         try:
-            mlt.mlt_moments(h, self.ab[0], self.ab[1], 0, self.base + i * self.NPROBES, self.deg,
+            mlt.mlt_moments(h, self.ab[0], self.ab[1], 0, self.base + (1024 + i) * self.NPROBES, self.deg,
                             precision=self._prec(mlt), out=self.h_out, stream=stream)
         finally:
             mlt.mlt_destroy(h)
@@ -646,6 +662,7 @@ class Stencil3D:
     unit = "probe-matvecs/s"
     NPROBES = 128
     DEG = 128
+    PROBE_SPAN = (1024 + 64) * 128
 
     def __init__(self, precision=None):
         from paper_2103_10516_gb300 import synth
@@ -683,7 +700,7 @@ class Stencil3D:
         self.group_width = mlt.mlt_autotune(self.M.handle, "fp32" if self.precision != "fp64" else "fp64", 4)
         self.out = torch.empty((self.NPROBES, self.DEG + 1), dtype=torch.float64, device="cuda")
         self.deg = np.full(self.NPROBES, self.DEG, dtype=np.int32)
-        self.base = rank * (1 << 24)
+        self.base = probe_base(rank)
 
     def step(self, mlt, stream, i):
         return mlt.mlt_moments(self.M.handle, self.ab[0], self.ab[1], 0, self.base + (i % 1024) * self.NPROBES,
@@ -699,7 +716,7 @@ class Stencil3D:
         r, c, v = self.h
         h = mlt.mlt_create_csr(self.d, self.d, self.nnz, r, c, v, stream=stream)
         try:
-            mlt.mlt_moments(h, self.ab[0], self.ab[1], 0, self.base + i * self.NPROBES, self.deg,
+            mlt.mlt_moments(h, self.ab[0], self.ab[1], 0, self.base + (1024 + i) * self.NPROBES, self.deg,
                             precision=self._prec(mlt), out=self.h_out, stream=stream)
         finally:
             mlt.mlt_destroy(h)
@@ -734,6 +751,7 @@ class EstradaLearned:
     dtype = "f32+bf16"
     L1, N = 64, 128
     COST = (8, 32, 64)
+    PROBE_SPAN = 1 << 28       # training, pilot, timed and e2e ranges below, all inside it
 
     def __init__(self, scale=None):
         from paper_2103_10516_gb300 import synth
@@ -776,23 +794,23 @@ class EstradaLearned:
         M0.close()
         self.M = mlt.Matrix(self.csr, scale=self.scale)
         self.group_width = mlt.mlt_autotune(self.M.handle, "fp32", 4)
-        base = rank << 30
+        base = probe_base(rank)
         plain, t_p = self._timed(torch, lambda: self.M.mlmc(
             "exp", -10.0, 10.0, self.N, seed=3, m_pilot=10, mode="budget", target=self.budget,
             precision="fp64", stream=sp))
         self.S = mlt.Surrogate(5)
-        P = mlt.learned_params("exp", -10.0, 10.0, self.N, self.L1, 1, 1, 1, seed=7, probe_offset=base + (1 << 24),
+        P = mlt.learned_params("exp", -10.0, 10.0, self.N, self.L1, 1, 1, 1, seed=7, probe_offset=base,
                                precision="fp32", stream=sp)
         loss, t_train = self._timed(torch, lambda: mlt.mlt_learned_train(
-            self.M.handle, self.S.handle, P, self.ntrain, base + (1 << 20), 40, 2048, 2e-3))
+            self.M.handle, self.S.handle, P, self.ntrain, base, 40, 2048, 2e-3))
         pil = mlt.learned_params("exp", -10.0, 10.0, self.N, self.L1, 512, 128, 32, seed=11,
-                                 probe_offset=base + (1 << 26), precision="fp32", stream=sp)
+                                 probe_offset=base + (1 << 22), precision="fp32", stream=sp)
         pilot, t_pil = self._timed(torch, lambda: mlt.mlt_learned_estimate(self.M.handle, self.S.handle, pil))
         V = [max(v, 1e-300) for v in pilot["level_var"]]
         s2 = plain["stderr"] ** 2
         tot = sum(np.sqrt(v * c) for v, c in zip(V, self.COST))
         self.m = [max(2, int(np.ceil(np.sqrt(v / c) * tot / s2))) for v, c in zip(V, self.COST)]
-        self.base = base + (1 << 28)
+        self.base = base + (1 << 23)
         self.cmp = {"plain_fp64": {"estimate": plain["estimate"], "stderr": plain["stderr"],
                                    "gpu_s": round(t_p, 4), "levels": plain["levels"], "m": plain["m"],
                                    "budget_matvecs": self.budget},
@@ -830,7 +848,7 @@ class EstradaLearned:
                                stream=stream)
         try:
             P = mlt.learned_params("exp", -10.0, 10.0, self.N, self.L1, *self.m, seed=17,
-                                   probe_offset=self.base + (i + 1000) * sum(self.m), precision="fp32",
+                                   probe_offset=base_e2e(self.base) + i * sum(self.m), precision="fp32",
                                    stream=stream)
             mlt.mlt_learned_estimate(h, self.S.handle, P)
         finally:
@@ -842,6 +860,11 @@ class EstradaLearned:
         deg = np.full(nprobes, 16, dtype=np.int32)
         oracle.moments(self.csr, -10.0, 10.0, 0, offset, deg, scale=self.scale)
         return nprobes * 16
+
+
+def base_e2e(timed_base):
+    """Probe ids of the learned workload's end-to-end steps: past its timed ones."""
+    return timed_base + (1 << 26)
 
 
 WORKLOADS = {c.name: c for c in (Triangles, LogDet64, EstradaRmat22, Diffusion64Batched, NuclearGram,
