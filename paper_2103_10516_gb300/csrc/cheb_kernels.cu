@@ -16,11 +16,14 @@
 //
 // Work split (fixed per matrix, so every result is reproducible): rows cost
 // kRowCost units plus one per entry; the unit axis is cut into chunks of Uc
-// units.  A row of degree <= Uc belongs to the chunk holding its first unit.
-// Longer rows are cut into fixed segments of Uc entries whose partial products
-// go to a scratch table; a second kernel adds each row's segments in order and
-// applies the recurrence there.  Work items (chunks, then segments) are dealt
-// round-robin to groups of G lanes; a group always owns the same columns.
+// units.  A row of degree <= Ul (>= Uc) belongs to the chunk holding its first
+// unit.  Longer rows are cut into fixed segments of Ul entries whose partial
+// products go to a scratch table; a second kernel adds each row's segments in
+// order and applies the recurrence there.  Work items (chunks, then segments)
+// are dealt round-robin to groups of G lanes on a grid no larger than the
+// resident one; a group always owns the same columns.  Chunks are small (about
+// a thousand per SM), so at any moment the groups work on one narrow band of
+// rows and the rows of V gathered by neighbouring rows are still in L2.
 //
 // Reductions are deterministic: each CTA writes per-column partial sums in a
 // fixed order, and a separate kernel adds the CTA partials in CTA order.
@@ -45,6 +48,8 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kSlots = 16;          // steps whose partials are buffered before a reduction
 constexpr int64_t kRowCost = 4;     // units charged per row (the epilogue) on top of its entries
+constexpr int64_t kChunksPerSm = 1024;  // work chunks per SM in the split of an operand
+constexpr int64_t kLongRow = 1024;  // rows above max(Uc, this) are cut into segments
 
 template <typename T> struct Lanes;
 template <> struct Lanes<double> { static constexpr int N = 2; };   // 16-byte vectors
@@ -99,7 +104,7 @@ struct StepArgs {
     const int64_t* ids;    // global id of each column's probe (direct mode)
     double* partials;      // [gridDim.x][2][ldv] for this launch
     // work split of this operand
-    int64_t nch, Uc, nseg;
+    int64_t nch, Uc, Ul, nseg;
     int nlong;
     const int64_t* crow;
     const int32_t* seg_row;
@@ -265,7 +270,7 @@ __global__ void __launch_bounds__(kThreads) cheb_step_kernel(StepArgs<T> a)
                     if (pr >= u1) break;
                     if (pr < u0) continue;
                     const int64_t end = __ldg(a.rowptr + r + 1);
-                    if (end - beg > a.Uc) continue;          // long row: done by segments
+                    if (end - beg > a.Ul) continue;          // long row: done by segments
                     row_product<T, G>(a, L, beg, end, acc);
                     if (L.vok) epilogue<T>(a, r, L.c0, acc, s_self, s_cross);
                 }
@@ -273,7 +278,7 @@ __global__ void __launch_bounds__(kThreads) cheb_step_kernel(StepArgs<T> a)
                 const int64_t sidx = it - a.nch;
                 const int64_t r = __ldg(a.seg_row + sidx);
                 const int64_t k0 = __ldg(a.seg_k0 + sidx);
-                const int64_t k1 = min(k0 + a.Uc, __ldg(a.rowptr + r + 1));
+                const int64_t k1 = min(k0 + a.Ul, __ldg(a.rowptr + r + 1));
                 row_product<T, G>(a, L, k0, k1, acc);
                 if (L.vok) {
                     Pack<T, N> p;
@@ -402,11 +407,28 @@ int pow2_at_least(int v)
 
 // Launch the step (and, with long rows, the segment kernel after it).  The
 // CTA partials of the two kernels sit next to each other in `part`.
+// Resident CTAs per SM of one instance of the step kernel.
 template <typename T, int G>
-int launch_step_g(StepArgs<T> a, int max_main, int max_long, int* nblocks_out, cudaStream_t s)
+int resident_ctas()
+{
+    static const int occ = [] {
+        int o = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, cheb_step_kernel<T, G>, kThreads, 0) != cudaSuccess) {
+            cudaGetLastError();
+            o = 0;
+        }
+        return o;
+    }();
+    return occ;
+}
+
+template <typename T, int G>
+int launch_step_g(StepArgs<T> a, int max_main, int max_long, int num_sms, int* nblocks_out, cudaStream_t s)
 {
     const int gpb = kThreads / G;
     const long long items = (a.nch + a.nseg) * (long long)a.nchunks;
+    const int occ = resident_ctas<T, G>();
+    if (occ > 0) max_main = std::min(max_main, occ * num_sms);   // one resident wave
     int nb = (int)std::max<long long>(1, std::min<long long>((items + gpb - 1) / gpb, max_main));
     if ((long long)nb * gpb < a.nchunks) nb = (a.nchunks + gpb - 1) / gpb;
     {
@@ -430,15 +452,15 @@ int launch_step_g(StepArgs<T> a, int max_main, int max_long, int* nblocks_out, c
 }
 
 template <typename T>
-int launch_step(int G, const StepArgs<T>& a, int max_main, int max_long, int* nb, cudaStream_t s)
+int launch_step(int G, const StepArgs<T>& a, int max_main, int max_long, int num_sms, int* nb, cudaStream_t s)
 {
     switch (G) {
-    case 1: return launch_step_g<T, 1>(a, max_main, max_long, nb, s);
-    case 2: return launch_step_g<T, 2>(a, max_main, max_long, nb, s);
-    case 4: return launch_step_g<T, 4>(a, max_main, max_long, nb, s);
-    case 8: return launch_step_g<T, 8>(a, max_main, max_long, nb, s);
-    case 16: return launch_step_g<T, 16>(a, max_main, max_long, nb, s);
-    default: return launch_step_g<T, 32>(a, max_main, max_long, nb, s);
+    case 1: return launch_step_g<T, 1>(a, max_main, max_long, num_sms, nb, s);
+    case 2: return launch_step_g<T, 2>(a, max_main, max_long, num_sms, nb, s);
+    case 4: return launch_step_g<T, 4>(a, max_main, max_long, num_sms, nb, s);
+    case 8: return launch_step_g<T, 8>(a, max_main, max_long, num_sms, nb, s);
+    case 16: return launch_step_g<T, 16>(a, max_main, max_long, num_sms, nb, s);
+    default: return launch_step_g<T, 32>(a, max_main, max_long, num_sms, nb, s);
     }
 }
 
@@ -447,6 +469,7 @@ void set_split(StepArgs<T>& a, const SpmmPlan& P, T* segpart)
 {
     a.nch = P.nch;
     a.Uc = P.Uc;
+    a.Ul = P.Ul;
     a.nseg = P.nseg;
     a.nlong = P.nlong;
     a.crow = P.crow;
@@ -506,7 +529,7 @@ int run_steps(mlt_matrix* M, const MomentPlan& plan, GroupCtx& g, int k0, int k1
             pa.vgather = cur; pa.vcur = nullptr; pa.vprev_out = W; pa.mode = 2;
             pa.partials = nullptr;
             set_split(pa, M->plan_A, segpart);
-            if ((rc = launch_step<T>(G, pa, g.max_main, g.max_long, &nb, s))) return rc;
+            if ((rc = launch_step<T>(G, pa, g.max_main, g.max_long, M->num_sms, &nb, s))) return rc;
             sa.rowptr = AT.rowptr; sa.col = AT.col; sa.val = valAT; sa.nrows = AT.nrows;
             sa.vgather = W;
             set_split(sa, M->plan_AT, segpart);
@@ -521,7 +544,7 @@ int run_steps(mlt_matrix* M, const MomentPlan& plan, GroupCtx& g, int k0, int k1
         ReduceArgs& ra = g.ra;
         const int slot = k - ra.step0;
         sa.partials = g.part + (size_t)slot * g.max_blocks * 2 * g.ldv;
-        if ((rc = launch_step<T>(G, sa, g.max_main, g.max_long, &nb, s))) return rc;
+        if ((rc = launch_step<T>(G, sa, g.max_main, g.max_long, M->num_sms, &nb, s))) return rc;
         ra.nblocks[slot] = nb;
         ra.act[slot] = act;
         ra.nslots = slot + 1;
@@ -640,11 +663,13 @@ int ensure_spmm_plan(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, cudaStream_t s
     std::vector<int64_t> rp(n + 1);
     MLT_CUDA_TRY(cudaMemcpyAsync(rp.data(), C.rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     MLT_CUDA_TRY(cudaStreamSynchronize(s));
-    // about 64 chunks per SM: small matrices get chunks of a row or two, so even
-    // a narrow probe block keeps every SM busy; large ones cap at 4096 units
+    // about kChunksPerSm chunks per SM (at least 8 units each, at most 4096):
+    // with the resident grid dealing them round-robin, the rows being worked
+    // on at any moment form a band of about 1/(kChunksPerSm/32) of the matrix
     const int64_t units = C.nnz + kRowCost * n;
-    int64_t Uc = units / (64LL * M->num_sms);
+    int64_t Uc = units / (kChunksPerSm * M->num_sms);
     Uc = std::max<int64_t>(8, std::min<int64_t>(4096, Uc));
+    const int64_t Ul = std::max<int64_t>(Uc, kLongRow);
     const int64_t nch = std::max<int64_t>(1, (units + Uc - 1) / Uc);
     std::vector<int64_t> crow(nch);
     {
@@ -659,10 +684,10 @@ int ensure_spmm_plan(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, cudaStream_t s
     std::vector<int64_t> seg_k0, long_seg0;
     for (int64_t r = 0; r < n; ++r) {
         const int64_t deg = rp[r + 1] - rp[r];
-        if (deg <= Uc) continue;
+        if (deg <= Ul) continue;
         long_rows.push_back((int32_t)r);
         long_seg0.push_back((int64_t)seg_row.size());
-        for (int64_t k0 = rp[r]; k0 < rp[r + 1]; k0 += Uc) {
+        for (int64_t k0 = rp[r]; k0 < rp[r + 1]; k0 += Ul) {
             seg_row.push_back((int32_t)r);
             seg_k0.push_back(k0);
         }
@@ -696,6 +721,7 @@ int ensure_spmm_plan(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, cudaStream_t s
     MLT_CUDA_TRY(cudaStreamSynchronize(s));
     P.nch = nch;
     P.Uc = Uc;
+    P.Ul = Ul;
     P.nseg = nseg;
     P.nlong = nlong;
     P.ready = true;
@@ -726,7 +752,7 @@ int spmv_f64(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, const double* x, doubl
     a.partials = nullptr;
     set_split(a, P, M->ws_seg.as<double>());
     int nb = 0;
-    return launch_step<double>(1, a, 8 * M->num_sms, 2 * M->num_sms, &nb, s);
+    return launch_step<double>(1, a, 8 * M->num_sms, 2 * M->num_sms, M->num_sms, &nb, s);
 }
 
 int ensure_fp32_values(mlt_matrix* M, cudaStream_t s)

@@ -61,7 +61,7 @@ struct DevCSR {
 // cheb_kernels.cu): chunks of Uc units and segments of rows longer than Uc.
 struct SpmmPlan {
     bool ready = false;
-    int64_t nch = 0, Uc = 0, nseg = 0;
+    int64_t nch = 0, Uc = 0, Ul = 0, nseg = 0;   // chunks, chunk units, long-row threshold, segments
     int nlong = 0;
     int64_t* crow = nullptr;       // row holding the first unit of each chunk
     int64_t* seg_k0 = nullptr;     // first entry of each segment
