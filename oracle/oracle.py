@@ -296,19 +296,58 @@ def allocate(levels, V, cost_model="symmetric", mode="budget", target=1.0, m_pil
     return m
 
 
+def exact_low_traces(m, a, b, gram=False, scale=1.0):
+    """tr T_j(At) for the low degrees whose traces are cheap to get exactly
+    (the closing remark of Section 5.4), At = alpha A + beta I with
+    alpha = 2/(b-a), beta = -(a+b)/(b-a) (Section 2.2):
+      j = 0:  tr I = d
+      j = 1:  tr At = alpha tr A + beta d
+      j = 2:  tr(2 At^2 - I) = 2 (alpha^2 tr A^2 + 2 alpha beta tr A + beta^2 d) - d,
+              with tr A^2 = ||A||_F^2 for symmetric A.
+    For A = X^T X only j <= 1 (tr X^T X = ||X||_F^2; tr (X^T X)^2 would need the
+    product).  Every entry counts `scale` times its value (a pattern entry is 1);
+    X^T X scales by scale^2.  Sums are exact-rounded (math.fsum)."""
+    alpha = 2.0 / (b - a)
+    beta = -(a + b) / (b - a)
+    v = np.ones(m.nnz) if m.val is None else np.asarray(m.val, dtype=np.float64)
+    sq = math.fsum((v * v).tolist())
+    if gram:
+        d = float(m.ncols)
+        return [d, alpha * (scale * scale * sq) + beta * d]
+    d = float(m.nrows)
+    rows = np.repeat(np.arange(m.nrows), np.diff(m.rowptr))
+    tr_a = scale * math.fsum(v[rows == np.asarray(m.col)].tolist())
+    tr_a2 = scale * scale * sq
+    return [d, alpha * tr_a + beta * d, 2.0 * (alpha * alpha * tr_a2 + 2.0 * alpha * beta * tr_a + beta * beta * d) - d]
+
+
+def with_exact_low(rows, t):
+    """Moment rows with mu_j replaced by its exact trace t_j for every j the row
+    has and t covers: E[mu_j] = t_j, so each band stays unbiased and loses the
+    variance those terms carried."""
+    if t is None or rows.shape[0] == 0:
+        return rows
+    rows = np.array(rows, dtype=np.float64)
+    k = min(len(t), rows.shape[1])
+    rows[:, :k] = np.asarray(t[:k])
+    return rows
+
+
 def mlmc_fixed(m, fn, a, b, n, levels, samples, seed, p=0.0, gram=False, scale=1.0,
-               probe_offset=0):
+               probe_offset=0, exact_low=False):
     """Multilevel estimate with prescribed levels and sample counts (Eq.
     multiEstimator).  Level k draws probes with ids off_k .. off_k + m_k - 1,
-    off_1 = probe_offset, off_{k+1} = off_k + m_k; each is run to degree l_k."""
+    off_1 = probe_offset, off_{k+1} = off_k + m_k; each is run to degree l_k.
+    exact_low: mu_0..mu_2 (mu_0..mu_1 for X^T X) replaced by their exact traces."""
     c = cheb_coeffs(fn, a, b, n, p)
+    t = exact_low_traces(m, a, b, gram, scale) if exact_low else None
     out = _run_levels(m, c, a, b, levels, samples, [None] * len(levels), seed, gram, scale,
-                      probe_offset)
+                      probe_offset, t)
     out["coeffs"] = c
     return out
 
 
-def _run_levels(m, c, a, b, levels, fresh, reuse_rows, seed, gram, scale, offset):
+def _run_levels(m, c, a, b, levels, fresh, reuse_rows, seed, gram, scale, offset, t=None):
     est_terms = []
     var_terms = []
     means = []
@@ -318,6 +357,7 @@ def _run_levels(m, c, a, b, levels, fresh, reuse_rows, seed, gram, scale, offset
     for k, hi in enumerate(levels):
         deg = np.full(fresh[k], hi, dtype=np.int32)
         rows = moments(m, a, b, seed, offset, deg, gram, scale) if fresh[k] > 0 else np.zeros((0, hi + 1))
+        rows = with_exact_low(rows, t)
         offset += fresh[k]
         if reuse_rows[k] is not None:
             rows = np.vstack([reuse_rows[k][:, : hi + 1], rows])
@@ -337,14 +377,16 @@ def _run_levels(m, c, a, b, levels, fresh, reuse_rows, seed, gram, scale, offset
 
 
 def mlmc_auto(m, fn, a, b, n, seed, m_pilot, mode="budget", target=1.0, p=0.0,
-              cost_model="symmetric", max_levels=0, gram=False, scale=1.0, reuse_pilot=True):
+              cost_model="symmetric", max_levels=0, gram=False, scale=1.0, reuse_pilot=True,
+              exact_low=False):
     """Automatic multilevel estimate (Section 3.2): pilot of m_pilot probes (ids
     0 .. m_pilot-1) at degree n, variances of every band, level selection with the
     top-level constraint, allocation, then fresh probes per level (ids from
     m_pilot on, level by level).  The pilot rows are reused as the first m_pilot
     samples of the top level unless reuse_pilot is False."""
     c = cheb_coeffs(fn, a, b, n, p)
-    mu_p = moments(m, a, b, seed, 0, np.full(m_pilot, n, dtype=np.int32), gram, scale)
+    t = exact_low_traces(m, a, b, gram, scale) if exact_low else None
+    mu_p = with_exact_low(moments(m, a, b, seed, 0, np.full(m_pilot, n, dtype=np.int32), gram, scale), t)
     V = pilot_variances(c, mu_p)
     levels = select_levels(V, cost_model, m_pilot if reuse_pilot else 0, mode, target,
                            max_levels)
@@ -354,7 +396,7 @@ def mlmc_auto(m, fn, a, b, n, seed, m_pilot, mode="budget", target=1.0, p=0.0,
     if reuse_pilot:
         fresh[-1] = counts[-1] - m_pilot
         reuse[-1] = mu_p
-    out = _run_levels(m, c, a, b, levels, fresh, reuse, seed, gram, scale, m_pilot)
+    out = _run_levels(m, c, a, b, levels, fresh, reuse, seed, gram, scale, m_pilot, t)
     out["coeffs"] = c
     out["pilot_V"] = V
     out["pilot_mu"] = mu_p

@@ -193,3 +193,61 @@ def test_auto_mlmc_consistent(O):
     c = O.cheb_coeffs("log", 0.1, 8.1, n)
     trp = float(np.sum(O.cheb_eval(c, (2 * lam - 8.2) / 8.0)))
     assert abs(out["estimate"] - trp) < 5 * out["stderr"]
+
+
+# ---- exact low-degree traces (closing remark of Section 5.4) -----------------
+
+def _trace_cheb(lam, a, b, j):
+    th = np.arccos(np.clip((2 * lam - (a + b)) / (b - a), -1.0, 1.0))
+    return float(np.sum(np.cos(j * th)))
+
+
+@pytest.mark.parametrize("kind", ["values", "pattern_scaled", "gram"])
+def test_exact_low_traces_equal_exhaustive_mean_and_eigen(O, kind):
+    # t_j must equal both the mean of mu_j over all 2^d sign vectors (which is
+    # tr T_j exactly) and sum_i T_j(lambda_i) from a dense eigendecomposition
+    gram, scale = False, 1.0
+    if kind == "values":
+        m = synth.random_symmetric(10, 0.5, seed=4, diag_shift=1.5)
+        dense = m.to_dense()
+    elif kind == "pattern_scaled":
+        m = synth.random_graph(10, 0.4, seed=6)
+        scale = 0.7
+        dense = scale * m.to_dense()
+    else:
+        m = synth.sparse_gaussian(7, 9, 0.4, seed=3)
+        gram, scale = True, 1.3
+        X = scale * m.to_dense()
+        dense = X.T @ X
+    lam = np.linalg.eigvalsh(dense)
+    a, b = lam[0] - 0.5, lam[-1] + 0.5
+    t = O.exact_low_traces(m, a, b, gram, scale)
+    assert len(t) == (2 if gram else 3)
+    dim = dense.shape[0]
+    Z = np.array(list(itertools.product([-1.0, 1.0], repeat=dim)))
+    mu = O.moments_z(m, a, b, Z, 2, gram, scale)
+    for j, tj in enumerate(t):
+        assert abs(mu[:, j].mean() - tj) <= 1e-12 * dim
+        assert abs(_trace_cheb(lam, a, b, j) - tj) <= 1e-10 * dim
+
+
+def test_exact_low_keeps_bands_unbiased_and_cuts_variance(O):
+    # the substituted first band still averages to tr p_l exactly (exhaustive
+    # signs), and on random probes its variance is strictly below the plain one
+    d = 10
+    m = synth.random_symmetric(d, 0.5, seed=8, diag_shift=1.0)
+    lam = np.linalg.eigvalsh(m.to_dense())
+    a, b = lam[0] - 0.4, lam[-1] + 0.4
+    n = 8
+    c = O.cheb_coeffs("exp", a, b, n)
+    t = O.exact_low_traces(m, a, b)
+    Z = np.array(list(itertools.product([-1.0, 1.0], repeat=d)))
+    mu = O.with_exact_low(O.moments_z(m, a, b, Z, n), t)
+    q = O.band(c, mu, -1, n)
+    exact = sum(c[j] * _trace_cheb(lam, a, b, j) for j in range(n + 1))
+    assert abs(q.mean() - exact) <= 1e-10 * np.sum(np.abs(c)) * d
+    g = synth.random_symmetric(300, 0.05, seed=9, diag_shift=0.5)
+    plain = O.mlmc_fixed(g, "exp", -4.0, 4.0, 12, [4, 12], [200, 50], seed=3)
+    low = O.mlmc_fixed(g, "exp", -4.0, 4.0, 12, [4, 12], [200, 50], seed=3, exact_low=True)
+    assert low["level_var"][0] < plain["level_var"][0]
+    assert low["level_var"][1] == pytest.approx(plain["level_var"][1], rel=1e-12)
