@@ -321,26 +321,44 @@ def exact_low_traces(m, a, b, gram=False, scale=1.0):
     return [d, alpha * tr_a + beta * d, 2.0 * (alpha * alpha * tr_a2 + 2.0 * alpha * beta * tr_a + beta * beta * d) - d]
 
 
-def with_exact_low(rows, t):
-    """Moment rows with mu_j replaced by its exact trace t_j for every j the row
-    has and t covers: E[mu_j] = t_j, so each band stays unbiased and loses the
-    variance those terms carried."""
-    if t is None or rows.shape[0] == 0:
-        return rows
-    rows = np.array(rows, dtype=np.float64)
-    k = min(len(t), rows.shape[1])
-    rows[:, :k] = np.asarray(t[:k])
-    return rows
+def low_cv_level(q, rows, t):
+    """One level's mean and variance with the low-degree terms as control
+    variates (Section 5.4, applied to the bands as its closing remark
+    suggests): w_j = mu_j - tr T_j(At) for 1 <= j <= J has mean zero
+    (J = 2, or 1 for X^T X, and at most the level's degree), the band samples
+    q are regressed on (1, w) by least squares, and the level's estimate is the
+    intercept mean(q) - a . mean(w) with the residual variance (divisor
+    m - 1 - J).  Reusing the samples for the fit adds an O(1/m) bias, as in the
+    triangle estimator.  The fit is skipped (plain mean and variance) when
+    m <= J + 1 or when the centred covariates are degenerate:
+    det(W^T W) <= 1e-12 * prod(diag(W^T W)) (J = 2), or W^T W <= 0 (J = 1)."""
+    m = q.size
+    J = min(len(t) - 1, rows.shape[1] - 1)
+    plain = (math.fsum(q) / m, float(np.var(q, ddof=1)) if m > 1 else float("nan"))
+    if J < 1 or m <= J + 1:
+        return plain
+    W = rows[:, 1:J + 1] - np.asarray(t[1:J + 1])
+    Wc = W - W.mean(axis=0)
+    qc = q - q.mean()
+    G = Wc.T @ Wc
+    if J == 2:
+        if not (G[0, 0] * G[1, 1] - G[0, 1] ** 2 > 1e-12 * G[0, 0] * G[1, 1]):
+            return plain
+    elif not (G[0, 0] > 0.0):
+        return plain
+    coef, *_ = np.linalg.lstsq(np.column_stack([np.ones(m), W]), q, rcond=None)
+    res = q - np.column_stack([np.ones(m), W]) @ coef
+    return float(coef[0]), float(math.fsum((res * res).tolist()) / (m - 1 - J))
 
 
 def mlmc_fixed(m, fn, a, b, n, levels, samples, seed, p=0.0, gram=False, scale=1.0,
-               probe_offset=0, exact_low=False):
+               probe_offset=0, low_cv=False):
     """Multilevel estimate with prescribed levels and sample counts (Eq.
     multiEstimator).  Level k draws probes with ids off_k .. off_k + m_k - 1,
     off_1 = probe_offset, off_{k+1} = off_k + m_k; each is run to degree l_k.
-    exact_low: mu_0..mu_2 (mu_0..mu_1 for X^T X) replaced by their exact traces."""
+    low_cv: every level with the low-degree control variates of low_cv_level."""
     c = cheb_coeffs(fn, a, b, n, p)
-    t = exact_low_traces(m, a, b, gram, scale) if exact_low else None
+    t = exact_low_traces(m, a, b, gram, scale) if low_cv else None
     out = _run_levels(m, c, a, b, levels, samples, [None] * len(levels), seed, gram, scale,
                       probe_offset, t)
     out["coeffs"] = c
@@ -357,14 +375,16 @@ def _run_levels(m, c, a, b, levels, fresh, reuse_rows, seed, gram, scale, offset
     for k, hi in enumerate(levels):
         deg = np.full(fresh[k], hi, dtype=np.int32)
         rows = moments(m, a, b, seed, offset, deg, gram, scale) if fresh[k] > 0 else np.zeros((0, hi + 1))
-        rows = with_exact_low(rows, t)
         offset += fresh[k]
         if reuse_rows[k] is not None:
             rows = np.vstack([reuse_rows[k][:, : hi + 1], rows])
         q = band(c, rows, lo, hi)
         mk = q.size
-        mean = math.fsum(q) / mk
-        var = float(np.var(q, ddof=1)) if mk > 1 else float("nan")
+        if t is not None:
+            mean, var = low_cv_level(q, rows[:, : hi + 1], t)
+        else:
+            mean = math.fsum(q) / mk
+            var = float(np.var(q, ddof=1)) if mk > 1 else float("nan")
         means.append(mean)
         variances.append(var)
         counts.append(mk)
@@ -378,15 +398,15 @@ def _run_levels(m, c, a, b, levels, fresh, reuse_rows, seed, gram, scale, offset
 
 def mlmc_auto(m, fn, a, b, n, seed, m_pilot, mode="budget", target=1.0, p=0.0,
               cost_model="symmetric", max_levels=0, gram=False, scale=1.0, reuse_pilot=True,
-              exact_low=False):
+              low_cv=False):
     """Automatic multilevel estimate (Section 3.2): pilot of m_pilot probes (ids
     0 .. m_pilot-1) at degree n, variances of every band, level selection with the
     top-level constraint, allocation, then fresh probes per level (ids from
     m_pilot on, level by level).  The pilot rows are reused as the first m_pilot
     samples of the top level unless reuse_pilot is False."""
     c = cheb_coeffs(fn, a, b, n, p)
-    t = exact_low_traces(m, a, b, gram, scale) if exact_low else None
-    mu_p = with_exact_low(moments(m, a, b, seed, 0, np.full(m_pilot, n, dtype=np.int32), gram, scale), t)
+    t = exact_low_traces(m, a, b, gram, scale) if low_cv else None
+    mu_p = moments(m, a, b, seed, 0, np.full(m_pilot, n, dtype=np.int32), gram, scale)
     V = pilot_variances(c, mu_p)
     levels = select_levels(V, cost_model, m_pilot if reuse_pilot else 0, mode, target,
                            max_levels)

@@ -231,23 +231,46 @@ def test_exact_low_traces_equal_exhaustive_mean_and_eigen(O, kind):
         assert abs(_trace_cheb(lam, a, b, j) - tj) <= 1e-10 * dim
 
 
-def test_exact_low_keeps_bands_unbiased_and_cuts_variance(O):
-    # the substituted first band still averages to tr p_l exactly (exhaustive
-    # signs), and on random probes its variance is strictly below the plain one
-    d = 10
-    m = synth.random_symmetric(d, 0.5, seed=8, diag_shift=1.0)
-    lam = np.linalg.eigvalsh(m.to_dense())
-    a, b = lam[0] - 0.4, lam[-1] + 0.4
-    n = 8
-    c = O.cheb_coeffs("exp", a, b, n)
-    t = O.exact_low_traces(m, a, b)
-    Z = np.array(list(itertools.product([-1.0, 1.0], repeat=d)))
-    mu = O.with_exact_low(O.moments_z(m, a, b, Z, n), t)
-    q = O.band(c, mu, -1, n)
-    exact = sum(c[j] * _trace_cheb(lam, a, b, j) for j in range(n + 1))
-    assert abs(q.mean() - exact) <= 1e-10 * np.sum(np.abs(c)) * d
+def test_low_cv_level_regression_and_fallbacks(O):
+    # the fitted control variates: the intercept and residual variance equal
+    # the closed-form normal equations (centred 2x2 solve), the residual sum of
+    # squares never exceeds the plain one, and the documented fallbacks hold
+    rng = np.random.default_rng(0)
+    m = 400
+    t = [10.0, 0.3, -1.2]
+    rows = np.column_stack([np.full(m, 10.0), 0.3 + rng.standard_normal(m), -1.2 + rng.standard_normal(m)])
+    q = 5.0 + 2.0 * (rows[:, 1] - 0.3) - 0.7 * (rows[:, 2] + 1.2) + 0.1 * rng.standard_normal(m)
+    mean, var = O.low_cv_level(q, rows, t)
+    W = rows[:, 1:] - np.array(t[1:])
+    Wc, qc = W - W.mean(0), q - q.mean()
+    G = Wc.T @ Wc
+    r = Wc.T @ qc
+    det = G[0, 0] * G[1, 1] - G[0, 1] * G[1, 0]
+    a = np.array([G[1, 1] * r[0] - G[0, 1] * r[1], G[0, 0] * r[1] - G[1, 0] * r[0]]) / det
+    assert abs(mean - (q.mean() - a @ W.mean(0))) <= 1e-12 * abs(mean)
+    res = qc - Wc @ a
+    assert abs(var - res @ res / (m - 3)) <= 1e-10 * var
+    assert var * (m - 3) <= np.var(q, ddof=1) * (m - 1)
+    assert abs(a[0] - 2.0) < 0.05 and abs(a[1] + 0.7) < 0.05
+    # fallbacks: degree 0 (no covariate), too few samples, degenerate covariates
+    assert O.low_cv_level(q, rows[:, :1], t) == (pytest.approx(q.mean()), pytest.approx(np.var(q, ddof=1)))
+    assert O.low_cv_level(q[:3], rows[:3], t)[0] == pytest.approx(q[:3].mean())
+    flat = rows.copy()
+    flat[:, 2] = -1.2 + 2.0 * (flat[:, 1] - 0.3)       # w_2 = 2 w_1: singular
+    assert O.low_cv_level(q, flat, t)[0] == pytest.approx(q.mean())
+
+
+def test_low_cv_mlmc_unbiased_and_not_worse(O):
+    # with the fitted control variates the first level's residual variance never
+    # exceeds its plain variance on the same probes, and the estimate stays
+    # within a few standard errors of the exact trace (dense eigendecomposition)
     g = synth.random_symmetric(300, 0.05, seed=9, diag_shift=0.5)
-    plain = O.mlmc_fixed(g, "exp", -4.0, 4.0, 12, [4, 12], [200, 50], seed=3)
-    low = O.mlmc_fixed(g, "exp", -4.0, 4.0, 12, [4, 12], [200, 50], seed=3, exact_low=True)
-    assert low["level_var"][0] < plain["level_var"][0]
-    assert low["level_var"][1] == pytest.approx(plain["level_var"][1], rel=1e-12)
+    lam = np.linalg.eigvalsh(g.to_dense())
+    a, b = lam[0] - 0.3, lam[-1] + 0.3
+    c = O.cheb_coeffs("exp", a, b, 12)
+    exact = sum(c[j] * _trace_cheb(lam, a, b, j) for j in range(13))
+    for seed in (3, 4, 5):
+        plain = O.mlmc_fixed(g, "exp", a, b, 12, [4, 12], [200, 50], seed=seed)
+        cv = O.mlmc_fixed(g, "exp", a, b, 12, [4, 12], [200, 50], seed=seed, low_cv=True)
+        assert cv["level_var"][0] * 197 <= plain["level_var"][0] * 199
+        assert abs(cv["estimate"] - exact) < 5 * cv["stderr"]
