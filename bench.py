@@ -16,8 +16,8 @@ One step is one pass of the whole hot path over one batch of synthetic input:
       levels {8, 32, 128} with {256, 64, 16} probes, FP64.  Units: probe-matvecs
       with the doubling evaluation (3072 per step).
   estrada_rmat22: FP32 Chebyshev moments of the scale-22 R-MAT adjacency
-      scaled to spectral radius <= 10 (interval [-10, 10]), 256 probes to
-      degree 128.  Units: probe-matvecs (64 per probe).
+      scaled to spectral radius 10 (a Lanczos bound; interval [-10, 10]),
+      256 probes to degree 128.  Units: probe-matvecs (64 per probe).
   diffusion64_batched: FP64 log-det level moments of 64 3D diffusion
       operators (10^3 .. 100^3 grids) in one CUDA-graph launch.  Units:
       probe-matvecs summed over the matrices.
@@ -66,6 +66,18 @@ PROBE_BASE_SHIFT = 28
 
 def probe_base(rank):
     return int(rank) << PROBE_BASE_SHIFT
+
+
+def estrada_scale(mlt, csr, radius=10.0):
+    """Scale that brings the adjacency's spectral radius to `radius`: the
+    Lanczos interval (60 steps, Ritz values widened by their residuals and 1%)
+    bounds the spectrum, so [-radius, radius] holds the scaled spectrum."""
+    M0 = mlt.Matrix(csr)
+    try:
+        lo, hi = mlt.mlt_spectrum_bounds(M0.handle, mlt.MLT_BOUNDS_LANCZOS, 60, 0)
+    finally:
+        M0.close()
+    return radius / max(abs(lo), abs(hi))
 
 
 def step_flops(d, nnz, probe_matvecs):
@@ -215,8 +227,15 @@ class Triangles:
         return {"workload": self.name, "graph": "R-MAT scale 20, edge factor 16, a=0.57 b=c=0.19, seed 0",
                 "d": self.d, "nnz": self.nnz, "probes": self.NPROBES, "block": self.BLOCK,
                 "control_variates": True,
-                "l2": "inputs larger than L2 (col 4*nnz = %.0f MB + rowptr %.0f MB + y 128 B/row = %.0f MB)"
-                      % (4e-6 * self.nnz, 8e-6 * self.d, 128e-6 * self.d)}
+                "l2": "inputs larger than L2 (col 4*nnz = %.0f MB + rowptr %.0f MB + y rows %.0f MB)"
+                      % (4e-6 * self.nnz, 8e-6 * self.d, 1e-6 * self._ybytes())}
+
+    def _ybytes(self):
+        """Bytes of y for one block: 128 per int8 row (degree <= 127), 256 per
+        int16 row (<= 32767), 512 per int32 row; isolated rows have none."""
+        deg = np.diff(self.csr.rowptr)
+        return int(128 * np.sum((deg > 0) & (deg <= 127)) + 256 * np.sum((deg > 127) & (deg <= 32767))
+                   + 512 * np.sum(deg > 32767))
 
     def kernel_bytes(self, launches_per_step):
         """Algorithmic bytes per launch (one 128-probe block) of each kernel:
@@ -226,9 +245,7 @@ class Triangles:
         pass 2 reads the out-list pointers, columns (nnz/2), small-section
         lengths and slots, and y of every row with an edge once."""
         d, nnz = self.d, self.nnz
-        deg = np.diff(self.csr.rowptr)
-        ybytes = int(128 * np.sum((deg > 0) & (deg <= 127)) + 256 * np.sum((deg > 127) & (deg <= 32767))
-                     + 512 * np.sum(deg > 32767))
+        ybytes = self._ybytes()
         return {
             "tri_zbits": 16 * d,
             "tri_pass1": 8 * (d + 1) + 4 * nnz + 16 * d + ybytes,
@@ -360,7 +377,8 @@ class EstradaRmat22:
     def config(self):
         return {"workload": self.name, "graph": "R-MAT scale 22, edge factor 16, seed 1",
                 "d": self.d, "nnz": self.nnz, "probes": self.NPROBES, "degree": self.DEG,
-                "precision": "fp32 vectors, fp64 dots", "interval": [-10.0, 10.0],
+                "precision": "fp32 vectors, compensated fp32 dots per thread, fp64 after",
+                "interval": [-10.0, 10.0], "scale": self.scale,
                 "group_width": getattr(self, "group_width", None),
                 "l2": "inputs larger than L2 (V 2 x %.0f MB)" % (self.d * self.NPROBES * 4e-6)}
 
@@ -368,12 +386,7 @@ class EstradaRmat22:
         return step_bytes(self.d, self.nnz, 4, 4, self.units(), launches_per_step)
 
     def setup(self, mlt, torch, rank):
-        from paper_2103_10516_gb300 import mlt as _m  # noqa: F401
-        # scale so that the Gershgorin radius is 10: spectrum inside [-10, 10]
-        self.M0 = mlt.Matrix(self.csr)
-        _, b = self.M0.bounds()
-        self.M0.close()
-        self.scale = 10.0 / b
+        self.scale = estrada_scale(mlt, self.csr)       # spectral radius 10: spectrum in [-10, 10]
         self.M = mlt.Matrix(self.csr, scale=self.scale)
         # probe-group width by the library's autotuner (untimed setup)
         self.group_width = mlt.mlt_autotune(self.M.handle, "fp32", 4)
@@ -734,30 +747,32 @@ class Stencil3D:
 class EstradaLearned:
     """The learned coarse level against the plain FP64 multilevel estimator,
     at equal standard error, on the Estrada index tr exp(A): R-MAT adjacency
-    (edge factor 16, seed 1) scaled to Gershgorin radius 10, interval
-    [-10, 10], n = 128.
+    (edge factor 16, seed 1) scaled to spectral radius 10 (a Lanczos bound),
+    interval [-10, 10], n = 128.
 
     Setup (untimed, reported in config["comparison"]):
       1. plain FP64 MLMC with levels and sample counts from a 10-probe pilot
          under a fixed matvec budget: estimate, standard error s_p, GPU time t_p;
-      2. the BF16 network trained on 2^16 FP32 probes ((mu_0..mu_15)/d ->
+      2. the BF16 network trained on 2^16 probes ((mu_0..mu_15)/d ->
          P_64/d), GPU time of training;
       3. a small pilot of the learned estimator gives the variances V_k of its
          levels (S, P_64 - S, P_128 - P_64); sample counts m_k follow the
          optimal allocation m_k = sqrt(V_k / C_k) sum_j sqrt(V_j C_j) / s_p^2
          (C = 8, 32, 64 recurrence steps) so that its standard error matches s_p.
-    Step (timed): one learned FP32 estimate with those m_k.  The reported
-    ratio is (s^2 t)_plain / (s^2 t)_learned, the variance-per-GPU-second gain."""
+    Step (timed): one learned estimate with those m_k, its moments in the
+    --precision given (fp32 by default, or fp64).  The reported ratio is
+    (s^2 t)_plain / (s^2 t)_learned, the variance-per-GPU-second gain."""
     name = "estrada_learned"
     unit = "probe-matvecs/s"
-    dtype = "f32+bf16"
     L1, N = 64, 128
     COST = (8, 32, 64)
     PROBE_SPAN = 1 << 28       # training, pilot, timed and e2e ranges below, all inside it
 
-    def __init__(self, scale=None):
+    def __init__(self, scale=None, precision=None):
         from paper_2103_10516_gb300 import synth
         self.scale_log2 = scale or 22
+        self.precision = precision or "fp32"
+        self.dtype = "f32+bf16" if self.precision == "fp32" else "f64+bf16"
         self.csr = synth.rmat_adjacency(self.scale_log2, 16, seed=1)
         self.d = self.csr.nrows
         self.nnz = self.csr.nnz
@@ -772,12 +787,15 @@ class EstradaLearned:
 
     def config(self):
         return {"workload": self.name, "graph": "R-MAT scale %d, edge factor 16, seed 1" % self.scale_log2,
-                "d": self.d, "nnz": self.nnz, "f": "exp", "interval": [-10.0, 10.0], "n": self.N,
-                "l1": self.L1, "train_probes": self.ntrain, "m": self.m, "comparison": self.cmp,
+                "d": self.d, "nnz": self.nnz, "f": "exp", "interval": [-10.0, 10.0], "scale": self.scale,
+                "n": self.N,
+                "l1": self.L1, "train_probes": self.ntrain, "precision": self.precision, "m": self.m,
+                "comparison": self.cmp,
                 "l2": "inputs larger than L2 (V blocks of 4 B x d per probe)"}
 
     def kernel_bytes(self, launches_per_step):
-        return step_bytes(self.d, self.nnz, 4, 4, self.units(), launches_per_step)
+        sv = 8 if self.precision == "fp64" else 4
+        return step_bytes(self.d, self.nnz, 4, sv, self.units(), launches_per_step)
 
     def _timed(self, torch, fn):
         st = torch.cuda.current_stream()
@@ -791,22 +809,20 @@ class EstradaLearned:
 
     def setup(self, mlt, torch, rank):
         sp = torch.cuda.current_stream().cuda_stream
-        M0 = mlt.Matrix(self.csr)
-        self.scale = 10.0 / M0.bounds()[1]
-        M0.close()
+        self.scale = estrada_scale(mlt, self.csr)       # spectral radius 10: spectrum in [-10, 10]
         self.M = mlt.Matrix(self.csr, scale=self.scale)
-        self.group_width = mlt.mlt_autotune(self.M.handle, "fp32", 4)
+        self.group_width = mlt.mlt_autotune(self.M.handle, self.precision, 4)
         base = probe_base(rank)
         plain, t_p = self._timed(torch, lambda: self.M.mlmc(
             "exp", -10.0, 10.0, self.N, seed=3, m_pilot=10, mode="budget", target=self.budget,
             precision="fp64", stream=sp))
         self.S = mlt.Surrogate(5)
         P = mlt.learned_params("exp", -10.0, 10.0, self.N, self.L1, 1, 1, 1, seed=7, probe_offset=base,
-                               precision="fp32", stream=sp)
+                               precision=self.precision, stream=sp)
         loss, t_train = self._timed(torch, lambda: mlt.mlt_learned_train(
             self.M.handle, self.S.handle, P, self.ntrain, base, 40, 2048, 2e-3))
         pil = mlt.learned_params("exp", -10.0, 10.0, self.N, self.L1, 512, 128, 32, seed=11,
-                                 probe_offset=base + (1 << 22), precision="fp32", stream=sp)
+                                 probe_offset=base + (1 << 22), precision=self.precision, stream=sp)
         pilot, t_pil = self._timed(torch, lambda: mlt.mlt_learned_estimate(self.M.handle, self.S.handle, pil))
         V = [max(v, 1e-300) for v in pilot["level_var"]]
         s2 = plain["stderr"] ** 2
@@ -815,14 +831,14 @@ class EstradaLearned:
         self.base = base + (1 << 23)
         self.cmp = {"plain_fp64": {"estimate": plain["estimate"], "stderr": plain["stderr"],
                                    "gpu_s": round(t_p, 4), "levels": plain["levels"], "m": plain["m"],
-                                   "budget_matvecs": self.budget},
-                    "learned_fp32": {"train_gpu_s": round(t_train, 3), "train_loss": loss,
-                                     "pilot_level_var": V, "pilot_gpu_s": round(t_pil, 4)}}
+                                   "level_var": plain["level_var"], "budget_matvecs": self.budget},
+                    "learned": {"precision": self.precision, "train_gpu_s": round(t_train, 3), "train_loss": loss,
+                                "pilot_level_var": V, "pilot_gpu_s": round(t_pil, 4)}}
         self.results = []
 
     def step(self, mlt, stream, i):
         P = mlt.learned_params("exp", -10.0, 10.0, self.N, self.L1, *self.m, seed=13,
-                               probe_offset=self.base + i * sum(self.m), precision="fp32", stream=stream)
+                               probe_offset=self.base + i * sum(self.m), precision=self.precision, stream=stream)
         r = mlt.mlt_learned_estimate(self.M.handle, self.S.handle, P)
         self.results.append((r["estimate"], r["stderr"]))
         return r
@@ -832,7 +848,7 @@ class EstradaLearned:
         if not self.results:
             return
         se = float(np.sqrt(np.mean([e[1] ** 2 for e in self.results])))
-        lp = self.cmp["learned_fp32"]
+        lp = self.cmp["learned"]
         lp.update({"estimate_first": self.results[0][0], "stderr": se, "gpu_s": round(ms_per_step / 1e3, 4),
                    "m": self.m})
         pl = self.cmp["plain_fp64"]
@@ -850,7 +866,7 @@ class EstradaLearned:
                                stream=stream)
         try:
             P = mlt.learned_params("exp", -10.0, 10.0, self.N, self.L1, *self.m, seed=17,
-                                   probe_offset=base_e2e(self.base) + i * sum(self.m), precision="fp32",
+                                   probe_offset=base_e2e(self.base) + i * sum(self.m), precision=self.precision,
                                    stream=stream)
             mlt.mlt_learned_estimate(h, self.S.handle, P)
         finally:
@@ -1045,15 +1061,18 @@ def run_reference(args, dist):
 
 def make_workload(args):
     cls = WORKLOADS[args.workload]
+    kw = {}
     if args.scale is not None:
         if cls is not EstradaLearned:
             raise SystemExit("--scale applies to the estrada_learned workload only")
-        return cls(args.scale)
+        kw["scale"] = args.scale
     if args.precision is not None:
-        if cls not in (NuclearGram, Stencil3D):
-            raise SystemExit("--precision applies to the nuclear_gram and stencil3d workloads only")
-        return cls(args.precision)
-    return cls()
+        if cls not in (NuclearGram, Stencil3D, EstradaLearned):
+            raise SystemExit("--precision applies to nuclear_gram, stencil3d and estrada_learned only")
+        if cls is EstradaLearned and args.precision == "mixed":
+            raise SystemExit("estrada_learned takes fp32 or fp64")
+        kw["precision"] = args.precision
+    return cls(**kw)
 
 
 def main():

@@ -84,6 +84,22 @@ extern "C" {
                               mu_2k = 2 V_k.V_k - mu_0,
                               mu_2k+1 = 2 V_k+1.V_k - mu_1 (ceil(n/2) matvecs) */
 
+/* ---- flags of mlt_mlmc_estimate (with those of mlt_moments) -------------- */
+#define MLT_LOW_CV 4u      /* the low-degree terms as control variates (Section
+                              5.4, applied to the bands as its closing remark
+                              suggests): per level, w_j = mu_j - tr T_j(At)
+                              (j = 1, 2; j = 1 for X^T X; j <= the level's
+                              degree) have mean zero; the band samples are
+                              fitted by least squares on (1, w) and the level
+                              reports the intercept and the residual variance
+                              (divisor m - 1 - J).  The fit reuses the samples
+                              (an O(1/m) bias, as in the triangle estimator)
+                              and is skipped when m <= J + 1 or the centred
+                              covariates are degenerate (det <= 1e-12 x the
+                              product of their sums of squares).  Levels and
+                              sample counts still come from the plain pilot
+                              variances. */
+
 /* ---- spectrum interval methods ------------------------------------------- */
 #define MLT_BOUNDS_GERSHGORIN 0
 #define MLT_BOUNDS_LANCZOS    1
@@ -250,6 +266,19 @@ void mlt_mlmc_default_params(mlt_mlmc_params* p);
  * parameters.
  */
 int mlt_mlmc_estimate(mlt_matrix* m, const mlt_mlmc_params* p, mlt_mlmc_result* r);
+
+/*
+ * Exact traces of the low-degree Chebyshev terms (closing remark of Section
+ * 5.4), At = alpha A + beta I on [a, b] (Section 2.2): t[0] = tr I = d,
+ * t[1] = tr At = alpha tr A + beta d, t[2] = tr T_2(At) = 2 tr At^2 - d with
+ * tr A^2 = ||A||_F^2 (A symmetric).  For a Gram handle only t[0], t[1]
+ * (tr X^T X = ||X||_F^2).  Values count scale times (a pattern entry is 1;
+ * X^T X scales by scale^2).  tr A and ||A||_F^2 are reduced on the device
+ * once per handle in a fixed order.  t: host double[3]; *count (may be NULL)
+ * receives 3, or 2 for a Gram handle.  Errors: MLT_EINVAL (null handle or
+ * t, a >= b), MLT_ECUDA.
+ */
+int mlt_low_traces(mlt_matrix* m, double a, double b, double* t, int* count, void* stream);
 
 /*
  * Triangle-count estimate tr(A^3)/6 for a symmetric 0/1 adjacency matrix with

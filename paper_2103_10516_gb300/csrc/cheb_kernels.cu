@@ -49,7 +49,7 @@ constexpr int kThreads = 256;
 constexpr int kSlots = 16;          // steps whose partials are buffered before a reduction
 constexpr int64_t kRowCost = 4;     // units charged per row (the epilogue) on top of its entries
 constexpr int64_t kChunksPerSm = 1024;  // work chunks per SM in the split of an operand
-constexpr int64_t kLongRow = 1024;  // rows above max(Uc, this) are cut into segments
+constexpr int64_t kLongRow = 128;   // rows above max(Uc, this) are cut into segments
 
 template <typename T> struct Lanes;
 template <> struct Lanes<double> { static constexpr int N = 2; };   // 16-byte vectors

@@ -210,6 +210,85 @@ __global__ void absrow_kernel(const int64_t* __restrict__ rowptr, const double* 
     }
 }
 
+// Per CTA: the sum of the diagonal and the sum of squared values of rows
+// blockIdx.x*256 + threadIdx.x (+ grid stride), reduced in a fixed tree.
+__global__ void __launch_bounds__(256) low_sums_kernel(const int64_t* __restrict__ rowptr,
+                                                       const int32_t* __restrict__ col,
+                                                       const double* __restrict__ val, int64_t nrows,
+                                                       double* __restrict__ part)
+{
+    __shared__ double sd[256], ss[256];
+    double dg = 0.0, sq = 0.0;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+            const double v = val ? val[k] : 1.0;
+            if (col[k] == r) dg += v;
+            sq += v * v;
+        }
+    }
+    sd[threadIdx.x] = dg;
+    ss[threadIdx.x] = sq;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sd[threadIdx.x] += sd[threadIdx.x + o];
+            ss[threadIdx.x] += ss[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = sd[0];
+        part[2 * blockIdx.x + 1] = ss[0];
+    }
+}
+
+// tr T_j(At) for j = 0, 1, 2 (j <= 1 for a Gram handle) from d, tr A and
+// ||A||_F^2 (closing remark of Section 5.4); the two sums are reduced on the
+// device once per handle, in a fixed order.
+int low_traces(mlt_matrix* M, double a, double b, double* t, int* count, cudaStream_t s)
+{
+    if (!M->low_ready) {
+        const int64_t nr = M->A.nrows;
+        const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((nr + 255) / 256, 16LL * M->num_sms));
+        int rc;
+        if ((rc = M->ws_out.ensure((size_t)2 * nb * sizeof(double), s))) return rc;
+        double* part = M->ws_out.as<double>();
+        {
+            ProfScope ps("low_sums", s);
+            low_sums_kernel<<<nb, 256, 0, s>>>(M->A.rowptr, M->A.col, M->A.val64, nr, part);
+        }
+        MLT_CUDA_TRY(cudaGetLastError());
+        std::vector<double> h(2 * (size_t)nb);
+        MLT_CUDA_TRY(cudaMemcpyAsync(h.data(), part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        MLT_CUDA_TRY(cudaStreamSynchronize(s));
+        double dg = 0.0, sq = 0.0;
+        for (int i = 0; i < nb; ++i) {
+            dg += h[2 * (size_t)i];
+            sq += h[2 * (size_t)i + 1];
+        }
+        M->low_diag = dg;
+        M->low_sq = sq;
+        M->low_ready = true;
+    }
+    const double alpha = 2.0 / (b - a), beta = -(a + b) / (b - a);
+    const double sc = M->scale;
+    const double d = (double)M->dim();
+    if (M->flags & MLT_GRAM) {
+        t[0] = d;
+        t[1] = alpha * (sc * sc * M->low_sq) + beta * d;
+        t[2] = 0.0;
+        if (count) *count = 2;
+        return MLT_OK;
+    }
+    const double tr_a = sc * M->low_diag, tr_a2 = sc * sc * M->low_sq;
+    t[0] = d;
+    t[1] = alpha * tr_a + beta * d;
+    t[2] = 2.0 * (alpha * alpha * tr_a2 + 2.0 * alpha * beta * tr_a + beta * beta * d) - d;
+    if (count) *count = 3;
+    return MLT_OK;
+}
+
 int gershgorin_device(mlt_matrix* M, double* lo, double* hi, cudaStream_t s)
 {
     int rc;
@@ -891,6 +970,16 @@ int mlt_mlmc_estimate(mlt_matrix* m, const mlt_mlmc_params* P, mlt_mlmc_result* 
         int64_t matvecs = 0;
         const int dir = (P->flags & MLT_DIRECT) ? 1 : 0;
         auto steps_of = [&](int l) -> int64_t { return dir ? l : (l + 1) / 2; };
+        if (P->flags & ~(MLT_DIRECT | MLT_LOW_CV)) return fail(MLT_EINVAL, "mlt_mlmc_estimate: unknown flags");
+        const unsigned mflags = P->flags & ~MLT_LOW_CV;     // the moment call's own flags
+        // with MLT_LOW_CV, w_j = mu_j - tr T_j(At) (1 <= j < nlow) are the control variates
+        double tlow[3] = {0.0, 0.0, 0.0};
+        int nlow = 0;
+        if (P->flags & MLT_LOW_CV) {
+            if (!(P->a < P->b)) return fail(MLT_EINVAL, "mlt_mlmc_estimate: need a < b");
+            rc = low_traces(m, P->a, P->b, tlow, &nlow, (cudaStream_t)P->stream);
+            if (rc) return rc;
+        }
         if (P->nlevels > 0) {
             if (P->nlevels > MLT_MAX_LEVELS) return fail(MLT_EINVAL, "mlt_mlmc_estimate: too many levels");
             for (int k = 0; k < P->nlevels; ++k) {
@@ -912,7 +1001,7 @@ int mlt_mlmc_estimate(mlt_matrix* m, const mlt_mlmc_params* P, mlt_mlmc_result* 
                 return fail(MLT_EINVAL, "mlt_mlmc_estimate: unknown mode");
             pilot.assign((size_t)m_pilot * (n + 1), 0.0);
             std::vector<int32_t> pdeg(m_pilot, n);
-            rc = mlt_moments(m, P->a, P->b, P->seed, 0, m_pilot, pdeg.data(), P->precision, P->flags,
+            rc = mlt_moments(m, P->a, P->b, P->seed, 0, m_pilot, pdeg.data(), P->precision, mflags,
                              pilot.data(), n + 1, P->stream);
             if (rc) return rc;
             matvecs += (int64_t)m_pilot * steps_of(n);
@@ -942,7 +1031,7 @@ int mlt_mlmc_estimate(mlt_matrix* m, const mlt_mlmc_params* P, mlt_mlmc_result* 
         }
         std::vector<double> mu((size_t)std::max<int64_t>(total, 1) * (n + 1));
         if (total > 0) {
-            rc = mlt_moments(m, P->a, P->b, P->seed, next_id, total, deg.data(), P->precision, P->flags,
+            rc = mlt_moments(m, P->a, P->b, P->seed, next_id, total, deg.data(), P->precision, mflags,
                              mu.data(), n + 1, P->stream);
             if (rc) return rc;
         }
@@ -954,23 +1043,70 @@ int mlt_mlmc_estimate(mlt_matrix* m, const mlt_mlmc_params* P, mlt_mlmc_result* 
         int lo = -1;
         for (int k = 0; k < L; ++k) {
             const int hi = levels[k];
-            std::vector<double> samples;
+            std::vector<double> samples, w1, w2;
             samples.reserve(counts[k]);
+            const int J = std::min(nlow - 1, hi);        // control variates this level has (0: none)
             auto band = [&](const double* row) {
                 double s = 0.0;
                 for (int j = lo + 1; j <= hi; ++j) s += c[j] * row[j];
-                return s;
+                samples.push_back(s);
+                if (J >= 1) w1.push_back(row[1] - tlow[1]);
+                if (J >= 2) w2.push_back(row[2] - tlow[2]);
             };
             if (k == L - 1 && m_pilot > 0 && P->reuse_pilot)
-                for (int p = 0; p < m_pilot; ++p) samples.push_back(band(&pilot[(size_t)p * (n + 1)]));
-            for (int64_t i = 0; i < fresh[k]; ++i, ++q) samples.push_back(band(&mu[(size_t)q * (n + 1)]));
+                for (int p = 0; p < m_pilot; ++p) band(&pilot[(size_t)p * (n + 1)]);
+            for (int64_t i = 0; i < fresh[k]; ++i, ++q) band(&mu[(size_t)q * (n + 1)]);
             const int64_t mk = (int64_t)samples.size();
             double mean = 0.0;
             for (double v : samples) mean += v;
             mean /= (double)mk;
             double ss = 0.0;
             for (double v : samples) ss += (v - mean) * (v - mean);
-            const double var = mk > 1 ? ss / (double)(mk - 1) : std::nan("");
+            double var = mk > 1 ? ss / (double)(mk - 1) : std::nan("");
+            // the low-degree control variates (Section 5.4): least squares of the
+            // band on (1, w); the level's estimate is the intercept, its variance
+            // the residual one (divisor m - 1 - J); skipped when m <= J + 1 or the
+            // centred covariates are degenerate
+            if (J >= 1 && mk > J + 1) {
+                double m1 = 0.0, m2 = 0.0;
+                for (int64_t i = 0; i < mk; ++i) {
+                    m1 += w1[i];
+                    if (J >= 2) m2 += w2[i];
+                }
+                m1 /= (double)mk;
+                m2 /= (double)mk;
+                double g11 = 0.0, g12 = 0.0, g22 = 0.0, r1 = 0.0, r2 = 0.0;
+                for (int64_t i = 0; i < mk; ++i) {
+                    const double e = samples[i] - mean, u = w1[i] - m1, v = J >= 2 ? w2[i] - m2 : 0.0;
+                    g11 += u * u;
+                    g12 += u * v;
+                    g22 += v * v;
+                    r1 += u * e;
+                    r2 += v * e;
+                }
+                double a1 = 0.0, a2 = 0.0;
+                bool ok = false;
+                if (J >= 2) {
+                    const double det = g11 * g22 - g12 * g12;
+                    if (det > 1e-12 * g11 * g22) {
+                        a1 = (g22 * r1 - g12 * r2) / det;
+                        a2 = (g11 * r2 - g12 * r1) / det;
+                        ok = true;
+                    }
+                } else if (g11 > 0.0) {
+                    a1 = r1 / g11;
+                    ok = true;
+                }
+                if (ok) {
+                    double rs = 0.0;
+                    for (int64_t i = 0; i < mk; ++i) {
+                        const double e = (samples[i] - mean) - a1 * (w1[i] - m1) - (J >= 2 ? a2 * (w2[i] - m2) : 0.0);
+                        rs += e * e;
+                    }
+                    mean = mean - a1 * m1 - a2 * m2;
+                    var = rs / (double)(mk - 1 - J);
+                }
+            }
             R->levels[k] = hi;
             R->m[k] = mk;
             R->level_mean[k] = mean;
@@ -990,6 +1126,17 @@ int mlt_mlmc_estimate(mlt_matrix* m, const mlt_mlmc_params* P, mlt_mlmc_result* 
         return fail(MLT_ENOMEM, "mlt_mlmc_estimate: host allocation failed");
     } catch (...) {
         return fail(MLT_ECUDA, "mlt_mlmc_estimate: exception");
+    }
+}
+
+int mlt_low_traces(mlt_matrix* m, double a, double b, double* t, int* count, void* stream)
+{
+    try {
+        if (!m || !t) return fail(MLT_EINVAL, "mlt_low_traces: null argument");
+        if (!(a < b) || !std::isfinite(a) || !std::isfinite(b)) return fail(MLT_EINVAL, "mlt_low_traces: need finite a < b");
+        return low_traces(m, a, b, t, count, (cudaStream_t)stream);
+    } catch (...) {
+        return fail(MLT_ECUDA, "mlt_low_traces: exception");
     }
 }
 

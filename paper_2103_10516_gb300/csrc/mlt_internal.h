@@ -103,6 +103,8 @@ struct mlt_matrix {
         int64_t nch1 = 0, nch2 = 0;
     } tri;
     int tri_state = 0;          // 0 unprepared, 1 ready, <0 error code
+    bool low_ready = false;     // sum of the diagonal and of squared values, unscaled
+    double low_diag = 0.0, low_sq = 0.0;
     double tri_bound = 0.0;     // sum_(i,j) deg_i deg_j
     int group_width = 0;        // probes per group chosen by mlt_autotune (0: from memory)
     // scratch

@@ -949,7 +949,7 @@ int tri_prepare(mlt_matrix* M, cudaStream_t s)
         ProfScope ps("tri_prepare", s);
         tri_prepare_kernel<<<grid_for(M->num_sms, d), kTriThreads, 0, s>>>(
             M->A.rowptr, M->A.col, d, out_ptr, nsmall, bslot, longlist, counters, bound);
-        tri_prepare_long_kernel<<<2 * M->num_sms, kTriThreads, 0, s>>>(M->A.rowptr, M->A.col, longlist, out_ptr,
+        tri_prepare_long_kernel<<<8 * M->num_sms, kTriThreads, 0, s>>>(M->A.rowptr, M->A.col, longlist, out_ptr,
                                                                        nsmall, counters, bound);
     }
     MLT_CUDA_TRY(cudaGetLastError());
@@ -990,7 +990,7 @@ int tri_prepare(mlt_matrix* M, cudaStream_t s)
         fill_out_kernel<<<grid_for(M->num_sms, d), kTriThreads, 0, s>>>(M->A.rowptr, M->A.col, d, out_ptr, nsmall,
                                                                         bslot, out_col, pairs, hc[3], counters + 4);
         if (hc[1] > 0)
-            fill_out_long_kernel<<<(unsigned)std::min<int64_t>(hc[1], 2LL * M->num_sms), kTriThreads, 0, s>>>(
+            fill_out_long_kernel<<<(unsigned)std::min<int64_t>(hc[1], 8LL * M->num_sms), kTriThreads, 0, s>>>(
                 M->A.rowptr, M->A.col, longlist, hc[1], out_ptr, nsmall, bslot, out_col, pairs, hc[3], counters + 4);
     }
     MLT_CUDA_TRY(cudaGetLastError());

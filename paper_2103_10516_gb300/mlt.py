@@ -24,6 +24,7 @@ MLT_GRAM, MLT_DEVICE_PTRS = 1, 2
 MLT_FN = {"log": 0, "sqrt": 1, "exp": 2, "inv": 3, "pow": 4, "cube": 5}
 MLT_PREC = {"fp64": 0, "fp32": 1}
 MLT_DIRECT = 1
+MLT_LOW_CV = 4
 MLT_BOUNDS_GERSHGORIN, MLT_BOUNDS_LANCZOS = 0, 1
 MLT_MAX_LEVELS = 1024
 MLT_MAX_DEGREE = 4096
@@ -36,7 +37,7 @@ EXPORTS = ["mlt_create_csr", "mlt_destroy", "mlt_matrix_info", "mlt_spectrum_bou
            "mlt_surrogate_create", "mlt_surrogate_destroy", "mlt_surrogate_set_params",
            "mlt_surrogate_get_params", "mlt_surrogate_loss_grad", "mlt_surrogate_train",
            "mlt_surrogate_predict", "mlt_learned_train", "mlt_learned_estimate",
-           "mlt_moments_batched", "mlt_autotune", "mlt_moments_noalloc"]
+           "mlt_moments_batched", "mlt_autotune", "mlt_moments_noalloc", "mlt_low_traces"]
 
 
 class MLTError(RuntimeError):
@@ -94,6 +95,7 @@ def lib():
     L.mlt_mlmc_estimate.argtypes = [vp, ctypes.POINTER(mlt_mlmc_params), ctypes.POINTER(mlt_mlmc_result)]
     L.mlt_triangle_trace.argtypes = [vp, u64, i64, i64, ci, ci, vp, ctypes.POINTER(dbl),
                                      ctypes.POINTER(dbl), vp]
+    L.mlt_low_traces.argtypes = [vp, dbl, dbl, vp, ctypes.POINTER(ci), vp]
     L.mlt_profile_start.argtypes = []
     L.mlt_profile_stop.argtypes = [ctypes.POINTER(mlt_kernel_stat), ci, ctypes.POINTER(ci)]
     L.mlt_last_error.argtypes = []
@@ -172,6 +174,14 @@ def mlt_spectrum_bounds(handle, method=MLT_BOUNDS_GERSHGORIN, steps=0, seed=0):
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(lib().mlt_spectrum_bounds(handle, method, steps, seed, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def mlt_low_traces(handle, a, b, stream=None):
+    """[tr T_0, tr T_1, tr T_2] of the mapped operator (two values for X^T X)."""
+    t = np.zeros(3)
+    k = ctypes.c_int()
+    _check(lib().mlt_low_traces(handle, float(a), float(b), _ptr(t), ctypes.byref(k), _stream(stream)))
+    return t[: k.value]
 
 
 def mlt_cheb_coeffs(fn, a, b, n, p=0.0):
@@ -281,7 +291,7 @@ class Matrix:
 
     def mlmc(self, fn, a, b, n, seed=0, levels=None, m=None, m_pilot=10, mode="budget",
              target=1000.0, cost_model="symmetric", max_levels=0, reuse_pilot=True,
-             precision="fp64", direct=False, p=0.0, stream=None):
+             precision="fp64", direct=False, p=0.0, low_cv=False, stream=None):
         P = mlt_mlmc_default_params()
         P.fn = MLT_FN[fn] if isinstance(fn, str) else fn
         P.fn_p = p
@@ -300,7 +310,7 @@ class Matrix:
         P.max_levels = int(max_levels)
         P.reuse_pilot = int(bool(reuse_pilot))
         P.precision = MLT_PREC[precision]
-        P.flags = MLT_DIRECT if direct else 0
+        P.flags = (MLT_DIRECT if direct else 0) | (MLT_LOW_CV if low_cv else 0)
         P.stream = _stream(stream)
         return mlt_mlmc_estimate(self.handle, P)
 

@@ -1,6 +1,8 @@
 """GPU parity of the multilevel estimator (mlt_mlmc_estimate) against the
 oracle on the same probes: same levels and sample counts, and estimates within
-1e-10 * sum|c_j| * d (each band is a c-weighted sum of moments with |mu_j| <= d)."""
+1e-10 * sum|c_j| * d (each band is a c-weighted sum of moments with |mu_j| <= d).
+Also the exact low-degree traces (mlt_low_traces) and the low-degree control
+variates (MLT_LOW_CV) of Section 5.4."""
 import numpy as np
 import pytest
 
@@ -61,3 +63,58 @@ def test_nuclear_norm_gram(L, O):
     ref = O.mlmc_fixed(X, "sqrt", a, b, 40, [4, 12, 40], [40, 12, 6], seed=0, gram=True)
     tol = 1e-10 * np.sum(np.abs(ref["coeffs"])) * 150
     assert abs(got["estimate"] - ref["estimate"]) <= tol
+
+
+@pytest.mark.parametrize("kind", ["values", "pattern_scaled", "gram", "fp32_values"])
+def test_low_traces_match_oracle(L, O, kind):
+    gram, scale, vdt = False, 1.0, None
+    if kind == "values":
+        m = synth.grid_laplacian_2d(40, shift=0.3)
+        a, b = 0.3, 8.3
+    elif kind == "pattern_scaled":
+        m = synth.rmat_adjacency(12, 8, seed=3)
+        scale = 0.05
+        a, b = -4.0, 4.0
+    elif kind == "gram":
+        m = synth.sparse_gaussian(500, 200, 0.02, seed=5)
+        gram, scale = True, 0.8
+        a, b = 0.0, 60.0
+    else:
+        m = synth.random_symmetric(700, 0.01, seed=4, diag_shift=2.0)
+        m = synth.CSR(m.nrows, m.ncols, m.rowptr, m.col, m.val.astype(np.float32).astype(np.float64))
+        vdt = np.float32
+        a, b = -3.0, 7.0
+    with L.Matrix(m, gram=gram, scale=scale, vals_dtype=vdt) as M:
+        got = L.mlt_low_traces(M.handle, a, b)
+    ref = O.exact_low_traces(m, a, b, gram, scale)
+    assert len(got) == len(ref)
+    # both sides add the same terms in different orders: the difference is a
+    # few roundings of the magnitudes the sums carry
+    alpha = 2.0 / (b - a)
+    v = np.ones(m.nnz) if m.val is None else np.abs(m.val)
+    mag = (m.ncols if gram else m.nrows) + abs(alpha) * scale * np.sum(v) + (alpha * scale) ** 2 * np.sum(v * v)
+    assert np.max(np.abs(got - np.array(ref))) <= 1e-13 * mag * 8
+
+
+def test_low_cv_mlmc_matches_oracle(L, O):
+    # fixed and automatic levels with the low-degree control variates: same
+    # levels, counts, estimates and level variances as the oracle, and no level
+    # whose residual variance exceeds its plain variance (least squares)
+    m = synth.random_symmetric(3000, 0.002, seed=11, diag_shift=1.0)
+    with L.Matrix(m) as M0:
+        lo, hi = M0.bounds()
+    ref = O.mlmc_fixed(m, "exp", lo, hi, 24, [4, 24], [300, 40], seed=5, low_cv=True)
+    plain = O.mlmc_fixed(m, "exp", lo, hi, 24, [4, 24], [300, 40], seed=5)
+    with L.Matrix(m) as M:
+        got = M.mlmc("exp", lo, hi, 24, seed=5, levels=[4, 24], m=[300, 40], low_cv=True)
+        auto = M.mlmc("exp", lo, hi, 24, seed=6, m_pilot=12, mode="budget", target=2000.0, low_cv=True)
+    tol = 1e-10 * np.sum(np.abs(ref["coeffs"])) * m.nrows
+    assert got["m"] == [300, 40]
+    assert abs(got["estimate"] - ref["estimate"]) <= tol
+    assert np.max(np.abs(np.array(got["level_mean"]) - ref["level_mean"])) <= tol
+    assert np.allclose(got["level_var"], ref["level_var"], rtol=1e-8)
+    for k, mk in enumerate((300, 40)):
+        assert got["level_var"][k] * (mk - 3) <= plain["level_var"][k] * (mk - 1) * (1 + 1e-9)
+    aref = O.mlmc_auto(m, "exp", lo, hi, 24, seed=6, m_pilot=12, mode="budget", target=2000.0, low_cv=True)
+    assert auto["levels"] == aref["levels"] and auto["m"] == aref["m"]
+    assert abs(auto["estimate"] - aref["estimate"]) <= tol
