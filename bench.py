@@ -3,7 +3,7 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload rmat20_triangles|logdet64|estrada_rmat22|diffusion64_batched|
-                                nuclear_gram|stencil3d|estrada_learned]
+                                nuclear_gram|nuclear_explicit|stencil3d|estrada_learned|level_study]
                     [--precision fp32|fp64|mixed] [--scale S]
 
 One step is one pass of the whole hot path over one batch of synthetic input:
@@ -24,9 +24,14 @@ One step is one pass of the whole hot path over one batch of synthetic input:
   nuclear_gram: moments of X^T X (X 2^18 x 2^16, density 1e-4) for the
       nuclear norm, 512 probes to degree 512, in the --precision given.
       Units: probe-matvecs (X then X^T).
+  nuclear_explicit: the same with A = X^T X formed once on the host and
+      applied as one SpMM per step (the bandwidth ablation).
   stencil3d: moments of the 7-point 3D diffusion operator on a 100^3 grid,
       128 probes to degree 128, in the --precision given (fp32 default): the
       streaming case of the fused step.
+  level_study: the automated-level experiments of Section 5 (level counts,
+      budget split, degree sweep against single-level) on a synthetic stand-in
+      for the paper's FA graph; the study is in config.
   estrada_learned: the learned coarse level (BF16 network, FP32 moments)
       against plain FP64 MLMC at equal standard error on the Estrada index of
       an R-MAT graph (scale 22 unless --scale); the comparison is in config.
@@ -664,6 +669,68 @@ class NuclearGram:
         return int(np.sum(deg))                  # direct recurrence: one probe-matvec per degree
 
 
+class NuclearExplicit(NuclearGram):
+    """The nuclear-norm workload with A = X^T X formed explicitly (a sparse
+    product on the host, about 11M entries) and run through the plain
+    recurrence: the bandwidth ablation of the two-SpMM Gram operator.  Same
+    probes, degree, precision and Lanczos interval (taken from the Gram
+    handle)."""
+    name = "nuclear_explicit"
+
+    def __init__(self, precision=None):
+        super().__init__(precision)
+        import scipy.sparse as sp
+        from paper_2103_10516_gb300 import synth
+        X = sp.csr_matrix((self.X.val, self.X.col, self.X.rowptr), shape=(self.X.nrows, self.X.ncols))
+        A = (X.T @ X).tocsr()
+        A.sort_indices()
+        self.A = synth.CSR(A.shape[0], A.shape[1], A.indptr.astype(np.int64), A.indices.astype(np.int32),
+                           A.data.astype(np.float64))
+        self.nnz_a = int(A.nnz)
+
+    def config(self):
+        c = super().config()
+        c.update({"workload": self.name, "operator": "A = X^T X formed explicitly (one SpMM per step)",
+                  "nnz_A": self.nnz_a})
+        return c
+
+    def kernel_bytes(self, launches_per_step):
+        sv = 8 if self.precision == "fp64" else 4
+        return step_bytes(self.d, self.nnz_a, 4 + sv, sv, self.units(), launches_per_step)
+
+    def setup(self, mlt, torch, rank):
+        G = mlt.Matrix(self.X, gram=True)
+        self.ab = [round(v, 6) for v in mlt.mlt_spectrum_bounds(G.handle, mlt.MLT_BOUNDS_LANCZOS, 50, 0)]
+        G.close()
+        self.M = mlt.Matrix(self.A)
+        self.group_width = mlt.mlt_autotune(self.M.handle, "fp32" if self.precision != "fp64" else "fp64", 4)
+        self.out = torch.empty((self.NPROBES, self.DEG + 1), dtype=torch.float64, device="cuda")
+        self.deg = np.full(self.NPROBES, self.DEG, dtype=np.int32)
+        self.base = probe_base(rank)
+
+    def e2e_setup(self, torch):
+        self.h = (torch.from_numpy(self.A.rowptr).pin_memory(), torch.from_numpy(self.A.col).pin_memory(),
+                  torch.from_numpy(self.A.val).pin_memory())
+        self.h_out = torch.empty((self.NPROBES, self.DEG + 1), dtype=torch.float64).pin_memory()
+        return (sum(t.numel() * t.element_size() for t in self.h), self.h_out.numel() * 8)
+
+    def e2e_step(self, mlt, stream, i):
+        r, c, v = self.h
+        h = mlt.mlt_create_csr(self.d, self.d, self.nnz_a, r, c, v, stream=stream)
+        try:
+            mlt.mlt_moments(h, self.ab[0], self.ab[1], 0, self.base + (1024 + i) * self.NPROBES, self.deg,
+                            precision=self._prec(mlt), out=self.h_out, stream=stream)
+        finally:
+            mlt.mlt_destroy(h)
+
+    def cpu_sample(self, oracle, nprobes, offset):
+        if not hasattr(self, "ab"):
+            self.ab = [0.0, gram_upper(self.X)]
+        deg = np.full(nprobes, 16, dtype=np.int32)
+        oracle.moments(self.A, self.ab[0], self.ab[1], 0, offset, deg)
+        return int(np.sum(deg))
+
+
 class Stencil3D:
     """Chebyshev moments of one large 3D diffusion operator: the 7-point
     operator on a 100^3 grid (d = 10^6, lognormal coefficients, seed 0, shift
@@ -684,7 +751,7 @@ class Stencil3D:
         self.nnz = self.csr.nnz
         self.precision = precision or "fp32"
         # DRAM bytes per launch (128 live probes) from an ncu capture of the FP32 step
-        self.TRAFFIC = {"cheb_step": 2.1725e9} if self.precision == "fp32" else {}
+        self.TRAFFIC = {"cheb_step": 1.5712e9} if self.precision == "fp32" else {}
         self.dtype = {"fp32": "f32", "fp64": "f64", "mixed": "f32+f64"}[self.precision]
 
     def _prec(self, mlt):
@@ -816,6 +883,11 @@ class EstradaLearned:
         plain, t_p = self._timed(torch, lambda: self.M.mlmc(
             "exp", -10.0, 10.0, self.N, seed=3, m_pilot=10, mode="budget", target=self.budget,
             precision="fp64", stream=sp))
+        # the same plain estimator with FP32 moments, to separate the precision
+        # from the learned level in the comparison
+        plain32, t_p32 = self._timed(torch, lambda: self.M.mlmc(
+            "exp", -10.0, 10.0, self.N, seed=3, m_pilot=10, mode="budget", target=self.budget,
+            precision="fp32", stream=sp))
         self.S = mlt.Surrogate(5)
         P = mlt.learned_params("exp", -10.0, 10.0, self.N, self.L1, 1, 1, 1, seed=7, probe_offset=base,
                                precision=self.precision, stream=sp)
@@ -832,6 +904,8 @@ class EstradaLearned:
         self.cmp = {"plain_fp64": {"estimate": plain["estimate"], "stderr": plain["stderr"],
                                    "gpu_s": round(t_p, 4), "levels": plain["levels"], "m": plain["m"],
                                    "level_var": plain["level_var"], "budget_matvecs": self.budget},
+                    "plain_fp32": {"estimate": plain32["estimate"], "stderr": plain32["stderr"],
+                                   "gpu_s": round(t_p32, 4), "levels": plain32["levels"], "m": plain32["m"]},
                     "learned": {"precision": self.precision, "train_gpu_s": round(t_train, 3), "train_loss": loss,
                                 "pilot_level_var": V, "pilot_gpu_s": round(t_pil, 4)}}
         self.results = []
@@ -854,6 +928,9 @@ class EstradaLearned:
         pl = self.cmp["plain_fp64"]
         gain = (pl["stderr"] ** 2 * pl["gpu_s"]) / (se ** 2 * lp["gpu_s"])
         self.cmp["variance_time_gain"] = round(gain, 3)
+        p32 = self.cmp["plain_fp32"]
+        self.cmp["variance_time_gain_vs_plain_fp32"] = round(
+            (p32["stderr"] ** 2 * p32["gpu_s"]) / (se ** 2 * lp["gpu_s"]), 3)
         n_runs_to_amortise = lp["train_gpu_s"] / max(pl["gpu_s"] * (pl["stderr"] ** 2 / se ** 2) - lp["gpu_s"], 1e-9)
         self.cmp["estimates_to_amortise_training"] = round(n_runs_to_amortise, 1)
 
@@ -880,13 +957,166 @@ class EstradaLearned:
         return nprobes * 16
 
 
+class LevelStudy:
+    """The automated-level experiments of Section 5 replayed on a synthetic
+    stand-in for the paper's directed graph FA (10,617 nodes, 72,176 edges):
+    a directed R-MAT graph (scale 14, a=0.57, b=c=0.19, seed 4) restricted to
+    its first 10,617 vertices, the first 72,176 distinct edges in generation
+    order, no self-loops.  f = sqrt of A^T A (the nuclear norm of A), interval
+    [0, b] with b from 50 Lanczos steps on A^T A, FP64.
+
+    Setup (untimed, reported in config["study"]):
+      level selection: TRIALS automatic estimates at n = 300 with a budget of
+        15,000 (steps of A^T A, ceil(l/2) per probe of degree l) and a 10-probe
+        pilot: level counts, the share of the budget spent at degree <= 50,
+        the degree of the second most expensive level, standard errors;
+      degree sweep: for n in SWEEP, single-level estimates (50 probes at
+        degree n) against automatic multilevel ones at the same cost
+        (budget 50 ceil(n/2)): median standard errors and median |errors|
+        against the exact nuclear norm, beside |tr p_n - tr f| from the exact
+        spectrum (a dense eigendecomposition of A^T A, for reference only).
+    Step (timed): one automatic estimate at n = 300, budget 15,000."""
+    name = "level_study"
+    unit = "probe-matvecs/s"
+    dtype = "f64"
+    D, E = 10617, 72176
+    N, BUDGET, PILOT = 300, 15000, 10
+    TRIALS = 100
+    SWEEP = (25, 50, 100, 150, 200, 250, 300, 350)
+    SWEEP_TRIALS = 30
+    PROBE_SPAN = 0     # probes ids restart per seed; each trial and rank has its own seed
+
+    def __init__(self):
+        from paper_2103_10516_gb300 import synth
+        r, c = synth.rmat_edges(14, 8, seed=4)
+        keep = (r < self.D) & (c < self.D) & (r != c)
+        key = r[keep] * self.D + c[keep]
+        _, first = np.unique(key, return_index=True)
+        key = key[np.sort(first)][: self.E]
+        self.X = synth._from_coo(self.D, self.D, key // self.D, key % self.D, None)
+        self.study = None
+        self.done = []
+
+    def units(self):
+        return float(np.mean(self.done)) if self.done else 1.0
+
+    def config(self):
+        return {"workload": self.name, "graph": "directed R-MAT stand-in for FA: %d nodes, %d edges" % (self.D, self.E),
+                "operator": "A^T A (two SpMMs per step)", "f": "sqrt", "n": self.N, "budget": self.BUDGET,
+                "m_pilot": self.PILOT, "interval": getattr(self, "ab", None), "study": self.study,
+                "l2": "L2-resident (A: %d entries); flushed between steps by a 256 MB write" % self.X.nnz}
+
+    def kernel_bytes(self, launches_per_step):
+        return {}
+
+    def kernel_flops(self, launches_per_step):
+        out = {}
+        fl = self.units() * (2 * self.X.nnz + 4 * self.D)     # one X or X^T product per launch
+        for k in ("cheb_step", "gram_spmm"):
+            if launches_per_step.get(k):
+                out[k] = fl / launches_per_step[k]
+        return out
+
+    def _trial(self, seed, n, stream, budget=None, single=None):
+        if single is not None:
+            return self.M.mlmc("sqrt", self.ab[0], self.ab[1], n, seed=seed, levels=[n], m=[single], stream=stream)
+        return self.M.mlmc("sqrt", self.ab[0], self.ab[1], n, seed=seed, m_pilot=self.PILOT, mode="budget",
+                           target=float(budget), stream=stream)
+
+    def setup(self, mlt, torch, rank):
+        sp = torch.cuda.current_stream().cuda_stream
+        self.M = mlt.Matrix(self.X, gram=True)
+        _, hi = mlt.mlt_spectrum_bounds(self.M.handle, mlt.MLT_BOUNDS_LANCZOS, 50, 0)
+        self.ab = [0.0, hi]
+        self.flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+        self.seed0 = (rank + 1) << 20
+        # exact spectrum of A^T A, for the error columns only
+        Xd = torch.zeros((self.D, self.D), dtype=torch.float64, device="cuda")
+        rows = np.repeat(np.arange(self.D), np.diff(self.X.rowptr))
+        Xd[torch.from_numpy(rows).cuda(), torch.from_numpy(self.X.col.astype(np.int64)).cuda()] = 1.0
+        lam = torch.linalg.eigvalsh(Xd.T @ Xd).clamp_min(0.0).cpu().numpy()
+        del Xd
+        tr_f = float(np.sum(np.sqrt(lam)))
+        x = np.clip((2 * lam - (self.ab[0] + self.ab[1])) / (self.ab[1] - self.ab[0]), -1.0, 1.0)
+        th = np.arccos(x)
+
+        def tr_p(n):
+            c = mlt.mlt_cheb_coeffs("sqrt", self.ab[0], self.ab[1], n)
+            return float(sum(c[j] * np.sum(np.cos(j * th)) for j in range(n + 1)))
+
+        # level selection at n = 300
+        nlev, share50, second, se = [], [], [], []
+        for t in range(self.TRIALS):
+            r = self._trial(self.seed0 + t, self.N, sp, budget=self.BUDGET)
+            cost = [mk * ((l + 1) // 2) for l, mk in zip(r["levels"], r["m"])]
+            nlev.append(len(r["levels"]))
+            share50.append(sum(cst for l, cst in zip(r["levels"], cost) if l <= 50) / sum(cost))
+            order = np.argsort(cost)[::-1]
+            second.append(int(r["levels"][order[1]]) if len(order) > 1 else int(r["levels"][0]))
+            se.append(r["stderr"])
+        sel = {"trials": self.TRIALS, "levels_median": float(np.median(nlev)), "levels_min": int(min(nlev)),
+               "levels_max": int(max(nlev)), "budget_share_deg_le_50_median": round(float(np.median(share50)), 3),
+               "second_costliest_degree_median": float(np.median(second)),
+               "second_costliest_degree_max": int(max(second)),
+               # a level drawn once has no sample variance: its trial's standard error is NaN
+               "stderr_median_finite": float(np.nanmedian(se)) if np.isfinite(se).any() else None,
+               "trials_with_a_single_sample_level": int(np.sum(~np.isfinite(se))),
+               "exact_nuclear_norm": tr_f}
+        # degree sweep at equal cost
+        sweep = []
+        for n in self.SWEEP:
+            s1, e1, s2, e2 = [], [], [], []
+            for t in range(self.SWEEP_TRIALS):
+                a = self._trial(self.seed0 + 10000 + t, n, sp, single=50)
+                b = self._trial(self.seed0 + 20000 + t, n, sp, budget=50 * ((n + 1) // 2))
+                s1.append(a["stderr"])
+                e1.append(abs(a["estimate"] - tr_f))
+                s2.append(b["stderr"])
+                e2.append(abs(b["estimate"] - tr_f))
+            sweep.append({"n": n, "poly_error": abs(tr_p(n) - tr_f), "single_stderr_median": float(np.median(s1)),
+                          "single_abs_error_median": float(np.median(e1)),
+                          "multi_stderr_median_finite": float(np.nanmedian(s2)) if np.isfinite(s2).any() else None,
+                          "multi_trials_with_a_single_sample_level": int(np.sum(~np.isfinite(s2))),
+                          "multi_abs_error_median": float(np.median(e2))})
+        self.study = {"level_selection": sel, "degree_sweep": sweep, "sweep_trials": self.SWEEP_TRIALS}
+
+    def step(self, mlt, stream, i):
+        self.flush.fill_(float(i))
+        r = self._trial(self.seed0 + 100000 + i, self.N, stream, budget=self.BUDGET)
+        self.done.append(r["matvecs"])
+        return r
+
+    def e2e_setup(self, torch):
+        self.h = (torch.from_numpy(self.X.rowptr).pin_memory(), torch.from_numpy(self.X.col).pin_memory())
+        return (self.h[0].numel() * 8 + self.h[1].numel() * 4, 8 * 2)
+
+    def e2e_step(self, mlt, stream, i):
+        h = mlt.mlt_create_csr(self.D, self.D, self.X.nnz, self.h[0], self.h[1], None, flags=mlt.MLT_GRAM,
+                               stream=stream)
+        try:
+            P = mlt.mlt_mlmc_default_params()
+            P.fn, P.a, P.b, P.n, P.seed = 1, self.ab[0], self.ab[1], self.N, self.seed0 + 200000 + i
+            P.m_pilot, P.target = self.PILOT, float(self.BUDGET)
+            P.stream = stream
+            mlt.mlt_mlmc_estimate(h, P)
+        finally:
+            mlt.mlt_destroy(h)
+
+    def cpu_sample(self, oracle, nprobes, offset):
+        if not hasattr(self, "ab"):
+            self.ab = [0.0, gram_upper(self.X)]
+        deg = np.full(nprobes, 64, dtype=np.int32)
+        oracle.moments(self.X, self.ab[0], self.ab[1], 0, offset, deg, gram=True)
+        return int(np.sum(deg))
+
+
 def base_e2e(timed_base):
     """Probe ids of the learned workload's end-to-end steps: past its timed ones."""
     return timed_base + (1 << 26)
 
 
 WORKLOADS = {c.name: c for c in (Triangles, LogDet64, EstradaRmat22, Diffusion64Batched, NuclearGram,
-                                            Stencil3D, EstradaLearned)}
+                                            NuclearExplicit, Stencil3D, EstradaLearned, LevelStudy)}
 
 
 # ---------------------------------------------------------------------------
@@ -1067,7 +1297,7 @@ def make_workload(args):
             raise SystemExit("--scale applies to the estrada_learned workload only")
         kw["scale"] = args.scale
     if args.precision is not None:
-        if cls not in (NuclearGram, Stencil3D, EstradaLearned):
+        if cls not in (NuclearGram, NuclearExplicit, Stencil3D, EstradaLearned):
             raise SystemExit("--precision applies to nuclear_gram, stencil3d and estrada_learned only")
         if cls is EstradaLearned and args.precision == "mixed":
             raise SystemExit("estrada_learned takes fp32 or fp64")
