@@ -50,6 +50,10 @@ constexpr int kSlots = 16;          // steps whose partials are buffered before 
 constexpr int64_t kRowCost = 4;     // units charged per row (the epilogue) on top of its entries
 constexpr int64_t kChunksPerSm = 1024;  // work chunks per SM in the split of an operand
 constexpr int64_t kLongRow = 128;   // rows above max(Uc, this) are cut into segments
+// Resident CTAs per SM the step kernel is compiled for (40 registers): more
+// rows in flight hide more gather latency than the few registers it spills
+// cost (measured against 4 and 5 on the 3D stencil, R-MAT and the 2D grid).
+constexpr int kStepCtasPerSm = 6;
 
 template <typename T> struct Lanes;
 template <> struct Lanes<double> { static constexpr int N = 2; };   // 16-byte vectors
@@ -252,7 +256,7 @@ __device__ __forceinline__ void cta_partials(const StepArgs<T>& a, const Lane<T,
 }
 
 template <typename T, int G>
-__global__ void __launch_bounds__(kThreads) cheb_step_kernel(StepArgs<T> a)
+__global__ void __launch_bounds__(kThreads, kStepCtasPerSm) cheb_step_kernel(StepArgs<T> a)
 {
     constexpr int N = Lanes<T>::N;
     const Lane<T, G> L(a);
