@@ -751,7 +751,7 @@ class Stencil3D:
         self.nnz = self.csr.nnz
         self.precision = precision or "fp32"
         # DRAM bytes per launch (128 live probes) from an ncu capture of the FP32 step
-        self.TRAFFIC = {"cheb_step": 1.5712e9} if self.precision == "fp32" else {}
+        self.TRAFFIC = {"cheb_step": 1.6308e9} if self.precision == "fp32" else {}
         self.dtype = {"fp32": "f32", "fp64": "f64", "mixed": "f32+f64"}[self.precision]
 
     def _prec(self, mlt):
