@@ -433,6 +433,34 @@ __global__ void zero_long_rows_kernel(const int32_t* __restrict__ longlist, int 
     }
 }
 
+// Entries t0 .. t0+D-1 of the current block of 32 (their row or slot in lane
+// t0+u's cj): D gathers are issued before the first is used.
+template <int D, typename Load, typename Use>
+__device__ __forceinline__ void gather_batch(int cj, int t0, Load load, Use use)
+{
+    decltype(load(0)) w[D];
+#pragma unroll
+    for (int u = 0; u < D; ++u) w[u] = load(__shfl_sync(kFull, cj, t0 + u));
+#pragma unroll
+    for (int u = 0; u < D; ++u) use(w[u]);
+}
+
+// The n (<= 32, warp-uniform) entries of a block: batches of kGather while
+// that many remain, then one of 4, then one at a time, so a short out-list
+// wastes no gather slot and no slot needs a bounds test (pass 2; pass 1's
+// short rows keep predicated batches, which measured faster there).
+template <typename Load, typename Use>
+__device__ __forceinline__ void gather_block(int cj, int n, Load load, Use use)
+{
+    int t0 = 0;
+    for (; t0 + kGather <= n; t0 += kGather) gather_batch<kGather>(cj, t0, load, use);
+    if (kGather > 4 && t0 + 4 <= n) {
+        gather_batch<4>(cj, t0, load, use);
+        t0 += 4;
+    }
+    for (; t0 < n; ++t0) gather_batch<1>(cj, t0, load, use);
+}
+
 // ---- pass 1 ------------------------------------------------------------------
 
 // The sign bits of probes 4*lane + q at row j, in bit 8q (q = 0..3).
@@ -693,8 +721,7 @@ __global__ void __launch_bounds__(kTriThreads) tri_long_rows_kernel(
 // ---- pass 2 ------------------------------------------------------------------
 
 // s += y of the small targets (rows) listed in col[a, b), this lane's 4
-// probes; y8l = y8 + lane.  kGather gathers are in flight before the first
-// is used; lanes past the end load nothing and add zero.
+// probes; y8l = y8 + lane; the gathers batched by gather_block.
 __device__ __forceinline__ void sum_small(const int32_t* __restrict__ col, int64_t a, int64_t b,
                                           const uint32_t* __restrict__ y8l, int lane, int s[4])
 {
@@ -702,21 +729,13 @@ __device__ __forceinline__ void sum_small(const int32_t* __restrict__ col, int64
         const int64_t k = base + lane;
         const int cj = k < b ? __ldg(col + k) : 0;
         const int n = (int)min((int64_t)32, b - base);
-        for (int t0 = 0; t0 < n; t0 += kGather) {
-            uint32_t w[kGather];
-#pragma unroll
-            for (int u = 0; u < kGather; ++u) {
-                const int j = __shfl_sync(kFull, cj, t0 + u);
-                w[u] = t0 + u < n ? __ldg(y8l + (size_t)j * 32) : 0u;
-            }
-#pragma unroll
-            for (int u = 0; u < kGather; ++u) {
-                s[0] = __dp4a((int)w[u], 0x00000001, s[0]);
-                s[1] = __dp4a((int)w[u], 0x00000100, s[1]);
-                s[2] = __dp4a((int)w[u], 0x00010000, s[2]);
-                s[3] = __dp4a((int)w[u], 0x01000000, s[3]);
-            }
-        }
+        gather_block(cj, n, [&](int j) { return __ldg(y8l + (size_t)j * 32); },
+                     [&](uint32_t w) {
+                         s[0] = __dp4a((int)w, 0x00000001, s[0]);
+                         s[1] = __dp4a((int)w, 0x00000100, s[1]);
+                         s[2] = __dp4a((int)w, 0x00010000, s[2]);
+                         s[3] = __dp4a((int)w, 0x01000000, s[3]);
+                     });
     }
 }
 
@@ -728,21 +747,13 @@ __device__ __forceinline__ void sum_mid(const int32_t* __restrict__ col, int64_t
         const int64_t k = base + lane;
         const int cj = k < b ? __ldg(col + k) : 0;
         const int n = (int)min((int64_t)32, b - base);
-        for (int t0 = 0; t0 < n; t0 += kGather) {
-            uint2 w[kGather];
-#pragma unroll
-            for (int u = 0; u < kGather; ++u) {
-                const int j = __shfl_sync(kFull, cj, t0 + u);
-                w[u] = t0 + u < n ? __ldg(y16l + (size_t)j * 32) : make_uint2(0u, 0u);
-            }
-#pragma unroll
-            for (int u = 0; u < kGather; ++u) {
-                s[0] = __dp2a_lo((int)w[u].x, 0x0001, s[0]);
-                s[1] = __dp2a_lo((int)w[u].x, 0x0100, s[1]);
-                s[2] = __dp2a_lo((int)w[u].y, 0x0001, s[2]);
-                s[3] = __dp2a_lo((int)w[u].y, 0x0100, s[3]);
-            }
-        }
+        gather_block(cj, n, [&](int j) { return __ldg(y16l + (size_t)j * 32); },
+                     [&](uint2 w) {
+                         s[0] = __dp2a_lo((int)w.x, 0x0001, s[0]);
+                         s[1] = __dp2a_lo((int)w.x, 0x0100, s[1]);
+                         s[2] = __dp2a_lo((int)w.y, 0x0001, s[2]);
+                         s[3] = __dp2a_lo((int)w.y, 0x0100, s[3]);
+                     });
     }
 }
 
