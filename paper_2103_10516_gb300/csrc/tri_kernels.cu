@@ -107,118 +107,6 @@ __global__ void zbits_kernel(int64_t d, uint64_t seedmix, int64_t id0, int nb, u
     }
 }
 
-// ---- preparation: orientation, classes, slots -------------------------------
-
-// Neighbour c (degree dc) of row r (degree deg) is an out-target of r when its
-// (degree, index) key is larger.
-__device__ __forceinline__ bool is_target(int64_t r, int64_t deg, int c, int64_t dc)
-{
-    return dc > deg || (dc == deg && c > r);
-}
-
-// Rows of degree <= kLongRow, a warp each: out-list lengths by class into
-// outcnt (later scanned into out_ptr) and nsmall, the pair count, self-loop
-// detection, and the bound sum_j deg_i deg_j certifying that x3 fits in int64.
-// Every row gets its slot here (rows above kSmallDeg) and longer rows are
-// listed for tri_prepare_long_kernel.  Slot order is irrelevant to every result.
-__global__ void tri_prepare_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                   int64_t d, int64_t* __restrict__ outcnt, int32_t* __restrict__ nsmall,
-                                   int32_t* __restrict__ bslot, int32_t* __restrict__ longlist,
-                                   int* counters /* [0] nbig, [1] nlong, [2] selfloop, [3] npairs */,
-                                   double* bound)
-{
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    double wsum = 0.0;
-    for (int64_t r = warp; r < d; r += nwarps) {
-        const int64_t beg = rowptr[r], end = rowptr[r + 1];
-        const int64_t deg = end - beg;
-        if (lane == 0) {
-            bslot[r] = deg > kSmallDeg ? atomicAdd(counters + 0, 1) : -1;
-            if (deg > kLongRow) longlist[atomicAdd(counters + 1, 1)] = (int32_t)r;
-        }
-        if (deg > kLongRow) continue;
-        int ns = 0, nm = 0, nh = 0;
-        double dsum = 0.0;
-        for (int64_t base = beg; base < end; base += 32) {
-            const int64_t k = base + lane;
-            bool t = false;
-            int64_t dc = 0;
-            if (k < end) {
-                const int c = col[k];
-                dc = rowptr[c + 1] - rowptr[c];
-                dsum += (double)dc;
-                if (c == r) atomicOr(counters + 2, 1);
-                t = is_target(r, deg, c, dc);
-            }
-            ns += __popc(__ballot_sync(kFull, t && dc <= kSmallDeg));
-            nm += __popc(__ballot_sync(kFull, t && dc > kSmallDeg && dc <= kMidDeg));
-            nh += __popc(__ballot_sync(kFull, t && dc > kMidDeg));
-        }
-        for (int o = 16; o; o >>= 1) dsum += __shfl_xor_sync(kFull, dsum, o);
-        if (lane == 0) {
-            outcnt[r] = ns + nm;
-            nsmall[r] = ns;
-            if (nh) atomicAdd(counters + 3, nh);
-            wsum += dsum * (double)deg;
-        }
-    }
-    if (lane == 0 && wsum != 0.0) atomicAdd(bound, wsum);
-}
-
-// The same for the rows listed by tri_prepare_kernel, a CTA each.
-__global__ void __launch_bounds__(kTriThreads) tri_prepare_long_kernel(
-    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ longlist,
-    int64_t* __restrict__ outcnt, int32_t* __restrict__ nsmall, int* counters, double* bound)
-{
-    __shared__ int cnt[3];
-    __shared__ double dsh;
-    const int nlong = *(volatile int*)(counters + 1);
-    for (int i = blockIdx.x; i < nlong; i += gridDim.x) {
-        const int64_t r = longlist[i];
-        const int64_t beg = rowptr[r], end = rowptr[r + 1];
-        const int64_t deg = end - beg;
-        if (threadIdx.x < 3) cnt[threadIdx.x] = 0;
-        if (threadIdx.x == 0) dsh = 0.0;
-        __syncthreads();
-        int ns = 0, nm = 0, nh = 0;
-        double dsum = 0.0;
-        for (int64_t k = beg + threadIdx.x; k < end; k += blockDim.x) {
-            const int c = col[k];
-            const int64_t dc = rowptr[c + 1] - rowptr[c];
-            dsum += (double)dc;
-            if (c == r) atomicOr(counters + 2, 1);
-            if (is_target(r, deg, c, dc)) {
-                const int cl = row_class(dc);
-                ns += cl == kClassSmall;
-                nm += cl == kClassMid;
-                nh += cl == kClassHuge;
-            }
-        }
-        for (int o = 16; o; o >>= 1) {
-            ns += __shfl_xor_sync(kFull, ns, o);
-            nm += __shfl_xor_sync(kFull, nm, o);
-            nh += __shfl_xor_sync(kFull, nh, o);
-            dsum += __shfl_xor_sync(kFull, dsum, o);
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicAdd(cnt + 0, ns);
-            atomicAdd(cnt + 1, nm);
-            atomicAdd(cnt + 2, nh);
-            atomicAdd(&dsh, dsum);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            outcnt[r] = cnt[0] + cnt[1];
-            nsmall[r] = cnt[0];
-            if (cnt[2]) atomicAdd(counters + 3, cnt[2]);
-            atomicAdd(bound, dsh * (double)deg);
-        }
-        __syncthreads();
-    }
-}
-
 // ---- exclusive prefix scan of int64 counts, in place (three passes) --------
 
 __device__ __forceinline__ int64_t block_inclusive_scan(int64_t v, int64_t* warp_tot)
@@ -294,109 +182,6 @@ __global__ void scan_apply_kernel(int64_t* __restrict__ x, int64_t n, const int6
     }
 }
 
-// ---- out-lists -------------------------------------------------------------
-
-// One pair of the huge-target list: how to read y_i, and the target's slot.
-__device__ __forceinline__ int4 make_pair(int64_t r, int64_t deg, const int32_t* __restrict__ bslot,
-                                          int target_slot)
-{
-    const int cl = row_class(deg);
-    return make_int4(cl, cl == kClassSmall ? (int)r : bslot[r], target_slot, 0);
-}
-
-// Rows of degree <= kLongRow, a warp each: the out-list of row r in neighbour
-// order, small targets (their row) before mid targets (their slot); targets of
-// class huge are appended to the pair list.
-__global__ void fill_out_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, int64_t d,
-                                const int64_t* __restrict__ out_ptr, const int32_t* __restrict__ nsmall,
-                                const int32_t* __restrict__ bslot, int32_t* __restrict__ out_col,
-                                int4* __restrict__ pairs, int npairs, int* pair_ctr)
-{
-    const int lane = threadIdx.x & 31;
-    const unsigned below = (1u << lane) - 1u;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = warp; r < d; r += nwarps) {
-        const int64_t beg = rowptr[r], end = rowptr[r + 1];
-        const int64_t deg = end - beg;
-        if (deg > kLongRow) continue;
-        const int64_t os = out_ptr[r], om = os + nsmall[r];
-        int64_t cs = 0, cm = 0;
-        for (int64_t base = beg; base < end; base += 32) {
-            const int64_t k = base + lane;
-            int c = 0, cl = -1;
-            if (k < end) {
-                c = col[k];
-                const int64_t dc = rowptr[c + 1] - rowptr[c];
-                if (is_target(r, deg, c, dc)) cl = row_class(dc);
-            }
-            const unsigned ms = __ballot_sync(kFull, cl == kClassSmall);
-            const unsigned mm = __ballot_sync(kFull, cl == kClassMid);
-            if (cl == kClassSmall) out_col[os + cs + __popc(ms & below)] = c;
-            if (cl == kClassMid) out_col[om + cm + __popc(mm & below)] = bslot[c];
-            if (cl == kClassHuge) {
-                const int at = atomicAdd(pair_ctr, 1);
-                if (at < npairs) pairs[at] = make_pair(r, deg, bslot, bslot[c]);   // at < npairs by construction
-            }
-            cs += __popc(ms);
-            cm += __popc(mm);
-        }
-    }
-}
-
-// The same for rows longer than kLongRow, a CTA each (order kept across warps).
-__global__ void __launch_bounds__(kTriThreads) fill_out_long_kernel(
-    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ longlist,
-    int nlong, const int64_t* __restrict__ out_ptr, const int32_t* __restrict__ nsmall,
-    const int32_t* __restrict__ bslot, int32_t* __restrict__ out_col, int4* __restrict__ pairs, int npairs,
-    int* pair_ctr)
-{
-    __shared__ int ws[kTriThreads / 32], wm[kTriThreads / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const unsigned below = (1u << lane) - 1u;
-    for (int i = blockIdx.x; i < nlong; i += gridDim.x) {
-        const int64_t r = longlist[i];
-        const int64_t beg = rowptr[r], end = rowptr[r + 1];
-        const int64_t deg = end - beg;
-        const int64_t os = out_ptr[r], om = os + nsmall[r];
-        int64_t cs = 0, cm = 0;
-        for (int64_t base = beg; base < end; base += blockDim.x) {
-            const int64_t k = base + threadIdx.x;
-            int c = 0, cl = -1;
-            if (k < end) {
-                c = col[k];
-                const int64_t dc = rowptr[c + 1] - rowptr[c];
-                if (is_target(r, deg, c, dc)) cl = row_class(dc);
-            }
-            const unsigned ms = __ballot_sync(kFull, cl == kClassSmall);
-            const unsigned mm = __ballot_sync(kFull, cl == kClassMid);
-            if (lane == 0) {
-                ws[wid] = __popc(ms);
-                wm[wid] = __popc(mm);
-            }
-            __syncthreads();
-            int ps = 0, pm = 0, ts = 0, tm = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-                if (w < wid) {
-                    ps += ws[w];
-                    pm += wm[w];
-                }
-                ts += ws[w];
-                tm += wm[w];
-            }
-            if (cl == kClassSmall) out_col[os + cs + ps + __popc(ms & below)] = c;
-            if (cl == kClassMid) out_col[om + cm + pm + __popc(mm & below)] = bslot[c];
-            if (cl == kClassHuge) {
-                const int at = atomicAdd(pair_ctr, 1);
-                if (at < npairs) pairs[at] = make_pair(r, deg, bslot, bslot[c]);   // at < npairs by construction
-            }
-            cs += ts;
-            cm += tm;
-            __syncthreads();
-        }
-    }
-}
-
 // crow[c] = the row whose units hold unit c*kChunk: the largest r with
 // ptr[r] + kRowCost*r <= c*kChunk.
 __global__ void chunk_rows_kernel(const int64_t* __restrict__ ptr, int64_t d, int64_t nch,
@@ -421,6 +206,341 @@ __device__ __forceinline__ int64_t next_chunk(unsigned long long* counter, int l
     unsigned long long c = 0;
     if (lane == 0) c = atomicAdd(counter, 1ull);
     return (int64_t)__shfl_sync(kFull, c, 0);
+}
+
+// ---- preparation: orientation, classes, slots, out-lists ---------------------
+
+// Neighbour c (degree dc) of row r (degree deg) is an out-target of r when its
+// (degree, index) key is larger.
+__device__ __forceinline__ bool is_target(int64_t r, int deg, int c, int dc)
+{
+    return dc > deg || (dc == deg && c > r);
+}
+
+// A thread per row: its degree as int32 (nnz < 2^31), a y16 / y32 slot for
+// rows above kSmallDeg, and the list of rows above kLongRow, whose out-list
+// counts and fill cursors start at zero here (the entry passes add to them).
+// Slots and list positions come from warp-aggregated atomics: their order is
+// irrelevant to every result.
+__global__ void tri_degrees_kernel(const int64_t* __restrict__ rowptr, int64_t d, int32_t* __restrict__ deg32,
+                                   int32_t* __restrict__ bslot, int32_t* __restrict__ longlist,
+                                   int64_t* __restrict__ outcnt, int32_t* __restrict__ nsmall,
+                                   int32_t* __restrict__ cur, int* counters /* [0] nbig, [1] nlong */)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); r0 < d; r0 += stride) {
+        const int64_t r = r0 + lane;
+        const bool valid = r < d;
+        const int deg = valid ? (int)(rowptr[r + 1] - rowptr[r]) : 0;
+        const bool big = valid && deg > kSmallDeg, lng = valid && deg > kLongRow;
+        const unsigned mb = __ballot_sync(kFull, big), ml = __ballot_sync(kFull, lng);
+        int sb = 0, sl = 0;
+        if (lane == 0) {
+            if (mb) sb = atomicAdd(counters + 0, __popc(mb));
+            if (ml) sl = atomicAdd(counters + 1, __popc(ml));
+        }
+        sb = __shfl_sync(kFull, sb, 0);
+        sl = __shfl_sync(kFull, sl, 0);
+        if (!valid) continue;
+        deg32[r] = deg;
+        const int slot = big ? sb + __popc(mb & below) : -1;
+        bslot[r] = slot;
+        if (big) {
+            cur[2 * (size_t)slot] = 0;
+            cur[2 * (size_t)slot + 1] = 0;
+        }
+        if (lng) {
+            longlist[sl + __popc(ml & below)] = (int32_t)r;
+            outcnt[r] = 0;
+            nsmall[r] = 0;
+        }
+    }
+}
+
+// Walk the rows of unit chunk c exactly as pass 1 does: a row above kLongRow
+// is cut at the chunk's edges (long_part(r, deg, a, b) for its entries
+// [a, b)); every shorter row belongs to the chunk holding its first unit,
+// and runs of 1 to 32 of them are handed to group(r, f, s0, e0) with row
+// r + lane's entry range [s0, e0) in lane `lane` (meaningful for lanes below f).
+template <typename Group, typename LongPart>
+__device__ __forceinline__ void walk_chunk(const int64_t* __restrict__ rowptr, int64_t d, int64_t c,
+                                           const int64_t* __restrict__ crow, int lane, Group group,
+                                           LongPart long_part)
+{
+    const int64_t u0 = c * kChunk, u1 = u0 + kChunk;
+    int64_t r = crow[c];
+    while (r < d) {
+        const int64_t beg = __ldg(rowptr + r);
+        const int64_t pr = beg + kRowCost * r;
+        if (pr >= u1) break;
+        const int64_t deg = __ldg(rowptr + r + 1) - beg;
+        if (deg > kLongRow) {
+            const int64_t e0 = pr + kRowCost;
+            const int64_t a = beg + max((int64_t)0, u0 - e0);
+            const int64_t b = beg + min(deg, u1 - e0);
+            if (a < b) long_part(r, (int)deg, a, b);
+            ++r;
+            continue;
+        }
+        if (pr < u0) {
+            ++r;
+            continue;
+        }
+        for (;;) {
+            const int64_t rr = r + lane;
+            int s0 = 0, e0 = 0;
+            bool ok = false;
+            if (rr < d) {
+                const int64_t x0 = __ldg(rowptr + rr), x1 = __ldg(rowptr + rr + 1);
+                s0 = (int)x0;
+                e0 = (int)x1;
+                ok = (x0 + kRowCost * rr < u1) && (x1 - x0 <= kLongRow);
+            }
+            const unsigned okm = __ballot_sync(kFull, ok);
+            const int f = (okm == kFull) ? 32 : (__ffs(~okm) - 1);
+            if (f > 0) group(r, f, s0, e0);
+            r += f;
+            if (f < 32) break;
+        }
+    }
+}
+
+// One batch of up to 32 consecutive entries [base, B) of a run of f short
+// rows (row r + i starts at s0 of lane i): this lane's entry, its row's
+// position i in the run, the row's degree, and whether this lane is the first
+// of its row in the batch (row segments are contiguous in lane order).
+struct RunEntry {
+    int k, idx, deg;
+    bool valid;
+};
+
+__device__ __forceinline__ RunEntry run_entry(int base, int B, int f, int s0, int dg, int lane)
+{
+    RunEntry e;
+    e.k = base + lane;
+    e.valid = e.k < B;
+    int idx = 0;   // the last row of the run starting at or before k
+#pragma unroll
+    for (int st = 16; st; st >>= 1) {
+        const int cand = idx + st;
+        const int sv = __shfl_sync(kFull, s0, min(cand, 31));
+        if (cand < f && sv <= e.k) idx = cand;
+    }
+    e.idx = idx;
+    e.deg = __shfl_sync(kFull, dg, idx);
+    return e;
+}
+
+// Lanes [l, next head) hold the row segment that starts at head lane l.
+__device__ __forceinline__ unsigned segment_from(unsigned heads, int l)
+{
+    const unsigned above = heads & ~((2u << l) - 1u);
+    const unsigned upto = above ? (1u << (__ffs(above) - 1)) - 1u : kFull;
+    return upto & ~((1u << l) - 1u);
+}
+
+// Class of entry k's target as seen from its row (-1: not an out-target).
+__device__ __forceinline__ int target_class(int64_t row, int deg, int c, int dc)
+{
+    return is_target(row, deg, c, dc) ? row_class(dc) : -1;
+}
+
+// Counting pass over the chunks of pass 1: per row the out-list length
+// (outcnt, scanned into out_ptr next) and its small section (nsmall); the
+// number of edges into huge rows; self-loops; and the bound sum over entries
+// of deg_i deg_j certifying that x3 fits in int64.  Short rows are written
+// whole by their chunk; long rows add their parts.
+__global__ void __launch_bounds__(kTriThreads) tri_classify_kernel(
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ deg32,
+    int64_t d, int64_t nch, const int64_t* __restrict__ crow, int64_t* __restrict__ outcnt,
+    int32_t* __restrict__ nsmall, int* counters /* [2] selfloop, [3] npairs */, double* bound,
+    unsigned long long* __restrict__ chunk_ctr)
+{
+    __shared__ int sc[kTriThreads / 32][32], mc[kTriThreads / 32][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    sc[wid][lane] = 0;
+    mc[wid][lane] = 0;
+    __syncwarp();
+    double wsum = 0.0;
+    int nh = 0;
+    bool loop = false;
+    auto group = [&](int64_t r, int f, int s0, int e0) {
+        const int A = __shfl_sync(kFull, s0, 0), B = __shfl_sync(kFull, e0, f - 1);
+        const int dg = e0 - s0;
+        for (int base = A; base < B; base += 32) {
+            const RunEntry e = run_entry(base, B, f, s0, dg, lane);
+            const int64_t row = r + e.idx;
+            int cl = -1;
+            if (e.valid) {
+                const int c = __ldg(col + e.k);
+                const int dc = __ldg(deg32 + c);
+                loop |= c == row;
+                wsum += (double)dc * (double)e.deg;
+                cl = target_class(row, e.deg, c, dc);
+            }
+            const unsigned ms = __ballot_sync(kFull, cl == kClassSmall);
+            const unsigned mm = __ballot_sync(kFull, cl == kClassMid);
+            nh += __popc(__ballot_sync(kFull, cl == kClassHuge));
+            const int prev = __shfl_up_sync(kFull, e.idx, 1);
+            const bool head = e.valid && (lane == 0 || prev != e.idx);
+            const unsigned heads = __ballot_sync(kFull, head);
+            if (head) {
+                const unsigned seg = segment_from(heads, lane);
+                sc[wid][e.idx] += __popc(ms & seg);
+                mc[wid][e.idx] += __popc(mm & seg);
+            }
+            __syncwarp();
+        }
+        if (lane < f) {
+            outcnt[r + lane] = sc[wid][lane] + mc[wid][lane];
+            nsmall[r + lane] = sc[wid][lane];
+        }
+        sc[wid][lane] = 0;
+        mc[wid][lane] = 0;
+        __syncwarp();
+    };
+    auto long_part = [&](int64_t r, int deg, int64_t a, int64_t b) {
+        int ns = 0, nm = 0;
+        for (int64_t base = a; base < b; base += 32) {
+            const int64_t k = base + lane;
+            int cl = -1;
+            if (k < b) {
+                const int c = __ldg(col + k);
+                const int dc = __ldg(deg32 + c);
+                loop |= c == r;
+                wsum += (double)dc * (double)deg;
+                cl = target_class(r, deg, c, dc);
+            }
+            ns += __popc(__ballot_sync(kFull, cl == kClassSmall));
+            nm += __popc(__ballot_sync(kFull, cl == kClassMid));
+            nh += __popc(__ballot_sync(kFull, cl == kClassHuge));
+        }
+        if (lane == 0) {
+            if (ns + nm) atomicAdd(reinterpret_cast<unsigned long long*>(outcnt + r), (unsigned long long)(ns + nm));
+            if (ns) atomicAdd(nsmall + r, ns);
+        }
+    };
+    for (int64_t c = next_chunk(chunk_ctr, lane); c < nch; c = next_chunk(chunk_ctr, lane))
+        walk_chunk(rowptr, d, c, crow, lane, group, long_part);
+    for (int o = 16; o; o >>= 1) wsum += __shfl_xor_sync(kFull, wsum, o);
+    if (__any_sync(kFull, loop) && lane == 0) atomicOr(counters + 2, 1);
+    if (lane == 0) {
+        if (nh) atomicAdd(counters + 3, nh);
+        if (wsum != 0.0) atomicAdd(bound, wsum);
+    }
+}
+
+// One pair of the huge-target list: how to read y_i, and the target's slot.
+__device__ __forceinline__ int4 make_pair(int64_t r, int deg, const int32_t* __restrict__ bslot, int target_slot)
+{
+    const int cl = row_class(deg);
+    return make_int4(cl, cl == kClassSmall ? (int)r : __ldg(bslot + r), target_slot, 0);
+}
+
+// Fill pass, the same walk: each out-list gets its small targets (their row)
+// before its mid targets (their slot); edges into huge rows go to the pair
+// list.  A short row's entries keep neighbour order (running offsets per row
+// of the run in shared memory); a long row's parts take their places from
+// per-row cursors, so their order within a section is arbitrary, which pass 2
+// (integer sums) does not see.
+__global__ void __launch_bounds__(kTriThreads) tri_fill_kernel(
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const int32_t* __restrict__ deg32,
+    int64_t d, int64_t nch, const int64_t* __restrict__ crow, const int64_t* __restrict__ out_ptr,
+    const int32_t* __restrict__ nsmall, const int32_t* __restrict__ bslot, int32_t* __restrict__ cur,
+    int32_t* __restrict__ out_col, int4* __restrict__ pairs, int npairs, int* pair_ctr,
+    unsigned long long* __restrict__ chunk_ctr)
+{
+    __shared__ int sc[kTriThreads / 32][32], mc[kTriThreads / 32][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    sc[wid][lane] = 0;
+    mc[wid][lane] = 0;
+    __syncwarp();
+    // edges into huge rows: places for this batch's pairs, in lane order
+    auto add_pairs = [&](int cl, int64_t row, int deg, int c) {
+        const unsigned mh = __ballot_sync(kFull, cl == kClassHuge);
+        if (!mh) return;
+        int p0 = 0;
+        if (lane == 0) p0 = atomicAdd(pair_ctr, __popc(mh));
+        p0 = __shfl_sync(kFull, p0, 0);
+        const int at = p0 + __popc(mh & below);
+        if (cl == kClassHuge && at < npairs)   // at < npairs by construction
+            pairs[at] = make_pair(row, deg, bslot, __ldg(bslot + c));
+    };
+    auto group = [&](int64_t r, int f, int s0, int e0) {
+        const int A = __shfl_sync(kFull, s0, 0), B = __shfl_sync(kFull, e0, f - 1);
+        const int dg = e0 - s0;
+        int64_t op = 0;
+        int ns = 0;
+        if (lane < f && e0 > s0) {
+            op = __ldg(out_ptr + r + lane);
+            ns = __ldg(nsmall + r + lane);
+        }
+        for (int base = A; base < B; base += 32) {
+            const RunEntry e = run_entry(base, B, f, s0, dg, lane);
+            const int64_t row = r + e.idx;
+            int c = 0, cl = -1;
+            if (e.valid) {
+                c = __ldg(col + e.k);
+                cl = target_class(row, e.deg, c, __ldg(deg32 + c));
+            }
+            const unsigned ms = __ballot_sync(kFull, cl == kClassSmall);
+            const unsigned mm = __ballot_sync(kFull, cl == kClassMid);
+            const int prev = __shfl_up_sync(kFull, e.idx, 1);
+            const bool head = e.valid && (lane == 0 || prev != e.idx);
+            const unsigned heads = __ballot_sync(kFull, head);
+            const int64_t rop = __shfl_sync(kFull, op, e.idx);
+            const int rns = __shfl_sync(kFull, ns, e.idx);
+            if (cl >= 0) {
+                const int h = 31 - __clz(heads & ((2u << lane) - 1u));   // head of this lane's segment
+                const unsigned before = below & ~((1u << h) - 1u);
+                if (cl == kClassSmall)
+                    out_col[rop + sc[wid][e.idx] + __popc(ms & before)] = c;
+                else if (cl == kClassMid)
+                    out_col[rop + rns + mc[wid][e.idx] + __popc(mm & before)] = __ldg(bslot + c);
+            }
+            add_pairs(cl, row, e.deg, c);
+            __syncwarp();
+            if (head) {
+                const unsigned seg = segment_from(heads, lane);
+                sc[wid][e.idx] += __popc(ms & seg);
+                mc[wid][e.idx] += __popc(mm & seg);
+            }
+            __syncwarp();
+        }
+        sc[wid][lane] = 0;
+        mc[wid][lane] = 0;
+        __syncwarp();
+    };
+    auto long_part = [&](int64_t r, int deg, int64_t a, int64_t b) {
+        const int64_t op = __ldg(out_ptr + r);
+        const int rns = __ldg(nsmall + r);
+        int32_t* rc = cur + 2 * (size_t)__ldg(bslot + r);
+        for (int64_t base = a; base < b; base += 32) {
+            const int64_t k = base + lane;
+            int c = 0, cl = -1;
+            if (k < b) {
+                c = __ldg(col + k);
+                cl = target_class(r, deg, c, __ldg(deg32 + c));
+            }
+            const unsigned ms = __ballot_sync(kFull, cl == kClassSmall);
+            const unsigned mm = __ballot_sync(kFull, cl == kClassMid);
+            int bs = 0, bm = 0;
+            if (lane == 0) {
+                if (ms) bs = atomicAdd(rc, __popc(ms));
+                if (mm) bm = atomicAdd(rc + 1, __popc(mm));
+            }
+            bs = __shfl_sync(kFull, bs, 0);
+            bm = __shfl_sync(kFull, bm, 0);
+            if (cl == kClassSmall) out_col[op + bs + __popc(ms & below)] = c;
+            else if (cl == kClassMid) out_col[op + rns + bm + __popc(mm & below)] = __ldg(bslot + c);
+            add_pairs(cl, r, deg, c);
+        }
+    };
+    for (int64_t c = next_chunk(chunk_ctr, lane); c < nch; c = next_chunk(chunk_ctr, lane))
+        walk_chunk(rowptr, d, c, crow, lane, group, long_part);
 }
 
 __global__ void zero_long_rows_kernel(const int32_t* __restrict__ longlist, int nlong,
@@ -917,12 +1037,6 @@ __global__ void __launch_bounds__(kTriThreads) tri_pairs_kernel(
         if (sx[t]) atomicAdd(xacc + 3 * t + 2, (unsigned long long)sx[t]);
 }
 
-int grid_for(int num_sms, int64_t warps_needed)
-{
-    const int64_t blocks = (warps_needed * 32 + kTriThreads - 1) / kTriThreads;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, 8LL * num_sms));
-}
-
 }  // namespace
 
 int tri_prepare(mlt_matrix* M, cudaStream_t s)
@@ -932,14 +1046,17 @@ int tri_prepare(mlt_matrix* M, cudaStream_t s)
     const int64_t d = M->A.nrows;
     const int64_t nnz = M->A.nnz;
     const int64_t nch1 = std::max<int64_t>(1, (nnz + kRowCost * d + kChunk - 1) / kChunk);
-    int occ1 = 0, occ2 = 0;
+    int occ1 = 0, occ2 = 0, occc = 0, occf = 0;
     MLT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, tri_pass1_kernel, kTriThreads, 0));
     MLT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, tri_pass2_kernel, kTriThreads, 0));
+    MLT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occc, tri_classify_kernel, kTriThreads, 0));
+    MLT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occf, tri_fill_kernel, kTriThreads, 0));
     const size_t dd = (size_t)std::max<int64_t>(d, 1);
     const int64_t nsb = (d + kScanBlock - 1) / kScanBlock;
     int rc;
-    // out_ptr[d+1], crow1[nch1], crow2[nch1], scan sums[nsb], nsmall[d], bslot[d], longlist[d], counters
-    if ((rc = M->ws_tri.ensure((dd + 1) * 8 + 2 * (size_t)nch1 * 8 + (size_t)(nsb + 1) * 8 + dd * 4 * 3 + 1024,
+    // out_ptr[d+1], crow1[nch1], crow2[nch1], scan sums[nsb+1]; nsmall, bslot,
+    // longlist, deg32 [d] and the fill cursors [2d]; counters
+    if ((rc = M->ws_tri.ensure((dd + 1) * 8 + 2 * (size_t)nch1 * 8 + (size_t)(nsb + 1) * 8 + dd * 4 * 6 + 1024,
                                s)))
         return rc;
     char* base = M->ws_tri.as<char>();
@@ -950,18 +1067,25 @@ int tri_prepare(mlt_matrix* M, cudaStream_t s)
     int32_t* nsmall = reinterpret_cast<int32_t*>(bsum + nsb + 1);
     int32_t* bslot = nsmall + dd;
     int32_t* longlist = bslot + dd;
-    // nbig, nlong, selfloop, npairs, pair cursor, then the bound and the chunk
-    // counters (16-byte aligned: the int32 arrays before it may end anywhere)
-    int* counters = reinterpret_cast<int*>((reinterpret_cast<uintptr_t>(longlist + dd) + 15) & ~(uintptr_t)15);
+    int32_t* deg32 = longlist + dd;
+    int32_t* cur = deg32 + dd;
+    // nbig, nlong, selfloop, npairs, pair cursor, then the bound and four
+    // chunk counters (pass 1, pass 2, counting, filling); 16-byte aligned: the
+    // int32 arrays before it may end anywhere
+    int* counters = reinterpret_cast<int*>((reinterpret_cast<uintptr_t>(cur + 2 * dd) + 15) & ~(uintptr_t)15);
     double* bound = reinterpret_cast<double*>(counters + 6);
     unsigned long long* chunk_ctr = reinterpret_cast<unsigned long long*>(bound + 1);
-    MLT_CUDA_TRY(cudaMemsetAsync(counters, 0, 6 * sizeof(int) + sizeof(double), s));
+    MLT_CUDA_TRY(cudaMemsetAsync(counters, 0, 6 * sizeof(int) + sizeof(double) + 4 * sizeof(unsigned long long), s));
+    const int gridc = std::max(1, occc) * M->num_sms, gridf = std::max(1, occf) * M->num_sms;
     {
         ProfScope ps("tri_prepare", s);
-        tri_prepare_kernel<<<grid_for(M->num_sms, d), kTriThreads, 0, s>>>(
-            M->A.rowptr, M->A.col, d, out_ptr, nsmall, bslot, longlist, counters, bound);
-        tri_prepare_long_kernel<<<8 * M->num_sms, kTriThreads, 0, s>>>(M->A.rowptr, M->A.col, longlist, out_ptr,
-                                                                       nsmall, counters, bound);
+        const int gd = (int)std::max<int64_t>(1, std::min<int64_t>((d + 255) / 256, 16LL * M->num_sms));
+        tri_degrees_kernel<<<gd, 256, 0, s>>>(M->A.rowptr, d, deg32, bslot, longlist, out_ptr, nsmall, cur,
+                                              counters);
+        const int g1 = (int)std::min<int64_t>((nch1 + 255) / 256, 16LL * M->num_sms);
+        chunk_rows_kernel<<<std::max(g1, 1), 256, 0, s>>>(M->A.rowptr, d, nch1, crow1);
+        tri_classify_kernel<<<gridc, kTriThreads, 0, s>>>(M->A.rowptr, M->A.col, deg32, d, nch1, crow1, out_ptr,
+                                                          nsmall, counters, bound, chunk_ctr + 2);
     }
     MLT_CUDA_TRY(cudaGetLastError());
     if (d > 0) {
@@ -998,17 +1122,13 @@ int tri_prepare(mlt_matrix* M, cudaStream_t s)
     const int64_t nch2 = std::max<int64_t>(1, (nnz_out + kRowCost * d + kChunk - 1) / kChunk);
     {
         ProfScope ps("tri_fill_out", s);
-        fill_out_kernel<<<grid_for(M->num_sms, d), kTriThreads, 0, s>>>(M->A.rowptr, M->A.col, d, out_ptr, nsmall,
-                                                                        bslot, out_col, pairs, hc[3], counters + 4);
-        if (hc[1] > 0)
-            fill_out_long_kernel<<<(unsigned)std::min<int64_t>(hc[1], 8LL * M->num_sms), kTriThreads, 0, s>>>(
-                M->A.rowptr, M->A.col, longlist, hc[1], out_ptr, nsmall, bslot, out_col, pairs, hc[3], counters + 4);
+        tri_fill_kernel<<<gridf, kTriThreads, 0, s>>>(M->A.rowptr, M->A.col, deg32, d, nch1, crow1, out_ptr, nsmall,
+                                                      bslot, cur, out_col, pairs, (int)npairs, counters + 4,
+                                                      chunk_ctr + 3);
     }
     MLT_CUDA_TRY(cudaGetLastError());
     {
         ProfScope ps("tri_chunk_rows", s);
-        const int g1 = (int)std::min<int64_t>((nch1 + 255) / 256, 16LL * M->num_sms);
-        chunk_rows_kernel<<<std::max(g1, 1), 256, 0, s>>>(M->A.rowptr, d, nch1, crow1);
         const int g2 = (int)std::min<int64_t>((nch2 + 255) / 256, 16LL * M->num_sms);
         chunk_rows_kernel<<<std::max(g2, 1), 256, 0, s>>>(out_ptr, d, nch2, crow2);
     }
