@@ -131,8 +131,17 @@ int mlt_create_csr(int64_t nrows, int64_t ncols, int64_t nnz,
                    int val_type, double scale, unsigned flags, void* stream,
                    mlt_matrix** out);
 
-/* Release a handle and every device buffer it owns (NULL is a no-op). */
+/* Release a handle and every device buffer it owns (NULL is a no-op).  The
+ * call waits for the device to finish its work first.  The buffers go back to
+ * the library's memory pool (see mlt_release_cached), not to the driver. */
 int mlt_destroy(mlt_matrix* m);
+
+/* Return to the driver the device memory that destroyed handles left cached.
+ * Handles take their device memory from one stream-ordered pool per device
+ * that keeps freed blocks for later handles (a handle created after another
+ * was destroyed maps no new memory); memory of live handles is untouched.
+ * No counterpart in the paper: memory management only.  Errors: MLT_ECUDA. */
+int mlt_release_cached(void);
 
 /* Operator dimension d (nrows, or ncols for a Gram handle) and stored nnz. */
 int mlt_matrix_info(const mlt_matrix* m, int64_t* dim, int64_t* nnz);

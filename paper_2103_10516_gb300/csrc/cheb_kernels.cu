@@ -702,9 +702,9 @@ int ensure_spmm_plan(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, cudaStream_t s
     const size_t bytes = nch * sizeof(int64_t) + nseg * (sizeof(int64_t) + sizeof(int32_t)) +
                          (nlong + 1) * sizeof(int64_t) + nlong * sizeof(int32_t) + 64;
     char* mem = nullptr;
-    if (cudaMalloc((void**)&mem, bytes) != cudaSuccess) {
+    if (pool_malloc((void**)&mem, bytes, s) != cudaSuccess) {
         cudaGetLastError();
-        return fail(MLT_ENOMEM, "cudaMalloc (work split) failed");
+        return fail(MLT_ENOMEM, "device allocation (work split) failed");
     }
     P.mem = mem;
     P.crow = reinterpret_cast<int64_t*>(mem);
@@ -764,8 +764,8 @@ int ensure_fp32_values(mlt_matrix* M, cudaStream_t s)
     auto conv = [&](DevCSR& C, void*& own) -> int {
         if (C.val32 || !C.val64 || C.nnz == 0) return MLT_OK;
         float* p = nullptr;
-        cudaError_t e = cudaMallocAsync((void**)&p, (size_t)C.nnz * sizeof(float), s);
-        if (e != cudaSuccess) return fail(MLT_ENOMEM, "cudaMallocAsync (fp32 values) failed");
+        cudaError_t e = pool_malloc((void**)&p, (size_t)C.nnz * sizeof(float), s);
+        if (e != cudaSuccess) return fail(MLT_ENOMEM, "device allocation (fp32 values) failed");
         const int nb = (int)std::min<int64_t>((C.nnz + 255) / 256, 16LL * M->num_sms);
         ProfScope ps("to_float", s);
         to_float_kernel<<<std::max(nb, 1), 256, 0, s>>>(C.val64, p, C.nnz);

@@ -84,6 +84,52 @@ ProfScope::~ProfScope()
     cudaEventRecord(g_prof[idx].e1, s);
 }
 
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+}  // namespace
+
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (!g_pools[dev]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.handleTypes = cudaMemHandleTypeNone;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            if ((e = cudaMemPoolCreate(&g_pools[dev], &props)) != cudaSuccess) {
+                g_pools[dev] = nullptr;
+                return e;
+            }
+            uint64_t keep = ~(uint64_t)0;   // never trim at synchronisation
+            if ((e = cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess)
+                return e;
+        }
+        pool = g_pools[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+// Every pool's cached blocks back to the driver (blocks in use stay).
+cudaError_t trim_pools()
+{
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    for (cudaMemPool_t pool : g_pools) {
+        if (!pool) continue;
+        cudaError_t e = cudaMemPoolTrimTo(pool, 0);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 int DevBuf::ensure(size_t want, cudaStream_t s)
 {
     if (want <= bytes) return MLT_OK;
@@ -94,7 +140,7 @@ int DevBuf::ensure(size_t want, cudaStream_t s)
     }
     size_t sz = want + want / 8;
     sz = (sz + (1u << 21) - 1) & ~((size_t)(1u << 21) - 1);
-    cudaError_t e = cudaMallocAsync(&p, sz, s);
+    cudaError_t e = pool_malloc(&p, sz, s);
     if (e != cudaSuccess) {
         p = nullptr;
         cudaGetLastError();
@@ -104,9 +150,11 @@ int DevBuf::ensure(size_t want, cudaStream_t s)
     return MLT_OK;
 }
 
+// The device is idle for this buffer (a handle is released after a
+// synchronisation), so the block returns to the pool at once.
 void DevBuf::release()
 {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, 0);
     p = nullptr;
     bytes = 0;
 }
@@ -128,9 +176,9 @@ static int dev_alloc_copy(T** dst, const void* src, size_t count, bool src_dev, 
 {
     *dst = nullptr;
     if (count == 0) count = 1;
-    if (cudaMallocAsync((void**)dst, count * sizeof(T), s) != cudaSuccess) {
+    if (pool_malloc((void**)dst, count * sizeof(T), s) != cudaSuccess) {
         cudaGetLastError();
-        return fail(MLT_ENOMEM, "cudaMallocAsync for the matrix failed");
+        return fail(MLT_ENOMEM, "device allocation for the matrix failed");
     }
     if (src) {
         MLT_CUDA_TRY(cudaMemcpyAsync(*dst, src, count * sizeof(T),
@@ -336,7 +384,7 @@ static void free_matrix(mlt_matrix* M)
     void* owned[] = {M->own_rowptr, M->own_col, M->own_val, M->own_val32, M->own_t_rowptr,
                      M->own_t_col, M->own_t_val, M->own_t_val32, M->plan_A.mem, M->plan_AT.mem};
     for (void* p : owned)
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, 0);   // called with the handle's work finished
     mlt::DevBuf* bufs[] = {&M->ws_v[0], &M->ws_v[1], &M->ws_v2[0], &M->ws_v2[1], &M->ws_w, &M->ws_part, &M->ws_dots,
                            &M->ws_misc, &M->ws_out, &M->ws_y, &M->ws_y16, &M->ws_y32, &M->ws_z, &M->ws_x,
                            &M->ws_tri, &M->ws_seg, &M->ws_upcol};
@@ -625,9 +673,9 @@ int mlt_create_csr(int64_t nrows, int64_t ncols, int64_t nnz, const int64_t* row
         {
             const size_t words = (size_t)(nnz / 32 + 1);
             char* scratch = nullptr;
-            if (cudaMallocAsync((void**)&scratch, 256 + words * sizeof(unsigned), s) != cudaSuccess) {
+            if (pool_malloc((void**)&scratch, 256 + words * sizeof(unsigned), s) != cudaSuccess) {
                 cudaGetLastError();
-                return bail(fail(MLT_ENOMEM, "cudaMallocAsync failed"));
+                return bail(fail(MLT_ENOMEM, "device allocation for CSR validation failed"));
             }
             int* bad = reinterpret_cast<int*>(scratch);
             unsigned* starts = reinterpret_cast<unsigned*>(scratch + 256);
@@ -759,6 +807,11 @@ int mlt_destroy(mlt_matrix* m)
     delete m;
     if (cur != dev) cudaSetDevice(cur);
     return MLT_OK;
+}
+
+int mlt_release_cached(void)
+{
+    return cuda_fail(mlt::trim_pools(), "mlt_release_cached");
 }
 
 int mlt_matrix_info(const mlt_matrix* m, int64_t* dim, int64_t* nnz)

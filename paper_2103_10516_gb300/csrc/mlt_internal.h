@@ -39,6 +39,11 @@ struct ProfPause {
     ~ProfPause();
 };
 
+// Stream-ordered device allocation from the library's pool on the current
+// device: freed blocks stay cached there for later handles instead of going
+// back to the driver at each synchronisation (mlt_release_cached trims it).
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t s);
+
 // A grow-only device buffer owned by a matrix handle.
 struct DevBuf {
     void* p = nullptr;

@@ -37,7 +37,8 @@ EXPORTS = ["mlt_create_csr", "mlt_destroy", "mlt_matrix_info", "mlt_spectrum_bou
            "mlt_surrogate_create", "mlt_surrogate_destroy", "mlt_surrogate_set_params",
            "mlt_surrogate_get_params", "mlt_surrogate_loss_grad", "mlt_surrogate_train",
            "mlt_surrogate_predict", "mlt_learned_train", "mlt_learned_estimate",
-           "mlt_moments_batched", "mlt_autotune", "mlt_moments_noalloc", "mlt_low_traces"]
+           "mlt_moments_batched", "mlt_autotune", "mlt_moments_noalloc", "mlt_low_traces",
+           "mlt_release_cached"]
 
 
 class MLTError(RuntimeError):
@@ -86,6 +87,7 @@ def lib():
                                       ctypes.c_uint64, ctypes.c_double, ctypes.c_int, ctypes.c_uint)
     L.mlt_create_csr.argtypes = [i64, i64, i64, vp, vp, vp, ci, dbl, cu, vp, ctypes.POINTER(vp)]
     L.mlt_destroy.argtypes = [vp]
+    L.mlt_release_cached.argtypes = []
     L.mlt_matrix_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.mlt_spectrum_bounds.argtypes = [vp, ci, ci, u64, ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     L.mlt_cheb_coeffs.argtypes = [ci, dbl, dbl, dbl, ci, vp]
@@ -162,6 +164,11 @@ def mlt_create_csr(nrows, ncols, nnz, rowptr, col, vals=None, val_type=None, sca
 def mlt_destroy(handle):
     if handle:
         _check(lib().mlt_destroy(handle))
+
+
+def mlt_release_cached():
+    """Return the device memory cached by destroyed handles to the driver."""
+    _check(lib().mlt_release_cached())
 
 
 def mlt_matrix_info(handle):

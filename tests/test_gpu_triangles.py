@@ -157,3 +157,25 @@ def test_degree_classes_and_huge_rows(L, O):
     assert np.array_equal(x, O.triangle_moments(g, 4, 250, 160))
     er, sr, _, _ = O.triangle_estimate(x, g.nnz, True)
     assert est == er and se == sr
+
+
+def test_pooled_memory_reuse(L, O):
+    # handles take their memory from the library's pool: a handle built in the
+    # blocks a destroyed handle (another graph, stale contents) left behind
+    # gives the same moments, and returning the cache to the driver is clean
+    ga = synth.rmat_adjacency(13, 16, seed=4)
+    gb = synth.random_graph(3000, 0.004, seed=9)
+    xs = []
+    for g in (ga, gb, ga):
+        x = np.zeros((256, 3), dtype=np.int64)
+        with L.Matrix(g) as G:
+            G.triangles(2, 7, 256, x=x)
+        xs.append(x)
+    assert np.array_equal(xs[0], xs[2])
+    assert np.array_equal(xs[0], O.triangle_moments(ga, 2, 7, 256))
+    assert np.array_equal(xs[1], O.triangle_moments(gb, 2, 7, 256))
+    L.mlt_release_cached()
+    x = np.zeros((256, 3), dtype=np.int64)
+    with L.Matrix(gb) as G:
+        G.triangles(2, 7, 256, x=x)
+    assert np.array_equal(x, xs[1])
