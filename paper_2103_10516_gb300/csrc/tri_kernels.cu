@@ -59,6 +59,7 @@ constexpr int kGather = 8;            // gathers each lane keeps in flight (divi
 constexpr unsigned kFull = 0xFFFFFFFFu;
 static_assert(32 % kGather == 0, "a gather batch never crosses a 32-entry column block");
 constexpr int kScanBlock = 1024;      // elements per CTA of the prefix scan
+constexpr int kPass2CtasPerSm = 6;    // pass 2 compiled for six resident CTAs (40 registers)
 static_assert(kLongRow <= kMidDeg && kChunk <= kLongRow, "rows handled whole by pass 1 must be small or mid");
 
 enum RowClass { kClassSmall = 0, kClassMid = 1, kClassHuge = 2 };
@@ -629,48 +630,109 @@ __device__ __forceinline__ void count_negatives(const int32_t* __restrict__ col,
 // The same counts, bit-sliced, for spans of at least kSliceMin entries (and
 // at most kLongRow).  Lane l takes entry l/4 of every batch of 8 entries and
 // sign word l%4 of it (32 probes), and counts each of the 32 bit positions in
-// eight bit planes: bit t of c[p] is bit p of position t's count (a lane sees
-// at most kLongRow/8 = 128 words, so eight planes never overflow).  Adding a
-// word is a ripple-carry increment, 16 bitwise operations for 32 probes.
-// The eight entry slots are then summed lane against lane with a bit-sliced
-// adder (totals <= 1024 need 11 planes), and each lane reads its own four
-// probes out of the planes of word l/8.
+// P bit planes: bit t of c[p] is bit p of position t's count.  Blocks of 64
+// (P >= 4) and then 32 entries give each lane eight or four words at once
+// (that many gathers in flight), added with carry-save adders: for four
+// words, c0 + x0 + x1 = c0' + 2 t0 and c0' + x2 + x3 = c0'' + 2 t1, then
+// c1 + t0 + t1 = c1' + 2 f, and f ripples into planes 2 .. P-1 (15 + 2(P-2)
+// bitwise operations, where a ripple-carry increment takes 3P per word);
+// eight words add two such groups and c2 + f0 + f1 = c2' + 2 e.  The rest of
+// the span adds one word per batch of 8 by ripple.  The eight entry slots are
+// then summed lane against lane with a bit-sliced adder whose sums gain one
+// plane per level, and each lane reads its own four probes out of the planes
+// of word l/8.  P is the fewest planes that hold the words one lane sees,
+// ceil(n / 8) for a span of n entries (the planes always hold a lane's exact
+// count).
 constexpr int kSliceMin = 16;
-static_assert(kLongRow / 8 <= 255 && kLongRow <= 2047, "plane counts of the sliced counter");
+static_assert(kLongRow <= 1024, "eight planes hold a lane's count of at most 128 words");
 
-__device__ __forceinline__ void count_negatives_sliced(const int32_t* __restrict__ col, int64_t a, int64_t b,
-                                                       const uint32_t* __restrict__ zb, int lane, int cnt[4])
+// a + b + c = s + 2 carry, bitwise (a full adder per bit position); s replaces a.
+__device__ __forceinline__ void carry_save(uint32_t& a, uint32_t b, uint32_t c, uint32_t& carry)
 {
-    uint32_t c[11];
+    const uint32_t u = a ^ b;
+    carry = (a & b) | (u & c);
+    a = u ^ c;
+}
+
+template <int P>
+__device__ __forceinline__ void count_negatives_sliced_p(const int32_t* __restrict__ col, int64_t a, int64_t b,
+                                                         const uint32_t* __restrict__ zb, int lane, int cnt[4])
+{
+    constexpr int Q = P + 3;   // planes of the sum of eight slots
+    uint32_t c[Q];
 #pragma unroll
-    for (int p = 0; p < 11; ++p) c[p] = 0u;
+    for (int p = 0; p < Q; ++p) c[p] = 0u;
+    static_assert(P >= 3, "the carry-save blocks use planes 0, 1 and 2");
     const int slot = lane >> 2, w = lane & 3;
-    for (int64_t base = a; base < b; base += 8) {
+    int64_t base = a;
+    if constexpr (P >= 4) {
+        for (; base + 64 <= b; base += 64) {
+            const int cj0 = __ldg(col + base + lane), cj1 = __ldg(col + base + 32 + lane);
+            uint32_t x[8];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = __ldg(zb + (size_t)__shfl_sync(kFull, cj0, 8 * u + slot) * 4 + w);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[4 + u] = __ldg(zb + (size_t)__shfl_sync(kFull, cj1, 8 * u + slot) * 4 + w);
+            uint32_t t0, t1, t2, t3, f0, f1, e;
+            carry_save(c[0], x[0], x[1], t0);
+            carry_save(c[0], x[2], x[3], t1);
+            carry_save(c[1], t0, t1, f0);
+            carry_save(c[0], x[4], x[5], t2);
+            carry_save(c[0], x[6], x[7], t3);
+            carry_save(c[1], t2, t3, f1);
+            carry_save(c[2], f0, f1, e);
+#pragma unroll
+            for (int p = 3; p < P; ++p) {
+                const uint32_t t = c[p] & e;
+                c[p] ^= e;
+                e = t;
+            }
+        }
+    }
+    for (; base + 32 <= b; base += 32) {
+        const int cj = __ldg(col + base + lane);
+        uint32_t x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = __ldg(zb + (size_t)__shfl_sync(kFull, cj, 8 * u + slot) * 4 + w);
+        uint32_t t0, t1, f;
+        carry_save(c[0], x[0], x[1], t0);
+        carry_save(c[0], x[2], x[3], t1);
+        carry_save(c[1], t0, t1, f);
+#pragma unroll
+        for (int p = 2; p < P; ++p) {
+            const uint32_t t = c[p] & f;
+            c[p] ^= f;
+            f = t;
+        }
+    }
+    for (; base < b; base += 8) {
         const int64_t k = base + slot;
         uint32_t x = 0u;
         if (k < b) x = __ldg(zb + (size_t)__ldg(col + k) * 4 + w);
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
+        for (int p = 0; p < P; ++p) {
             const uint32_t t = c[p] & x;
             c[p] ^= x;
             x = t;
         }
     }
 #pragma unroll
-    for (int m = 4; m <= 16; m <<= 1) {
+    for (int lv = 0; lv < 3; ++lv) {
+        const int m = 4 << lv;
         uint32_t carry = 0u;
 #pragma unroll
-        for (int p = 0; p < 11; ++p) {
+        for (int p = 0; p < P + lv; ++p) {
             const uint32_t o = __shfl_xor_sync(kFull, c[p], m);
             const uint32_t sum = c[p] ^ o ^ carry;
             carry = (c[p] & o) | (carry & (c[p] ^ o));
             c[p] = sum;
         }
+        c[P + lv] = carry;
     }
     const int src = lane >> 3, sh = lane & 7;
     uint32_t lo = 0u, hi = 0u;   // 16-bit lanes: probes q = 0, 2 and q = 1, 3
 #pragma unroll
-    for (int p = 0; p < 11; ++p) {
+    for (int p = 0; p < Q; ++p) {
         const uint32_t t = (__shfl_sync(kFull, c[p], src) >> sh) & 0x01010101u;
         lo += (t & 0x00010001u) << p;
         hi += ((t >> 8) & 0x00010001u) << p;
@@ -681,15 +743,31 @@ __device__ __forceinline__ void count_negatives_sliced(const int32_t* __restrict
     cnt[3] += (int)(hi >> 16);
 }
 
+// A span of n = b - a entries, kSliceMin <= n <= kLongRow: a lane sees at
+// most ceil(n / 8) words, 7 / 15 / 31 / 63 / 128 needing 3 / 4 / 5 / 6 / 8
+// planes (a long row's part inside one chunk has at most kChunk = 256).
+__device__ __forceinline__ void count_negatives_sliced(const int32_t* __restrict__ col, int64_t a, int64_t b,
+                                                       const uint32_t* __restrict__ zb, int lane, int cnt[4])
+{
+    const int64_t n = b - a;
+    if (n <= 56) count_negatives_sliced_p<3>(col, a, b, zb, lane, cnt);
+    else if (n <= 120) count_negatives_sliced_p<4>(col, a, b, zb, lane, cnt);
+    else if (n <= 248) count_negatives_sliced_p<5>(col, a, b, zb, lane, cnt);
+    else if (n <= 504) count_negatives_sliced_p<6>(col, a, b, zb, lane, cnt);
+    else count_negatives_sliced_p<8>(col, a, b, zb, lane, cnt);
+}
+
 // Store y for probes 4*lane .. 4*lane+3 of row r (degree deg, slot if deg >
-// kSmallDeg) in its class's array, and add its x1, x2 terms.
+// kSmallDeg) in its class's array, and add its x1, x2 terms (Acc: int for
+// the sums of one pass-1 chunk, long long otherwise).
+template <typename Acc>
 __device__ __forceinline__ void store_row(int64_t r, int64_t deg, const int yv[4], uint32_t own, int32_t slot,
                                           uint32_t* __restrict__ y8, uint2* __restrict__ y16,
-                                          int32_t* __restrict__ y32, int lane, long long x1[4], long long x2[4])
+                                          int32_t* __restrict__ y32, int lane, Acc x1[4], Acc x2[4])
 {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const long long yq = yv[q];
+        const Acc yq = yv[q];
         x1[q] += ((own >> (8 * q)) & 1u) ? -yq : yq;
         x2[q] += yq * yq;
     }
@@ -705,10 +783,14 @@ __device__ __forceinline__ void store_row(int64_t r, int64_t deg, const int yv[4
     }
 }
 
+// y of a row handled whole by one chunk, from its negative-sign counts.  x1
+// and x2 take int sums: the rows a chunk owns hold at most kChunk + kLongRow
+// entries, so their sum of y^2 <= kLongRow * (kChunk + kLongRow) < 2^31.
+static_assert((int64_t)kLongRow * (kChunk + kLongRow) < (1LL << 31), "int sums of x2 over one chunk");
 __device__ __forceinline__ void finish_pass1_row(int64_t r, int deg, int cnt[4], uint32_t own,
                                                  const int32_t* __restrict__ bslot, uint32_t* __restrict__ y8,
                                                  uint2* __restrict__ y16, int32_t* __restrict__ y32, int lane,
-                                                 long long x1[4], long long x2[4])
+                                                 int x1[4], int x2[4])
 {
     if (deg > 0) {
         const int yv[4] = {deg - 2 * cnt[0], deg - 2 * cnt[1], deg - 2 * cnt[2], deg - 2 * cnt[3]};
@@ -741,6 +823,7 @@ __global__ void __launch_bounds__(kTriThreads) tri_pass1_kernel(
     for (int64_t c = next_chunk(counter, lane); c < nch; c = next_chunk(counter, lane)) {
         const int64_t u0 = c * kChunk, u1 = u0 + kChunk;
         int64_t r = crow[c];
+        int cx1[4] = {0, 0, 0, 0}, cx2[4] = {0, 0, 0, 0};   // this chunk's rows
         while (r < d) {
             const int64_t beg = __ldg(rowptr + r);
             const int64_t pr = beg + kRowCost * r;          // first unit of row r
@@ -790,11 +873,16 @@ __global__ void __launch_bounds__(kTriThreads) tri_pass1_kernel(
                     int cnt[4] = {0, 0, 0, 0};
                     if (b - a >= kSliceMin) count_negatives_sliced(col, a, b, zb, lane, cnt);
                     else count_negatives(col, a, b, zb, lane, cnt);
-                    finish_pass1_row(row, b - a, cnt, own, bslot, y8, y16, y32, lane, x1, x2);
+                    finish_pass1_row(row, b - a, cnt, own, bslot, y8, y16, y32, lane, cx1, cx2);
                 }
                 r += f;
                 if (f < 32) break;
             }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            x1[q] += cx1[q];
+            x2[q] += cx2[q];
         }
     }
     flush_x(sx, 0, x1, lane);
@@ -913,7 +1001,7 @@ __device__ __forceinline__ void finish_pass2_row(uint2 own, int32_t slot, int s[
 // Pass 2: x3 = 2 sum_i y_i sum_{j in out(i)} y_j over the oriented out-lists
 // (|s| <= kLongRow * kMidDeg < 2^31: a row part never holds more than
 // kLongRow entries and every main target is small or mid).
-__global__ void __launch_bounds__(kTriThreads) tri_pass2_kernel(
+__global__ void __launch_bounds__(kTriThreads, kPass2CtasPerSm) tri_pass2_kernel(
     const int64_t* __restrict__ out_ptr, const int32_t* __restrict__ out_col, const int32_t* __restrict__ nsmall,
     const int32_t* __restrict__ bslot, int64_t d, int64_t nch, const int64_t* __restrict__ crow,
     const uint32_t* __restrict__ y8, const uint2* __restrict__ y16,
