@@ -424,6 +424,95 @@ def mlmc_auto(m, fn, a, b, n, seed, m_pilot, mode="budget", target=1.0, p=0.0,
 
 
 # ---------------------------------------------------------------------------
+# Hutch++ on the Chebyshev interpolant: the variance reduction Section 5.3
+# suggests for the Estrada index (the method of Meyer, Musco, Musco and
+# Woodruff, 2021: deflate an orthonormal basis Q of the range of p(At) S, take
+# tr(Q^T p(At) Q) exactly and Hutchinson's estimate on the rest)
+# ---------------------------------------------------------------------------
+
+def _operator(m, gram=False, scale=1.0):
+    """v -> A v on blocks (dim x k): A = scale * m, or X^T X with X = scale * m."""
+    import scipy.sparse as sp
+    val = np.ones(m.nnz) if m.val is None else np.asarray(m.val, dtype=np.float64)
+    X = sp.csr_matrix((val * scale, np.asarray(m.col), np.asarray(m.rowptr)), shape=(m.nrows, m.ncols))
+    if gram:
+        return lambda v: X.T @ (X @ v)
+    return lambda v: X @ v
+
+
+def poly_apply(m, a, b, c, X, gram=False, scale=1.0):
+    """Y = p(At) X, p = sum_j c_j T_j (Section 2.2, Eq. chebSeries), by the
+    three-term recurrence W_0 = X, W_1 = At X, W_{j+1} = 2 At W_j - W_{j-1}
+    (Eq. recurrence) and Y = sum_j c_j W_j; At = alpha A + beta I with
+    alpha = 2/(b-a), beta = -(a+b)/(b-a)."""
+    A = _operator(m, gram, scale)
+    alpha = 2.0 / (b - a)
+    beta = -(a + b) / (b - a)
+
+    def At(v):
+        return alpha * A(v) + beta * v
+
+    W0 = np.array(X, dtype=np.float64)
+    Y = c[0] * W0
+    if len(c) == 1:
+        return Y
+    W1 = At(W0)
+    Y = Y + c[1] * W1
+    for j in range(2, len(c)):
+        W0, W1 = W1, 2.0 * At(W1) - W0
+        Y = Y + c[j] * W1
+    return Y
+
+
+def hutchpp_parts(m, a, b, c, S, G, gram=False, scale=1.0, drop_tol=1e-10):
+    """Hutch++ with explicit sketch vectors S (dim x s) and remainder probes G
+    (dim x g) on tr p(At), p = sum_j c_j T_j:
+      Q       orthonormal basis of p(At) S (numpy's QR); a column whose residual
+              |R_jj| is at most drop_tol times its own norm is dependent and dropped,
+      t1      tr(Q^T p(At) Q) = sum_i sum_j c_j q_i^T T_j(At) q_i,
+      samples g_i'^T p(At) g_i' with g_i' = (I - Q Q^T) g_i.
+    The estimate is t1 + mean(samples).  Returns (t1, samples, rank of Q)."""
+    n = len(c) - 1
+    S = np.asarray(S, dtype=np.float64)
+    G = np.asarray(G, dtype=np.float64)
+    if S.shape[1] > 0:
+        Y = poly_apply(m, a, b, c, S, gram, scale)
+        Q, R = np.linalg.qr(Y)
+        keep = np.abs(np.diag(R)) > drop_tol * np.linalg.norm(Y, axis=0)
+        Q = Q[:, keep]
+    else:
+        Q = np.zeros((S.shape[0], 0))
+
+    def quad(V):
+        if V.shape[1] == 0:
+            return np.zeros(0)
+        mu = moments_z(m, a, b, V.T, n, gram, scale)
+        return mu @ np.asarray(c, dtype=np.float64)
+
+    t1 = math.fsum(quad(Q).tolist())
+    Gp = G - Q @ (Q.T @ G)
+    return t1, quad(Gp), int(Q.shape[1])
+
+
+def hutchpp(m, a, b, c, seed, probe_offset, s, g, gram=False, scale=1.0):
+    """Hutch++ with Rademacher sketch and remainder probes: S has the probes
+    with ids probe_offset .. probe_offset + s - 1, G the next g.  The standard
+    error is that of the remainder mean (divisor g - 1; NaN for g < 2)."""
+    d = m.ncols if gram else m.nrows
+    S = np.zeros((d, s))
+    G = np.zeros((d, g))
+    for i in range(s):
+        S[:, i] = rademacher(seed, probe_offset + i, d)
+    for i in range(g):
+        G[:, i] = rademacher(seed, probe_offset + s + i, d)
+    t1, samples, rank = hutchpp_parts(m, a, b, c, S, G, gram, scale)
+    t2 = math.fsum(samples.tolist()) / g if g > 0 else 0.0
+    se = math.sqrt(float(np.var(samples, ddof=1)) / g) if g > 1 else float("nan")
+    return {"estimate": t1 + t2, "stderr": se, "t_sketch": t1, "t_rest": t2, "samples": samples,
+            "rank": rank}
+
+
+# ---------------------------------------------------------------------------
 # Triangle counting (Section 2.1 Example; Section 5.4)
 # ---------------------------------------------------------------------------
 
