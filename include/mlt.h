@@ -290,6 +290,57 @@ int mlt_mlmc_estimate(mlt_matrix* m, const mlt_mlmc_params* p, mlt_mlmc_result* 
 int mlt_low_traces(mlt_matrix* m, double a, double b, double* t, int* count, void* stream);
 
 /*
+ * Y = p(At) X for a block of ncols vectors, p = sum_{k=0..n} c[k] T_k with the
+ * coefficients of mlt_cheb_coeffs (Section 2.2, Eq. chebSeries), At the map of
+ * [a, b] onto [-1, 1] applied to the handle's operator (A scaled, or X^T X).
+ * Evaluated by Clenshaw's recurrence for Chebyshev sums: n operator
+ * applications per vector, FP64 throughout.
+ * X, Y: d x ncols, row-major with row strides ldx, ldy >= ncols (entry i of
+ * vector j at X[i * ldx + j]); host memory, or device memory with
+ * MLT_DEVICE_PTRS in flags; they must not overlap.  Y is complete on return
+ * (the call synchronises `stream`).
+ * Errors: MLT_EINVAL (null pointers, n outside [1, MLT_MAX_DEGREE], a >= b,
+ * ncols outside [1, 4096], strides below ncols, unknown flags), MLT_ENOMEM,
+ * MLT_ECUDA.
+ */
+int mlt_poly_apply(mlt_matrix* m, double a, double b, const double* c, int n,
+                   const double* X, int64_t ldx, double* Y, int64_t ldy, int ncols,
+                   unsigned flags, void* stream);
+
+/*
+ * Hutch++ on tr p(At), the variance reduction Section 5.3 proposes for the
+ * Estrada index (the method of Meyer, Musco, Musco and Woodruff, 2021).
+ * p = sum_{k=0..n} c[k] T_k as in mlt_poly_apply.  With S the s Rademacher
+ * probes of ids probe_offset .. probe_offset + s - 1 and G the g probes that
+ * follow (the generator of mlt_moments):
+ *   Q         orthonormal basis of p(At) S: classical Gram-Schmidt with every
+ *             column projected twice; a column left with at most 1e-10 of its
+ *             norm is dependent and dropped (rank counts those kept);
+ *   t_sketch  tr(Q^T p(At) Q), from the doubling moments of Q's columns;
+ *   samples   q_i = g_i'^T p(At) g_i' with g_i' = (I - Q Q^T) g_i;
+ *   estimate  t_sketch + t_rest, t_rest the mean of the q_i, and std_error
+ *             sqrt(var(q) / g) (divisor g - 1; NaN when g < 2).
+ * Unbiased for tr p(At) whatever Q is, since Q does not depend on G; exact
+ * when Q spans the whole space.  Cost: s*n + (s + g)*ceil(n/2) operator
+ * applications (matvecs), FP64 throughout.
+ * samples: g doubles (host) or NULL.  0 <= s <= 128, 0 <= g <= 1024, s + g >= 1.
+ * Errors: MLT_EINVAL (null m, c or out; n outside [1, MLT_MAX_DEGREE]; a >= b;
+ * s, g out of range; probe ids beyond 2^32), MLT_ENOMEM, MLT_ECUDA.
+ */
+typedef struct {
+    double estimate;
+    double std_error;
+    double t_sketch;
+    double t_rest;
+    int rank;
+    int64_t matvecs;
+} mlt_hutchpp_result;
+
+int mlt_hutchpp_estimate(mlt_matrix* m, double a, double b, const double* c, int n,
+                         uint64_t seed, int64_t probe_offset, int s, int g,
+                         double* samples, mlt_hutchpp_result* out, void* stream);
+
+/*
  * Triangle-count estimate tr(A^3)/6 for a symmetric 0/1 adjacency matrix with
  * no self-loops (Section 2.1 Example; Section 5.4).  For probes
  * probe_offset .. probe_offset+nprobes-1 it computes, exactly in int64,

@@ -101,7 +101,9 @@ struct StepArgs {
     const T* vcur;         // V_k at the row itself
     T* vprev_out;          // in: V_{k-1} (unless first); out: V_{k+1}
     T alpha, beta;         // At = alpha A + beta I
-    int mode;              // 0 first step, 1 recurrence step, 2 plain product
+    int mode;              // 0 first step, 1 recurrence step, 2 plain product, 3 Clenshaw step
+    const T* addv;         // mode 3: out = m1 * At V_k - V_{k-1} + coef * addv (no dots)
+    T coef, m1;
     int direct;            // dots are z . V_{k+1} instead of V.V and V.V_k
     int B;                 // probes in the group (columns >= B are padding)
     uint64_t seedmix;
@@ -194,6 +196,14 @@ __device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0
         return;
     }
     const P xc = *reinterpret_cast<const P*>(a.vcur + off);
+    if (std::is_same<T, double>::value && a.mode == 3) {   // Clenshaw steps run in FP64 only
+        const P xp = *reinterpret_cast<const P*>(a.vprev_out + off);
+        const P xa = *reinterpret_cast<const P*>(a.addv + off);
+#pragma unroll
+        for (int q = 0; q < N; ++q) out.v[q] = a.m1 * (a.alpha * acc[q] + a.beta * xc.v[q]) - xp.v[q] + a.coef * xa.v[q];
+        *reinterpret_cast<P*>(a.vprev_out + off) = out;
+        return;
+    }
     if (a.mode == 0) {
 #pragma unroll
         for (int q = 0; q < N; ++q) out.v[q] = a.alpha * acc[q] + a.beta * xc.v[q];
@@ -293,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, kStepCtasPerSm) cheb_step_kernel(Ste
             }
         }
     }
-    if (a.mode == 2) return;
+    if (a.mode >= 2) return;
     cta_partials<T, G>(a, L, s_self, s_cross);
 }
 
@@ -319,7 +329,7 @@ __global__ void __launch_bounds__(kThreads) cheb_long_kernel(StepArgs<T> a)
             epilogue<T>(a, a.long_rows[i], L.c0, acc, s_self, s_cross);
         }
     }
-    if (a.mode == 2) return;
+    if (a.mode >= 2) return;
     cta_partials<T, G>(a, L, s_self, s_cross);
 }
 
@@ -436,7 +446,7 @@ int launch_step_g(StepArgs<T> a, int max_main, int max_long, int num_sms, int* n
     int nb = (int)std::max<long long>(1, std::min<long long>((items + gpb - 1) / gpb, max_main));
     if ((long long)nb * gpb < a.nchunks) nb = (a.nchunks + gpb - 1) / gpb;
     {
-        ProfScope ps(a.mode == 2 ? "gram_spmm" : "cheb_step", s);
+        ProfScope ps(a.mode == 2 ? "gram_spmm" : (a.mode == 3 ? "clenshaw_step" : "cheb_step"), s);
         cheb_step_kernel<T, G><<<nb, kThreads, 0, s>>>(a);
     }
     MLT_CUDA_TRY(cudaGetLastError());
@@ -447,7 +457,7 @@ int launch_step_g(StepArgs<T> a, int max_main, int max_long, int num_sms, int* n
         if ((long long)nl * gpb < a.nchunks) nl = (a.nchunks + gpb - 1) / gpb;
         StepArgs<T> b = a;
         if (b.partials) b.partials += (size_t)nb * 2 * a.ldv;
-        ProfScope ps(a.mode == 2 ? "gram_spmm_long" : "cheb_step_long", s);
+        ProfScope ps(a.mode == 2 ? "gram_spmm_long" : (a.mode == 3 ? "clenshaw_step_long" : "cheb_step_long"), s);
         cheb_long_kernel<T, G><<<nl, kThreads, 0, s>>>(b);
     }
     MLT_CUDA_TRY(cudaGetLastError());
@@ -654,7 +664,127 @@ int run_group(mlt_matrix* M, const MomentPlan& plan, int ks, double a, double b,
     return MLT_OK;
 }
 
+// out[i] = coef * x[i] over n elements (x null: zeros).
+__global__ void scaled_copy_kernel(double* __restrict__ out, const double* __restrict__ x, double coef, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = x ? coef * x[i] : 0.0;
+}
+
+// The context of FP64 steps over an explicit block of `cols` vectors with row
+// stride ldv (buffers sized, map At = alpha A + beta I set).
+int block_ctx(mlt_matrix* M, int ldv, int cols, int K, double a, double b, GroupCtx& g, cudaStream_t s)
+{
+    g.gram = (M->flags & MLT_GRAM) != 0;
+    g.d = g.gram ? M->A.ncols : M->A.nrows;
+    g.ldv = ldv;
+    int rc;
+    if ((rc = ensure_spmm_plan(M, M->A, M->plan_A, s))) return rc;
+    if (g.gram && (rc = ensure_spmm_plan(M, M->AT, M->plan_AT, s))) return rc;
+    if (g.gram && (rc = M->ws_w.ensure((size_t)M->A.nrows * ldv * sizeof(double), s))) return rc;
+    const int64_t nseg = std::max(M->plan_A.nseg, g.gram ? M->plan_AT.nseg : (int64_t)0);
+    if ((rc = M->ws_seg.ensure((size_t)std::max<int64_t>(nseg, 1) * ldv * sizeof(double), s))) return rc;
+    g.max_main = 8 * M->num_sms;
+    g.max_long = 2 * M->num_sms;
+    g.max_blocks = g.max_main + g.max_long;
+    if ((rc = M->ws_part.ensure((size_t)kSlots * g.max_blocks * 2 * ldv * sizeof(double), s))) return rc;
+    if ((rc = M->ws_dots.ensure((size_t)std::max(K, 1) * 2 * cols * sizeof(double), s))) return rc;
+    g.part = M->ws_part.as<double>();
+    g.dots = M->ws_dots.as<double>();
+    g.seedmix = 0;
+    g.ra = ReduceArgs{};
+    const double sc = g.gram ? M->scale * M->scale : M->scale;
+    g.alpha = 2.0 / (b - a) * sc;
+    g.beta = -(a + b) / (b - a);
+    return MLT_OK;
+}
+
 }  // namespace
+
+// Y = p(At) X by Clenshaw's recurrence for p = sum_k c_k T_k: b_{n+1} = 0,
+// b_n = c_n X, b_k = 2 At b_{k+1} - b_{k+2} + c_k X (k = n-1 .. 1), and
+// p(At) X = At b_1 - b_2 + c_0 X: n operator applications.  b_j lives in
+// P[(n + 1 - j) & 1], so each step overwrites b_{k+2} in place.
+int poly_apply_block(mlt_matrix* M, double a, double b, const double* c, int n, const double* X, double* Y, int ldv,
+                     int ncols, double* P0, double* P1, cudaStream_t s)
+{
+    GroupCtx g;
+    int rc;
+    if ((rc = block_ctx(M, ldv, ncols, 1, a, b, g, s))) return rc;
+    const int64_t total = g.d * (int64_t)ldv;
+    const int nbk = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 16LL * M->num_sms));
+    double* P[2] = {P0, P1};
+    {
+        ProfScope ps("clenshaw_init", s);
+        scaled_copy_kernel<<<nbk, 256, 0, s>>>(P[0], nullptr, 0.0, total);
+        scaled_copy_kernel<<<nbk, 256, 0, s>>>(P[1], X, c[n], total);
+    }
+    MLT_CUDA_TRY(cudaGetLastError());
+    const int nvec = (ncols + Lanes<double>::N - 1) / Lanes<double>::N;
+    const int G = pow2_at_least(std::min(nvec, 32));
+    const DevCSR& A = M->A;
+    const DevCSR& AT = M->AT;
+    for (int k = n - 1; k >= 0; --k) {
+        double* cur = P[(n - k) & 1];          // b_{k+1}
+        double* out = P[(n + 1 - k) & 1];      // in: b_{k+2}; out: b_k (or the result at k = 0)
+        StepArgs<double> sa{};
+        sa.ldv = ldv;
+        sa.nvec = nvec;
+        sa.nchunks = (nvec + G - 1) / G;
+        sa.alpha = g.alpha;
+        sa.beta = g.beta;
+        sa.B = ncols;
+        int nb = 0;
+        if (g.gram) {
+            StepArgs<double> pa = sa;
+            pa.rowptr = A.rowptr; pa.col = A.col; pa.val = A.val64; pa.nrows = A.nrows;
+            pa.vgather = cur; pa.vcur = nullptr; pa.vprev_out = M->ws_w.as<double>(); pa.mode = 2;
+            set_split(pa, M->plan_A, M->ws_seg.as<double>());
+            if ((rc = launch_step<double>(G, pa, g.max_main, g.max_long, M->num_sms, &nb, s))) return rc;
+            sa.rowptr = AT.rowptr; sa.col = AT.col; sa.val = AT.val64; sa.nrows = AT.nrows;
+            sa.vgather = M->ws_w.as<double>();
+            set_split(sa, M->plan_AT, M->ws_seg.as<double>());
+        } else {
+            sa.rowptr = A.rowptr; sa.col = A.col; sa.val = A.val64; sa.nrows = A.nrows;
+            sa.vgather = cur;
+            set_split(sa, M->plan_A, M->ws_seg.as<double>());
+        }
+        sa.vcur = cur;
+        sa.vprev_out = out;
+        sa.mode = 3;
+        sa.addv = X;
+        sa.coef = c[k];
+        sa.m1 = k > 0 ? 2.0 : 1.0;
+        if ((rc = launch_step<double>(G, sa, g.max_main, g.max_long, M->num_sms, &nb, s))) return rc;
+    }
+    double* res = P[(n + 1) & 1];
+    if (res != Y) MLT_CUDA_TRY(cudaMemcpyAsync(Y, res, (size_t)total * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return MLT_OK;
+}
+
+// Doubling moments of an explicit FP64 block: V0 holds the start vectors (row
+// stride ldv, columns >= cols zero) and V1 is scratch of the same size, both
+// overwritten.  After K steps dots[k][0][c] = V_{k+1}.V_{k+1} and
+// dots[k][1][c] = V_{k+1}.V_k for column c (device, in the handle's scratch).
+int moments_block(mlt_matrix* M, double a, double b, double* V0, double* V1, int ldv, int cols, int K,
+                  const double** dots_dev, cudaStream_t s)
+{
+    GroupCtx g;
+    int rc;
+    if ((rc = block_ctx(M, ldv, cols, K, a, b, g, s))) return rc;
+    std::vector<int> act(std::max(K, 1), cols);
+    MomentPlan plan{};
+    plan.dim = g.d;
+    plan.B = cols;
+    plan.ldv = ldv;
+    plan.K = K;
+    plan.act = act.data();
+    plan.direct = 0;
+    double* V[2] = {V0, V1};
+    if ((rc = run_steps<double>(M, plan, g, 0, K, V, M->ws_w.as<double>(), M->ws_seg.as<double>(), s))) return rc;
+    *dots_dev = g.dots;
+    return MLT_OK;
+}
 
 // Build the fixed work split of one CSR operand (once per matrix): chunk size
 // Uc from the unit count so that there are a few dozen chunks per SM, the row

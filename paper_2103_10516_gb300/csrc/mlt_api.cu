@@ -387,7 +387,8 @@ static void free_matrix(mlt_matrix* M)
         if (p) cudaFreeAsync(p, 0);   // called with the handle's work finished
     mlt::DevBuf* bufs[] = {&M->ws_v[0], &M->ws_v[1], &M->ws_v2[0], &M->ws_v2[1], &M->ws_w, &M->ws_part, &M->ws_dots,
                            &M->ws_misc, &M->ws_out, &M->ws_y, &M->ws_y16, &M->ws_y32, &M->ws_z, &M->ws_x,
-                           &M->ws_tri, &M->ws_seg, &M->ws_upcol};
+                           &M->ws_tri, &M->ws_seg, &M->ws_upcol, &M->ws_blk[0], &M->ws_blk[1], &M->ws_blk[2],
+                           &M->ws_blk[3]};
     for (auto* b : bufs) b->release();
 }
 

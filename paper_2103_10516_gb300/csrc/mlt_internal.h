@@ -116,6 +116,7 @@ struct mlt_matrix {
     mlt::SpmmPlan plan_A, plan_AT;
     mlt::DevBuf ws_v[2], ws_v2[2], ws_w, ws_part, ws_dots, ws_misc, ws_out, ws_y, ws_y16, ws_y32, ws_z, ws_x, ws_tri,
         ws_seg, ws_upcol;
+    mlt::DevBuf ws_blk[4];      // explicit FP64 vector blocks (polynomial application, Hutch++)
     int64_t dim() const { return (flags & MLT_GRAM) ? A.ncols : A.nrows; }
 };
 
@@ -162,6 +163,13 @@ int enqueue_moment_job(MomentJob& J, cudaStream_t s);
 int finish_moment_job(MomentJob& J, cudaStream_t s);
 
 int ensure_fp32_values(mlt_matrix* M, cudaStream_t s);
+// FP64 blocks of explicit vectors (row-major, row stride ldv even, columns
+// >= cols zero): Y = p(At) X with P0, P1 as scratch (cheb_kernels.cu), and
+// the doubling moments of a start block V0 (V1 scratch; dots stay on the device).
+int poly_apply_block(mlt_matrix* M, double a, double b, const double* c, int n, const double* X, double* Y, int ldv,
+                     int ncols, double* P0, double* P1, cudaStream_t s);
+int moments_block(mlt_matrix* M, double a, double b, double* V0, double* V1, int ldv, int cols, int K,
+                  const double** dots_dev, cudaStream_t s);
 int ensure_spmm_plan(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, cudaStream_t s);
 int spmv_f64(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, const double* x, double* y, cudaStream_t s);
 int lanczos_bounds(mlt_matrix* M, int steps, uint64_t seed, double* lo, double* hi, cudaStream_t s);

@@ -38,7 +38,7 @@ EXPORTS = ["mlt_create_csr", "mlt_destroy", "mlt_matrix_info", "mlt_spectrum_bou
            "mlt_surrogate_get_params", "mlt_surrogate_loss_grad", "mlt_surrogate_train",
            "mlt_surrogate_predict", "mlt_learned_train", "mlt_learned_estimate",
            "mlt_moments_batched", "mlt_autotune", "mlt_moments_noalloc", "mlt_low_traces",
-           "mlt_release_cached"]
+           "mlt_release_cached", "mlt_poly_apply", "mlt_hutchpp_estimate"]
 
 
 class MLTError(RuntimeError):
@@ -55,6 +55,12 @@ class mlt_mlmc_params(ctypes.Structure):
                 ("mode", ctypes.c_int), ("target", ctypes.c_double), ("cost_model", ctypes.c_int),
                 ("max_levels", ctypes.c_int), ("reuse_pilot", ctypes.c_int),
                 ("precision", ctypes.c_int), ("flags", ctypes.c_uint), ("stream", ctypes.c_void_p)]
+
+
+class mlt_hutchpp_result(ctypes.Structure):
+    _fields_ = [("estimate", ctypes.c_double), ("std_error", ctypes.c_double),
+                ("t_sketch", ctypes.c_double), ("t_rest", ctypes.c_double),
+                ("rank", ctypes.c_int), ("matvecs", ctypes.c_int64)]
 
 
 class mlt_mlmc_result(ctypes.Structure):
@@ -98,6 +104,9 @@ def lib():
     L.mlt_triangle_trace.argtypes = [vp, u64, i64, i64, ci, ci, vp, ctypes.POINTER(dbl),
                                      ctypes.POINTER(dbl), vp]
     L.mlt_low_traces.argtypes = [vp, dbl, dbl, vp, ctypes.POINTER(ci), vp]
+    L.mlt_poly_apply.argtypes = [vp, dbl, dbl, vp, ci, vp, i64, vp, i64, ci, cu, vp]
+    L.mlt_hutchpp_estimate.argtypes = [vp, dbl, dbl, vp, ci, u64, i64, ci, ci, vp,
+                                       ctypes.POINTER(mlt_hutchpp_result), vp]
     L.mlt_profile_start.argtypes = []
     L.mlt_profile_stop.argtypes = [ctypes.POINTER(mlt_kernel_stat), ci, ctypes.POINTER(ci)]
     L.mlt_last_error.argtypes = []
@@ -181,6 +190,29 @@ def mlt_spectrum_bounds(handle, method=MLT_BOUNDS_GERSHGORIN, steps=0, seed=0):
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(lib().mlt_spectrum_bounds(handle, method, steps, seed, ctypes.byref(a), ctypes.byref(b)))
     return a.value, b.value
+
+
+def mlt_poly_apply(handle, a, b, c, X, Y=None, stream=None):
+    """Y = p(At) X for the columns of X (d x ncols; numpy on the host, or a CUDA
+    tensor), p = sum_k c[k] T_k.  Returns Y (a new array unless given)."""
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    dev = _is_cuda(X)
+    if Y is None:
+        Y = X.new_empty(X.shape) if dev else np.empty(X.shape, dtype=np.float64)
+    ncols = X.shape[1]
+    _check(lib().mlt_poly_apply(handle, float(a), float(b), _ptr(c), len(c) - 1, _ptr(X), ncols, _ptr(Y), ncols,
+                                ncols, MLT_DEVICE_PTRS if dev else 0, _stream(stream)))
+    return Y
+
+
+def mlt_hutchpp_estimate(handle, a, b, c, seed, probe_offset, s, g, samples=None, stream=None):
+    """Hutch++ on tr p(At); returns the mlt_hutchpp_result (and fills `samples`,
+    a float64 array of g entries, when given)."""
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    r = mlt_hutchpp_result()
+    _check(lib().mlt_hutchpp_estimate(handle, float(a), float(b), _ptr(c), len(c) - 1, seed, probe_offset, s, g,
+                                      _ptr(samples), ctypes.byref(r), _stream(stream)))
+    return r
 
 
 def mlt_low_traces(handle, a, b, stream=None):
