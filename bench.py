@@ -3,7 +3,8 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload rmat20_triangles|logdet64|estrada_rmat22|diffusion64_batched|
-                                nuclear_gram|nuclear_explicit|stencil3d|estrada_learned|level_study]
+                                nuclear_gram|nuclear_explicit|stencil3d|estrada_learned|level_study|
+                                estrada_hutchpp]
                     [--precision fp32|fp64|mixed] [--scale S]
 
 One step is one pass of the whole hot path over one batch of synthetic input:
@@ -35,6 +36,10 @@ One step is one pass of the whole hot path over one batch of synthetic input:
   estrada_learned: the learned coarse level (BF16 network, FP32 moments)
       against plain FP64 MLMC at equal standard error on the Estrada index of
       an R-MAT graph (scale 22 unless --scale); the comparison is in config.
+  estrada_hutchpp: Hutch++ (64 sketch + 64 remainder probes, FP64) on the
+      configuration-5 Estrada problem, with plain FP64 Hutchinson at the same
+      16,384 operator applications run once afterwards; both standard errors
+      are in config.  Units: operator applications (probe-matvecs).
 
 Under torchrun every rank runs its own probes (disjoint probe ids): weak
 scaling with no collective on the data path; the timing is the max over ranks.
@@ -424,6 +429,114 @@ class EstradaRmat22:
         deg = np.full(nprobes, 16, dtype=np.int32)
         oracle.moments(self.csr, -10.0, 10.0, 0, offset, deg, scale=self.scale)
         return nprobes * 16      # the oracle runs direct: one matvec per degree
+
+class EstradaHutchpp:
+    """Hutch++ (Section 5.3's proposal for the Estrada index) against plain
+    Hutchinson at the same operator applications, on configuration 5's matrix:
+    R-MAT scale 22 (seed 1) scaled to spectral radius 10, exp on [-10, 10],
+    degree 128, FP64.  A step is one Hutch++ estimate with S = 64 sketch and
+    G = 64 remainder probes, 64*128 + 128*64 = 16,384 operator applications:
+    the cost of 256 doubling probes, configuration 5's step.  After the timed
+    steps, one Hutch++ estimate and plain FP64 Hutchinson with 256 probes run
+    on fresh probe ids, and the line's config carries both standard errors."""
+    name = "estrada_hutchpp"
+    unit = "probe-matvecs/s"
+    dtype = "f64"
+    S, G, DEG = 64, 64, 128
+    PROBE_SPAN = 1088 * 128 + 128 + 256   # timed, e2e, then the comparison's two runs
+
+    def __init__(self):
+        from paper_2103_10516_gb300 import synth
+        self.csr = synth.rmat_adjacency(22, 16, seed=1)
+        self.d = self.csr.nrows
+        self.nnz = self.csr.nnz
+        self.scale = None
+        self.cmp = None
+
+    def units(self):
+        return self.S * self.DEG + (self.S + self.G) * ((self.DEG + 1) // 2)
+
+    def config(self):
+        return {"workload": self.name, "graph": "R-MAT scale 22, edge factor 16, seed 1",
+                "d": self.d, "nnz": self.nnz, "f": "exp", "interval": [-10.0, 10.0], "degree": self.DEG,
+                "scale": self.scale, "sketch_probes": self.S, "remainder_probes": self.G,
+                "precision": "fp64", "comparison": self.cmp,
+                "l2": "inputs larger than L2 (four 64-column FP64 blocks of %.0f MB)" % (self.d * 64 * 8e-6)}
+
+    def kernel_bytes(self, launches_per_step):
+        """Per launch: the matrix (4-byte columns, pattern values) and rowptr, plus per
+        column 8-byte rows of V_k, V_{k-1} (and the Clenshaw addend) read and the
+        output written."""
+        out = {}
+        mat = 4 * self.nnz + 8 * (self.d + 1)
+        if launches_per_step.get("clenshaw_step"):
+            out["clenshaw_step"] = mat + 4 * 8 * self.d * self.S
+        n = launches_per_step.get("cheb_step")
+        if n:
+            out["cheb_step"] = mat + 3 * 8 * self.d * (self.S + self.G) * ((self.DEG + 1) // 2) / n
+        return out
+
+    def kernel_flops(self, launches_per_step):
+        out = {}
+        if launches_per_step.get("clenshaw_step"):
+            out["clenshaw_step"] = self.S * (2 * self.nnz + 8 * self.d)
+        n = launches_per_step.get("cheb_step")
+        if n:
+            out["cheb_step"] = step_flops(self.d, self.nnz, (self.S + self.G) * ((self.DEG + 1) // 2)) / n
+        return out
+
+    def setup(self, mlt, torch, rank):
+        self.mlt = mlt
+        self.scale = estrada_scale(mlt, self.csr)
+        self.M = mlt.Matrix(self.csr, scale=self.scale)
+        self.c = mlt.mlt_cheb_coeffs("exp", -10.0, 10.0, self.DEG)
+        self.base = probe_base(rank)
+
+    def step(self, mlt, stream, i):
+        return mlt.mlt_hutchpp_estimate(self.M.handle, -10.0, 10.0, self.c, 0,
+                                        self.base + (i % 1024) * (self.S + self.G), self.S, self.G, stream=stream)
+
+    def finish(self, ms):
+        mlt = self.mlt
+        off = self.base + 1088 * 128
+        r = mlt.mlt_hutchpp_estimate(self.M.handle, -10.0, 10.0, self.c, 0, off, self.S, self.G)
+        nplain = (self.units() + (self.DEG + 1) // 2 - 1) // ((self.DEG + 1) // 2)
+        mu = mlt.mlt_moments(self.M.handle, -10.0, 10.0, 0, off + self.S + self.G, [self.DEG] * nplain,
+                             precision="fp64")
+        q = mu @ self.c
+        se = float(np.std(q, ddof=1) / np.sqrt(nplain))
+        self.cmp = {"hutchpp": {"estimate": r.estimate, "stderr": r.std_error, "t_sketch": r.t_sketch,
+                                "rank": r.rank, "matvecs": r.matvecs},
+                    "hutchinson": {"estimate": float(np.mean(q)), "stderr": se, "probes": nplain,
+                                   "matvecs": nplain * ((self.DEG + 1) // 2)},
+                    "variance_ratio": (se / r.std_error) ** 2 if r.std_error > 0 else None}
+
+    def e2e_setup(self, torch):
+        self.h_rowptr = torch.from_numpy(self.csr.rowptr).pin_memory()
+        self.h_col = torch.from_numpy(self.csr.col).pin_memory()
+        self.h_samples = np.zeros(self.G)
+        return (self.h_rowptr.numel() * 8 + self.h_col.numel() * 4, 8 * self.G + 48)
+
+    def e2e_step(self, mlt, stream, i):
+        h = mlt.mlt_create_csr(self.d, self.d, self.nnz, self.h_rowptr, self.h_col, None,
+                               scale=self.scale, stream=stream)
+        try:
+            mlt.mlt_hutchpp_estimate(h, -10.0, 10.0, self.c, 0, self.base + (1024 + i) * (self.S + self.G),
+                                     self.S, self.G, samples=self.h_samples, stream=stream)
+        finally:
+            mlt.mlt_destroy(h)
+
+    def cpu_sample(self, oracle, nprobes, offset):
+        """The oracle's Hutch++ at degree 2 with s = g = nprobes / 16 (direct
+        recurrences: n operator applications per vector and per moment run)."""
+        if self.scale is None:
+            self.scale = 10.0 / gershgorin_upper(self.csr)
+        n = 2
+        c = oracle.cheb_coeffs("exp", -10.0, 10.0, n)
+        s = g = max(1, nprobes // 16)
+        oracle.hutchpp(self.csr, -10.0, 10.0, c, 0, offset, s, g, scale=self.scale)
+        return s * n + (s + g) * n
+
 
 def gershgorin_upper(c):
     """max_i (a_ii + sum_{j != i} |a_ij|): an upper bound on the spectrum of a
@@ -1116,7 +1229,8 @@ def base_e2e(timed_base):
 
 
 WORKLOADS = {c.name: c for c in (Triangles, LogDet64, EstradaRmat22, Diffusion64Batched, NuclearGram,
-                                            NuclearExplicit, Stencil3D, EstradaLearned, LevelStudy)}
+                                            NuclearExplicit, Stencil3D, EstradaLearned, LevelStudy,
+                                            EstradaHutchpp)}
 
 
 # ---------------------------------------------------------------------------
