@@ -445,7 +445,8 @@ class EstradaHutchpp:
     S, G, DEG = 64, 64, 128
     PROBE_SPAN = 1088 * 128 + 128 + 256   # timed, e2e, then the comparison's two runs
 
-    def __init__(self):
+    def __init__(self, precision="fp32"):
+        self.precision = precision   # of the sketch p(At) S; everything else is FP64
         from paper_2103_10516_gb300 import synth
         self.csr = synth.rmat_adjacency(22, 16, seed=1)
         self.d = self.csr.nrows
@@ -460,7 +461,7 @@ class EstradaHutchpp:
         return {"workload": self.name, "graph": "R-MAT scale 22, edge factor 16, seed 1",
                 "d": self.d, "nnz": self.nnz, "f": "exp", "interval": [-10.0, 10.0], "degree": self.DEG,
                 "scale": self.scale, "sketch_probes": self.S, "remainder_probes": self.G,
-                "precision": "fp64", "comparison": self.cmp,
+                "precision": "sketch %s, all else fp64" % self.precision, "comparison": self.cmp,
                 "l2": "inputs larger than L2 (four 64-column FP64 blocks of %.0f MB)" % (self.d * 64 * 8e-6)}
 
     def kernel_bytes(self, launches_per_step):
@@ -494,12 +495,14 @@ class EstradaHutchpp:
 
     def step(self, mlt, stream, i):
         return mlt.mlt_hutchpp_estimate(self.M.handle, -10.0, 10.0, self.c, 0,
-                                        self.base + (i % 1024) * (self.S + self.G), self.S, self.G, stream=stream)
+                                        self.base + (i % 1024) * (self.S + self.G), self.S, self.G,
+                                        precision=self.precision, stream=stream)
 
     def finish(self, ms):
         mlt = self.mlt
         off = self.base + 1088 * 128
-        r = mlt.mlt_hutchpp_estimate(self.M.handle, -10.0, 10.0, self.c, 0, off, self.S, self.G)
+        r = mlt.mlt_hutchpp_estimate(self.M.handle, -10.0, 10.0, self.c, 0, off, self.S, self.G,
+                                     precision=self.precision)
         nplain = (self.units() + (self.DEG + 1) // 2 - 1) // ((self.DEG + 1) // 2)
         mu = mlt.mlt_moments(self.M.handle, -10.0, 10.0, 0, off + self.S + self.G, [self.DEG] * nplain,
                              precision="fp64")
@@ -522,7 +525,8 @@ class EstradaHutchpp:
                                scale=self.scale, stream=stream)
         try:
             mlt.mlt_hutchpp_estimate(h, -10.0, 10.0, self.c, 0, self.base + (1024 + i) * (self.S + self.G),
-                                     self.S, self.G, samples=self.h_samples, stream=stream)
+                                     self.S, self.G, precision=self.precision, samples=self.h_samples,
+                                     stream=stream)
         finally:
             mlt.mlt_destroy(h)
 
@@ -1411,8 +1415,11 @@ def make_workload(args):
             raise SystemExit("--scale applies to the estrada_learned workload only")
         kw["scale"] = args.scale
     if args.precision is not None:
-        if cls not in (NuclearGram, NuclearExplicit, Stencil3D, EstradaLearned):
-            raise SystemExit("--precision applies to nuclear_gram, stencil3d and estrada_learned only")
+        if cls not in (NuclearGram, NuclearExplicit, Stencil3D, EstradaLearned, EstradaHutchpp):
+            raise SystemExit("--precision applies to nuclear_gram, stencil3d, estrada_learned and "
+                             "estrada_hutchpp only")
+        if cls is EstradaHutchpp and args.precision == "mixed":
+            raise SystemExit("estrada_hutchpp takes fp32 or fp64 (the sketch's precision)")
         if cls is EstradaLearned and args.precision == "mixed":
             raise SystemExit("estrada_learned takes fp32 or fp64")
         kw["precision"] = args.precision

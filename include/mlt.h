@@ -322,10 +322,15 @@ int mlt_poly_apply(mlt_matrix* m, double a, double b, const double* c, int n,
  *             sqrt(var(q) / g) (divisor g - 1; NaN when g < 2).
  * Unbiased for tr p(At) whatever Q is, since Q does not depend on G; exact
  * when Q spans the whole space.  Cost: s*n + (s + g)*ceil(n/2) operator
- * applications (matvecs), FP64 throughout.
+ * applications (matvecs).
+ * precision: MLT_PREC_FP64 (all FP64), or MLT_PREC_FP32 to evaluate the sketch
+ * p(At) S in FP32 (the handle's FP32 values); Q, its trace, the deflation and
+ * the remainder stay FP64.  Rounding in the sketch only moves span(Q), which
+ * changes the variance but not the expectation.
  * samples: g doubles (host) or NULL.  0 <= s <= 128, 0 <= g <= 1024, s + g >= 1.
  * Errors: MLT_EINVAL (null m, c or out; n outside [1, MLT_MAX_DEGREE]; a >= b;
- * s, g out of range; probe ids beyond 2^32), MLT_ENOMEM, MLT_ECUDA.
+ * s, g out of range; probe ids beyond 2^32; other precisions), MLT_ENOMEM,
+ * MLT_ECUDA.
  */
 typedef struct {
     double estimate;
@@ -337,7 +342,7 @@ typedef struct {
 } mlt_hutchpp_result;
 
 int mlt_hutchpp_estimate(mlt_matrix* m, double a, double b, const double* c, int n,
-                         uint64_t seed, int64_t probe_offset, int s, int g,
+                         uint64_t seed, int64_t probe_offset, int s, int g, int precision,
                          double* samples, mlt_hutchpp_result* out, void* stream);
 
 /*

@@ -181,7 +181,7 @@ __device__ __forceinline__ void row_product(const StepArgs<T>& a, const Lane<T, 
 }
 
 // V_{k+1}[r] from acc = (A V_k)[r], and the fused dot products.
-template <typename T>
+template <typename T, bool CL>
 __device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0, const T (&acc)[Lanes<T>::N],
                                          DotAcc<T> (&s_self)[Lanes<T>::N], DotAcc<T> (&s_cross)[Lanes<T>::N])
 {
@@ -196,7 +196,7 @@ __device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0
         return;
     }
     const P xc = *reinterpret_cast<const P*>(a.vcur + off);
-    if (std::is_same<T, double>::value && a.mode == 3) {   // Clenshaw steps run in FP64 only
+    if constexpr (CL) {   // Clenshaw step (mode 3): compiled into its own kernels only
         const P xp = *reinterpret_cast<const P*>(a.vprev_out + off);
         const P xa = *reinterpret_cast<const P*>(a.addv + off);
 #pragma unroll
@@ -265,7 +265,7 @@ __device__ __forceinline__ void cta_partials(const StepArgs<T>& a, const Lane<T,
     }
 }
 
-template <typename T, int G>
+template <typename T, int G, bool CL>
 __global__ void __launch_bounds__(kThreads, kStepCtasPerSm) cheb_step_kernel(StepArgs<T> a)
 {
     constexpr int N = Lanes<T>::N;
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kThreads, kStepCtasPerSm) cheb_step_kernel(Ste
                     const int64_t end = __ldg(a.rowptr + r + 1);
                     if (end - beg > a.Ul) continue;          // long row: done by segments
                     row_product<T, G>(a, L, beg, end, acc);
-                    if (L.vok) epilogue<T>(a, r, L.c0, acc, s_self, s_cross);
+                    if (L.vok) epilogue<T, CL>(a, r, L.c0, acc, s_self, s_cross);
                 }
             } else {
                 const int64_t sidx = it - a.nch;
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kThreads, kStepCtasPerSm) cheb_step_kernel(Ste
 }
 
 // Long rows: add the segment products in segment order, then the recurrence.
-template <typename T, int G>
+template <typename T, int G, bool CL>
 __global__ void __launch_bounds__(kThreads) cheb_long_kernel(StepArgs<T> a)
 {
     constexpr int N = Lanes<T>::N;
@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(kThreads) cheb_long_kernel(StepArgs<T> a)
 #pragma unroll
                 for (int q = 0; q < N; ++q) acc[q] += p.v[q];
             }
-            epilogue<T>(a, a.long_rows[i], L.c0, acc, s_self, s_cross);
+            epilogue<T, CL>(a, a.long_rows[i], L.c0, acc, s_self, s_cross);
         }
     }
     if (a.mode >= 2) return;
@@ -427,7 +427,8 @@ int resident_ctas()
 {
     static const int occ = [] {
         int o = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, cheb_step_kernel<T, G>, kThreads, 0) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, cheb_step_kernel<T, G, false>, kThreads, 0) !=
+            cudaSuccess) {
             cudaGetLastError();
             o = 0;
         }
@@ -447,7 +448,8 @@ int launch_step_g(StepArgs<T> a, int max_main, int max_long, int num_sms, int* n
     if ((long long)nb * gpb < a.nchunks) nb = (a.nchunks + gpb - 1) / gpb;
     {
         ProfScope ps(a.mode == 2 ? "gram_spmm" : (a.mode == 3 ? "clenshaw_step" : "cheb_step"), s);
-        cheb_step_kernel<T, G><<<nb, kThreads, 0, s>>>(a);
+        if (a.mode == 3) cheb_step_kernel<T, G, true><<<nb, kThreads, 0, s>>>(a);
+        else cheb_step_kernel<T, G, false><<<nb, kThreads, 0, s>>>(a);
     }
     MLT_CUDA_TRY(cudaGetLastError());
     int nl = 0;
@@ -458,7 +460,8 @@ int launch_step_g(StepArgs<T> a, int max_main, int max_long, int num_sms, int* n
         StepArgs<T> b = a;
         if (b.partials) b.partials += (size_t)nb * 2 * a.ldv;
         ProfScope ps(a.mode == 2 ? "gram_spmm_long" : (a.mode == 3 ? "clenshaw_step_long" : "cheb_step_long"), s);
-        cheb_long_kernel<T, G><<<nl, kThreads, 0, s>>>(b);
+        if (a.mode == 3) cheb_long_kernel<T, G, true><<<nl, kThreads, 0, s>>>(b);
+        else cheb_long_kernel<T, G, false><<<nl, kThreads, 0, s>>>(b);
     }
     MLT_CUDA_TRY(cudaGetLastError());
     *nblocks_out = nb + nl;
@@ -665,10 +668,11 @@ int run_group(mlt_matrix* M, const MomentPlan& plan, int ks, double a, double b,
 }
 
 // out[i] = coef * x[i] over n elements (x null: zeros).
-__global__ void scaled_copy_kernel(double* __restrict__ out, const double* __restrict__ x, double coef, int64_t n)
+template <typename T>
+__global__ void scaled_copy_kernel(T* __restrict__ out, const T* __restrict__ x, T coef, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = x ? coef * x[i] : 0.0;
+        out[i] = x ? coef * x[i] : T(0);
 }
 
 // The context of FP64 steps over an explicit block of `cols` vectors with row
@@ -701,65 +705,82 @@ int block_ctx(mlt_matrix* M, int ldv, int cols, int K, double a, double b, Group
 
 }  // namespace
 
-// Y = p(At) X by Clenshaw's recurrence for p = sum_k c_k T_k: b_{n+1} = 0,
+// Y = p(At) X by Clenshaw's recurrence for p = sum_k c_k T_k (in FP64, or in
+// FP32 with the handle's FP32 values): b_{n+1} = 0,
 // b_n = c_n X, b_k = 2 At b_{k+1} - b_{k+2} + c_k X (k = n-1 .. 1), and
 // p(At) X = At b_1 - b_2 + c_0 X: n operator applications.  b_j lives in
 // P[(n + 1 - j) & 1], so each step overwrites b_{k+2} in place.
-int poly_apply_block(mlt_matrix* M, double a, double b, const double* c, int n, const double* X, double* Y, int ldv,
-                     int ncols, double* P0, double* P1, cudaStream_t s)
+template <typename T>
+int poly_apply_block_t(mlt_matrix* M, double a, double b, const double* c, int n, const T* X, T* Y, int ldv,
+                       int ncols, T* P0, T* P1, cudaStream_t s)
 {
     GroupCtx g;
     int rc;
     if ((rc = block_ctx(M, ldv, ncols, 1, a, b, g, s))) return rc;
+    if (std::is_same<T, float>::value && (rc = ensure_fp32_values(M, s))) return rc;
+    const T* valA = std::is_same<T, double>::value ? (const T*)M->A.val64 : (const T*)M->A.val32;
+    const T* valAT = std::is_same<T, double>::value ? (const T*)M->AT.val64 : (const T*)M->AT.val32;
     const int64_t total = g.d * (int64_t)ldv;
     const int nbk = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 16LL * M->num_sms));
-    double* P[2] = {P0, P1};
+    T* P[2] = {P0, P1};
     {
         ProfScope ps("clenshaw_init", s);
-        scaled_copy_kernel<<<nbk, 256, 0, s>>>(P[0], nullptr, 0.0, total);
-        scaled_copy_kernel<<<nbk, 256, 0, s>>>(P[1], X, c[n], total);
+        scaled_copy_kernel<T><<<nbk, 256, 0, s>>>(P[0], nullptr, T(0), total);
+        scaled_copy_kernel<T><<<nbk, 256, 0, s>>>(P[1], X, (T)c[n], total);
     }
     MLT_CUDA_TRY(cudaGetLastError());
-    const int nvec = (ncols + Lanes<double>::N - 1) / Lanes<double>::N;
+    const int nvec = (ncols + Lanes<T>::N - 1) / Lanes<T>::N;
     const int G = pow2_at_least(std::min(nvec, 32));
     const DevCSR& A = M->A;
     const DevCSR& AT = M->AT;
     for (int k = n - 1; k >= 0; --k) {
-        double* cur = P[(n - k) & 1];          // b_{k+1}
-        double* out = P[(n + 1 - k) & 1];      // in: b_{k+2}; out: b_k (or the result at k = 0)
-        StepArgs<double> sa{};
+        T* cur = P[(n - k) & 1];               // b_{k+1}
+        T* out = P[(n + 1 - k) & 1];           // in: b_{k+2}; out: b_k (or the result at k = 0)
+        StepArgs<T> sa{};
         sa.ldv = ldv;
         sa.nvec = nvec;
         sa.nchunks = (nvec + G - 1) / G;
-        sa.alpha = g.alpha;
-        sa.beta = g.beta;
+        sa.alpha = (T)g.alpha;
+        sa.beta = (T)g.beta;
         sa.B = ncols;
         int nb = 0;
         if (g.gram) {
-            StepArgs<double> pa = sa;
-            pa.rowptr = A.rowptr; pa.col = A.col; pa.val = A.val64; pa.nrows = A.nrows;
-            pa.vgather = cur; pa.vcur = nullptr; pa.vprev_out = M->ws_w.as<double>(); pa.mode = 2;
-            set_split(pa, M->plan_A, M->ws_seg.as<double>());
-            if ((rc = launch_step<double>(G, pa, g.max_main, g.max_long, M->num_sms, &nb, s))) return rc;
-            sa.rowptr = AT.rowptr; sa.col = AT.col; sa.val = AT.val64; sa.nrows = AT.nrows;
-            sa.vgather = M->ws_w.as<double>();
-            set_split(sa, M->plan_AT, M->ws_seg.as<double>());
+            StepArgs<T> pa = sa;
+            pa.rowptr = A.rowptr; pa.col = A.col; pa.val = valA; pa.nrows = A.nrows;
+            pa.vgather = cur; pa.vcur = nullptr; pa.vprev_out = M->ws_w.as<T>(); pa.mode = 2;
+            set_split(pa, M->plan_A, M->ws_seg.as<T>());
+            if ((rc = launch_step<T>(G, pa, g.max_main, g.max_long, M->num_sms, &nb, s))) return rc;
+            sa.rowptr = AT.rowptr; sa.col = AT.col; sa.val = valAT; sa.nrows = AT.nrows;
+            sa.vgather = M->ws_w.as<T>();
+            set_split(sa, M->plan_AT, M->ws_seg.as<T>());
         } else {
-            sa.rowptr = A.rowptr; sa.col = A.col; sa.val = A.val64; sa.nrows = A.nrows;
+            sa.rowptr = A.rowptr; sa.col = A.col; sa.val = valA; sa.nrows = A.nrows;
             sa.vgather = cur;
-            set_split(sa, M->plan_A, M->ws_seg.as<double>());
+            set_split(sa, M->plan_A, M->ws_seg.as<T>());
         }
         sa.vcur = cur;
         sa.vprev_out = out;
         sa.mode = 3;
         sa.addv = X;
-        sa.coef = c[k];
-        sa.m1 = k > 0 ? 2.0 : 1.0;
-        if ((rc = launch_step<double>(G, sa, g.max_main, g.max_long, M->num_sms, &nb, s))) return rc;
+        sa.coef = (T)c[k];
+        sa.m1 = k > 0 ? T(2) : T(1);
+        if ((rc = launch_step<T>(G, sa, g.max_main, g.max_long, M->num_sms, &nb, s))) return rc;
     }
-    double* res = P[(n + 1) & 1];
-    if (res != Y) MLT_CUDA_TRY(cudaMemcpyAsync(Y, res, (size_t)total * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    T* res = P[(n + 1) & 1];
+    if (res != Y) MLT_CUDA_TRY(cudaMemcpyAsync(Y, res, (size_t)total * sizeof(T), cudaMemcpyDeviceToDevice, s));
     return MLT_OK;
+}
+
+int poly_apply_block(mlt_matrix* M, double a, double b, const double* c, int n, const double* X, double* Y, int ldv,
+                     int ncols, double* P0, double* P1, cudaStream_t s)
+{
+    return poly_apply_block_t<double>(M, a, b, c, n, X, Y, ldv, ncols, P0, P1, s);
+}
+
+int poly_apply_block_f32(mlt_matrix* M, double a, double b, const double* c, int n, const float* X, float* Y,
+                         int ldv, int ncols, float* P0, float* P1, cudaStream_t s)
+{
+    return poly_apply_block_t<float>(M, a, b, c, n, X, Y, ldv, ncols, P0, P1, s);
 }
 
 // Doubling moments of an explicit FP64 block: V0 holds the start vectors (row

@@ -168,6 +168,8 @@ int ensure_fp32_values(mlt_matrix* M, cudaStream_t s);
 // the doubling moments of a start block V0 (V1 scratch; dots stay on the device).
 int poly_apply_block(mlt_matrix* M, double a, double b, const double* c, int n, const double* X, double* Y, int ldv,
                      int ncols, double* P0, double* P1, cudaStream_t s);
+int poly_apply_block_f32(mlt_matrix* M, double a, double b, const double* c, int n, const float* X, float* Y,
+                         int ldv, int ncols, float* P0, float* P1, cudaStream_t s);
 int moments_block(mlt_matrix* M, double a, double b, double* V0, double* V1, int ldv, int cols, int K,
                   const double** dots_dev, cudaStream_t s);
 int ensure_spmm_plan(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, cudaStream_t s);

@@ -105,7 +105,7 @@ def lib():
                                      ctypes.POINTER(dbl), vp]
     L.mlt_low_traces.argtypes = [vp, dbl, dbl, vp, ctypes.POINTER(ci), vp]
     L.mlt_poly_apply.argtypes = [vp, dbl, dbl, vp, ci, vp, i64, vp, i64, ci, cu, vp]
-    L.mlt_hutchpp_estimate.argtypes = [vp, dbl, dbl, vp, ci, u64, i64, ci, ci, vp,
+    L.mlt_hutchpp_estimate.argtypes = [vp, dbl, dbl, vp, ci, u64, i64, ci, ci, ci, vp,
                                        ctypes.POINTER(mlt_hutchpp_result), vp]
     L.mlt_profile_start.argtypes = []
     L.mlt_profile_stop.argtypes = [ctypes.POINTER(mlt_kernel_stat), ci, ctypes.POINTER(ci)]
@@ -205,13 +205,14 @@ def mlt_poly_apply(handle, a, b, c, X, Y=None, stream=None):
     return Y
 
 
-def mlt_hutchpp_estimate(handle, a, b, c, seed, probe_offset, s, g, samples=None, stream=None):
-    """Hutch++ on tr p(At); returns the mlt_hutchpp_result (and fills `samples`,
-    a float64 array of g entries, when given)."""
+def mlt_hutchpp_estimate(handle, a, b, c, seed, probe_offset, s, g, precision="fp64", samples=None, stream=None):
+    """Hutch++ on tr p(At) (precision "fp32": the sketch in FP32); returns the
+    mlt_hutchpp_result (and fills `samples`, a float64 array of g entries)."""
     c = np.ascontiguousarray(c, dtype=np.float64)
     r = mlt_hutchpp_result()
+    prec = MLT_PREC[precision] if isinstance(precision, str) else precision
     _check(lib().mlt_hutchpp_estimate(handle, float(a), float(b), _ptr(c), len(c) - 1, seed, probe_offset, s, g,
-                                      _ptr(samples), ctypes.byref(r), _stream(stream)))
+                                      prec, _ptr(samples), ctypes.byref(r), _stream(stream)))
     return r
 
 

@@ -152,3 +152,30 @@ def test_hutchpp_rejects_bad_arguments(L, O):
                 L.mlt_hutchpp_estimate(M.handle, *args)
         with pytest.raises(L.MLTError):
             L.mlt_poly_apply(M.handle, 0.1, 8.1, c[:1], np.ones((m.nrows, 2)))
+
+
+def test_hutchpp_fp32_sketch(L, O):
+    # the sketch in FP32 only moves span(Q): a full sketch is still exact, and on
+    # a well-conditioned problem every part stays within FP32 rounding of the
+    # all-FP64 oracle (sketch error ~1e-7 relative moves span(Q) by as much)
+    d = 40
+    g = synth.random_graph(d, 0.2, seed=12)
+    lam = np.linalg.eigvalsh(g.to_dense())
+    a, b = lam[0] - 0.3, lam[-1] + 0.3
+    c = O.cheb_coeffs("exp", a, b, 30)
+    exact = math.fsum(O.cheb_eval(c, (2 * lam - (a + b)) / (b - a)).tolist())
+    with L.Matrix(g) as M:
+        r = L.mlt_hutchpp_estimate(M.handle, a, b, c, 1, 0, d, 3, precision="fp32")
+    assert r.rank == d and abs(r.estimate - exact) <= 1e-9 * abs(exact)
+    m = synth.grid_laplacian_2d(16, shift=0.1)
+    c = O.cheb_coeffs("log", 0.1, 8.1, 32)
+    ref = O.hutchpp(m, 0.1, 8.1, c, 5, 100, 8, 16)
+    samples = np.zeros(16)
+    with L.Matrix(m) as M:
+        r = L.mlt_hutchpp_estimate(M.handle, 0.1, 8.1, c, 5, 100, 8, 16, precision="fp32", samples=samples)
+        with pytest.raises(L.MLTError):
+            L.mlt_hutchpp_estimate(M.handle, 0.1, 8.1, c, 5, 100, 8, 16, precision=2)
+    sc = np.sum(np.abs(c))
+    assert r.rank == 8
+    assert abs(r.t_sketch - ref["t_sketch"]) <= 1e-5 * sc * 8
+    assert np.max(np.abs(samples - ref["samples"])) <= 1e-5 * sc * m.nrows
