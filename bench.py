@@ -11,7 +11,7 @@ One step is one pass of the whole hot path over one batch of synthetic input:
 
   rmat20_triangles (default): exact int64 triangle moments of an R-MAT graph
       (scale 20, edge factor 16, a=0.57, b=c=0.19, seed 0; symmetric, no
-      self-loops or duplicates) for 1024 Rademacher probes in blocks of 128,
+      self-loops or duplicates) for 1024 Rademacher probes in blocks of 256,
       plus the control-variate estimate.  Units: probe-matvecs (2 per probe).
   logdet64: multilevel log-det of the 64x64 Dirichlet Laplacian + 0.1 I,
       levels {8, 32, 128} with {256, 64, 16} probes, FP64.  Units: probe-matvecs
@@ -221,7 +221,7 @@ class Triangles:
     unit = "probe-matvecs/s"
     dtype = "int64"
     NPROBES = 1024
-    BLOCK = 128
+    BLOCK = 256
     PROBE_SPAN = (4096 + 64) * 1024     # timed steps cycle through 4096 blocks; e2e steps follow
 
     def __init__(self):
@@ -241,31 +241,32 @@ class Triangles:
                       % (4e-6 * self.nnz, 8e-6 * self.d, 1e-6 * self._ybytes())}
 
     def _ybytes(self):
-        """Bytes of y for one block: 128 per int8 row (degree <= 127), 256 per
-        int16 row (<= 32767), 512 per int32 row; isolated rows have none."""
+        """Bytes of y for one block: 256 per int8 row (degree <= 127), 512 per
+        int16 row (<= 32767), 1024 per int32 row; isolated rows have none."""
         deg = np.diff(self.csr.rowptr)
-        return int(128 * np.sum((deg > 0) & (deg <= 127)) + 256 * np.sum((deg > 127) & (deg <= 32767))
-                   + 512 * np.sum(deg > 32767))
+        return int(256 * np.sum((deg > 0) & (deg <= 127)) + 512 * np.sum((deg > 127) & (deg <= 32767))
+                   + 1024 * np.sum(deg > 32767))
 
     def kernel_bytes(self, launches_per_step):
-        """Algorithmic bytes per launch (one 128-probe block) of each kernel:
+        """Algorithmic bytes per launch (one 256-probe block) of each kernel:
         every array touched once, gathered rows assumed cached.  y of a row
-        takes 128 B (degree <= 127, int8), 256 B (<= 32767, int16) or 512 B
-        (int32).  Pass 1 reads rowptr, col and the sign bits and writes y;
-        pass 2 reads the out-list pointers, columns (nnz/2), small-section
-        lengths and slots, and y of every row with an edge once."""
+        takes 256 B (degree <= 127, int8), 512 B (<= 32767, int16) or 1 KB
+        (int32); the sign bits 32 B.  Pass 1 reads rowptr, col and the sign
+        bits and writes y; pass 2 reads the out-list pointers, columns
+        (nnz/2), small-section lengths and slots, and y of every row with an
+        edge once."""
         d, nnz = self.d, self.nnz
         ybytes = self._ybytes()
         return {
-            "tri_zbits": 16 * d,
-            "tri_pass1": 8 * (d + 1) + 4 * nnz + 16 * d + ybytes,
+            "tri_zbits": 32 * d,
+            "tri_pass1": 8 * (d + 1) + 4 * nnz + 32 * d + ybytes,
             "tri_pass2": 8 * (d + 1) + 4 * (nnz // 2) + 8 * d + ybytes,
         }
 
     # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
     # from an ncu capture of this workload, per kernel; to be re-taken
     # whenever the kernel changes
-    TRAFFIC = {"tri_pass1": 218.01e6, "tri_pass2": 182.08e6}
+    TRAFFIC = {}   # the 256-probe passes have not been captured yet
 
     # ours
     def setup(self, mlt, torch, rank):

@@ -351,12 +351,13 @@ int mlt_hutchpp_estimate(mlt_matrix* m, double a, double b, const double* c, int
  * probe_offset .. probe_offset+nprobes-1 it computes, exactly in int64,
  * x1 = z^T A z, x2 = z^T A^2 z, x3 = z^T A^3 z (two sparse products per probe
  * block, using the symmetry of the quadratic form), in blocks of `block`
- * probes (block must be 128).  With use_cv the estimate is
+ * probes (block must be 256; a last, partial block costs a full one).  With
+ * use_cv the estimate is
  * [mean x3 - a2 (mean x2 - nnz) - a1 mean x1] / 6 with a1, a2 the least-squares
  * slopes of x3 on (x1, x2) (Section 5.4; tr A = 0, tr A^2 = nnz); without it,
  * mean x3 / 6.  x (host or device int64[nprobes*3], may be NULL) receives the
  * per-probe moments.  Errors: MLT_EINVAL (not a square pattern matrix, a
- * self-loop, nprobes < 1, block != 128); MLT_ERANGE when the bound
+ * self-loop, nprobes < 1, block != 256); MLT_ERANGE when the bound
  * sum_(i,j) deg_i deg_j on |x3| reaches 2^62.
  */
 int mlt_triangle_trace(mlt_matrix* m, uint64_t seed, int64_t probe_offset,

@@ -1202,7 +1202,7 @@ int mlt_triangle_trace(mlt_matrix* m, uint64_t seed, int64_t probe_offset, int64
         if (m->val_type != MLT_PATTERN || (m->flags & MLT_GRAM) || m->A.nrows != m->A.ncols)
             return fail(MLT_EINVAL, "mlt_triangle_trace: needs a square 0/1 pattern matrix");
         if (nprobes < 1) return fail(MLT_EINVAL, "mlt_triangle_trace: need at least one probe");
-        if (block != 128) return fail(MLT_EINVAL, "mlt_triangle_trace: block must be 128");
+        if (block != 256) return fail(MLT_EINVAL, "mlt_triangle_trace: block must be 256");
         if (probe_offset < 0 || probe_offset + nprobes > (1LL << 32))
             return fail(MLT_EINVAL, "mlt_triangle_trace: probe ids must lie in [0, 2^32)");
         cudaStream_t s = (cudaStream_t)stream;

@@ -1,6 +1,6 @@
 // Exact integer triangle moments (Section 2.1 Example; Section 5.4).
 //
-// For a block of 128 Rademacher probes and a symmetric 0/1 adjacency matrix A
+// For a block of 256 Rademacher probes and a symmetric 0/1 adjacency matrix A
 // with no self-loops, per probe:
 //   y  = A z                      (pass 1; |y_i| <= deg_i)
 //   x1 = z . y = z^T A z,  x2 = y . y = z^T A^2 z
@@ -13,18 +13,27 @@
 // in L2.
 //
 // Row classes by degree (|y_i| <= deg_i makes each storage exact):
-//   small  deg <= 127    : y in y8, 128 x int8 per row (one 128-byte line)
-//   mid    deg <= 32767  : y in y16, 128 x int16 per row, slot bslot[i]
-//   huge   deg >  32767  : y in y32, 128 x int32 per row, slot bslot[i]
+//   small  deg <= 127    : y in y8, 256 x int8 per row (two 128-byte lines)
+//   mid    deg <= 32767  : y in y16, 256 x int16 per row, slot bslot[i]
+//   huge   deg >  32767  : y in y32, 256 x int32 per row, slot bslot[i]
 // Each out-list is stored as [small targets (column index) | mid targets (y16
 // slot)], so the inner loops need no escape test.  Edges into huge rows (a
 // handful of vertices) go to a separate pair list with its own kernel.
 //
+// Lanes and probes: the block is two halves of 128 probes, and lane l owns
+// probes 4l..4l+3 of each (block probes 4l + q and 128 + 4l + q), so every
+// gathered row serves 256 probes while each lane keeps the 4-probe byte
+// arithmetic per half.
 // Layout (device):
-//   zb      : 4 x uint32 per row; bit t + 8q of word w = 1 when z_i of probe
-//             32w + 4t + q is -1, so lane l (probes 4l..4l+3) reads its four
-//             signs one byte apart from word l/8 shifted right by l%8
-//   y32     : also the pass-1 accumulator of rows longer than a chunk
+//   zb      : 8 x uint32 (one 32-byte sector) per row; word 2w + h holds the
+//             signs of probes 128h + 32w .. +31, bit t + 8q set when z_i of
+//             probe 128h + 32w + 4t + q is -1.  Lane l loads words 2(l/8) and
+//             2(l/8) + 1 as one uint2 and shifts both right by l%8: its four
+//             signs of each half, one byte apart
+//   y8, y16 : per row, lane l's uint2 (int8) or uint4 (int16) holds its four
+//             values of half 0, then of half 1
+//   y32     : 256 x int32 per slot in block-probe order; also the pass-1
+//             accumulator of rows longer than a chunk
 //   out_ptr : row pointer of the oriented out-lists, out_col their entries,
 //             nsmall the length of each list's small section
 //   pairs   : (class of i, row or slot of i, y32 slot of the huge target)
@@ -49,7 +58,9 @@ namespace mlt {
 namespace {
 
 constexpr int kTriThreads = 256;
-constexpr int kProbes = 128;
+constexpr int kProbes = 256;       // probes per block: two halves of 128
+constexpr int kHalf = 128;
+constexpr int kZWords = kProbes / 32;   // sign words per row
 constexpr int kSmallDeg = 127;        // y of rows up to this degree fits int8
 constexpr int kMidDeg = 32767;        // ... int16; rows above it keep int32
 constexpr int64_t kRowCost = 4;       // units charged per row on top of its entries
@@ -59,7 +70,7 @@ constexpr int kGather = 8;            // gathers each lane keeps in flight (divi
 constexpr unsigned kFull = 0xFFFFFFFFu;
 static_assert(32 % kGather == 0, "a gather batch never crosses a 32-entry column block");
 constexpr int kScanBlock = 1024;      // elements per CTA of the prefix scan
-constexpr int kPass2CtasPerSm = 6;    // pass 2 compiled for six resident CTAs (40 registers)
+constexpr int kPass2CtasPerSm = 4;    // pass 2 compiled for four resident CTAs (64 registers)
 static_assert(kLongRow <= kMidDeg && kChunk <= kLongRow, "rows handled whole by pass 1 must be small or mid");
 
 enum RowClass { kClassSmall = 0, kClassMid = 1, kClassHuge = 2 };
@@ -84,20 +95,21 @@ __device__ __forceinline__ uint32_t interleave_bytes(uint32_t x)
     return out;
 }
 
-// zb[i * 4 + w]: the signs of probes id0 + 32 w .. + 31 at row i in the
-// byte-interleaved order above (0 for probes past nb).  The 32 bits come from
-// one or two 64-probe hash words.
+// zb[i * 8 + 2w + h]: the signs of block probes 128h + 32w .. + 31 at row i
+// in the byte-interleaved order above (0 for probes past nb).  The 32 bits
+// come from one or two 64-probe hash words.
 __global__ void zbits_kernel(int64_t d, uint64_t seedmix, int64_t id0, int nb, uint32_t* __restrict__ zb)
 {
-    const int64_t total = d * 4;
+    const int64_t total = d * kZWords;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t i = (uint64_t)(e >> 2);
-        const int w = (int)(e & 3);
-        const int valid = min(32, max(0, nb - 32 * w));
+        const uint64_t i = (uint64_t)(e >> 3);
+        const int w8 = (int)(e & 7);
+        const int pb = kHalf * (w8 & 1) + 32 * (w8 >> 1);   // first block probe of the word
+        const int valid = min(32, max(0, nb - pb));
         uint32_t bits = 0;
         if (valid > 0) {
-            const uint64_t p0 = (uint64_t)(id0 + 32 * w);
+            const uint64_t p0 = (uint64_t)(id0 + pb);
             const int o = (int)(p0 & 63);
             uint64_t v = probe_word(seedmix, p0 >> 6, i) >> o;
             if (o > 32) v |= probe_word(seedmix, (p0 >> 6) + 1, i) << (64 - o);
@@ -566,16 +578,19 @@ __device__ __forceinline__ void gather_batch(int cj, int t0, Load load, Use use)
     for (int u = 0; u < D; ++u) use(w[u]);
 }
 
-// The n (<= 32, warp-uniform) entries of a block: batches of kGather while
-// that many remain, then one of 4, then one at a time, so a short out-list
+// The n (<= 32, warp-uniform) entries of a block: batches of D while that
+// many remain, then one of 4 (D = 8), then one at a time, so a short out-list
 // wastes no gather slot and no slot needs a bounds test (pass 2; pass 1's
-// short rows keep predicated batches, which measured faster there).
-template <typename Load, typename Use>
+// short rows keep predicated batches, which measured faster there).  D
+// bounds the registers the batch holds: 8 x uint2 or 4 x uint4 keep the same
+// bytes in flight per lane.
+template <int D, typename Load, typename Use>
 __device__ __forceinline__ void gather_block(int cj, int n, Load load, Use use)
 {
+    static_assert(D == 8 || D == 4, "batches of 8 then 4, or of 4");
     int t0 = 0;
-    for (; t0 + kGather <= n; t0 += kGather) gather_batch<kGather>(cj, t0, load, use);
-    if (kGather > 4 && t0 + 4 <= n) {
+    for (; t0 + D <= n; t0 += D) gather_batch<D>(cj, t0, load, use);
+    if (D > 4 && t0 + 4 <= n) {
         gather_batch<4>(cj, t0, load, use);
         t0 += 4;
     }
@@ -584,14 +599,17 @@ __device__ __forceinline__ void gather_block(int cj, int n, Load load, Use use)
 
 // ---- pass 1 ------------------------------------------------------------------
 
-// The sign bits of probes 4*lane + q at row j, in bit 8q (q = 0..3).
-__device__ __forceinline__ uint32_t sign_bytes(const uint32_t* __restrict__ zb, int64_t j, int lane)
+// This lane's sign bits of row j: .x for half 0 (probes 4*lane + q), .y for
+// half 1 (128 + 4*lane + q), probe q in bit 8q.
+__device__ __forceinline__ uint2 sign_pair(const uint2* __restrict__ zb2, int64_t j, int lane)
 {
-    return (__ldg(zb + (size_t)j * 4 + (lane >> 3)) >> (lane & 7)) & 0x01010101u;
+    const uint2 w = __ldg(zb2 + (size_t)j * 4 + (lane >> 3));
+    const int sh = lane & 7;
+    return make_uint2((w.x >> sh) & 0x01010101u, (w.y >> sh) & 0x01010101u);
 }
 
 // Byte q of `packed` counts sign bit q; folded into int counters before it can wrap.
-__device__ __forceinline__ void fold(uint32_t& packed, int cnt[4])
+__device__ __forceinline__ void fold(uint32_t& packed, int* cnt)
 {
     cnt[0] += packed & 0xFF;
     cnt[1] += (packed >> 8) & 0xFF;
@@ -600,51 +618,55 @@ __device__ __forceinline__ void fold(uint32_t& packed, int cnt[4])
     packed = 0;
 }
 
-// Negative-sign counts over entries [a, b) of one row, for this lane's 4
-// probes.  kGather gathers are in flight before the first is used; lanes
-// past the end load nothing and add zero.
+// Negative-sign counts over entries [a, b) of one row, for this lane's 8
+// probes (cnt[0..3] half 0, cnt[4..7] half 1).  kGather gathers are in flight
+// before the first is used; lanes past the end load nothing and add zero.
 __device__ __forceinline__ void count_negatives(const int32_t* __restrict__ col, int64_t a, int64_t b,
-                                                const uint32_t* __restrict__ zb, int lane, int cnt[4])
+                                                const uint2* __restrict__ zb2, int lane, int cnt[8])
 {
-    const uint32_t* zbl = zb + (lane >> 3);
+    const uint2* zbl = zb2 + (lane >> 3);
     const int sh = lane & 7;
-    uint32_t packed = 0;
+    uint32_t pa = 0, pb = 0;
     for (int64_t base = a; base < b; base += 32) {
         const int64_t k = base + lane;
         const int cj = k < b ? __ldg(col + k) : 0;
         const int n = (int)min((int64_t)32, b - base);
         for (int t0 = 0; t0 < n; t0 += kGather) {
-            uint32_t w[kGather];
+            uint2 w[kGather];
 #pragma unroll
             for (int u = 0; u < kGather; ++u) {
                 const int j = __shfl_sync(kFull, cj, t0 + u);
-                w[u] = t0 + u < n ? __ldg(zbl + (size_t)j * 4) : 0u;
+                w[u] = t0 + u < n ? __ldg(zbl + (size_t)j * 4) : make_uint2(0u, 0u);
             }
 #pragma unroll
-            for (int u = 0; u < kGather; ++u) packed += (w[u] >> sh) & 0x01010101u;
+            for (int u = 0; u < kGather; ++u) {
+                pa += (w[u].x >> sh) & 0x01010101u;
+                pb += (w[u].y >> sh) & 0x01010101u;
+            }
         }
-        fold(packed, cnt);
+        fold(pa, cnt);
+        fold(pb, cnt + 4);
     }
 }
 
 // The same counts, bit-sliced, for spans of at least kSliceMin entries (and
-// at most kLongRow).  Lane l takes entry l/4 of every batch of 8 entries and
-// sign word l%4 of it (32 probes), and counts each of the 32 bit positions in
-// P bit planes: bit t of c[p] is bit p of position t's count.  Blocks of 64
-// (P >= 4) and then 32 entries give each lane eight or four words at once
-// (that many gathers in flight), added with carry-save adders: for four
-// words, c0 + x0 + x1 = c0' + 2 t0 and c0' + x2 + x3 = c0'' + 2 t1, then
-// c1 + t0 + t1 = c1' + 2 f, and f ripples into planes 2 .. P-1 (15 + 2(P-2)
-// bitwise operations, where a ripple-carry increment takes 3P per word);
-// eight words add two such groups and c2 + f0 + f1 = c2' + 2 e.  The rest of
-// the span adds one word per batch of 8 by ripple.  The eight entry slots are
-// then summed lane against lane with a bit-sliced adder whose sums gain one
-// plane per level, and each lane reads its own four probes out of the planes
-// of word l/8.  P is the fewest planes that hold the words one lane sees,
-// ceil(n / 8) for a span of n entries (the planes always hold a lane's exact
-// count).
-constexpr int kSliceMin = 16;
-static_assert(kLongRow <= 1024, "eight planes hold a lane's count of at most 128 words");
+// at most kLongRow).  Lane l takes entry l/8 of every batch of 4 entries and
+// sign word l%8 of it (32 probes of one half), and counts each of the 32 bit
+// positions in P bit planes: bit t of c[p] is bit p of position t's count.
+// Blocks of 32 (P >= 4) and then 16 entries give each lane eight or four
+// words at once (that many gathers in flight), added with carry-save adders:
+// for four words, c0 + x0 + x1 = c0' + 2 t0 and c0' + x2 + x3 = c0'' + 2 t1,
+// then c1 + t0 + t1 = c1' + 2 f, and f ripples into planes 2 .. P-1 (15 +
+// 2(P-2) bitwise operations, where a ripple-carry increment takes 3P per
+// word); eight words add two such groups and c2 + f0 + f1 = c2' + 2 e.  The
+// rest of the span adds one word per batch of 4 by ripple.  The four entry
+// slots are then summed lane against lane with a bit-sliced adder whose sums
+// gain one plane per level, and each lane reads its own probes out of the
+// planes of words 2(l/8) (half 0) and 2(l/8) + 1 (half 1).  P is the fewest
+// planes that hold the words one lane sees, ceil(n / 4) for a span of n
+// entries (the planes always hold a lane's exact count).
+constexpr int kSliceMin = 16;   // long rows' parts below it use count_negatives
+static_assert(kLongRow <= 1024, "nine planes hold a lane's count of at most 256 words");
 
 // a + b + c = s + 2 carry, bitwise (a full adder per bit position); s replaces a.
 __device__ __forceinline__ void carry_save(uint32_t& a, uint32_t b, uint32_t c, uint32_t& carry)
@@ -654,25 +676,40 @@ __device__ __forceinline__ void carry_save(uint32_t& a, uint32_t b, uint32_t c, 
     a = u ^ c;
 }
 
+// This lane's four counts of the word held (after the adder) by lane src.
+template <int Q>
+__device__ __forceinline__ void read_counts(const uint32_t (&c)[Q], int src, int sh, int* cnt)
+{
+    uint32_t lo = 0u, hi = 0u;   // 16-bit lanes: probes q = 0, 2 and q = 1, 3
+#pragma unroll
+    for (int p = 0; p < Q; ++p) {
+        const uint32_t t = (__shfl_sync(kFull, c[p], src) >> sh) & 0x01010101u;
+        lo += (t & 0x00010001u) << p;
+        hi += ((t >> 8) & 0x00010001u) << p;
+    }
+    cnt[0] += (int)(lo & 0xFFFFu);
+    cnt[1] += (int)(hi & 0xFFFFu);
+    cnt[2] += (int)(lo >> 16);
+    cnt[3] += (int)(hi >> 16);
+}
+
 template <int P>
 __device__ __forceinline__ void count_negatives_sliced_p(const int32_t* __restrict__ col, int64_t a, int64_t b,
-                                                         const uint32_t* __restrict__ zb, int lane, int cnt[4])
+                                                         const uint32_t* __restrict__ zb, int lane, int cnt[8])
 {
-    constexpr int Q = P + 3;   // planes of the sum of eight slots
+    constexpr int Q = P + 2;   // planes of the sum of four slots
+    static_assert(P >= 3, "the carry-save blocks use planes 0, 1 and 2");
     uint32_t c[Q];
 #pragma unroll
     for (int p = 0; p < Q; ++p) c[p] = 0u;
-    static_assert(P >= 3, "the carry-save blocks use planes 0, 1 and 2");
-    const int slot = lane >> 2, w = lane & 3;
+    const int slot = lane >> 3, w8 = lane & 7;
     int64_t base = a;
     if constexpr (P >= 4) {
-        for (; base + 64 <= b; base += 64) {
-            const int cj0 = __ldg(col + base + lane), cj1 = __ldg(col + base + 32 + lane);
+        for (; base + 32 <= b; base += 32) {
+            const int cj = __ldg(col + base + lane);
             uint32_t x[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) x[u] = __ldg(zb + (size_t)__shfl_sync(kFull, cj0, 8 * u + slot) * 4 + w);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) x[4 + u] = __ldg(zb + (size_t)__shfl_sync(kFull, cj1, 8 * u + slot) * 4 + w);
+            for (int u = 0; u < 8; ++u) x[u] = __ldg(zb + (size_t)__shfl_sync(kFull, cj, 4 * u + slot) * 8 + w8);
             uint32_t t0, t1, t2, t3, f0, f1, e;
             carry_save(c[0], x[0], x[1], t0);
             carry_save(c[0], x[2], x[3], t1);
@@ -689,11 +726,11 @@ __device__ __forceinline__ void count_negatives_sliced_p(const int32_t* __restri
             }
         }
     }
-    for (; base + 32 <= b; base += 32) {
-        const int cj = __ldg(col + base + lane);
+    for (; base + 16 <= b; base += 16) {
+        const int cj = base + lane < b ? __ldg(col + base + lane) : 0;
         uint32_t x[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) x[u] = __ldg(zb + (size_t)__shfl_sync(kFull, cj, 8 * u + slot) * 4 + w);
+        for (int u = 0; u < 4; ++u) x[u] = __ldg(zb + (size_t)__shfl_sync(kFull, cj, 4 * u + slot) * 8 + w8);
         uint32_t t0, t1, f;
         carry_save(c[0], x[0], x[1], t0);
         carry_save(c[0], x[2], x[3], t1);
@@ -705,10 +742,10 @@ __device__ __forceinline__ void count_negatives_sliced_p(const int32_t* __restri
             f = t;
         }
     }
-    for (; base < b; base += 8) {
+    for (; base < b; base += 4) {
         const int64_t k = base + slot;
         uint32_t x = 0u;
-        if (k < b) x = __ldg(zb + (size_t)__ldg(col + k) * 4 + w);
+        if (k < b) x = __ldg(zb + (size_t)__ldg(col + k) * 8 + w8);
 #pragma unroll
         for (int p = 0; p < P; ++p) {
             const uint32_t t = c[p] & x;
@@ -717,8 +754,8 @@ __device__ __forceinline__ void count_negatives_sliced_p(const int32_t* __restri
         }
     }
 #pragma unroll
-    for (int lv = 0; lv < 3; ++lv) {
-        const int m = 4 << lv;
+    for (int lv = 0; lv < 2; ++lv) {
+        const int m = 8 << lv;
         uint32_t carry = 0u;
 #pragma unroll
         for (int p = 0; p < P + lv; ++p) {
@@ -729,57 +766,63 @@ __device__ __forceinline__ void count_negatives_sliced_p(const int32_t* __restri
         }
         c[P + lv] = carry;
     }
-    const int src = lane >> 3, sh = lane & 7;
-    uint32_t lo = 0u, hi = 0u;   // 16-bit lanes: probes q = 0, 2 and q = 1, 3
-#pragma unroll
-    for (int p = 0; p < Q; ++p) {
-        const uint32_t t = (__shfl_sync(kFull, c[p], src) >> sh) & 0x01010101u;
-        lo += (t & 0x00010001u) << p;
-        hi += ((t >> 8) & 0x00010001u) << p;
-    }
-    cnt[0] += (int)(lo & 0xFFFFu);
-    cnt[1] += (int)(hi & 0xFFFFu);
-    cnt[2] += (int)(lo >> 16);
-    cnt[3] += (int)(hi >> 16);
+    const int src = 2 * (lane >> 3), sh = lane & 7;
+    read_counts<Q>(c, src, sh, cnt);
+    read_counts<Q>(c, src + 1, sh, cnt + 4);
 }
 
 // A span of n = b - a entries, kSliceMin <= n <= kLongRow: a lane sees at
-// most ceil(n / 8) words, 7 / 15 / 31 / 63 / 128 needing 3 / 4 / 5 / 6 / 8
+// most ceil(n / 4) words, 7 / 15 / 31 / 63 / 127 / 255 / 256 needing 3 to 9
 // planes (a long row's part inside one chunk has at most kChunk = 256).
 __device__ __forceinline__ void count_negatives_sliced(const int32_t* __restrict__ col, int64_t a, int64_t b,
-                                                       const uint32_t* __restrict__ zb, int lane, int cnt[4])
+                                                       const uint32_t* __restrict__ zb, int lane, int cnt[8])
 {
     const int64_t n = b - a;
-    if (n <= 56) count_negatives_sliced_p<3>(col, a, b, zb, lane, cnt);
-    else if (n <= 120) count_negatives_sliced_p<4>(col, a, b, zb, lane, cnt);
-    else if (n <= 248) count_negatives_sliced_p<5>(col, a, b, zb, lane, cnt);
-    else if (n <= 504) count_negatives_sliced_p<6>(col, a, b, zb, lane, cnt);
-    else count_negatives_sliced_p<8>(col, a, b, zb, lane, cnt);
+    if (n <= 28) count_negatives_sliced_p<3>(col, a, b, zb, lane, cnt);
+    else if (n <= 60) count_negatives_sliced_p<4>(col, a, b, zb, lane, cnt);
+    else if (n <= 124) count_negatives_sliced_p<5>(col, a, b, zb, lane, cnt);
+    else if (n <= 252) count_negatives_sliced_p<6>(col, a, b, zb, lane, cnt);
+    else if (n <= 508) count_negatives_sliced_p<7>(col, a, b, zb, lane, cnt);
+    else if (n <= 1020) count_negatives_sliced_p<8>(col, a, b, zb, lane, cnt);
+    else count_negatives_sliced_p<9>(col, a, b, zb, lane, cnt);
 }
 
-// Store y for probes 4*lane .. 4*lane+3 of row r (degree deg, slot if deg >
+__device__ __forceinline__ uint32_t pack_bytes(const int* v)
+{
+    return (uint32_t)(v[0] & 0xFF) | ((uint32_t)(v[1] & 0xFF) << 8) | ((uint32_t)(v[2] & 0xFF) << 16) |
+           ((uint32_t)(v[3] & 0xFF) << 24);
+}
+
+__device__ __forceinline__ uint32_t pack_halves(int lo, int hi)
+{
+    return (uint32_t)(lo & 0xFFFF) | ((uint32_t)hi << 16);
+}
+
+// Store y for this lane's 8 probes of row r (degree deg, slot if deg >
 // kSmallDeg) in its class's array, and add its x1, x2 terms (Acc: int for
 // the sums of one pass-1 chunk, long long otherwise).
 template <typename Acc>
-__device__ __forceinline__ void store_row(int64_t r, int64_t deg, const int yv[4], uint32_t own, int32_t slot,
-                                          uint32_t* __restrict__ y8, uint2* __restrict__ y16,
-                                          int32_t* __restrict__ y32, int lane, Acc x1[4], Acc x2[4])
+__device__ __forceinline__ void store_row(int64_t r, int64_t deg, const int yv[8], uint2 own, int32_t slot,
+                                          uint2* __restrict__ y8, uint4* __restrict__ y16,
+                                          int32_t* __restrict__ y32, int lane, Acc x1[8], Acc x2[8])
 {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 8; ++q) {
         const Acc yq = yv[q];
-        x1[q] += ((own >> (8 * q)) & 1u) ? -yq : yq;
+        const uint32_t ob = q < 4 ? own.x >> (8 * q) : own.y >> (8 * (q - 4));
+        x1[q] += (ob & 1u) ? -yq : yq;
         x2[q] += yq * yq;
     }
     const int cl = row_class(deg);
     if (cl == kClassSmall) {
-        y8[(size_t)r * 32 + lane] = (uint32_t)(yv[0] & 0xFF) | ((uint32_t)(yv[1] & 0xFF) << 8) |
-                                    ((uint32_t)(yv[2] & 0xFF) << 16) | ((uint32_t)(yv[3] & 0xFF) << 24);
+        y8[(size_t)r * 32 + lane] = make_uint2(pack_bytes(yv), pack_bytes(yv + 4));
     } else if (cl == kClassMid) {
-        y16[(size_t)slot * 32 + lane] = make_uint2((uint32_t)(yv[0] & 0xFFFF) | ((uint32_t)yv[1] << 16),
-                                                   (uint32_t)(yv[2] & 0xFFFF) | ((uint32_t)yv[3] << 16));
+        y16[(size_t)slot * 32 + lane] = make_uint4(pack_halves(yv[0], yv[1]), pack_halves(yv[2], yv[3]),
+                                                   pack_halves(yv[4], yv[5]), pack_halves(yv[6], yv[7]));
     } else {
-        *reinterpret_cast<int4*>(y32 + (size_t)slot * kProbes + 4 * lane) = make_int4(yv[0], yv[1], yv[2], yv[3]);
+        int32_t* yr = y32 + (size_t)slot * kProbes + 4 * lane;
+        *reinterpret_cast<int4*>(yr) = make_int4(yv[0], yv[1], yv[2], yv[3]);
+        *reinterpret_cast<int4*>(yr + kHalf) = make_int4(yv[4], yv[5], yv[6], yv[7]);
     }
 }
 
@@ -787,43 +830,49 @@ __device__ __forceinline__ void store_row(int64_t r, int64_t deg, const int yv[4
 // and x2 take int sums: the rows a chunk owns hold at most kChunk + kLongRow
 // entries, so their sum of y^2 <= kLongRow * (kChunk + kLongRow) < 2^31.
 static_assert((int64_t)kLongRow * (kChunk + kLongRow) < (1LL << 31), "int sums of x2 over one chunk");
-__device__ __forceinline__ void finish_pass1_row(int64_t r, int deg, int cnt[4], uint32_t own,
-                                                 const int32_t* __restrict__ bslot, uint32_t* __restrict__ y8,
-                                                 uint2* __restrict__ y16, int32_t* __restrict__ y32, int lane,
-                                                 int x1[4], int x2[4])
+__device__ __forceinline__ void finish_pass1_row(int64_t r, int deg, int cnt[8], uint2 own,
+                                                 const int32_t* __restrict__ bslot, uint2* __restrict__ y8,
+                                                 uint4* __restrict__ y16, int32_t* __restrict__ y32, int lane,
+                                                 int x1[8], int x2[8])
 {
     if (deg > 0) {
-        const int yv[4] = {deg - 2 * cnt[0], deg - 2 * cnt[1], deg - 2 * cnt[2], deg - 2 * cnt[3]};
+        int yv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) yv[q] = deg - 2 * cnt[q];
         store_row(r, deg, yv, own, deg > kSmallDeg ? __ldg(bslot + r) : -1, y8, y16, y32, lane, x1, x2);
     }
-    cnt[0] = cnt[1] = cnt[2] = cnt[3] = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) cnt[q] = 0;
 }
 
-__device__ __forceinline__ void flush_x(long long (*sx)[kProbes], int which, const long long v[4], int lane)
+// sx[which][block probe] += this lane's 8 values.
+template <typename Acc>
+__device__ __forceinline__ void flush_x(long long (*sx)[kProbes], int which, const Acc v[8], int lane)
 {
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (v[q]) atomicAdd((unsigned long long*)&sx[which][4 * lane + q], (unsigned long long)v[q]);
+    for (int q = 0; q < 8; ++q)
+        if (v[q]) atomicAdd((unsigned long long*)&sx[which][(q < 4 ? 0 : kHalf) + 4 * lane + (q & 3)],
+                            (unsigned long long)(long long)v[q]);
 }
 
-// Pass 1: y = A z for 128 probes, plus x1 = z.y and x2 = y.y (rows of degree
+// Pass 1: y = A z for 256 probes, plus x1 = z.y and x2 = y.y (rows of degree
 // <= kLongRow; longer rows only accumulate their counts here).
 __global__ void __launch_bounds__(kTriThreads) tri_pass1_kernel(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, int64_t d, int64_t nch,
     const int64_t* __restrict__ crow, const int32_t* __restrict__ bslot,
-    const uint32_t* __restrict__ zb, uint32_t* __restrict__ y8, uint2* __restrict__ y16,
+    const uint32_t* __restrict__ zb, uint2* __restrict__ y8, uint4* __restrict__ y16,
     int32_t* __restrict__ y32, unsigned long long* __restrict__ xacc, unsigned long long* __restrict__ counter)
 {
     __shared__ long long sx[2][kProbes];
     for (int t = threadIdx.x; t < 2 * kProbes; t += blockDim.x) (&sx[0][0])[t] = 0;
     __syncthreads();
 
+    const uint2* zb2 = reinterpret_cast<const uint2*>(zb);
     const int lane = threadIdx.x & 31;
-    long long x1[4] = {0, 0, 0, 0}, x2[4] = {0, 0, 0, 0};
     for (int64_t c = next_chunk(counter, lane); c < nch; c = next_chunk(counter, lane)) {
         const int64_t u0 = c * kChunk, u1 = u0 + kChunk;
         int64_t r = crow[c];
-        int cx1[4] = {0, 0, 0, 0}, cx2[4] = {0, 0, 0, 0};   // this chunk's rows
+        int cx1[8] = {0, 0, 0, 0, 0, 0, 0, 0}, cx2[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // this chunk's rows
         while (r < d) {
             const int64_t beg = __ldg(rowptr + r);
             const int64_t pr = beg + kRowCost * r;          // first unit of row r
@@ -835,13 +884,13 @@ __global__ void __launch_bounds__(kTriThreads) tri_pass1_kernel(
                 const int64_t a = beg + max((int64_t)0, u0 - e0);
                 const int64_t b = beg + min(deg, u1 - e0);
                 if (a < b) {
-                    int cnt[4] = {0, 0, 0, 0};
+                    int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
                     if (b - a >= kSliceMin) count_negatives_sliced(col, a, b, zb, lane, cnt);
-                    else count_negatives(col, a, b, zb, lane, cnt);
+                    else count_negatives(col, a, b, zb2, lane, cnt);
                     int32_t* acc = y32 + (size_t)__ldg(bslot + r) * kProbes + 4 * lane;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (cnt[q]) atomicAdd(acc + q, cnt[q]);
+                    for (int q = 0; q < 8; ++q)
+                        if (cnt[q]) atomicAdd(acc + (q < 4 ? 0 : kHalf) + (q & 3), cnt[q]);
                 }
                 ++r;
                 continue;
@@ -869,24 +918,19 @@ __global__ void __launch_bounds__(kTriThreads) tri_pass1_kernel(
                     const int b = __shfl_sync(kFull, a1, cur);
                     if (a == b) continue;
                     const int64_t row = r + cur;
-                    const uint32_t own = sign_bytes(zb, row, lane);   // fetched before the entries
-                    int cnt[4] = {0, 0, 0, 0};
+                    const uint2 own = sign_pair(zb2, row, lane);   // fetched before the entries
+                    int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
                     if (b - a >= kSliceMin) count_negatives_sliced(col, a, b, zb, lane, cnt);
-                    else count_negatives(col, a, b, zb, lane, cnt);
+                    else count_negatives(col, a, b, zb2, lane, cnt);
                     finish_pass1_row(row, b - a, cnt, own, bslot, y8, y16, y32, lane, cx1, cx2);
                 }
                 r += f;
                 if (f < 32) break;
             }
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            x1[q] += cx1[q];
-            x2[q] += cx2[q];
-        }
+        flush_x(sx, 0, cx1, lane);   // the chunk's sums, into the CTA's 64-bit totals
+        flush_x(sx, 1, cx2, lane);
     }
-    flush_x(sx, 0, x1, lane);
-    flush_x(sx, 1, x2, lane);
     __syncthreads();
     for (int t = threadIdx.x; t < kProbes; t += blockDim.x) {
         if (sx[0][t]) atomicAdd(xacc + 3 * t + 0, (unsigned long long)sx[0][t]);
@@ -898,24 +942,27 @@ __global__ void __launch_bounds__(kTriThreads) tri_pass1_kernel(
 // terms (a huge row's y replaces its counts in y32, lane by lane).
 __global__ void __launch_bounds__(kTriThreads) tri_long_rows_kernel(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ longlist, int nlong,
-    const int32_t* __restrict__ bslot, const uint32_t* __restrict__ zb, uint32_t* __restrict__ y8,
-    uint2* __restrict__ y16, int32_t* __restrict__ y32, unsigned long long* __restrict__ xacc)
+    const int32_t* __restrict__ bslot, const uint32_t* __restrict__ zb, uint2* __restrict__ y8,
+    uint4* __restrict__ y16, int32_t* __restrict__ y32, unsigned long long* __restrict__ xacc)
 {
     __shared__ long long sx[2][kProbes];
     for (int t = threadIdx.x; t < 2 * kProbes; t += blockDim.x) (&sx[0][0])[t] = 0;
     __syncthreads();
+    const uint2* zb2 = reinterpret_cast<const uint2*>(zb);
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    long long x1[4] = {0, 0, 0, 0}, x2[4] = {0, 0, 0, 0};
+    long long x1[8] = {0, 0, 0, 0, 0, 0, 0, 0}, x2[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t i = warp; i < nlong; i += nwarps) {
         const int64_t r = longlist[i];
-        const int64_t deg = rowptr[r + 1] - rowptr[r];
+        const int dg = (int)(rowptr[r + 1] - rowptr[r]);
         const int32_t slot = bslot[r];
-        const int4 c = *reinterpret_cast<const int4*>(y32 + (size_t)slot * kProbes + 4 * lane);
-        const int dg = (int)deg;
-        const int yv[4] = {dg - 2 * c.x, dg - 2 * c.y, dg - 2 * c.z, dg - 2 * c.w};
-        store_row(r, deg, yv, sign_bytes(zb, r, lane), slot, y8, y16, y32, lane, x1, x2);
+        const int32_t* cr = y32 + (size_t)slot * kProbes + 4 * lane;
+        const int4 ca = *reinterpret_cast<const int4*>(cr);
+        const int4 cb = *reinterpret_cast<const int4*>(cr + kHalf);
+        const int yv[8] = {dg - 2 * ca.x, dg - 2 * ca.y, dg - 2 * ca.z, dg - 2 * ca.w,
+                           dg - 2 * cb.x, dg - 2 * cb.y, dg - 2 * cb.z, dg - 2 * cb.w};
+        store_row(r, dg, yv, sign_pair(zb2, r, lane), slot, y8, y16, y32, lane, x1, x2);
     }
     flush_x(sx, 0, x1, lane);
     flush_x(sx, 1, x2, lane);
@@ -928,74 +975,101 @@ __global__ void __launch_bounds__(kTriThreads) tri_long_rows_kernel(
 
 // ---- pass 2 ------------------------------------------------------------------
 
-// s += y of the small targets (rows) listed in col[a, b), this lane's 4
+// s += y of the small targets (rows) listed in col[a, b), this lane's 8
 // probes; y8l = y8 + lane; the gathers batched by gather_block.
 __device__ __forceinline__ void sum_small(const int32_t* __restrict__ col, int64_t a, int64_t b,
-                                          const uint32_t* __restrict__ y8l, int lane, int s[4])
+                                          const uint2* __restrict__ y8l, int lane, int s[8])
 {
     for (int64_t base = a; base < b; base += 32) {
         const int64_t k = base + lane;
         const int cj = k < b ? __ldg(col + k) : 0;
         const int n = (int)min((int64_t)32, b - base);
-        gather_block(cj, n, [&](int j) { return __ldg(y8l + (size_t)j * 32); },
-                     [&](uint32_t w) {
-                         s[0] = __dp4a((int)w, 0x00000001, s[0]);
-                         s[1] = __dp4a((int)w, 0x00000100, s[1]);
-                         s[2] = __dp4a((int)w, 0x00010000, s[2]);
-                         s[3] = __dp4a((int)w, 0x01000000, s[3]);
+        gather_block<8>(cj, n, [&](int j) { return __ldg(y8l + (size_t)j * 32); },
+                     [&](uint2 w) {
+                         s[0] = __dp4a((int)w.x, 0x00000001, s[0]);
+                         s[1] = __dp4a((int)w.x, 0x00000100, s[1]);
+                         s[2] = __dp4a((int)w.x, 0x00010000, s[2]);
+                         s[3] = __dp4a((int)w.x, 0x01000000, s[3]);
+                         s[4] = __dp4a((int)w.y, 0x00000001, s[4]);
+                         s[5] = __dp4a((int)w.y, 0x00000100, s[5]);
+                         s[6] = __dp4a((int)w.y, 0x00010000, s[6]);
+                         s[7] = __dp4a((int)w.y, 0x01000000, s[7]);
                      });
     }
 }
 
 // s += y of the mid targets (y16 slots) listed in col[a, b); y16l = y16 + lane.
 __device__ __forceinline__ void sum_mid(const int32_t* __restrict__ col, int64_t a, int64_t b,
-                                        const uint2* __restrict__ y16l, int lane, int s[4])
+                                        const uint4* __restrict__ y16l, int lane, int s[8])
 {
     for (int64_t base = a; base < b; base += 32) {
         const int64_t k = base + lane;
         const int cj = k < b ? __ldg(col + k) : 0;
         const int n = (int)min((int64_t)32, b - base);
-        gather_block(cj, n, [&](int j) { return __ldg(y16l + (size_t)j * 32); },
-                     [&](uint2 w) {
+        gather_block<4>(cj, n, [&](int j) { return __ldg(y16l + (size_t)j * 32); },
+                     [&](uint4 w) {
                          s[0] = __dp2a_lo((int)w.x, 0x0001, s[0]);
                          s[1] = __dp2a_lo((int)w.x, 0x0100, s[1]);
                          s[2] = __dp2a_lo((int)w.y, 0x0001, s[2]);
                          s[3] = __dp2a_lo((int)w.y, 0x0100, s[3]);
+                         s[4] = __dp2a_lo((int)w.z, 0x0001, s[4]);
+                         s[5] = __dp2a_lo((int)w.z, 0x0100, s[5]);
+                         s[6] = __dp2a_lo((int)w.w, 0x0001, s[6]);
+                         s[7] = __dp2a_lo((int)w.w, 0x0100, s[7]);
                      });
     }
 }
 
-// y of a small or mid row, this lane's 4 probes, from its raw words (a huge
-// row has no out-entries: every neighbour above it is huge too).
-__device__ __forceinline__ uint2 load_own(int64_t row, int32_t slot, const uint32_t* __restrict__ y8l,
-                                          const uint2* __restrict__ y16l)
+// y of a small or mid row, this lane's 8 probes, as raw words (a huge row has
+// no out-entries: every neighbour above it is huge too).
+__device__ __forceinline__ uint4 load_own(int64_t row, int32_t slot, const uint2* __restrict__ y8l,
+                                          const uint4* __restrict__ y16l)
 {
-    return slot < 0 ? make_uint2(__ldg(y8l + (size_t)row * 32), 0u) : __ldg(y16l + (size_t)slot * 32);
+    if (slot < 0) {
+        const uint2 w = __ldg(y8l + (size_t)row * 32);
+        return make_uint4(w.x, w.y, 0u, 0u);
+    }
+    return __ldg(y16l + (size_t)slot * 32);
 }
 
-__device__ __forceinline__ void unpack_own(uint2 w, int32_t slot, int yi[4])
+__device__ __forceinline__ void unpack_own(uint4 w, int32_t slot, int yi[8])
 {
     if (slot < 0) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) yi[q] = (int)(int8_t)(w.x >> (8 * q));
+        for (int q = 0; q < 4; ++q) {
+            yi[q] = (int)(int8_t)(w.x >> (8 * q));
+            yi[4 + q] = (int)(int8_t)(w.y >> (8 * q));
+        }
     } else {
-        yi[0] = (int)(int16_t)(w.x & 0xFFFF);
-        yi[1] = (int)w.x >> 16;
-        yi[2] = (int)(int16_t)(w.y & 0xFFFF);
-        yi[3] = (int)w.y >> 16;
+        const uint32_t v[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            yi[2 * h] = (int)(int16_t)(v[h] & 0xFFFF);
+            yi[2 * h + 1] = (int)v[h] >> 16;
+        }
     }
 }
 
 // x3 += y_i * s, then s = 0.
-__device__ __forceinline__ void finish_pass2_row(uint2 own, int32_t slot, int s[4], long long x3[4])
+__device__ __forceinline__ void finish_pass2_row(uint4 own, int32_t slot, int s[8], long long x3[8])
 {
-    int yi[4];
+    int yi[8];
     unpack_own(own, slot, yi);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 8; ++q) {
         x3[q] += (long long)yi[q] * s[q];
         s[q] = 0;
     }
+}
+
+// sx[block probe] += 2 * x3 of this lane's 8 probes.
+__device__ __forceinline__ void flush_x3(long long* sx, const long long x3[8], int lane)
+{
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        if (x3[q])
+            atomicAdd((unsigned long long*)&sx[(q < 4 ? 0 : kHalf) + 4 * lane + (q & 3)],
+                      (unsigned long long)(2 * x3[q]));
 }
 
 // Pass 2: x3 = 2 sum_i y_i sum_{j in out(i)} y_j over the oriented out-lists
@@ -1004,7 +1078,7 @@ __device__ __forceinline__ void finish_pass2_row(uint2 own, int32_t slot, int s[
 __global__ void __launch_bounds__(kTriThreads, kPass2CtasPerSm) tri_pass2_kernel(
     const int64_t* __restrict__ out_ptr, const int32_t* __restrict__ out_col, const int32_t* __restrict__ nsmall,
     const int32_t* __restrict__ bslot, int64_t d, int64_t nch, const int64_t* __restrict__ crow,
-    const uint32_t* __restrict__ y8, const uint2* __restrict__ y16,
+    const uint2* __restrict__ y8, const uint4* __restrict__ y16,
     unsigned long long* __restrict__ xacc, unsigned long long* __restrict__ counter)
 {
     __shared__ long long sx[kProbes];
@@ -1012,10 +1086,10 @@ __global__ void __launch_bounds__(kTriThreads, kPass2CtasPerSm) tri_pass2_kernel
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
-    const uint32_t* y8l = y8 + lane;
-    const uint2* y16l = y16 + lane;
-    long long x3[4] = {0, 0, 0, 0};
-    int s[4] = {0, 0, 0, 0};
+    const uint2* y8l = y8 + lane;
+    const uint4* y16l = y16 + lane;
+    long long x3[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t c = next_chunk(counter, lane); c < nch; c = next_chunk(counter, lane)) {
         const int64_t u0 = c * kChunk, u1 = u0 + kChunk;
         int64_t r = crow[c];
@@ -1032,7 +1106,7 @@ __global__ void __launch_bounds__(kTriThreads, kPass2CtasPerSm) tri_pass2_kernel
                 if (a < b) {
                     const int64_t mid = beg + __ldg(nsmall + r);
                     const int32_t slot = __ldg(bslot + r);
-                    const uint2 own = load_own(r, slot, y8l, y16l);
+                    const uint4 own = load_own(r, slot, y8l, y16l);
                     sum_small(out_col, a, min(b, mid), y8l, lane, s);
                     sum_mid(out_col, max(a, mid), b, y16l, lane, s);
                     finish_pass2_row(own, slot, s, x3);
@@ -1068,7 +1142,7 @@ __global__ void __launch_bounds__(kTriThreads, kPass2CtasPerSm) tri_pass2_kernel
                     if (a == b) continue;
                     const int m = a + __shfl_sync(kFull, ns, cur);
                     const int32_t slot = __shfl_sync(kFull, sl, cur);
-                    const uint2 own = load_own(r + cur, slot, y8l, y16l);   // fetched before the entries
+                    const uint4 own = load_own(r + cur, slot, y8l, y16l);   // fetched before the entries
                     sum_small(out_col, a, m, y8l, lane, s);
                     sum_mid(out_col, m, b, y16l, lane, s);
                     finish_pass2_row(own, slot, s, x3);
@@ -1078,9 +1152,7 @@ __global__ void __launch_bounds__(kTriThreads, kPass2CtasPerSm) tri_pass2_kernel
             }
         }
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (x3[q]) atomicAdd((unsigned long long*)&sx[4 * lane + q], (unsigned long long)(2 * x3[q]));
+    flush_x3(sx, x3, lane);
     __syncthreads();
     for (int t = threadIdx.x; t < kProbes; t += blockDim.x)
         if (sx[t]) atomicAdd(xacc + 3 * t + 2, (unsigned long long)sx[t]);
@@ -1088,7 +1160,7 @@ __global__ void __launch_bounds__(kTriThreads, kPass2CtasPerSm) tri_pass2_kernel
 
 // Pass 2 for the edges into huge rows: x3 += 2 y_i y_h per pair, a warp per pair.
 __global__ void __launch_bounds__(kTriThreads) tri_pairs_kernel(
-    const int4* __restrict__ pairs, int64_t npairs, const uint32_t* __restrict__ y8, const uint2* __restrict__ y16,
+    const int4* __restrict__ pairs, int64_t npairs, const uint2* __restrict__ y8, const uint4* __restrict__ y16,
     const int32_t* __restrict__ y32, unsigned long long* __restrict__ xacc)
 {
     __shared__ long long sx[kProbes];
@@ -1097,29 +1169,28 @@ __global__ void __launch_bounds__(kTriThreads) tri_pairs_kernel(
     const int lane = threadIdx.x & 31;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    long long x3[4] = {0, 0, 0, 0};
+    long long x3[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t p = warp; p < npairs; p += nwarps) {
         const int4 pr = pairs[p];
-        int yi[4];
+        int yi[8];
         if (pr.x == kClassHuge) {
-            const int4 t = *reinterpret_cast<const int4*>(y32 + (size_t)pr.y * kProbes + 4 * lane);
-            yi[0] = t.x;
-            yi[1] = t.y;
-            yi[2] = t.z;
-            yi[3] = t.w;
+            const int32_t* yr = y32 + (size_t)pr.y * kProbes + 4 * lane;
+            const int4 ta = *reinterpret_cast<const int4*>(yr);
+            const int4 tb = *reinterpret_cast<const int4*>(yr + kHalf);
+            yi[0] = ta.x; yi[1] = ta.y; yi[2] = ta.z; yi[3] = ta.w;
+            yi[4] = tb.x; yi[5] = tb.y; yi[6] = tb.z; yi[7] = tb.w;
         } else {
             const int32_t slot = pr.x == kClassSmall ? -1 : pr.y;
             unpack_own(load_own(pr.y, slot, y8 + lane, y16 + lane), slot, yi);
         }
-        const int4 h = *reinterpret_cast<const int4*>(y32 + (size_t)pr.z * kProbes + 4 * lane);
-        x3[0] += (long long)yi[0] * h.x;
-        x3[1] += (long long)yi[1] * h.y;
-        x3[2] += (long long)yi[2] * h.z;
-        x3[3] += (long long)yi[3] * h.w;
-    }
+        const int32_t* hr = y32 + (size_t)pr.z * kProbes + 4 * lane;
+        const int4 ha = *reinterpret_cast<const int4*>(hr);
+        const int4 hb = *reinterpret_cast<const int4*>(hr + kHalf);
+        const int h[8] = {ha.x, ha.y, ha.z, ha.w, hb.x, hb.y, hb.z, hb.w};
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (x3[q]) atomicAdd((unsigned long long*)&sx[4 * lane + q], (unsigned long long)(2 * x3[q]));
+        for (int q = 0; q < 8; ++q) x3[q] += (long long)yi[q] * h[q];
+    }
+    flush_x3(sx, x3, lane);
     __syncthreads();
     for (int t = threadIdx.x; t < kProbes; t += blockDim.x)
         if (sx[t]) atomicAdd(xacc + 3 * t + 2, (unsigned long long)sx[t]);
@@ -1248,20 +1319,20 @@ int tri_block(mlt_matrix* M, uint64_t seed, int64_t id0, int nb, int64_t* x_dev,
     int rc;
     const size_t dd = (size_t)std::max<int64_t>(d, 1);
     const size_t nbig = (size_t)std::max(T.nbig, 1);
-    if ((rc = M->ws_z.ensure(dd * 4 * sizeof(uint32_t), s))) return rc;
+    if ((rc = M->ws_z.ensure(dd * kZWords * sizeof(uint32_t), s))) return rc;
     if ((rc = M->ws_y.ensure(dd * kProbes, s))) return rc;
     if ((rc = M->ws_y16.ensure(nbig * kProbes * sizeof(int16_t), s))) return rc;
     if ((rc = M->ws_y32.ensure(nbig * kProbes * sizeof(int32_t), s))) return rc;
     if ((rc = M->ws_x.ensure((size_t)kProbes * 3 * sizeof(unsigned long long), s))) return rc;
     uint32_t* zb = M->ws_z.as<uint32_t>();
-    uint32_t* y8 = M->ws_y.as<uint32_t>();
-    uint2* y16 = M->ws_y16.as<uint2>();
+    uint2* y8 = M->ws_y.as<uint2>();
+    uint4* y16 = M->ws_y16.as<uint4>();
     int32_t* y32 = M->ws_y32.as<int32_t>();
     unsigned long long* xacc = M->ws_x.as<unsigned long long>();
     MLT_CUDA_TRY(cudaMemsetAsync(xacc, 0, (size_t)kProbes * 3 * sizeof(unsigned long long), s));
     MLT_CUDA_TRY(cudaMemsetAsync(T.counters, 0, 2 * sizeof(unsigned long long), s));
     {
-        const int64_t total = d * 4;
+        const int64_t total = d * kZWords;
         const int g = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 16LL * M->num_sms));
         ProfScope ps("tri_zbits", s);
         zbits_kernel<<<g, 256, 0, s>>>(d, seed * kGolden, id0, nb, zb);

@@ -261,7 +261,7 @@ def mlt_mlmc_estimate(handle, params):
             "level_var": list(r.level_var[:L]), "probes": r.probes, "matvecs": r.matvecs}
 
 
-def mlt_triangle_trace(handle, seed, probe_offset, nprobes, block=128, use_cv=True, x=None,
+def mlt_triangle_trace(handle, seed, probe_offset, nprobes, block=256, use_cv=True, x=None,
                        stream=None):
     """Returns (estimate, stderr); per-probe (x1, x2, x3) go to `x` if given."""
     est, se = ctypes.c_double(), ctypes.c_double()
@@ -327,7 +327,7 @@ class Matrix:
         return mlt_spectrum_bounds(self.handle)
 
     def triangles(self, seed, probe_offset, nprobes, use_cv=True, x=None, stream=None):
-        return mlt_triangle_trace(self.handle, seed, probe_offset, nprobes, 128, use_cv, x, stream)
+        return mlt_triangle_trace(self.handle, seed, probe_offset, nprobes, 256, use_cv, x, stream)
 
     def mlmc(self, fn, a, b, n, seed=0, levels=None, m=None, m_pilot=10, mode="budget",
              target=1000.0, cost_model="symmetric", max_levels=0, reuse_pilot=True,

@@ -79,20 +79,22 @@ def test_rejects_bad_inputs(L):
         assert e.value.code == L.MLT_EINVAL
     g = synth.random_graph(20, 0.3, seed=0)
     with L.Matrix(g) as M:
-        with pytest.raises(L.MLTError):
-            L.mlt_triangle_trace(M.handle, 0, 0, 10, block=64)
+        for blk in (64, 128):
+            with pytest.raises(L.MLTError):
+                L.mlt_triangle_trace(M.handle, 0, 0, 10, block=blk)
         with pytest.raises(L.MLTError):
             M.triangles(0, 0, 0)
 
 
 def test_full_size_rmat20_sampled(L, O):
     # the R-MAT scale-20 triangle workload at full size: 1024 probes in blocks
-    # of 128; a sample of probes (first, block edges, last) against the oracle
+    # of 256; a sample of probes (first, half and block edges, last) against the
+    # oracle
     g = synth.rmat_adjacency(20, 16, seed=0)
     x = np.zeros((1024, 3), dtype=np.int64)
     with L.Matrix(g) as G:
         est, se = G.triangles(0, 0, 1024, x=x)
-    for p in (0, 127, 128, 1023):
+    for p in (0, 3, 127, 128, 131, 255, 256, 1023):
         assert np.array_equal(x[p], O.triangle_moments(g, 0, p, 1)[0]), p
     er, sr, _, _ = O.triangle_estimate(x, g.nnz, True)   # same sums -> same bits
     assert est == er and se == sr
