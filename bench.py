@@ -266,7 +266,7 @@ class Triangles:
     # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
     # from an ncu capture of this workload, per kernel; to be re-taken
     # whenever the kernel changes
-    TRAFFIC = {}   # the 256-probe passes have not been captured yet
+    TRAFFIC = {"tri_pass1": 331.13e6, "tri_pass2": 326.95e6}
 
     # ours
     def setup(self, mlt, torch, rank):
