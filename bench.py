@@ -11,7 +11,8 @@ One step is one pass of the whole hot path over one batch of synthetic input:
 
   rmat20_triangles (default): exact int64 triangle moments of an R-MAT graph
       (scale 20, edge factor 16, a=0.57, b=c=0.19, seed 0; symmetric, no
-      self-loops or duplicates) for 1024 Rademacher probes in blocks of 256,
+      self-loops or duplicates) for 1024 Rademacher probes in blocks of 128,
+      two blocks per launch,
       plus the control-variate estimate.  Units: probe-matvecs (2 per probe).
   logdet64: multilevel log-det of the 64x64 Dirichlet Laplacian + 0.1 I,
       levels {8, 32, 128} with {256, 64, 16} probes, FP64.  Units: probe-matvecs
@@ -235,7 +236,8 @@ class Triangles:
 
     def config(self):
         return {"workload": self.name, "graph": "R-MAT scale 20, edge factor 16, a=0.57 b=c=0.19, seed 0",
-                "d": self.d, "nnz": self.nnz, "probes": self.NPROBES, "block": self.BLOCK,
+                "d": self.d, "nnz": self.nnz, "probes": self.NPROBES, "block": 128,
+                "blocks_per_launch": self.BLOCK // 128,
                 "control_variates": True,
                 "l2": "inputs larger than L2 (col 4*nnz = %.0f MB + rowptr %.0f MB + y rows %.0f MB)"
                       % (4e-6 * self.nnz, 8e-6 * self.d, 1e-6 * self._ybytes())}
