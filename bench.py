@@ -268,7 +268,7 @@ class Triangles:
     # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
     # from an ncu capture of this workload, per kernel; to be re-taken
     # whenever the kernel changes
-    TRAFFIC = {"tri_pass1": 331.13e6, "tri_pass2": 326.95e6}
+    TRAFFIC = {"tri_pass1": 331.13e6}   # tri_pass2 changed since its capture (it now takes the pairs)
 
     # ours
     def setup(self, mlt, torch, rank):

@@ -97,26 +97,51 @@ __device__ __forceinline__ uint32_t interleave_bytes(uint32_t x)
 
 // zb[i * 8 + 2w + h]: the signs of block probes 128h + 32w .. + 31 at row i
 // in the byte-interleaved order above (0 for probes past nb).  The 32 bits
-// come from one or two 64-probe hash words.
-__global__ void zbits_kernel(int64_t d, uint64_t seedmix, int64_t id0, int nb, uint32_t* __restrict__ zb)
+// come from one or two 64-probe hash words; when id0 is a multiple of 64 (a
+// run of blocks that starts aligned), words 4m + h and 4m + 2 + h share one
+// hash word (probes 128h + 64m .. +63), computed once.  The same launch zeroes
+// the y32 accumulators of the nlong rows longer than a chunk.
+__global__ void zbits_kernel(int64_t d, uint64_t seedmix, int64_t id0, int nb, uint32_t* __restrict__ zb,
+                             const int32_t* __restrict__ longlist, int nlong, const int32_t* __restrict__ bslot,
+                             int32_t* __restrict__ y32)
 {
-    const int64_t total = d * kZWords;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t i = (uint64_t)(e >> 3);
-        const int w8 = (int)(e & 7);
-        const int pb = kHalf * (w8 & 1) + 32 * (w8 >> 1);   // first block probe of the word
-        const int valid = min(32, max(0, nb - pb));
-        uint32_t bits = 0;
-        if (valid > 0) {
-            const uint64_t p0 = (uint64_t)(id0 + pb);
-            const int o = (int)(p0 & 63);
-            uint64_t v = probe_word(seedmix, p0 >> 6, i) >> o;
-            if (o > 32) v |= probe_word(seedmix, (p0 >> 6) + 1, i) << (64 - o);
-            bits = (uint32_t)v;
-            if (valid < 32) bits &= (1u << valid) - 1u;
+    const int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if ((id0 & 63) == 0) {
+        for (int64_t e = t0; e < d * 4; e += stride) {
+            const uint64_t i = (uint64_t)(e >> 2);
+            const int h = (int)(e & 1), m = (int)((e >> 1) & 1);
+            const int pb = kHalf * h + 64 * m;            // first block probe of the hash word
+            const int valid = min(64, max(0, nb - pb));
+            uint64_t v = 0;
+            if (valid > 0) {
+                v = probe_word(seedmix, (uint64_t)(id0 + pb) >> 6, i);
+                if (valid < 64) v &= (1ull << valid) - 1ull;
+            }
+            zb[i * kZWords + 4 * m + h] = interleave_bytes((uint32_t)v);
+            zb[i * kZWords + 4 * m + 2 + h] = interleave_bytes((uint32_t)(v >> 32));
         }
-        zb[e] = interleave_bytes(bits);
+    } else {
+        for (int64_t e = t0; e < d * kZWords; e += stride) {
+            const uint64_t i = (uint64_t)(e >> 3);
+            const int w8 = (int)(e & 7);
+            const int pb = kHalf * (w8 & 1) + 32 * (w8 >> 1);   // first block probe of the word
+            const int valid = min(32, max(0, nb - pb));
+            uint32_t bits = 0;
+            if (valid > 0) {
+                const uint64_t p0 = (uint64_t)(id0 + pb);
+                const int o = (int)(p0 & 63);
+                uint64_t v = probe_word(seedmix, p0 >> 6, i) >> o;
+                if (o > 32) v |= probe_word(seedmix, (p0 >> 6) + 1, i) << (64 - o);
+                bits = (uint32_t)v;
+                if (valid < 32) bits &= (1u << valid) - 1u;
+            }
+            zb[e] = interleave_bytes(bits);
+        }
+    }
+    for (int64_t e = t0; e < (int64_t)nlong * kProbes; e += stride) {
+        const int r = longlist[e / kProbes];
+        y32[(size_t)bslot[r] * kProbes + (e % kProbes)] = 0;
     }
 }
 
@@ -554,16 +579,6 @@ __global__ void __launch_bounds__(kTriThreads) tri_fill_kernel(
     };
     for (int64_t c = next_chunk(chunk_ctr, lane); c < nch; c = next_chunk(chunk_ctr, lane))
         walk_chunk(rowptr, d, c, crow, lane, group, long_part);
-}
-
-__global__ void zero_long_rows_kernel(const int32_t* __restrict__ longlist, int nlong,
-                                      const int32_t* __restrict__ bslot, int32_t* __restrict__ y32)
-{
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)nlong * kProbes;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int r = longlist[e / kProbes];
-        y32[(size_t)bslot[r] * kProbes + (e % kProbes)] = 0;
-    }
 }
 
 // Entries t0 .. t0+D-1 of the current block of 32 (their row or slot in lane
@@ -1068,14 +1083,40 @@ __device__ __forceinline__ void flush_x3(long long* sx, const long long x3[8], i
                       (unsigned long long)(2 * x3[q]));
 }
 
+// One edge into a huge row, a warp per pair: x3 += y_i y_h for this lane's 8 probes.
+constexpr int64_t kPairBatch = 16;
+__device__ __forceinline__ void pair_product(const int4 pr, const uint2* __restrict__ y8, const uint4* __restrict__ y16,
+                                             const int32_t* __restrict__ y32, int lane, long long x3[8])
+{
+    int yi[8];
+    if (pr.x == kClassHuge) {
+        const int32_t* yr = y32 + (size_t)pr.y * kProbes + 4 * lane;
+        const int4 ta = *reinterpret_cast<const int4*>(yr);
+        const int4 tb = *reinterpret_cast<const int4*>(yr + kHalf);
+        yi[0] = ta.x; yi[1] = ta.y; yi[2] = ta.z; yi[3] = ta.w;
+        yi[4] = tb.x; yi[5] = tb.y; yi[6] = tb.z; yi[7] = tb.w;
+    } else {
+        const int32_t slot = pr.x == kClassSmall ? -1 : pr.y;
+        unpack_own(load_own(pr.y, slot, y8 + lane, y16 + lane), slot, yi);
+    }
+    const int32_t* hr = y32 + (size_t)pr.z * kProbes + 4 * lane;
+    const int4 ha = *reinterpret_cast<const int4*>(hr);
+    const int4 hb = *reinterpret_cast<const int4*>(hr + kHalf);
+    const int h[8] = {ha.x, ha.y, ha.z, ha.w, hb.x, hb.y, hb.z, hb.w};
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x3[q] += (long long)yi[q] * h[q];
+}
+
 // Pass 2: x3 = 2 sum_i y_i sum_{j in out(i)} y_j over the oriented out-lists
 // (|s| <= kLongRow * kMidDeg < 2^31: a row part never holds more than
-// kLongRow entries and every main target is small or mid).
+// kLongRow entries and every main target is small or mid), then the pairs of
+// edges into huge rows, which fill the warps that the chunks leave idle.
 __global__ void __launch_bounds__(kTriThreads, kPass2CtasPerSm) tri_pass2_kernel(
     const int64_t* __restrict__ out_ptr, const int32_t* __restrict__ out_col, const int32_t* __restrict__ nsmall,
     const int32_t* __restrict__ bslot, int64_t d, int64_t nch, const int64_t* __restrict__ crow,
-    const uint2* __restrict__ y8, const uint4* __restrict__ y16,
-    unsigned long long* __restrict__ xacc, unsigned long long* __restrict__ counter)
+    const uint2* __restrict__ y8, const uint4* __restrict__ y16, const int32_t* __restrict__ y32,
+    const int4* __restrict__ pairs, int64_t npairs, unsigned long long* __restrict__ xacc,
+    unsigned long long* __restrict__ counter, unsigned long long* __restrict__ pair_counter)
 {
     __shared__ long long sx[kProbes];
     for (int t = threadIdx.x; t < kProbes; t += blockDim.x) sx[t] = 0;
@@ -1148,44 +1189,10 @@ __global__ void __launch_bounds__(kTriThreads, kPass2CtasPerSm) tri_pass2_kernel
             }
         }
     }
-    flush_x3(sx, x3, lane);
-    __syncthreads();
-    for (int t = threadIdx.x; t < kProbes; t += blockDim.x)
-        if (sx[t]) atomicAdd(xacc + 3 * t + 2, (unsigned long long)sx[t]);
-}
-
-// Pass 2 for the edges into huge rows: x3 += 2 y_i y_h per pair, a warp per pair.
-__global__ void __launch_bounds__(kTriThreads) tri_pairs_kernel(
-    const int4* __restrict__ pairs, int64_t npairs, const uint2* __restrict__ y8, const uint4* __restrict__ y16,
-    const int32_t* __restrict__ y32, unsigned long long* __restrict__ xacc)
-{
-    __shared__ long long sx[kProbes];
-    for (int t = threadIdx.x; t < kProbes; t += blockDim.x) sx[t] = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    long long x3[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int64_t p = warp; p < npairs; p += nwarps) {
-        const int4 pr = pairs[p];
-        int yi[8];
-        if (pr.x == kClassHuge) {
-            const int32_t* yr = y32 + (size_t)pr.y * kProbes + 4 * lane;
-            const int4 ta = *reinterpret_cast<const int4*>(yr);
-            const int4 tb = *reinterpret_cast<const int4*>(yr + kHalf);
-            yi[0] = ta.x; yi[1] = ta.y; yi[2] = ta.z; yi[3] = ta.w;
-            yi[4] = tb.x; yi[5] = tb.y; yi[6] = tb.z; yi[7] = tb.w;
-        } else {
-            const int32_t slot = pr.x == kClassSmall ? -1 : pr.y;
-            unpack_own(load_own(pr.y, slot, y8 + lane, y16 + lane), slot, yi);
-        }
-        const int32_t* hr = y32 + (size_t)pr.z * kProbes + 4 * lane;
-        const int4 ha = *reinterpret_cast<const int4*>(hr);
-        const int4 hb = *reinterpret_cast<const int4*>(hr + kHalf);
-        const int h[8] = {ha.x, ha.y, ha.z, ha.w, hb.x, hb.y, hb.z, hb.w};
-#pragma unroll
-        for (int q = 0; q < 8; ++q) x3[q] += (long long)yi[q] * h[q];
-    }
+    // the edges into huge rows, kPairBatch at a time once the chunks are gone
+    for (int64_t p0 = next_chunk(pair_counter, lane) * kPairBatch; p0 < npairs;
+         p0 = next_chunk(pair_counter, lane) * kPairBatch)
+        for (int64_t p = p0; p < min(p0 + kPairBatch, npairs); ++p) pair_product(pairs[p], y8, y16, y32, lane, x3);
     flush_x3(sx, x3, lane);
     __syncthreads();
     for (int t = threadIdx.x; t < kProbes; t += blockDim.x)
@@ -1326,18 +1333,14 @@ int tri_block(mlt_matrix* M, uint64_t seed, int64_t id0, int nb, int64_t* x_dev,
     int32_t* y32 = M->ws_y32.as<int32_t>();
     unsigned long long* xacc = M->ws_x.as<unsigned long long>();
     MLT_CUDA_TRY(cudaMemsetAsync(xacc, 0, (size_t)kProbes * 3 * sizeof(unsigned long long), s));
-    MLT_CUDA_TRY(cudaMemsetAsync(T.counters, 0, 2 * sizeof(unsigned long long), s));
+    // chunk counters of pass 1 and pass 2 and pass 2's pair counter (the third
+    // slot served the preparation's counting pass before any block ran)
+    MLT_CUDA_TRY(cudaMemsetAsync(T.counters, 0, 3 * sizeof(unsigned long long), s));
     {
         const int64_t total = d * kZWords;
         const int g = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 16LL * M->num_sms));
         ProfScope ps("tri_zbits", s);
-        zbits_kernel<<<g, 256, 0, s>>>(d, seed * kGolden, id0, nb, zb);
-    }
-    MLT_CUDA_TRY(cudaGetLastError());
-    if (T.nlong > 0) {
-        const int g = (int)std::min<int64_t>(((int64_t)T.nlong * kProbes + 255) / 256, 4LL * M->num_sms);
-        ProfScope ps("tri_zero_long", s);
-        zero_long_rows_kernel<<<std::max(g, 1), 256, 0, s>>>(T.longlist, T.nlong, T.bslot, y32);
+        zbits_kernel<<<g, 256, 0, s>>>(d, seed * kGolden, id0, nb, zb, T.longlist, T.nlong, T.bslot, y32);
     }
     MLT_CUDA_TRY(cudaGetLastError());
     {
@@ -1357,13 +1360,8 @@ int tri_block(mlt_matrix* M, uint64_t seed, int64_t id0, int nb, int64_t* x_dev,
     {
         ProfScope ps("tri_pass2", s);
         tri_pass2_kernel<<<T.grid2, kTriThreads, 0, s>>>(T.out_ptr, T.out_col, T.nsmall, T.bslot, d, T.nch2,
-                                                         T.crow2, y8, y16, xacc, T.counters + 1);
-    }
-    MLT_CUDA_TRY(cudaGetLastError());
-    if (T.npairs > 0) {
-        const int g = (int)std::min<int64_t>((T.npairs * 32 + kTriThreads - 1) / kTriThreads, 4LL * M->num_sms);
-        ProfScope ps("tri_pairs", s);
-        tri_pairs_kernel<<<std::max(g, 1), kTriThreads, 0, s>>>(T.pairs, T.npairs, y8, y16, y32, xacc);
+                                                         T.crow2, y8, y16, y32, T.pairs, T.npairs, xacc,
+                                                         T.counters + 1, T.counters + 2);
     }
     MLT_CUDA_TRY(cudaGetLastError());
     MLT_CUDA_TRY(cudaMemcpyAsync(x_dev, xacc, (size_t)nb * 3 * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
