@@ -444,12 +444,14 @@ class EstradaHutchpp:
     on fresh probe ids, and the line's config carries both standard errors."""
     name = "estrada_hutchpp"
     unit = "probe-matvecs/s"
-    dtype = "f64"
     S, G, DEG = 64, 64, 128
     PROBE_SPAN = 1088 * 128 + 128 + 256   # timed, e2e, then the comparison's two runs
 
-    def __init__(self, precision="fp32"):
-        self.precision = precision   # of the sketch p(At) S; everything else is FP64
+    def __init__(self, precision="df64"):
+        # fp32: FP32 sketch, the rest FP64; fp64: all FP64; df64: FP32 sketch and
+        # double-float moments (FP64-class accuracy on the FP32 pipes)
+        self.precision = precision
+        self.dtype = "df64" if precision == "df64" else "f64"
         from paper_2103_10516_gb300 import synth
         self.csr = synth.rmat_adjacency(22, 16, seed=1)
         self.d = self.csr.nrows
@@ -464,7 +466,9 @@ class EstradaHutchpp:
         return {"workload": self.name, "graph": "R-MAT scale 22, edge factor 16, seed 1",
                 "d": self.d, "nnz": self.nnz, "f": "exp", "interval": [-10.0, 10.0], "degree": self.DEG,
                 "scale": self.scale, "sketch_probes": self.S, "remainder_probes": self.G,
-                "precision": "sketch %s, all else fp64" % self.precision, "comparison": self.cmp,
+                "precision": {"fp32": "fp32 sketch, all else fp64", "fp64": "all fp64",
+                              "df64": "fp32 sketch, double-float moments, all else fp64"}[self.precision],
+                "comparison": self.cmp,
                 "l2": "inputs larger than L2 (four 64-column FP64 blocks of %.0f MB)" % (self.d * 64 * 8e-6)}
 
     def kernel_bytes(self, launches_per_step):
@@ -481,6 +485,8 @@ class EstradaHutchpp:
         return out
 
     def kernel_flops(self, launches_per_step):
+        if self.precision == "df64":
+            return {}   # double-float steps are rated against HBM, not the FP64 rate
         out = {}
         if launches_per_step.get("clenshaw_step"):
             out["clenshaw_step"] = self.S * (2 * self.nnz + 8 * self.d)
@@ -713,7 +719,7 @@ class NuclearGram:
         self.d = self.X.ncols
         self.nnz = self.X.nnz
         self.precision = precision or "fp32"
-        self.dtype = {"fp32": "f32", "fp64": "f64", "mixed": "f32+f64"}[self.precision]
+        self.dtype = {"fp32": "f32", "fp64": "f64", "df64": "df64", "mixed": "f32+f64"}[self.precision]
         self.drift = None
 
     def _prec(self, mlt):
@@ -729,14 +735,14 @@ class NuclearGram:
                 "interval": getattr(self, "ab", None), "group_width": getattr(self, "group_width", None),
                 "max_abs_dmu_vs_fp64_over_d": self.drift,
                 "l2": "inputs larger than L2 per step (V blocks 2 x %.0f MB, X and X^T %.0f MB)"
-                      % (self.d * self.NPROBES * (8 if self.precision == "fp64" else 4) * 1e-6,
+                      % (self.d * self.NPROBES * (8 if self.precision in ("fp64", "df64") else 4) * 1e-6,
                          2 * 12 * self.nnz * 1e-6)}
 
     def kernel_bytes(self, launches_per_step):
         """Per launch of each SpMM: its matrix once, and per live probe the
         gathered vector read once and the output written (X V -> W: V read, W
         written; X^T W -> V_{k+1}: W, V_k and V_{k-1} read, V_{k+1} written)."""
-        sv = 8 if self.precision == "fp64" else 4
+        sv = 8 if self.precision in ("fp64", "df64") else 4
         m, n, nnz = self.X.nrows, self.X.ncols, self.nnz
         out = {}
         pm = self.units()
@@ -751,7 +757,7 @@ class NuclearGram:
     def setup(self, mlt, torch, rank):
         self.M = mlt.Matrix(self.X, gram=True)
         self.ab = [round(v, 6) for v in mlt.mlt_spectrum_bounds(self.M.handle, mlt.MLT_BOUNDS_LANCZOS, 50, 0)]
-        self.group_width = mlt.mlt_autotune(self.M.handle, "fp32" if self.precision != "fp64" else "fp64", 4)
+        self.group_width = mlt.mlt_autotune(self.M.handle, "fp32" if self.precision == "mixed" else self.precision, 4)
         self.out = torch.empty((self.NPROBES, self.DEG + 1), dtype=torch.float64, device="cuda")
         self.deg = np.full(self.NPROBES, self.DEG, dtype=np.int32)
         self.base = probe_base(rank)
@@ -815,7 +821,7 @@ class NuclearExplicit(NuclearGram):
         return c
 
     def kernel_bytes(self, launches_per_step):
-        sv = 8 if self.precision == "fp64" else 4
+        sv = 8 if self.precision in ("fp64", "df64") else 4
         return step_bytes(self.d, self.nnz_a, 4 + sv, sv, self.units(), launches_per_step)
 
     def setup(self, mlt, torch, rank):
@@ -823,7 +829,7 @@ class NuclearExplicit(NuclearGram):
         self.ab = [round(v, 6) for v in mlt.mlt_spectrum_bounds(G.handle, mlt.MLT_BOUNDS_LANCZOS, 50, 0)]
         G.close()
         self.M = mlt.Matrix(self.A)
-        self.group_width = mlt.mlt_autotune(self.M.handle, "fp32" if self.precision != "fp64" else "fp64", 4)
+        self.group_width = mlt.mlt_autotune(self.M.handle, "fp32" if self.precision == "mixed" else self.precision, 4)
         self.out = torch.empty((self.NPROBES, self.DEG + 1), dtype=torch.float64, device="cuda")
         self.deg = np.full(self.NPROBES, self.DEG, dtype=np.int32)
         self.base = probe_base(rank)
@@ -872,7 +878,7 @@ class Stencil3D:
         self.precision = precision or "fp32"
         # DRAM bytes per launch (128 live probes) from an ncu capture of the FP32 step
         self.TRAFFIC = {"cheb_step": 1.6308e9} if self.precision == "fp32" else {}
-        self.dtype = {"fp32": "f32", "fp64": "f64", "mixed": "f32+f64"}[self.precision]
+        self.dtype = {"fp32": "f32", "fp64": "f64", "df64": "df64", "mixed": "f32+f64"}[self.precision]
 
     def _prec(self, mlt):
         return mlt.mixed_at(32) if self.precision == "mixed" else self.precision
@@ -886,10 +892,10 @@ class Stencil3D:
                 "precision": self.precision, "interval": getattr(self, "ab", None),
                 "group_width": getattr(self, "group_width", None),
                 "l2": "inputs larger than L2 (V blocks 2 x %.0f MB)"
-                      % (self.d * self.NPROBES * (8 if self.precision == "fp64" else 4) * 1e-6)}
+                      % (self.d * self.NPROBES * (8 if self.precision in ("fp64", "df64") else 4) * 1e-6)}
 
     def kernel_bytes(self, launches_per_step):
-        sv = 8 if self.precision == "fp64" else 4
+        sv = 8 if self.precision in ("fp64", "df64") else 4
         return step_bytes(self.d, self.nnz, 4 + sv, sv, self.units(), launches_per_step)
 
     def kernel_flops(self, launches_per_step):
@@ -899,7 +905,7 @@ class Stencil3D:
     def setup(self, mlt, torch, rank):
         self.M = mlt.Matrix(self.csr)
         self.ab = [0.1, self.M.bounds()[1]]
-        self.group_width = mlt.mlt_autotune(self.M.handle, "fp32" if self.precision != "fp64" else "fp64", 4)
+        self.group_width = mlt.mlt_autotune(self.M.handle, "fp32" if self.precision == "mixed" else self.precision, 4)
         self.out = torch.empty((self.NPROBES, self.DEG + 1), dtype=torch.float64, device="cuda")
         self.deg = np.full(self.NPROBES, self.DEG, dtype=np.int32)
         self.base = probe_base(rank)
@@ -981,7 +987,7 @@ class EstradaLearned:
                 "l2": "inputs larger than L2 (V blocks of 4 B x d per probe)"}
 
     def kernel_bytes(self, launches_per_step):
-        sv = 8 if self.precision == "fp64" else 4
+        sv = 8 if self.precision in ("fp64", "df64") else 4
         return step_bytes(self.d, self.nnz, 4, sv, self.units(), launches_per_step)
 
     def _timed(self, torch, fn):
@@ -1421,9 +1427,10 @@ def make_workload(args):
         if cls not in (NuclearGram, NuclearExplicit, Stencil3D, EstradaLearned, EstradaHutchpp):
             raise SystemExit("--precision applies to nuclear_gram, stencil3d, estrada_learned and "
                              "estrada_hutchpp only")
-        if cls is EstradaHutchpp and args.precision == "mixed":
-            raise SystemExit("estrada_hutchpp takes fp32 or fp64 (the sketch's precision)")
-        if cls is EstradaLearned and args.precision == "mixed":
+        if cls is EstradaHutchpp and args.precision not in ("fp32", "fp64", "df64"):
+            raise SystemExit("estrada_hutchpp takes fp32 (the sketch), fp64 (all) or df64 (fp32 sketch, "
+                             "double-float moments)")
+        if cls is EstradaLearned and args.precision not in ("fp32", "fp64"):
             raise SystemExit("estrada_learned takes fp32 or fp64")
         kw["precision"] = args.precision
     return cls(**kw)
@@ -1436,7 +1443,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat20_triangles", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default=None, choices=["fp32", "fp64", "mixed"])
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp64", "df64", "mixed"])
     ap.add_argument("--scale", type=int, default=None, help="R-MAT scale of estrada_learned")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -72,6 +72,10 @@ extern "C" {
 #define MLT_PREC_FP64 0    /* vectors, SpMM and dots in FP64                 */
 #define MLT_PREC_FP32 1    /* vectors and SpMM in FP32, dots summed in FP64  */
 #define MLT_PREC_MIXED 2   /* FP32 steps first, FP64 after: see below       */
+#define MLT_PREC_DF64 3    /* vectors, SpMM and per-thread dots as double-
+                              float pairs (hi + lo, about 48 significant
+                              bits) on the FP32 pipes, FP64 from the CTA
+                              sums on: FP64-class moments at FP32 speed     */
 /* MLT_PREC_MIXED_AT(k): the first k recurrence steps (degrees up to 2k with
  * the doubling identities, up to k in direct mode) run with FP32 vectors, the
  * rest with FP64 vectors (the two live vectors are widened at the switch);
@@ -323,10 +327,12 @@ int mlt_poly_apply(mlt_matrix* m, double a, double b, const double* c, int n,
  * Unbiased for tr p(At) whatever Q is, since Q does not depend on G; exact
  * when Q spans the whole space.  Cost: s*n + (s + g)*ceil(n/2) operator
  * applications (matvecs).
- * precision: MLT_PREC_FP64 (all FP64), or MLT_PREC_FP32 to evaluate the sketch
- * p(At) S in FP32 (the handle's FP32 values); Q, its trace, the deflation and
- * the remainder stay FP64.  Rounding in the sketch only moves span(Q), which
- * changes the variance but not the expectation.
+ * precision: MLT_PREC_FP64 (all FP64); MLT_PREC_FP32 to evaluate the sketch
+ * p(At) S in FP32 (the handle's FP32 values), Q, its trace, the deflation and
+ * the remainder staying FP64; or MLT_PREC_DF64, the FP32 sketch with the
+ * moments of Q and of the remainder probes in double-float pairs.  Rounding
+ * in the sketch only moves span(Q), which changes the variance but not the
+ * expectation.
  * samples: g doubles (host) or NULL.  0 <= s <= 128, 0 <= g <= 1024, s + g >= 1.
  * Errors: MLT_EINVAL (null m, c or out; n outside [1, MLT_MAX_DEGREE]; a >= b;
  * s, g out of range; probe ids beyond 2^32; other precisions), MLT_ENOMEM,

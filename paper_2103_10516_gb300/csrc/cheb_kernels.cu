@@ -39,6 +39,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "df64.cuh"
 #include "mlt_internal.h"
 #include "rng.cuh"
 
@@ -58,6 +59,7 @@ constexpr int kStepCtasPerSm = 6;
 template <typename T> struct Lanes;
 template <> struct Lanes<double> { static constexpr int N = 2; };   // 16-byte vectors
 template <> struct Lanes<float> { static constexpr int N = 4; };
+template <> struct Lanes<df64> { static constexpr int N = 2; };     // 16-byte vectors of pairs
 
 template <typename T, int N> struct alignas(sizeof(T) * N) Pack { T v[N]; };
 
@@ -87,6 +89,43 @@ template <> struct DotAcc<float> {
     }
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
+template <> struct DotAcc<df64> {
+    df64 s = df64(0);
+    __device__ __forceinline__ void add_prod(df64 a, df64 b) { s = a * b + s; }
+    __device__ __forceinline__ void add(df64 x) { s = s + x; }
+    __device__ __forceinline__ double value() const { return df_to_double(s); }
+};
+
+// A matrix value through the read-only cache.
+template <typename T>
+__device__ __forceinline__ T ldg_val(const T* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ df64 ldg_val<df64>(const df64* p)
+{
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return df64(v.x, v.y);
+}
+
+// A register value from lane src of the group.
+template <typename T>
+__device__ __forceinline__ T shfl_val(unsigned mask, T v, int src, int width)
+{
+    return __shfl_sync(mask, v, src, width);
+}
+template <>
+__device__ __forceinline__ df64 shfl_val<df64>(unsigned mask, df64 v, int src, int width)
+{
+    return df64(__shfl_sync(mask, v.hi, src, width), __shfl_sync(mask, v.lo, src, width));
+}
+
+// The operand's values in precision T (null for a pattern matrix).
+template <typename T>
+const T* vals_of(const DevCSR& C)
+{
+    if (std::is_same<T, double>::value) return reinterpret_cast<const T*>(C.val64);
+    if (std::is_same<T, float>::value) return reinterpret_cast<const T*>(C.val32);
+    return reinterpret_cast<const T*>(C.valdf);
+}
 
 template <typename T>
 struct StepArgs {
@@ -164,13 +203,13 @@ __device__ __forceinline__ void row_product(const StepArgs<T>& a, const Lane<T, 
         T vj = T(0);
         if (k < k1) {
             cj = __ldg(a.col + k);
-            vj = a.val ? __ldg(a.val + k) : T(1);
+            vj = a.val ? ldg_val(a.val + k) : T(1);
         }
         const int cnt = (int)min((int64_t)G, k1 - base);
 #pragma unroll 4
         for (int t = 0; t < cnt; ++t) {
             const int c = __shfl_sync(L.gmask, cj, t, G);
-            const T v = __shfl_sync(L.gmask, vj, t, G);
+            const T v = shfl_val(L.gmask, vj, t, G);
             if (L.vok) {
                 const P x = *reinterpret_cast<const P*>(a.vgather + (size_t)c * a.ldv + L.c0);
 #pragma unroll
@@ -519,8 +558,8 @@ int run_steps(mlt_matrix* M, const MomentPlan& plan, GroupCtx& g, int k0, int k1
     constexpr int N = Lanes<T>::N;
     const DevCSR& A = M->A;
     const DevCSR& AT = M->AT;
-    const T* valA = std::is_same<T, double>::value ? (const T*)A.val64 : (const T*)A.val32;
-    const T* valAT = std::is_same<T, double>::value ? (const T*)AT.val64 : (const T*)AT.val32;
+    const T* valA = vals_of<T>(A);
+    const T* valAT = vals_of<T>(AT);
     int rc;
     for (int k = k0; k < k1; ++k) {
         const int act = plan.act[k];
@@ -667,6 +706,63 @@ int run_group(mlt_matrix* M, const MomentPlan& plan, int ks, double a, double b,
     return MLT_OK;
 }
 
+// One probe group in double-float arithmetic throughout (MLT_PREC_DF64): the
+// steps of run_group with df64 vectors, SpMM and per-thread dot products, the
+// CTA partials and everything after them in FP64.
+int run_group_df(mlt_matrix* M, const MomentPlan& plan, double a, double b, uint64_t seed, double* mu_dev,
+                 int64_t ld_mu, int* err_flag, cudaStream_t s, bool alloc_only)
+{
+    GroupCtx g;
+    g.gram = (M->flags & MLT_GRAM) != 0;
+    g.d = plan.dim;
+    g.ldv = plan.ldv;
+    const size_t n = (size_t)g.d * g.ldv;
+    const size_t wrows = g.gram ? (size_t)M->A.nrows * g.ldv : 0;
+    int rc;
+    if ((rc = ensure_spmm_plan(M, M->A, M->plan_A, s))) return rc;
+    if (g.gram && (rc = ensure_spmm_plan(M, M->AT, M->plan_AT, s))) return rc;
+    if ((rc = ensure_df_values(M, s))) return rc;
+    if ((rc = M->ws_v[0].ensure(n * sizeof(df64), s)) || (rc = M->ws_v[1].ensure(n * sizeof(df64), s))) return rc;
+    df64* V[2] = {M->ws_v[0].as<df64>(), M->ws_v[1].as<df64>()};
+    if (g.gram && (rc = M->ws_w.ensure(wrows * sizeof(df64), s))) return rc;
+    const int64_t nseg = std::max(M->plan_A.nseg, g.gram ? M->plan_AT.nseg : (int64_t)0);
+    if ((rc = M->ws_seg.ensure((size_t)std::max<int64_t>(nseg, 1) * g.ldv * sizeof(df64), s))) return rc;
+    g.max_main = 8 * M->num_sms;
+    g.max_long = 2 * M->num_sms;
+    g.max_blocks = g.max_main + g.max_long;
+    if ((rc = M->ws_part.ensure((size_t)kSlots * g.max_blocks * 2 * g.ldv * sizeof(double), s))) return rc;
+    if ((rc = M->ws_dots.ensure((size_t)std::max(plan.K, 1) * 2 * plan.B * sizeof(double), s))) return rc;
+    g.part = M->ws_part.as<double>();
+    g.dots = M->ws_dots.as<double>();
+    g.seedmix = seed * kGolden;
+    g.ra = ReduceArgs{};
+    const double sc = g.gram ? M->scale * M->scale : M->scale;
+    g.alpha = 2.0 / (b - a) * sc;
+    g.beta = -(a + b) / (b - a);
+    if (alloc_only) return MLT_OK;
+    {
+        const int nb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, 16LL * M->num_sms);
+        ProfScope ps("init_probes", s);
+        init_probes_kernel<df64><<<std::max(nb, 1), 256, 0, s>>>(V[0], g.d, g.ldv, plan.B, plan.ids_dev, g.seedmix);
+    }
+    MLT_CUDA_TRY(cudaGetLastError());
+    if ((rc = run_steps<df64>(M, plan, g, 0, plan.K, V, M->ws_w.as<df64>(), M->ws_seg.as<df64>(), s))) return rc;
+    {
+        dim3 grid((unsigned)std::min<int64_t>((ld_mu + 127) / 128, 64), plan.B);
+        ProfScope ps("finalize_moments", s);
+        finalize_moments_kernel<<<grid, 128, 0, s>>>(g.dots, plan.B, plan.deg_dev, plan.row_dev, mu_dev, ld_mu,
+                                                     (double)g.d, plan.direct, err_flag);
+        MLT_CUDA_TRY(cudaGetLastError());
+    }
+    return MLT_OK;
+}
+
+__global__ void to_df_kernel(const double* __restrict__ in, df64* __restrict__ out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = df64(in[i]);
+}
+
 // out[i] = coef * x[i] over n elements (x null: zeros).
 template <typename T>
 __global__ void scaled_copy_kernel(T* __restrict__ out, const T* __restrict__ x, T coef, int64_t n)
@@ -718,8 +814,9 @@ int poly_apply_block_t(mlt_matrix* M, double a, double b, const double* c, int n
     int rc;
     if ((rc = block_ctx(M, ldv, ncols, 1, a, b, g, s))) return rc;
     if (std::is_same<T, float>::value && (rc = ensure_fp32_values(M, s))) return rc;
-    const T* valA = std::is_same<T, double>::value ? (const T*)M->A.val64 : (const T*)M->A.val32;
-    const T* valAT = std::is_same<T, double>::value ? (const T*)M->AT.val64 : (const T*)M->AT.val32;
+    if (std::is_same<T, df64>::value && (rc = ensure_df_values(M, s))) return rc;
+    const T* valA = vals_of<T>(M->A);
+    const T* valAT = vals_of<T>(M->AT);
     const int64_t total = g.d * (int64_t)ldv;
     const int nbk = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 16LL * M->num_sms));
     T* P[2] = {P0, P1};
@@ -785,10 +882,10 @@ int poly_apply_block_f32(mlt_matrix* M, double a, double b, const double* c, int
 
 // Doubling moments of an explicit FP64 block: V0 holds the start vectors (row
 // stride ldv, columns >= cols zero) and V1 is scratch of the same size, both
-// overwritten.  After K steps dots[k][0][c] = V_{k+1}.V_{k+1} and
+// overwritten; with df the steps run in double-float pairs.  After K steps dots[k][0][c] = V_{k+1}.V_{k+1} and
 // dots[k][1][c] = V_{k+1}.V_k for column c (device, in the handle's scratch).
 int moments_block(mlt_matrix* M, double a, double b, double* V0, double* V1, int ldv, int cols, int K,
-                  const double** dots_dev, cudaStream_t s)
+                  const double** dots_dev, bool df, cudaStream_t s)
 {
     GroupCtx g;
     int rc;
@@ -801,8 +898,24 @@ int moments_block(mlt_matrix* M, double a, double b, double* V0, double* V1, int
     plan.K = K;
     plan.act = act.data();
     plan.direct = 0;
-    double* V[2] = {V0, V1};
-    if ((rc = run_steps<double>(M, plan, g, 0, K, V, M->ws_w.as<double>(), M->ws_seg.as<double>(), s))) return rc;
+    if (df) {
+        // the start block becomes double-float pairs in place (both 8 bytes an entry)
+        if ((rc = ensure_df_values(M, s))) return rc;
+        const int64_t n = g.d * (int64_t)ldv;
+        const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 16LL * M->num_sms));
+        df64* W0 = reinterpret_cast<df64*>(V0);
+        {
+            ProfScope ps("to_df", s);
+            to_df_kernel<<<nb, 256, 0, s>>>(V0, W0, n);
+        }
+        MLT_CUDA_TRY(cudaGetLastError());
+        df64* V[2] = {W0, reinterpret_cast<df64*>(V1)};
+        if ((rc = run_steps<df64>(M, plan, g, 0, K, V, M->ws_w.as<df64>(), M->ws_seg.as<df64>(), s))) return rc;
+    } else {
+        double* V[2] = {V0, V1};
+        if ((rc = run_steps<double>(M, plan, g, 0, K, V, M->ws_w.as<double>(), M->ws_seg.as<double>(), s)))
+            return rc;
+    }
     *dots_dev = g.dots;
     return MLT_OK;
 }
@@ -910,6 +1023,27 @@ int spmv_f64(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, const double* x, doubl
     return launch_step<double>(1, a, 8 * M->num_sms, 2 * M->num_sms, M->num_sms, &nb, s);
 }
 
+int ensure_df_values(mlt_matrix* M, cudaStream_t s)
+{
+    auto conv = [&](DevCSR& C, void*& own) -> int {
+        if (C.valdf || !C.val64 || C.nnz == 0) return MLT_OK;
+        df64* p = nullptr;
+        cudaError_t e = pool_malloc((void**)&p, (size_t)C.nnz * sizeof(df64), s);
+        if (e != cudaSuccess) return fail(MLT_ENOMEM, "device allocation (double-float values) failed");
+        const int nb = (int)std::min<int64_t>((C.nnz + 255) / 256, 16LL * M->num_sms);
+        ProfScope ps("to_df", s);
+        to_df_kernel<<<std::max(nb, 1), 256, 0, s>>>(C.val64, p, C.nnz);
+        MLT_CUDA_TRY(cudaGetLastError());
+        own = p;
+        C.valdf = p;
+        return MLT_OK;
+    };
+    int rc = conv(M->A, M->own_val_df);
+    if (rc) return rc;
+    if (M->flags & MLT_GRAM) rc = conv(M->AT, M->own_t_val_df);
+    return rc;
+}
+
 int ensure_fp32_values(mlt_matrix* M, cudaStream_t s)
 {
     auto conv = [&](DevCSR& C, void*& own) -> int {
@@ -935,6 +1069,8 @@ int run_moments_group(mlt_matrix* M, int precision, const MomentPlan& plan, doub
                       uint64_t seed, double* mu_dev, int64_t ld_mu, int* err_flag, cudaStream_t s,
                       bool alloc_only)
 {
+    if (precision == MLT_PREC_DF64)
+        return run_group_df(M, plan, a, b, seed, mu_dev, ld_mu, err_flag, s, alloc_only);
     // FP64: no FP32 steps; FP32: all steps FP32; mixed: FP32 for the first k steps
     int ks = 0;
     if (precision == MLT_PREC_FP32) ks = plan.K;

@@ -318,7 +318,7 @@ int column_norms(const OrthoScratch& w, const double* X, int ld, int cols, int64
 // shape), from the doubling moments: mu_0 = v.v, mu_1 = v.V_1,
 // mu_{2k+2} = 2 V_{k+1}.V_{k+1} - mu_0, mu_{2k+1} = 2 V_{k+1}.V_k - mu_1.
 int quad_forms(mlt_matrix* M, const OrthoScratch& w, double a, double b, const double* c, int n, double* V,
-               double* scratch, int ld, int cols, int64_t d, std::vector<double>& out, cudaStream_t s)
+               double* scratch, int ld, int cols, int64_t d, bool df, std::vector<double>& out, cudaStream_t s)
 {
     out.assign(cols, 0.0);
     if (cols == 0) return MLT_OK;
@@ -328,7 +328,7 @@ int quad_forms(mlt_matrix* M, const OrthoScratch& w, double a, double b, const d
     MLT_CUDA_TRY(cudaMemcpyAsync(mu0.data(), w.norms, cols * sizeof(double), cudaMemcpyDeviceToHost, s));
     const int K = (n + 1) / 2;
     const double* dots_dev = nullptr;
-    if ((rc = moments_block(M, a, b, V, scratch, ld, cols, K, &dots_dev, s))) return rc;
+    if ((rc = moments_block(M, a, b, V, scratch, ld, cols, K, &dots_dev, df, s))) return rc;
     std::vector<double> dots((size_t)K * 2 * cols);
     MLT_CUDA_TRY(cudaMemcpyAsync(dots.data(), dots_dev, dots.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     MLT_CUDA_TRY(cudaStreamSynchronize(s));
@@ -532,9 +532,10 @@ int mlt_hutchpp_estimate(mlt_matrix* m, double a, double b, const double* c, int
         if (s_cols + g_cols < 1) return fail(MLT_EINVAL, "mlt_hutchpp_estimate: s + g must be at least 1");
         if (probe_offset < 0 || probe_offset + s_cols + g_cols > (int64_t)1 << 32)
             return fail(MLT_EINVAL, "mlt_hutchpp_estimate: probe ids must lie in [0, 2^32)");
-        if (precision != MLT_PREC_FP64 && precision != MLT_PREC_FP32)
-            return fail(MLT_EINVAL, "mlt_hutchpp_estimate: precision must be MLT_PREC_FP64 or MLT_PREC_FP32");
-        const bool f32 = precision == MLT_PREC_FP32;
+        if (precision != MLT_PREC_FP64 && precision != MLT_PREC_FP32 && precision != MLT_PREC_DF64)
+            return fail(MLT_EINVAL, "mlt_hutchpp_estimate: precision must be MLT_PREC_FP64, _FP32 or _DF64");
+        const bool f32 = precision != MLT_PREC_FP64;   // the sketch in FP32
+        const bool dfm = precision == MLT_PREC_DF64;   // the moments in double-float pairs
         cudaStream_t s = (cudaStream_t)stream;
         const int64_t d = op_dim(m);
         if (d < 1) return fail(MLT_EINVAL, "mlt_hutchpp_estimate: empty operator");
@@ -591,8 +592,8 @@ int mlt_hutchpp_estimate(mlt_matrix* m, double a, double b, const double* c, int
             for (int k : kept) rank += k;
         }
         std::vector<double> tq, tg;
-        if ((rc = quad_forms(m, w, a, b, c, n, Q, Sb, ls, s_cols, d, tq, s))) return rc;
-        if ((rc = quad_forms(m, w, a, b, c, n, Gb, Sb, lg, g_cols, d, tg, s))) return rc;
+        if ((rc = quad_forms(m, w, a, b, c, n, Q, Sb, ls, s_cols, d, dfm, tq, s))) return rc;
+        if ((rc = quad_forms(m, w, a, b, c, n, Gb, Sb, lg, g_cols, d, dfm, tg, s))) return rc;
         double t1 = 0.0, t2 = 0.0;
         for (double v : tq) t1 += v;
         for (double v : tg) t2 += v;

@@ -382,7 +382,8 @@ int gershgorin_device(mlt_matrix* M, double* lo, double* hi, cudaStream_t s)
 static void free_matrix(mlt_matrix* M)
 {
     void* owned[] = {M->own_rowptr, M->own_col, M->own_val, M->own_val32, M->own_t_rowptr,
-                     M->own_t_col, M->own_t_val, M->own_t_val32, M->plan_A.mem, M->plan_AT.mem};
+                     M->own_t_col, M->own_t_val, M->own_t_val32, M->own_val_df, M->own_t_val_df,
+                     M->plan_A.mem, M->plan_AT.mem};
     for (void* p : owned)
         if (p) cudaFreeAsync(p, 0);   // called with the handle's work finished
     mlt::DevBuf* bufs[] = {&M->ws_v[0], &M->ws_v[1], &M->ws_v2[0], &M->ws_v2[1], &M->ws_w, &M->ws_part, &M->ws_dots,
@@ -426,7 +427,7 @@ int prepare_moment_job(mlt_matrix* m, double a, double b, uint64_t seed, int64_t
     if (nprobes > 0 && (!degree || !mu)) return fail(MLT_EINVAL, "mlt_moments: null degree or mu");
     if (!(a < b) || !std::isfinite(a) || !std::isfinite(b))
         return fail(MLT_EINVAL, "mlt_moments: need finite a < b");
-    if (precision != MLT_PREC_FP64 && precision != MLT_PREC_FP32 &&
+    if (precision != MLT_PREC_FP64 && precision != MLT_PREC_FP32 && precision != MLT_PREC_DF64 &&
         !((precision & 0xFF) == MLT_PREC_MIXED && precision >= 0))
         return fail(MLT_EINVAL, "mlt_moments: unknown precision");
     if (flags & ~MLT_DIRECT) return fail(MLT_EINVAL, "mlt_moments: unknown flags");

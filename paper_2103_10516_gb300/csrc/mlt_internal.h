@@ -60,6 +60,7 @@ struct DevCSR {
     const int32_t* col = nullptr;
     const double* val64 = nullptr;   // null for a pattern matrix
     const float* val32 = nullptr;    // FP32 copy of the values (lazily made)
+    const void* valdf = nullptr;     // double-float copy (df64 pairs, lazily made)
 };
 
 // Fixed work split of one CSR operand for the moment engine (see
@@ -92,6 +93,8 @@ struct mlt_matrix {
     void* own_val32 = nullptr;
     void* own_t_rowptr = nullptr; void* own_t_col = nullptr; void* own_t_val = nullptr;
     void* own_t_val32 = nullptr;
+    void* own_val_df = nullptr;
+    void* own_t_val_df = nullptr;
     // triangle preparation (inside ws_tri; out_col and pairs inside ws_upcol)
     struct {
         int64_t* out_ptr = nullptr;  // row pointer of the degree-oriented out-lists
@@ -163,6 +166,7 @@ int enqueue_moment_job(MomentJob& J, cudaStream_t s);
 int finish_moment_job(MomentJob& J, cudaStream_t s);
 
 int ensure_fp32_values(mlt_matrix* M, cudaStream_t s);
+int ensure_df_values(mlt_matrix* M, cudaStream_t s);
 // FP64 blocks of explicit vectors (row-major, row stride ldv even, columns
 // >= cols zero): Y = p(At) X with P0, P1 as scratch (cheb_kernels.cu), and
 // the doubling moments of a start block V0 (V1 scratch; dots stay on the device).
@@ -171,7 +175,7 @@ int poly_apply_block(mlt_matrix* M, double a, double b, const double* c, int n, 
 int poly_apply_block_f32(mlt_matrix* M, double a, double b, const double* c, int n, const float* X, float* Y,
                          int ldv, int ncols, float* P0, float* P1, cudaStream_t s);
 int moments_block(mlt_matrix* M, double a, double b, double* V0, double* V1, int ldv, int cols, int K,
-                  const double** dots_dev, cudaStream_t s);
+                  const double** dots_dev, bool df, cudaStream_t s);
 int ensure_spmm_plan(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, cudaStream_t s);
 int spmv_f64(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, const double* x, double* y, cudaStream_t s);
 int lanczos_bounds(mlt_matrix* M, int steps, uint64_t seed, double* lo, double* hi, cudaStream_t s);

@@ -22,7 +22,7 @@ MLT_OK, MLT_EINVAL, MLT_ENOMEM, MLT_ECUDA, MLT_ERANGE, MLT_ETIMEOUT = 0, -1, -2,
 MLT_F64, MLT_F32, MLT_PATTERN = 0, 1, 2
 MLT_GRAM, MLT_DEVICE_PTRS = 1, 2
 MLT_FN = {"log": 0, "sqrt": 1, "exp": 2, "inv": 3, "pow": 4, "cube": 5}
-MLT_PREC = {"fp64": 0, "fp32": 1}
+MLT_PREC = {"fp64": 0, "fp32": 1, "df64": 3}
 MLT_DIRECT = 1
 MLT_LOW_CV = 4
 MLT_BOUNDS_GERSHGORIN, MLT_BOUNDS_LANCZOS = 0, 1

@@ -179,3 +179,23 @@ def test_hutchpp_fp32_sketch(L, O):
     assert r.rank == 8
     assert abs(r.t_sketch - ref["t_sketch"]) <= 1e-5 * sc * 8
     assert np.max(np.abs(samples - ref["samples"])) <= 1e-5 * sc * m.nrows
+
+
+def test_hutchpp_df64_moments(L, O):
+    # double-float moments keep the FP64 tolerances of the remainder samples and
+    # the sketch trace (the FP32 sketch only moves span(Q): a full sketch is exact)
+    d = 40
+    g = synth.random_graph(d, 0.2, seed=12)
+    lam = np.linalg.eigvalsh(g.to_dense())
+    a, b = lam[0] - 0.3, lam[-1] + 0.3
+    c = O.cheb_coeffs("exp", a, b, 30)
+    exact = math.fsum(O.cheb_eval(c, (2 * lam - (a + b)) / (b - a)).tolist())
+    with L.Matrix(g) as M:
+        r = L.mlt_hutchpp_estimate(M.handle, a, b, c, 1, 0, d, 3, precision="df64")
+    assert r.rank == d and abs(r.estimate - exact) <= 1e-9 * abs(exact)
+    m = synth.grid_laplacian_2d(12, shift=0.1)
+    c = O.cheb_coeffs("log", 0.1, 8.1, 16)
+    with L.Matrix(m) as M:
+        r0 = L.mlt_hutchpp_estimate(M.handle, 0.1, 8.1, c, 3, 0, 0, 6, precision="df64")   # remainder only
+    mu = O.moments(m, 0.1, 8.1, 3, 0, [16] * 6)
+    assert abs(r0.estimate - float(np.mean(mu @ c))) <= 1e-10 * np.sum(np.abs(c)) * m.nrows

@@ -175,7 +175,7 @@ def test_rejects_malformed_csr(L):
     assert e.value.code == L.MLT_EINVAL
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("fp32", 64 * 2.0 ** -24)])
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("fp32", 64 * 2.0 ** -24), ("df64", TOL64)])
 def test_long_rows_in_segments(L, O, precision, tol):
     # every row of K_300 is longer than a work chunk: segment products are
     # added in order by the second kernel
@@ -262,3 +262,40 @@ def test_autotune_picks_a_width(L, O):
         assert w in (8, 16, 32, 64, 128)
         got = M.moments(0.1, 8.1, 0, 0, [12] * 50)
     assert np.max(np.abs(got - O.moments(m, 0.1, 8.1, 0, 0, [12] * 50))) <= TOL64 * m.nrows
+
+
+# Double-float vectors (about 48 significant bits) keep the FP64 tolerance:
+# their rounding, ~2^-47 of each value per operation over at most a few
+# hundred steps, stays orders of magnitude below 1e-10 * d.
+def test_df64_matches_fp64_tolerance(L, O):
+    m = synth.grid_laplacian_2d(64, shift=0.1)
+    deg = _c1_degrees()
+    with L.Matrix(m) as M:
+        got = M.moments(0.1, 8.1, 0, 0, deg, precision="df64")
+        direct = M.moments(0.1, 8.1, 0, 0, deg[:40], precision="df64", flags=L.MLT_DIRECT)
+    ref = O.moments(m, 0.1, 8.1, 0, 0, deg)
+    assert np.max(np.abs(got - ref)) <= TOL64 * m.nrows
+    assert np.max(np.abs(direct - ref[:40, :direct.shape[1]])) <= TOL64 * m.nrows
+    assert np.all(got[:, 0] == m.nrows)
+    g = synth.rmat_adjacency(12, 16, seed=2)      # pattern, scaled, hub rows in segments
+    sc = 0.02
+    with L.Matrix(g, scale=sc) as M:
+        a, b = M.bounds()
+        got = M.moments(a, b, 4, 9, [128] * 40 + [17] * 9, precision="df64")
+    ref = O.moments(g, a, b, 4, 9, [128] * 40 + [17] * 9, scale=sc)
+    assert np.max(np.abs(got - ref)) <= TOL64 * g.nrows
+    X = synth.sparse_gaussian(700, 240, 0.02, seed=3)   # Gram operator, FP64 values as pairs
+    deg = np.array([64] * 20 + [9] * 13, dtype=np.int32)
+    with L.Matrix(X, gram=True) as M:
+        a, b = M.bounds()
+        got = M.moments(a, b, 5, 0, deg, precision="df64")
+    ref = O.moments(X, a, b, 5, 0, deg, gram=True)
+    assert np.max(np.abs(got - ref)) <= TOL64 * 240
+
+
+def test_df64_mlmc_matches_oracle(L, O):
+    m = synth.grid_laplacian_2d(64, shift=0.1)
+    ref = O.mlmc_fixed(m, "log", 0.1, 8.1, 128, [8, 32, 128], [256, 64, 16], seed=0)
+    with L.Matrix(m) as M:
+        got = M.mlmc("log", 0.1, 8.1, 128, seed=0, levels=[8, 32, 128], m=[256, 64, 16], precision="df64")
+    assert abs(got["estimate"] - ref["estimate"]) <= 1e-10 * np.sum(np.abs(ref["coeffs"])) * m.nrows
