@@ -268,7 +268,7 @@ class Triangles:
     # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
     # from an ncu capture of this workload, per kernel; to be re-taken
     # whenever the kernel changes
-    TRAFFIC = {"tri_pass1": 331.13e6}   # tri_pass2 changed since its capture (it now takes the pairs)
+    TRAFFIC = {"tri_pass1": 331.45e6, "tri_pass2": 333.73e6}
 
     # ours
     def setup(self, mlt, torch, rank):
@@ -880,7 +880,7 @@ class Stencil3D:
         self.nnz = self.csr.nnz
         self.precision = precision or "fp32"
         # DRAM bytes per launch (128 live probes) from an ncu capture of the FP32 step
-        self.TRAFFIC = {"cheb_step": 1.6308e9} if self.precision == "fp32" else {}
+        self.TRAFFIC = {"fp32": {"cheb_step": 1.6308e9}, "df64": {"cheb_step": 2.0957e9}}.get(self.precision, {})
         self.dtype = {"fp32": "f32", "fp64": "f64", "df64": "df64", "mixed": "f32+f64"}[self.precision]
 
     def _prec(self, mlt):
