@@ -39,7 +39,8 @@
 //   pairs   : (class of i, row or slot of i, y32 slot of the huge target)
 // Work split: every row costs kRowCost "units" plus one per entry (all entries
 // in pass 1, out-entries in pass 2); the unit axis is cut into chunks of
-// kChunk units that warps of a persistent grid take from an atomic counter
+// kChunk1 (pass 1) or kChunk2 (pass 2) units that warps of a persistent grid
+// take from an atomic counter
 // (small chunks, so the last ones to finish leave little idle time).  A row of
 // degree <= kLongRow is handled whole by the chunk holding its first unit;
 // consecutive such rows are walked with the row ends of 32 rows at a time held
@@ -64,14 +65,16 @@ constexpr int kZWords = kProbes / 32;   // sign words per row
 constexpr int kSmallDeg = 127;        // y of rows up to this degree fits int8
 constexpr int kMidDeg = 32767;        // ... int16; rows above it keep int32
 constexpr int64_t kRowCost = 4;       // units charged per row on top of its entries
-constexpr int64_t kChunk = 256;       // units per dynamically scheduled chunk
+constexpr int64_t kChunk1 = 512;      // units per dynamically scheduled chunk: pass 1 (and preparation)
+constexpr int64_t kChunk2 = 256;      // ... and pass 2
 constexpr int64_t kLongRow = 1024;    // rows above this degree are cut at chunk edges
 constexpr int kGather = 8;            // gathers each lane keeps in flight (divides 32)
 constexpr unsigned kFull = 0xFFFFFFFFu;
 static_assert(32 % kGather == 0, "a gather batch never crosses a 32-entry column block");
 constexpr int kScanBlock = 1024;      // elements per CTA of the prefix scan
 constexpr int kPass2CtasPerSm = 4;    // pass 2 compiled for four resident CTAs (64 registers)
-static_assert(kLongRow <= kMidDeg && kChunk <= kLongRow, "rows handled whole by pass 1 must be small or mid");
+static_assert(kLongRow <= kMidDeg && kChunk1 <= kLongRow && kChunk2 <= kLongRow,
+              "rows handled whole by the passes must be small or mid");
 
 enum RowClass { kClassSmall = 0, kClassMid = 1, kClassHuge = 2 };
 
@@ -220,14 +223,14 @@ __global__ void scan_apply_kernel(int64_t* __restrict__ x, int64_t n, const int6
     }
 }
 
-// crow[c] = the row whose units hold unit c*kChunk: the largest r with
-// ptr[r] + kRowCost*r <= c*kChunk.
-__global__ void chunk_rows_kernel(const int64_t* __restrict__ ptr, int64_t d, int64_t nch,
+// crow[c] = the row whose units hold unit c*chunk: the largest r with
+// ptr[r] + kRowCost*r <= c*chunk.
+__global__ void chunk_rows_kernel(const int64_t* __restrict__ ptr, int64_t d, int64_t nch, int64_t chunk,
                                   int64_t* __restrict__ crow)
 {
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nch;
          c += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t u = c * kChunk;
+        const int64_t u = c * chunk;
         int64_t lo = 0, hi = d;
         while (hi - lo > 1) {
             const int64_t mid = (lo + hi) >> 1;
@@ -307,7 +310,7 @@ __device__ __forceinline__ void walk_chunk(const int64_t* __restrict__ rowptr, i
                                            const int64_t* __restrict__ crow, int lane, Group group,
                                            LongPart long_part)
 {
-    const int64_t u0 = c * kChunk, u1 = u0 + kChunk;
+    const int64_t u0 = c * kChunk1, u1 = u0 + kChunk1;
     int64_t r = crow[c];
     while (r < d) {
         const int64_t beg = __ldg(rowptr + r);
@@ -838,9 +841,9 @@ __device__ __forceinline__ void store_row(int64_t r, int64_t deg, const int yv[8
 }
 
 // y of a row handled whole by one chunk, from its negative-sign counts.  x1
-// and x2 take int sums: the rows a chunk owns hold at most kChunk + kLongRow
-// entries, so their sum of y^2 <= kLongRow * (kChunk + kLongRow) < 2^31.
-static_assert((int64_t)kLongRow * (kChunk + kLongRow) < (1LL << 31), "int sums of x2 over one chunk");
+// and x2 take int sums: the rows a chunk owns hold at most kChunk1 + kLongRow
+// entries, so their sum of y^2 <= kLongRow * (kChunk1 + kLongRow) < 2^31.
+static_assert((int64_t)kLongRow * (kChunk1 + kLongRow) < (1LL << 31), "int sums of x2 over one chunk");
 __device__ __forceinline__ void finish_pass1_row(int64_t r, int deg, int cnt[8], uint2 own,
                                                  const int32_t* __restrict__ bslot, uint2* __restrict__ y8,
                                                  uint4* __restrict__ y16, int32_t* __restrict__ y32, int lane,
@@ -881,7 +884,7 @@ __global__ void __launch_bounds__(kTriThreads) tri_pass1_kernel(
     const uint2* zb2 = reinterpret_cast<const uint2*>(zb);
     const int lane = threadIdx.x & 31;
     for (int64_t c = next_chunk(counter, lane); c < nch; c = next_chunk(counter, lane)) {
-        const int64_t u0 = c * kChunk, u1 = u0 + kChunk;
+        const int64_t u0 = c * kChunk1, u1 = u0 + kChunk1;
         int64_t r = crow[c];
         int cx1[8] = {0, 0, 0, 0, 0, 0, 0, 0}, cx2[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // this chunk's rows
         while (r < d) {
@@ -1128,7 +1131,7 @@ __global__ void __launch_bounds__(kTriThreads, kPass2CtasPerSm) tri_pass2_kernel
     long long x3[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t c = next_chunk(counter, lane); c < nch; c = next_chunk(counter, lane)) {
-        const int64_t u0 = c * kChunk, u1 = u0 + kChunk;
+        const int64_t u0 = c * kChunk2, u1 = u0 + kChunk2;
         int64_t r = crow[c];
         while (r < d) {
             const int64_t beg = __ldg(out_ptr + r);
@@ -1207,7 +1210,9 @@ int tri_prepare(mlt_matrix* M, cudaStream_t s)
     if (M->tri_state < 0) return fail(M->tri_state, "matrix is not a valid triangle-counting input");
     const int64_t d = M->A.nrows;
     const int64_t nnz = M->A.nnz;
-    const int64_t nch1 = std::max<int64_t>(1, (nnz + kRowCost * d + kChunk - 1) / kChunk);
+    const int64_t nch1 = std::max<int64_t>(1, (nnz + kRowCost * d + kChunk1 - 1) / kChunk1);
+    // pass 2's chunks cover the out-lists, at most nnz entries
+    const int64_t nch2max = std::max<int64_t>(1, (nnz + kRowCost * d + kChunk2 - 1) / kChunk2);
     int occ1 = 0, occ2 = 0, occc = 0, occf = 0;
     MLT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, tri_pass1_kernel, kTriThreads, 0));
     MLT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, tri_pass2_kernel, kTriThreads, 0));
@@ -1216,16 +1221,17 @@ int tri_prepare(mlt_matrix* M, cudaStream_t s)
     const size_t dd = (size_t)std::max<int64_t>(d, 1);
     const int64_t nsb = (d + kScanBlock - 1) / kScanBlock;
     int rc;
-    // out_ptr[d+1], crow1[nch1], crow2[nch1], scan sums[nsb+1]; nsmall, bslot,
-    // longlist, deg32 [d] and the fill cursors [2d]; counters
-    if ((rc = M->ws_tri.ensure((dd + 1) * 8 + 2 * (size_t)nch1 * 8 + (size_t)(nsb + 1) * 8 + dd * 4 * 6 + 1024,
+    // out_ptr[d+1], crow1[nch1], crow2[nch2max], scan sums[nsb+1]; nsmall,
+    // bslot, longlist, deg32 [d] and the fill cursors [2d]; counters
+    if ((rc = M->ws_tri.ensure((dd + 1) * 8 + (size_t)(nch1 + nch2max) * 8 + (size_t)(nsb + 1) * 8 + dd * 4 * 6 +
+                                   1024,
                                s)))
         return rc;
     char* base = M->ws_tri.as<char>();
     int64_t* out_ptr = reinterpret_cast<int64_t*>(base);
     int64_t* crow1 = out_ptr + dd + 1;
     int64_t* crow2 = crow1 + nch1;
-    int64_t* bsum = crow2 + nch1;
+    int64_t* bsum = crow2 + nch2max;
     int32_t* nsmall = reinterpret_cast<int32_t*>(bsum + nsb + 1);
     int32_t* bslot = nsmall + dd;
     int32_t* longlist = bslot + dd;
@@ -1245,7 +1251,7 @@ int tri_prepare(mlt_matrix* M, cudaStream_t s)
         tri_degrees_kernel<<<gd, 256, 0, s>>>(M->A.rowptr, d, deg32, bslot, longlist, out_ptr, nsmall, cur,
                                               counters);
         const int g1 = (int)std::min<int64_t>((nch1 + 255) / 256, 16LL * M->num_sms);
-        chunk_rows_kernel<<<std::max(g1, 1), 256, 0, s>>>(M->A.rowptr, d, nch1, crow1);
+        chunk_rows_kernel<<<std::max(g1, 1), 256, 0, s>>>(M->A.rowptr, d, nch1, kChunk1, crow1);
         tri_classify_kernel<<<gridc, kTriThreads, 0, s>>>(M->A.rowptr, M->A.col, deg32, d, nch1, crow1, out_ptr,
                                                           nsmall, counters, bound, chunk_ctr + 2);
     }
@@ -1281,7 +1287,7 @@ int tri_prepare(mlt_matrix* M, cudaStream_t s)
     if ((rc = M->ws_upcol.ensure(col_bytes + (size_t)std::max<int64_t>(npairs, 1) * sizeof(int4), s))) return rc;
     int32_t* out_col = M->ws_upcol.as<int32_t>();
     int4* pairs = reinterpret_cast<int4*>(M->ws_upcol.as<char>() + col_bytes);
-    const int64_t nch2 = std::max<int64_t>(1, (nnz_out + kRowCost * d + kChunk - 1) / kChunk);
+    const int64_t nch2 = std::max<int64_t>(1, (nnz_out + kRowCost * d + kChunk2 - 1) / kChunk2);
     {
         ProfScope ps("tri_fill_out", s);
         tri_fill_kernel<<<gridf, kTriThreads, 0, s>>>(M->A.rowptr, M->A.col, deg32, d, nch1, crow1, out_ptr, nsmall,
@@ -1292,7 +1298,7 @@ int tri_prepare(mlt_matrix* M, cudaStream_t s)
     {
         ProfScope ps("tri_chunk_rows", s);
         const int g2 = (int)std::min<int64_t>((nch2 + 255) / 256, 16LL * M->num_sms);
-        chunk_rows_kernel<<<std::max(g2, 1), 256, 0, s>>>(out_ptr, d, nch2, crow2);
+        chunk_rows_kernel<<<std::max(g2, 1), 256, 0, s>>>(out_ptr, d, nch2, kChunk2, crow2);
     }
     MLT_CUDA_TRY(cudaGetLastError());
     M->tri.out_ptr = out_ptr;
