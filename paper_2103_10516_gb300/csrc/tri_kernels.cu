@@ -68,7 +68,8 @@ constexpr int64_t kRowCost = 4;       // units charged per row on top of its ent
 constexpr int64_t kChunk1 = 512;      // units per dynamically scheduled chunk: pass 1 (and preparation)
 constexpr int64_t kChunk2 = 256;      // ... and pass 2
 constexpr int64_t kLongRow = 1024;    // rows above this degree are cut at chunk edges
-constexpr int kGather = 8;            // gathers each lane keeps in flight (divides 32)
+constexpr int kGather = 4;            // pass-1 short rows: gathers in flight per batch (divides 32);
+                                      // most such rows have a few entries, so wider batches idle
 constexpr unsigned kFull = 0xFFFFFFFFu;
 static_assert(32 % kGather == 0, "a gather batch never crosses a 32-entry column block");
 constexpr int kScanBlock = 1024;      // elements per CTA of the prefix scan
