@@ -63,16 +63,21 @@ template <> struct Lanes<df64> { static constexpr int N = 2; };     // 16-byte v
 
 template <typename T, int N> struct alignas(sizeof(T) * N) Pack { T v[N]; };
 
-// A thread's running dot product.
+// A thread's running dot product.  The kernels keep these in shared memory
+// (one slot per thread, see DotSlots): held in registers beside a row's
+// gathers they pushed the step kernel past the six-CTA register budget, and
+// the spilled copies went through L1 to L2.
 template <typename T> struct DotAcc;
 template <> struct DotAcc<double> {
-    double s = 0.0;
+    double s;
+    __device__ __forceinline__ void clear() { s = 0.0; }
     __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
     __device__ __forceinline__ void add(double x) { s += x; }
     __device__ __forceinline__ double value() const { return s; }
 };
 template <> struct DotAcc<float> {
-    float s = 0.0f, c = 0.0f;   // Kahan: s - c is the running sum
+    float s, c;   // Kahan: s - c is the running sum
+    __device__ __forceinline__ void clear() { s = c = 0.0f; }
     __device__ __forceinline__ void add(float x)
     {
         const float y = x - c;
@@ -90,11 +95,18 @@ template <> struct DotAcc<float> {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 template <> struct DotAcc<df64> {
-    df64 s = df64(0);
+    df64 s;
+    __device__ __forceinline__ void clear() { s = df64(0); }
     __device__ __forceinline__ void add_prod(df64 a, df64 b) { s = a * b + s; }
     __device__ __forceinline__ void add(df64 x) { s = s + x; }
     __device__ __forceinline__ double value() const { return df_to_double(s); }
 };
+
+// The CTA's running dots: [0] V_{k+1}.V_{k+1} (unused in direct mode), [1]
+// V_{k+1}.V_k or z.V_{k+1}; slot [q][tid] for the thread's column c0 + q, so a
+// warp's accesses are consecutive.
+template <typename T>
+using DotSlots = DotAcc<T>[2][Lanes<T>::N][kThreads];
 
 // A matrix value through the read-only cache.
 template <typename T>
@@ -222,7 +234,7 @@ __device__ __forceinline__ void row_product(const StepArgs<T>& a, const Lane<T, 
 // V_{k+1}[r] from acc = (A V_k)[r], and the fused dot products.
 template <typename T, bool CL>
 __device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0, const T (&acc)[Lanes<T>::N],
-                                         DotAcc<T> (&s_self)[Lanes<T>::N], DotAcc<T> (&s_cross)[Lanes<T>::N])
+                                         DotSlots<T>& dots)
 {
     constexpr int N = Lanes<T>::N;
     using P = Pack<T, N>;
@@ -252,43 +264,51 @@ __device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0
         for (int q = 0; q < N; ++q) out.v[q] = T(2) * (a.alpha * acc[q] + a.beta * xc.v[q]) - xp.v[q];
     }
     *reinterpret_cast<P*>(a.vprev_out + off) = out;
+    const int tid = threadIdx.x;
     if (!a.direct) {
 #pragma unroll
         for (int q = 0; q < N; ++q) {
-            s_self[q].add_prod(out.v[q], out.v[q]);
-            s_cross[q].add_prod(out.v[q], xc.v[q]);
+            DotAcc<T> s0 = dots[0][q][tid], s1 = dots[1][q][tid];
+            s0.add_prod(out.v[q], out.v[q]);
+            s1.add_prod(out.v[q], xc.v[q]);
+            dots[0][q][tid] = s0;
+            dots[1][q][tid] = s1;
         }
     } else {
 #pragma unroll
         for (int q = 0; q < N; ++q) {
             if (c0 + q >= a.B) break;
             const bool neg = probe_negative(a.seedmix, (uint64_t)a.ids[c0 + q], (uint64_t)r);
-            s_cross[q].add(neg ? -out.v[q] : out.v[q]);
+            DotAcc<T> s1 = dots[1][q][tid];
+            s1.add(neg ? -out.v[q] : out.v[q]);
+            dots[1][q][tid] = s1;
         }
+    }
+}
+
+// Zero the thread's dot slots (each thread only ever touches its own).
+template <typename T>
+__device__ __forceinline__ void clear_dots(DotSlots<T>& dots)
+{
+#pragma unroll
+    for (int q = 0; q < Lanes<T>::N; ++q) {
+        dots[0][q][threadIdx.x].clear();
+        dots[1][q][threadIdx.x].clear();
     }
 }
 
 // CTA reduction in a fixed order: column c collects the groups of this CTA
 // whose column chunk holds it, in group order.
 template <typename T, int G>
-__device__ __forceinline__ void cta_partials(const StepArgs<T>& a, const Lane<T, G>& L,
-                                             const DotAcc<T> (&s_self)[Lanes<T>::N],
-                                             const DotAcc<T> (&s_cross)[Lanes<T>::N])
+__device__ __forceinline__ void cta_partials(const StepArgs<T>& a, const Lane<T, G>& L, const DotSlots<T>& dots)
 {
     constexpr int N = Lanes<T>::N;
-    __shared__ double red[2][kThreads * N];
-    const int tid = threadIdx.x;
-#pragma unroll
-    for (int q = 0; q < N; ++q) {
-        red[0][tid * N + q] = s_self[q].value();
-        red[1][tid * N + q] = s_cross[q].value();
-    }
     __syncthreads();
     const int gpb = kThreads / G;
     const int ncols = a.nvec * N;
     double* part = a.partials + (size_t)blockIdx.x * 2 * a.ldv;
     const long long g0 = (long long)blockIdx.x * gpb;
-    for (int c = tid; c < ncols; c += kThreads) {
+    for (int c = threadIdx.x; c < ncols; c += kThreads) {
         const int v = c / N, q = c % N;
         const int ch = v / G, gl = v % G;
         double s0 = 0.0, s1 = 0.0;
@@ -296,8 +316,8 @@ __device__ __forceinline__ void cta_partials(const StepArgs<T>& a, const Lane<T,
             const long long gglob = g0 + g;
             if (gglob >= L.ncls * a.nchunks || (int)(gglob % a.nchunks) != ch) continue;
             const int t = g * G + gl;
-            s0 += red[0][t * N + q];
-            s1 += red[1][t * N + q];
+            s0 += dots[0][q][t].value();
+            s1 += dots[1][q][t].value();
         }
         part[c] = s0;
         part[a.ldv + c] = s1;
@@ -309,7 +329,8 @@ __global__ void __launch_bounds__(kThreads, kStepCtasPerSm) cheb_step_kernel(Ste
 {
     constexpr int N = Lanes<T>::N;
     const Lane<T, G> L(a);
-    DotAcc<T> s_self[N], s_cross[N];
+    __shared__ DotSlots<T> dots;
+    if constexpr (!CL) clear_dots<T>(dots);
 
     if (L.active) {
         const int64_t nitems = a.nch + a.nseg;
@@ -317,15 +338,18 @@ __global__ void __launch_bounds__(kThreads, kStepCtasPerSm) cheb_step_kernel(Ste
             T acc[N];
             if (it < a.nch) {
                 const int64_t u0 = it * a.Uc, u1 = u0 + a.Uc;
-                for (int64_t r = __ldg(a.crow + it); r < a.nrows; ++r) {
-                    const int64_t beg = __ldg(a.rowptr + r);
+                int64_t r = __ldg(a.crow + it);
+                int64_t beg = r < a.nrows ? __ldg(a.rowptr + r) : 0;
+                for (; r < a.nrows; ++r) {
                     const int64_t pr = beg + kRowCost * r;
                     if (pr >= u1) break;
-                    if (pr < u0) continue;
-                    const int64_t end = __ldg(a.rowptr + r + 1);
-                    if (end - beg > a.Ul) continue;          // long row: done by segments
-                    row_product<T, G>(a, L, beg, end, acc);
-                    if (L.vok) epilogue<T, CL>(a, r, L.c0, acc, s_self, s_cross);
+                    const int64_t end = __ldg(a.rowptr + r + 1);   // the next row's start
+                    // rows before u0 belong to the previous chunk; long rows are done by segments
+                    if (pr >= u0 && end - beg <= a.Ul) {
+                        row_product<T, G>(a, L, beg, end, acc);
+                        if (L.vok) epilogue<T, CL>(a, r, L.c0, acc, dots);
+                    }
+                    beg = end;
                 }
             } else {
                 const int64_t sidx = it - a.nch;
@@ -342,8 +366,8 @@ __global__ void __launch_bounds__(kThreads, kStepCtasPerSm) cheb_step_kernel(Ste
             }
         }
     }
-    if (a.mode >= 2) return;
-    cta_partials<T, G>(a, L, s_self, s_cross);
+    if (CL || a.mode >= 2) return;
+    cta_partials<T, G>(a, L, dots);
 }
 
 // Long rows: add the segment products in segment order, then the recurrence.
@@ -353,7 +377,8 @@ __global__ void __launch_bounds__(kThreads) cheb_long_kernel(StepArgs<T> a)
     constexpr int N = Lanes<T>::N;
     using P = Pack<T, N>;
     const Lane<T, G> L(a);
-    DotAcc<T> s_self[N], s_cross[N];
+    __shared__ DotSlots<T> dots;
+    if constexpr (!CL) clear_dots<T>(dots);
     if (L.active) {
         for (int64_t i = L.gcls; i < a.nlong; i += L.ncls) {
             if (!L.vok) continue;
@@ -365,11 +390,11 @@ __global__ void __launch_bounds__(kThreads) cheb_long_kernel(StepArgs<T> a)
 #pragma unroll
                 for (int q = 0; q < N; ++q) acc[q] += p.v[q];
             }
-            epilogue<T, CL>(a, a.long_rows[i], L.c0, acc, s_self, s_cross);
+            epilogue<T, CL>(a, a.long_rows[i], L.c0, acc, dots);
         }
     }
-    if (a.mode >= 2) return;
-    cta_partials<T, G>(a, L, s_self, s_cross);
+    if (CL || a.mode >= 2) return;
+    cta_partials<T, G>(a, L, dots);
 }
 
 struct ReduceArgs {
