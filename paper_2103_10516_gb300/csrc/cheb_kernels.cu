@@ -51,9 +51,10 @@ constexpr int kSlots = 16;          // steps whose partials are buffered before 
 constexpr int64_t kRowCost = 4;     // units charged per row (the epilogue) on top of its entries
 constexpr int64_t kChunksPerSm = 1024;  // work chunks per SM in the split of an operand
 constexpr int64_t kLongRow = 128;   // rows above max(Uc, this) are cut into segments
-// Resident CTAs per SM the step kernel is compiled for (40 registers): more
-// rows in flight hide more gather latency than the few registers it spills
-// cost (measured against 4 and 5 on the 3D stencil, R-MAT and the 2D grid).
+// Resident CTAs per SM the step kernel is compiled for (40 registers, with
+// the running dots in shared memory so that nothing spills): more rows in
+// flight hide more gather latency than the wider budgets of 4 or 5 CTAs buy
+// (measured on the 3D stencil, R-MAT and the 2D grid).
 constexpr int kStepCtasPerSm = 6;
 
 template <typename T> struct Lanes;
