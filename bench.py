@@ -880,7 +880,7 @@ class Stencil3D:
         self.nnz = self.csr.nnz
         self.precision = precision or "fp32"
         # DRAM bytes per launch (128 live probes) from an ncu capture of the FP32 step
-        self.TRAFFIC = {"fp32": {"cheb_step": 1.5867e9}}.get(self.precision, {})
+        self.TRAFFIC = {"fp32": {"cheb_step": 1.5867e9}, "df64": {"cheb_step": 2.1287e9}}.get(self.precision, {})
         self.dtype = {"fp32": "f32", "fp64": "f64", "df64": "df64", "mixed": "f32+f64"}[self.precision]
 
     def _prec(self, mlt):
