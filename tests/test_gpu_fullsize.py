@@ -92,5 +92,5 @@ def test_estrada_rmat22_fp32_full_size(L, O):
         got = M.moments(-10.0, 10.0, 0, 0, deg, precision="fp32")
     tol = _tol32(128, g.nrows)
     _check_all(got, deg, g.nrows, tol)
-    _check_sampled(O, g, -10.0, 10.0, 0, 0, got, [(200, 2)], tol, scale=scale)
+    _check_sampled(O, g, -10.0, 10.0, 0, 0, got, [(255, 2)], tol, scale=scale)
 
