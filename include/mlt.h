@@ -317,9 +317,12 @@ int mlt_poly_apply(mlt_matrix* m, double a, double b, const double* c, int n,
  * p = sum_{k=0..n} c[k] T_k as in mlt_poly_apply.  With S the s Rademacher
  * probes of ids probe_offset .. probe_offset + s - 1 and G the g probes that
  * follow (the generator of mlt_moments):
- *   Q         orthonormal basis of p(At) S: classical Gram-Schmidt with every
- *             column projected twice; a column left with at most 1e-10 of its
- *             norm is dependent and dropped (rank counts those kept);
+ *   Q         orthonormal basis of p(At) S: Cholesky QR applied twice when
+ *             s <= 64 and both Gram matrices factor (every pivot above 1e-13
+ *             of its diagonal entry); otherwise classical Gram-Schmidt with
+ *             every column projected twice, where a column left with at most
+ *             1e-10 of its norm is dependent and dropped (rank counts the
+ *             columns kept);
  *   t_sketch  tr(Q^T p(At) Q), from the doubling moments of Q's columns;
  *   samples   q_i = g_i'^T p(At) g_i' with g_i' = (I - Q Q^T) g_i;
  *   estimate  t_sketch + t_rest, t_rest the mean of the q_i, and std_error
