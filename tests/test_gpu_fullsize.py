@@ -3,12 +3,11 @@ the same launch configuration (probe count, degree, precision, autotuned
 probe-group width), on sampled outputs the oracle computes one by one, and
 on properties that hold for every output.
 
-Tolerance.  FP32 vectors: every step rounds V to 2^-24 of its size, and the doubled
-moments carry |2 V_k.V_k| <= 2d, so after k steps the error is at most about
-k * 2^-24 * 2d times a small growth factor; (deg/2) * 2^-24 * d with a factor
-of two to spare, i.e. max(64, deg/2) * 2^-24 * d, bounds it.  (Emulating the
-FP32 recurrence on the CPU gives 0.1 of that on the 3D stencil and 0.02 on the
-Gram operator and the scaled R-MAT graph.)  Every moment of a spectrum inside
+Tolerance.  FP32 vectors: each of the deg/2 steps rounds V to 2^-24 of its
+size and these errors add up along the recurrence; the tests allow
+max(64, deg/2) * 2^-24 * d, the bound the smaller FP32 tests use up to degree
+128.  Emulating the FP32 recurrence on the CPU gives 0.1 of it on the 3D
+stencil and 0.02 on the Gram operator and the scaled R-MAT graph.  Every moment of a spectrum inside
 [a, b] also satisfies |mu_j| <= d.
 
 The sampled probes stay at low degree: the oracle sums in long double, which is
