@@ -610,6 +610,21 @@ def gershgorin(m):
     return lo, hi
 
 
+def interval(m, scale=1.0, gram=False):
+    """The default spectrum interval [a, b] of the operator, on the host: the
+    Gershgorin discs of scale * A, or [0, s^2 ||X||_1 ||X||_inf] for A = X^T X
+    with X = s * m, since ||X||_2^2 <= ||X||_1 ||X||_inf (Section 2.2 asks only
+    for a rough estimate of the extreme eigenvalues)."""
+    if gram:
+        v = np.ones(m.nnz) if m.val is None else np.abs(np.asarray(m.val, dtype=np.float64))
+        rows = np.repeat(np.arange(m.nrows), np.diff(np.asarray(m.rowptr)))
+        r = np.bincount(rows, weights=v, minlength=m.nrows).max() if m.nnz else 0.0
+        c = np.bincount(np.asarray(m.col), weights=v, minlength=m.ncols).max() if m.nnz else 0.0
+        return 0.0, scale * scale * float(r) * float(c)
+    lo, hi = gershgorin(m)
+    return (scale * lo, scale * hi) if scale >= 0 else (scale * hi, scale * lo)
+
+
 # ---------------------------------------------------------------------------
 # Learned coarse level: a 16 -> 128 -> 128 -> 1 ReLU network trained by mean
 # squared error (a project addition; its nearest relative in the paper is the

@@ -56,9 +56,9 @@ def test_auto_levels(L, O, mode, target, max_levels):
 
 def test_nuclear_norm_gram(L, O):
     X = synth.sparse_gaussian(400, 150, 0.03, seed=1)
+    _, b = O.interval(X, gram=True)
+    a = 1e-3 * b
     with L.Matrix(X, gram=True) as M:
-        a, b = M.bounds()
-        a = 1e-3 * b
         got = M.mlmc("sqrt", a, b, 40, seed=0, levels=[4, 12, 40], m=[40, 12, 6])
     ref = O.mlmc_fixed(X, "sqrt", a, b, 40, [4, 12, 40], [40, 12, 6], seed=0, gram=True)
     tol = 1e-10 * np.sum(np.abs(ref["coeffs"])) * 150
@@ -101,8 +101,7 @@ def test_low_cv_mlmc_matches_oracle(L, O):
     # levels, counts, estimates and level variances as the oracle, and no level
     # whose residual variance exceeds its plain variance (least squares)
     m = synth.random_symmetric(3000, 0.002, seed=11, diag_shift=1.0)
-    with L.Matrix(m) as M0:
-        lo, hi = M0.bounds()
+    lo, hi = O.interval(m)
     ref = O.mlmc_fixed(m, "exp", lo, hi, 24, [4, 24], [300, 40], seed=5, low_cv=True)
     plain = O.mlmc_fixed(m, "exp", lo, hi, 24, [4, 24], [300, 40], seed=5)
     with L.Matrix(m) as M:

@@ -75,9 +75,10 @@ def test_many_groups(L, O):
 def test_gram_operator(L, O):
     X = synth.sparse_gaussian(700, 240, 0.02, seed=3)
     deg = np.array([64] * 20 + [9] * 13, dtype=np.int32)
+    a, b = O.interval(X, gram=True)          # host interval: no oracle input from the GPU
     with L.Matrix(X, gram=True) as M:
-        a, b = M.bounds()
-        assert a == 0.0 and b > 0
+        ga, gb = M.bounds()
+        assert ga == 0.0 and gb > 0
         got = M.moments(a, b, 5, 0, deg)
     ref = O.moments(X, a, b, 5, 0, deg, gram=True)
     assert np.max(np.abs(got - ref)) <= TOL64 * 240
@@ -86,11 +87,11 @@ def test_gram_operator(L, O):
 def test_pattern_with_scale(L, O):
     g = synth.rmat_adjacency(10, 8, seed=2)
     sc = 0.05
+    a, b = O.interval(g, scale=sc)
     with L.Matrix(g, scale=sc) as M:
-        a, b = M.bounds()
+        ga, gb = M.bounds()                   # the library's Gershgorin interval, checked
         got = M.moments(a, b, 4, 9, [30] * 40)
-    ra, rb = O.gershgorin(g)
-    assert abs(a - ra * sc) < 1e-12 and abs(b - rb * sc) < 1e-12
+    assert abs(ga - a) < 1e-12 and abs(gb - b) < 1e-12
     ref = O.moments(g, a, b, 4, 9, [30] * 40, scale=sc)
     assert np.max(np.abs(got - ref)) <= TOL64 * g.nrows
 
@@ -180,8 +181,8 @@ def test_long_rows_in_segments(L, O, precision, tol):
     # every row of K_300 is longer than a work chunk: segment products are
     # added in order by the second kernel
     g = synth.complete_graph(300)
+    a, b = O.interval(g, scale=1.0 / 300)
     with L.Matrix(g, scale=1.0 / 300) as M:
-        a, b = M.bounds()
         got = M.moments(a, b, 6, 0, [25, 10, 3], precision=precision)
     ref = O.moments(g, a, b, 6, 0, [25, 10, 3], scale=1.0 / 300)
     assert np.max(np.abs(got - ref)) <= tol * g.nrows
@@ -279,15 +280,15 @@ def test_df64_matches_fp64_tolerance(L, O):
     assert np.all(got[:, 0] == m.nrows)
     g = synth.rmat_adjacency(12, 16, seed=2)      # pattern, scaled, hub rows in segments
     sc = 0.02
+    a, b = O.interval(g, scale=sc)
     with L.Matrix(g, scale=sc) as M:
-        a, b = M.bounds()
         got = M.moments(a, b, 4, 9, [128] * 40 + [17] * 9, precision="df64")
     ref = O.moments(g, a, b, 4, 9, [128] * 40 + [17] * 9, scale=sc)
     assert np.max(np.abs(got - ref)) <= TOL64 * g.nrows
     X = synth.sparse_gaussian(700, 240, 0.02, seed=3)   # Gram operator, FP64 values as pairs
     deg = np.array([64] * 20 + [9] * 13, dtype=np.int32)
+    a, b = O.interval(X, gram=True)
     with L.Matrix(X, gram=True) as M:
-        a, b = M.bounds()
         got = M.moments(a, b, 5, 0, deg, precision="df64")
     ref = O.moments(X, a, b, 5, 0, deg, gram=True)
     assert np.max(np.abs(got - ref)) <= TOL64 * 240

@@ -274,3 +274,25 @@ def test_low_cv_mlmc_unbiased_and_not_worse(O):
         cv = O.mlmc_fixed(g, "exp", a, b, 12, [4, 12], [200, 50], seed=seed, low_cv=True)
         assert cv["level_var"][0] * 197 <= plain["level_var"][0] * 199
         assert abs(cv["estimate"] - exact) < 5 * cv["stderr"]
+
+
+def test_interval_contains_the_spectrum(O):
+    # Gershgorin of scale * A, and [0, s^2 ||X||_1 ||X||_inf] for X^T X: both
+    # contain every eigenvalue (dense eigvalsh), and the Gershgorin form is the
+    # discs' extreme ends
+    cases = [(synth.grid_laplacian_2d(12, shift=0.1), 1.0), (synth.rmat_adjacency(8, 8, seed=2), 0.05),
+             (synth.random_symmetric(60, 0.1, seed=4, diag_shift=1.5), -0.5)]
+    for m, sc in cases:
+        a, b = O.interval(m, scale=sc)
+        lam = np.linalg.eigvalsh(sc * m.to_dense())
+        assert a <= lam[0] + 1e-12 and lam[-1] <= b + 1e-12
+        D = sc * m.to_dense()
+        r = np.sum(np.abs(D), axis=1) - np.abs(np.diag(D))
+        assert abs(a - np.min(np.diag(D) - r)) < 1e-12 and abs(b - np.max(np.diag(D) + r)) < 1e-12
+    X = synth.sparse_gaussian(90, 40, 0.1, seed=6)
+    for sc in (1.0, 0.3):
+        a, b = O.interval(X, scale=sc, gram=True)
+        D = sc * X.to_dense()
+        lam = np.linalg.eigvalsh(D.T @ D)
+        assert a == 0.0 and lam[-1] <= b
+        assert abs(b - np.abs(D).sum(axis=1).max() * np.abs(D).sum(axis=0).max()) < 1e-9 * b
