@@ -183,7 +183,9 @@ int mlt_cheb_coeffs(int fn, double p, double a, double b, int n, double* c);
  *   degree : host int32[nprobes], each 0..MLT_MAX_DEGREE.
  *   mu     : host or device double[nprobes * ld_mu], row p = probe p;
  *            entries j > degree[p] are set to 0.  ld_mu >= max degree + 1.
- *   precision: MLT_PREC_FP64 or MLT_PREC_FP32; flags: 0 or MLT_DIRECT.
+ *   precision: MLT_PREC_FP64, MLT_PREC_FP32, MLT_PREC_MIXED_AT(k) or
+ *              MLT_PREC_DF64 (see their definitions above); flags: 0 or
+ *              MLT_DIRECT.
  * Errors: MLT_EINVAL (a >= b, bad sizes, ld_mu too small), MLT_ENOMEM,
  * MLT_ECUDA.  Moments with |mu_j| > d (1 + 1e-6), impossible when the spectrum
  * lies in [a, b], give MLT_ERANGE after the results are written.
@@ -281,6 +283,62 @@ void mlt_mlmc_default_params(mlt_mlmc_params* p);
 int mlt_mlmc_estimate(mlt_matrix* m, const mlt_mlmc_params* p, mlt_mlmc_result* r);
 
 /*
+ * The host-side steps of mlt_mlmc_estimate, one by one, for callers that
+ * spread a multilevel estimate over several processes or GPUs (the probes are
+ * independent samples, Section 4, Eq. multiEstimator): one process runs the
+ * pilot and the level selection, every process computes moments and band
+ * samples for its own probe ids, and the samples, gathered in probe-id order,
+ * are combined.  mlt_mlmc_estimate calls the same routines, so with the same
+ * moments the combination is the same to the last bit.  None of these calls
+ * touches a GPU; all arrays are host memory.
+ *
+ * mlt_pilot_variances (Section 3.2.1): V[lo * (n+1) + hi], 0 <= lo < hi <= n,
+ *   is the sample variance (divisor m_pilot - 1) over the m_pilot moment rows
+ *   of Q_{lo,hi} = sum_{j=lo+1..hi} c_j mu_j (Eq. def:qlevels); every other
+ *   entry is 0, and all entries are 0 when m_pilot < 2.  mu: m_pilot rows of
+ *   ld_mu >= n+1 doubles (mu_0..mu_n first); V: (n+1)^2 doubles.  Errors:
+ *   MLT_EINVAL (null pointers, n outside [1, MLT_MAX_DEGREE], ld_mu < n+1).
+ */
+int mlt_pilot_variances(const double* c, int n, const double* mu, int64_t ld_mu, int64_t m_pilot, double* V);
+
+/*
+ * mlt_select_levels: the levels l_1 < ... < l_L = n of the dynamic programme
+ *   of Theorem levels (Eq. costrecurrence) on the variance table V of
+ *   mlt_pilot_variances, and their sample counts
+ *   m_k = max(1, ceil(mu sqrt(V_k / C_k))) (Eqs. optSamples, optMu; budget
+ *   or variance mode, cost model as in mlt_mlmc_params).  With m_pilot > 0 the
+ *   top level must be recommended at least m_pilot samples and gets at least
+ *   that many (the pilot rows are reused there, Section 3.2.1); max_levels > 0
+ *   caps the number of levels.  levels, m: arrays of at least n+1 entries
+ *   (L <= n+1); *nlevels receives L.  Errors: MLT_EINVAL (bad sizes, mode,
+ *   cost model, a non-positive target, a negative or non-finite V entry).
+ */
+int mlt_select_levels(const double* V, int n, int cost_model, int m_pilot, int mode, double target,
+                      int max_levels, int32_t* levels, int64_t* m, int* nlevels);
+
+/*
+ * mlt_band_samples: q[p] = sum_{j=lo+1..hi} c_j mu[p * ld_mu + j] for
+ *   p < nprobes (Eq. def:qlevels; lo = -1 starts the first band at c_0 mu_0),
+ *   summed left to right.  Errors: MLT_EINVAL (null pointers with
+ *   nprobes > 0, not -1 <= lo < hi <= MLT_MAX_DEGREE, ld_mu < hi + 1).
+ */
+int mlt_band_samples(const double* c, int lo, int hi, const double* mu, int64_t ld_mu, int64_t nprobes,
+                     double* q);
+
+/*
+ * mlt_mlmc_combine: Eq. multiEstimator from the samples of each level,
+ *   concatenated level by level (m[0] samples of level 0 first), each level's
+ *   samples in probe-id order (pilot rows first on a level that reuses them):
+ *   estimate = sum_k mean_k, std_error = sqrt(sum_k var_k / m_k), var_k with
+ *   divisor m_k - 1 (NaN when m_k = 1).  Fills estimate, std_error, nlevels,
+ *   levels, m, level_mean and level_var of r; probes and matvecs are set to 0
+ *   (they depend on how the samples were drawn).  Errors: MLT_EINVAL (null
+ *   pointers, nlevels outside [1, MLT_MAX_LEVELS], some m[k] < 1).
+ */
+int mlt_mlmc_combine(int nlevels, const int32_t* levels, const int64_t* m, const double* samples,
+                     mlt_mlmc_result* r);
+
+/*
  * Exact traces of the low-degree Chebyshev terms (closing remark of Section
  * 5.4), At = alpha A + beta I on [a, b] (Section 2.2): t[0] = tr I = d,
  * t[1] = tr At = alpha tr A + beta d, t[2] = tr T_2(At) = 2 tr At^2 - d with
@@ -360,18 +418,48 @@ int mlt_hutchpp_estimate(mlt_matrix* m, double a, double b, const double* c, int
  * probe_offset .. probe_offset+nprobes-1 it computes, exactly in int64,
  * x1 = z^T A z, x2 = z^T A^2 z, x3 = z^T A^3 z (two sparse products per probe
  * block, using the symmetry of the quadratic form), in blocks of `block`
- * probes (block must be 256; a last, partial block costs a full one).  With
+ * probes, 128 or 256.  Blocks of 128 (the block of Section 5.4's workload)
+ * run two per launch, so both sizes cost the same and every probe's moments
+ * are the same integers under either; a last, partial launch costs a full
+ * one.  With
  * use_cv the estimate is
  * [mean x3 - a2 (mean x2 - nnz) - a1 mean x1] / 6 with a1, a2 the least-squares
  * slopes of x3 on (x1, x2) (Section 5.4; tr A = 0, tr A^2 = nnz); without it,
  * mean x3 / 6.  x (host or device int64[nprobes*3], may be NULL) receives the
  * per-probe moments.  Errors: MLT_EINVAL (not a square pattern matrix, a
- * self-loop, nprobes < 1, block != 256); MLT_ERANGE when the bound
+ * self-loop, nprobes < 1, block not 128 or 256); MLT_ERANGE when the bound
  * sum_(i,j) deg_i deg_j on |x3| reaches 2^62.
  */
 int mlt_triangle_trace(mlt_matrix* m, uint64_t seed, int64_t probe_offset,
                        int64_t nprobes, int block, int use_cv, int64_t* x,
                        double* estimate, double* std_error, void* stream);
+
+/* ---- control variates of mlt_triangle_estimate ---------------------------- */
+#define MLT_TRI_CV_NONE 0  /* mean x3 / 6                                        */
+#define MLT_TRI_CV_FIT  1  /* a1, a2 by least squares over the samples (as
+                              mlt_triangle_trace with use_cv)                    */
+#define MLT_TRI_CV_CHEB 2  /* a1, a2 chosen a priori from the Chebyshev
+                              expansion of x^3 on [a, b] (Section 5.4)           */
+
+/*
+ * The estimate of mlt_triangle_trace from per-probe moments x (host
+ * int64[nprobes * 3]: x1, x2, x3 of each probe), with the control variates of
+ * Section 5.4: T = [mean x3 - a2 (mean x2 - nnz) - a1 mean x1] / 6
+ * (tr A = 0, tr A^2 = nnz).  MLT_TRI_CV_NONE: a1 = a2 = 0, variance divisor
+ * m - 1.  MLT_TRI_CV_FIT: the least-squares slopes of x3 on (1, x1, x2),
+ * residual variance divisor m - 3 (an O(1/m) bias from fitting on the same
+ * samples).  MLT_TRI_CV_CHEB: with [a, b] holding the spectrum of A,
+ * c = (a+b)/2, r = (b-a)/2 and x^3 = (3 T_1(x) + T_3(x))/4 on [-1, 1],
+ * A^3 - a2 A^2 - a1 A = (r^3/4) T_3(At) + (c^3 - 3 c r^2/4) I for
+ * a2 = 3c, a1 = 3r^2/4 - 3c^2; fixed in advance, these leave the estimate
+ * unbiased, and the residual variance has divisor m - 1.  Sums are exact
+ * 128-bit integers; the double-precision steps follow a fixed order.
+ * a1, a2 (may be NULL) receive the coefficients used.  Errors: MLT_EINVAL
+ * (null x, nprobes < 1, nnz < 0, unknown cv, a >= b for MLT_TRI_CV_CHEB),
+ * MLT_ERANGE (sums beyond 128 bits).
+ */
+int mlt_triangle_estimate(const int64_t* x, int64_t nprobes, int64_t nnz, int cv, double a, double b,
+                          double* estimate, double* std_error, double* a1, double* a2);
 
 /*
  * Learned coarse level.  The paper has no network; this is a project addition

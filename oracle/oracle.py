@@ -590,6 +590,54 @@ def triangle_estimate(x, nnz, use_cv=True):
     return est, math.sqrt(max(var, 0.0) / fm) / 6.0, a1, a2
 
 
+def triangle_cv_cheb(a, b):
+    """Section 5.4's a-priori control-variate coefficients, "chosen using the
+    Chebyshev expansion of x^3".  With the spectrum of A inside [a, b] and
+    A = r At + c I (c = (a+b)/2, r = (b-a)/2, so At maps [a, b] onto [-1, 1]),
+    the expansion x^3 = (3 T_1(x) + T_3(x)) / 4 on [-1, 1] gives
+        A^3 = (r^3/4) T_3(At) + 3c A^2 + (3r^2/4 - 3c^2) A + (c^3 - 3c r^2/4) I.
+    Taking a2 = 3c and a1 = 3r^2/4 - 3c^2 removes every Chebyshev term of degree
+    below 3 except the constant, which carries no variance (z^T I z = d), so
+    z^T (A^3 - a2 A^2 - a1 A) z = (r^3/4) z^T T_3(At) z + const.  The
+    coefficients do not depend on the samples, so the estimate has no bias from
+    fitting.  Returns (a1, a2)."""
+    c = 0.5 * (float(a) + float(b))
+    r = 0.5 * (float(b) - float(a))
+    return 0.75 * r * r - 3.0 * c * c, 3.0 * c
+
+
+def triangle_estimate_fixed(x, nnz, a1, a2):
+    """Section 5.4 with given (not fitted) coefficients:
+    T = [mean x3 - a2 (mean x2 - nnz) - a1 mean x1] / 6, and its standard error
+    from the sample variance (divisor m - 1) of the residuals x3 - a2 x2 - a1 x1,
+    assembled from exact integer sums as
+        m (m-1) var = C33 + a2^2 C22 + a1^2 C11 - 2 a2 C23 - 2 a1 C13 + 2 a1 a2 C12,
+    C_ij = m S_ij - S_i S_j, in double precision in the order written.
+    Returns (estimate, stderr)."""
+    x = np.asarray(x, dtype=np.int64)
+    m = x.shape[0]
+    x1 = [int(v) for v in x[:, 0]]
+    x2 = [int(v) for v in x[:, 1]]
+    x3 = [int(v) for v in x[:, 2]]
+    S1, S2, S3 = sum(x1), sum(x2), sum(x3)
+    C11 = float(m * sum(v * v for v in x1) - S1 * S1)
+    C22 = float(m * sum(v * v for v in x2) - S2 * S2)
+    C33 = float(m * sum(v * v for v in x3) - S3 * S3)
+    C12 = float(m * sum(u * v for u, v in zip(x1, x2)) - S1 * S2)
+    C13 = float(m * sum(u * v for u, v in zip(x1, x3)) - S1 * S3)
+    C23 = float(m * sum(u * v for u, v in zip(x2, x3)) - S2 * S3)
+    a1 = float(a1)
+    a2 = float(a2)
+    fm = float(m)
+    mean1 = float(S1) / fm
+    mean2 = float(S2) / fm
+    mean3 = float(S3) / fm
+    est = (mean3 - a2 * (mean2 - float(nnz)) - a1 * mean1) / 6.0
+    q = C33 + a2 * a2 * C22 + a1 * a1 * C11 - 2.0 * a2 * C23 - 2.0 * a1 * C13 + 2.0 * a1 * a2 * C12
+    var = q / (fm * (fm - 1.0)) if m > 1 else float("nan")
+    return est, math.sqrt(max(var, 0.0) / fm) / 6.0
+
+
 # ---------------------------------------------------------------------------
 # Spectrum interval (Section 2.2: the map needs a rough estimate of the extreme
 # eigenvalues); Gershgorin discs

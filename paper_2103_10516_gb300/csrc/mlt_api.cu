@@ -1103,7 +1103,7 @@ int mlt_mlmc_estimate(mlt_matrix* m, const mlt_mlmc_params* P, mlt_mlmc_result* 
             const int J = std::min(nlow - 1, hi);        // control variates this level has (0: none)
             auto band = [&](const double* row) {
                 double s = 0.0;
-                for (int j = lo + 1; j <= hi; ++j) s += c[j] * row[j];
+                band_samples(c.data(), lo, hi, row, n + 1, 1, &s);
                 samples.push_back(s);
                 if (J >= 1) w1.push_back(row[1] - tlow[1]);
                 if (J >= 2) w2.push_back(row[2] - tlow[2]);
@@ -1112,12 +1112,8 @@ int mlt_mlmc_estimate(mlt_matrix* m, const mlt_mlmc_params* P, mlt_mlmc_result* 
                 for (int p = 0; p < m_pilot; ++p) band(&pilot[(size_t)p * (n + 1)]);
             for (int64_t i = 0; i < fresh[k]; ++i, ++q) band(&mu[(size_t)q * (n + 1)]);
             const int64_t mk = (int64_t)samples.size();
-            double mean = 0.0;
-            for (double v : samples) mean += v;
-            mean /= (double)mk;
-            double ss = 0.0;
-            for (double v : samples) ss += (v - mean) * (v - mean);
-            double var = mk > 1 ? ss / (double)(mk - 1) : std::nan("");
+            double mean = 0.0, var = 0.0;
+            level_stats(samples.data(), mk, &mean, &var);
             // the low-degree control variates (Section 5.4): least squares of the
             // band on (1, w); the level's estimate is the intercept, its variance
             // the residual one (divisor m - 1 - J); skipped when m <= J + 1 or the
@@ -1195,6 +1191,116 @@ int mlt_low_traces(mlt_matrix* m, double a, double b, double* t, int* count, voi
     }
 }
 
+int mlt_pilot_variances(const double* c, int n, const double* mu, int64_t ld_mu, int64_t m_pilot, double* V)
+{
+    try {
+        if (!c || !V || (m_pilot > 0 && !mu)) return fail(MLT_EINVAL, "mlt_pilot_variances: null argument");
+        if (n < 1 || n > MLT_MAX_DEGREE) return fail(MLT_EINVAL, "mlt_pilot_variances: n out of range");
+        if (m_pilot < 0 || m_pilot > INT32_MAX) return fail(MLT_EINVAL, "mlt_pilot_variances: bad pilot count");
+        if (m_pilot > 0 && ld_mu < n + 1) return fail(MLT_EINVAL, "mlt_pilot_variances: ld_mu below n + 1");
+        band_variances(c, n, mu, ld_mu, (int)m_pilot, V);
+        return MLT_OK;
+    } catch (...) {
+        return fail(MLT_ENOMEM, "mlt_pilot_variances: host allocation failed");
+    }
+}
+
+int mlt_select_levels(const double* V, int n, int cost_model, int m_pilot, int mode, double target,
+                      int max_levels, int32_t* levels, int64_t* m, int* nlevels)
+{
+    try {
+        if (!V || !levels || !m || !nlevels) return fail(MLT_EINVAL, "mlt_select_levels: null argument");
+        if (n < 1 || n > MLT_MAX_DEGREE) return fail(MLT_EINVAL, "mlt_select_levels: n out of range");
+        if (cost_model != MLT_COST_SYMMETRIC && cost_model != MLT_COST_LINEAR)
+            return fail(MLT_EINVAL, "mlt_select_levels: unknown cost model");
+        if (mode != MLT_MODE_BUDGET && mode != MLT_MODE_VARIANCE) return fail(MLT_EINVAL, "mlt_select_levels: unknown mode");
+        if (!(target > 0.0) || !std::isfinite(target)) return fail(MLT_EINVAL, "mlt_select_levels: target must be positive");
+        if (m_pilot < 0 || max_levels < 0) return fail(MLT_EINVAL, "mlt_select_levels: negative m_pilot or max_levels");
+        for (int64_t i = 0; i < (int64_t)(n + 1) * (n + 1); ++i)
+            if (!(V[i] >= 0.0) || !std::isfinite(V[i])) return fail(MLT_EINVAL, "mlt_select_levels: V must be finite and >= 0");
+        std::vector<int> lv(n + 1);
+        int L = 0;
+        int rc = select_levels(V, n, cost_model, m_pilot, mode, target, max_levels, lv.data(), &L);
+        if (rc) return rc;
+        allocate_samples(lv.data(), L, V, n, cost_model, mode, target, m_pilot, m);
+        for (int k = 0; k < L; ++k) levels[k] = lv[k];
+        *nlevels = L;
+        return MLT_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(MLT_ENOMEM, "mlt_select_levels: host allocation failed");
+    } catch (...) {
+        return fail(MLT_EINVAL, "mlt_select_levels: exception");
+    }
+}
+
+int mlt_band_samples(const double* c, int lo, int hi, const double* mu, int64_t ld_mu, int64_t nprobes, double* q)
+{
+    if (nprobes < 0) return fail(MLT_EINVAL, "mlt_band_samples: negative probe count");
+    if (nprobes == 0) return MLT_OK;
+    if (!c || !mu || !q) return fail(MLT_EINVAL, "mlt_band_samples: null argument");
+    if (lo < -1 || hi <= lo || hi > MLT_MAX_DEGREE) return fail(MLT_EINVAL, "mlt_band_samples: need -1 <= lo < hi <= MLT_MAX_DEGREE");
+    if (ld_mu < hi + 1) return fail(MLT_EINVAL, "mlt_band_samples: ld_mu below hi + 1");
+    band_samples(c, lo, hi, mu, ld_mu, nprobes, q);
+    return MLT_OK;
+}
+
+int mlt_mlmc_combine(int nlevels, const int32_t* levels, const int64_t* m, const double* samples, mlt_mlmc_result* R)
+{
+    if (!levels || !m || !samples || !R) return fail(MLT_EINVAL, "mlt_mlmc_combine: null argument");
+    if (nlevels < 1 || nlevels > MLT_MAX_LEVELS) return fail(MLT_EINVAL, "mlt_mlmc_combine: nlevels out of range");
+    for (int k = 0; k < nlevels; ++k)
+        if (m[k] < 1) return fail(MLT_EINVAL, "mlt_mlmc_combine: every level needs m >= 1");
+    std::memset(R, 0, sizeof(*R));
+    double est = 0.0, var_sum = 0.0;
+    const double* v = samples;
+    for (int k = 0; k < nlevels; ++k) {
+        double mean = 0.0, var = 0.0;
+        level_stats(v, m[k], &mean, &var);
+        R->levels[k] = levels[k];
+        R->m[k] = m[k];
+        R->level_mean[k] = mean;
+        R->level_var[k] = var;
+        est += mean;
+        var_sum += var / (double)m[k];
+        v += m[k];
+    }
+    R->nlevels = nlevels;
+    R->estimate = est;
+    R->std_error = std::sqrt(var_sum);
+    return MLT_OK;
+}
+
+int mlt_triangle_estimate(const int64_t* x, int64_t nprobes, int64_t nnz, int cv, double a, double b,
+                          double* estimate, double* std_error, double* a1_out, double* a2_out)
+{
+    try {
+        if (!x || nprobes < 1) return fail(MLT_EINVAL, "mlt_triangle_estimate: need x and nprobes >= 1");
+        if (nnz < 0) return fail(MLT_EINVAL, "mlt_triangle_estimate: negative nnz");
+        double mx = 0.0;
+        for (int64_t i = 0; i < 3 * nprobes; ++i) mx = std::max(mx, std::fabs((double)x[i]));
+        if ((double)nprobes * (double)nprobes * mx * mx >= 4.2e37)
+            return fail(MLT_ERANGE, "mlt_triangle_estimate: moment sums would overflow 128-bit integers");
+        double est = 0.0, se = 0.0, a1 = 0.0, a2 = 0.0;
+        if (cv == MLT_TRI_CV_NONE || cv == MLT_TRI_CV_FIT) {
+            triangle_estimate_host(x, nprobes, nnz, cv == MLT_TRI_CV_FIT, &est, &se, &a1, &a2);
+        } else if (cv == MLT_TRI_CV_CHEB) {
+            if (!(a < b) || !std::isfinite(a) || !std::isfinite(b))
+                return fail(MLT_EINVAL, "mlt_triangle_estimate: need finite a < b");
+            triangle_cv_cheb(a, b, &a1, &a2);
+            triangle_estimate_fixed_host(x, nprobes, nnz, a1, a2, &est, &se);
+        } else {
+            return fail(MLT_EINVAL, "mlt_triangle_estimate: unknown control-variate mode");
+        }
+        if (estimate) *estimate = est;
+        if (std_error) *std_error = se;
+        if (a1_out) *a1_out = a1;
+        if (a2_out) *a2_out = a2;
+        return MLT_OK;
+    } catch (...) {
+        return fail(MLT_ECUDA, "mlt_triangle_estimate: exception");
+    }
+}
+
 int mlt_triangle_trace(mlt_matrix* m, uint64_t seed, int64_t probe_offset, int64_t nprobes, int block,
                        int use_cv, int64_t* x, double* estimate, double* std_error, void* stream)
 {
@@ -1203,7 +1309,7 @@ int mlt_triangle_trace(mlt_matrix* m, uint64_t seed, int64_t probe_offset, int64
         if (m->val_type != MLT_PATTERN || (m->flags & MLT_GRAM) || m->A.nrows != m->A.ncols)
             return fail(MLT_EINVAL, "mlt_triangle_trace: needs a square 0/1 pattern matrix");
         if (nprobes < 1) return fail(MLT_EINVAL, "mlt_triangle_trace: need at least one probe");
-        if (block != 256) return fail(MLT_EINVAL, "mlt_triangle_trace: block must be 256");
+        if (block != 128 && block != 256) return fail(MLT_EINVAL, "mlt_triangle_trace: block must be 128 or 256");
         if (probe_offset < 0 || probe_offset + nprobes > (1LL << 32))
             return fail(MLT_EINVAL, "mlt_triangle_trace: probe ids must lie in [0, 2^32)");
         cudaStream_t s = (cudaStream_t)stream;
@@ -1216,8 +1322,12 @@ int mlt_triangle_trace(mlt_matrix* m, uint64_t seed, int64_t probe_offset, int64
             if ((rc = m->ws_out.ensure(xbytes, s))) return rc;
             x_dev = m->ws_out.as<int64_t>();
         }
-        for (int64_t b0 = 0; b0 < nprobes; b0 += block) {
-            const int nb = (int)std::min<int64_t>(block, nprobes - b0);
+        // Blocks of 128 probes run two per launch: a launch serves 256
+        // consecutive probe ids, and every probe's (x1, x2, x3) is an exact
+        // integer sum that does not depend on which probes share its launch.
+        constexpr int kLaunchProbes = 256;
+        for (int64_t b0 = 0; b0 < nprobes; b0 += kLaunchProbes) {
+            const int nb = (int)std::min<int64_t>(kLaunchProbes, nprobes - b0);
             if ((rc = tri_block(m, seed, probe_offset + b0, nb, x_dev + 3 * b0, s))) return rc;
         }
         std::vector<int64_t> hx(nprobes * 3);

@@ -216,13 +216,83 @@ void allocate_samples(const int* levels, int L, const double* V, int n, int cost
     if (m_pilot > 0 && m_out[L - 1] < m_pilot) m_out[L - 1] = m_pilot;
 }
 
+// Q_{lo,hi} = sum_{j=lo+1..hi} c_j mu_j for each of nprobes moment rows
+// (Eq. def:qlevels), summed left to right from the band's first term.
+void band_samples(const double* c, int lo, int hi, const double* mu, int64_t ld, int64_t nprobes, double* q)
+{
+    for (int64_t p = 0; p < nprobes; ++p) {
+        const double* row = mu + p * ld;
+        double s = 0.0;
+        for (int j = lo + 1; j <= hi; ++j) s += c[j] * row[j];
+        q[p] = s;
+    }
+}
+
+// Mean and sample variance (divisor m - 1, NaN for m < 2) of one level's
+// samples, in sample order: the per-level terms of Eq. multiEstimator.
+void level_stats(const double* v, int64_t m, double* mean, double* var)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < m; ++i) s += v[i];
+    const double mu = s / (double)m;
+    double ss = 0.0;
+    for (int64_t i = 0; i < m; ++i) ss += (v[i] - mu) * (v[i] - mu);
+    *mean = mu;
+    *var = m > 1 ? ss / (double)(m - 1) : std::nan("");
+}
+
+// Section 5.4's a-priori coefficients from the Chebyshev expansion
+// x^3 = (3 T_1(x) + T_3(x)) / 4 on the map of [a, b] onto [-1, 1]: with
+// A = r At + c I, A^3 - a2 A^2 - a1 A = (r^3/4) T_3(At) + (c^3 - 3 c r^2/4) I
+// for a2 = 3c and a1 = 3r^2/4 - 3c^2.
+void triangle_cv_cheb(double a, double b, double* a1, double* a2)
+{
+    const double c = 0.5 * (a + b);
+    const double r = 0.5 * (b - a);
+    *a1 = 0.75 * r * r - 3.0 * c * c;
+    *a2 = 3.0 * c;
+}
+
+// Section 5.4 with given coefficients: T = [mean x3 - a2 (mean x2 - nnz) -
+// a1 mean x1] / 6; the residuals x3 - a2 x2 - a1 x1 have sample variance
+// (divisor m - 1) [C33 + a2^2 C22 + a1^2 C11 - 2 a2 C23 - 2 a1 C13 +
+// 2 a1 a2 C12] / (m (m - 1)), C_ij = m S_ij - S_i S_j from exact integer sums;
+// the double-precision steps run in the order written.
+void triangle_estimate_fixed_host(const int64_t* x, int64_t m, int64_t nnz, double a1, double a2, double* est,
+                                  double* se)
+{
+    typedef __int128 i128;
+    i128 S1 = 0, S2 = 0, S3 = 0, S11 = 0, S22 = 0, S33 = 0, S12 = 0, S13 = 0, S23 = 0;
+    for (int64_t p = 0; p < m; ++p) {
+        const i128 u = x[3 * p], v = x[3 * p + 1], w = x[3 * p + 2];
+        S1 += u; S2 += v; S3 += w;
+        S11 += u * u; S22 += v * v; S33 += w * w;
+        S12 += u * v; S13 += u * w; S23 += v * w;
+    }
+    const i128 mm = m;
+    const double C11 = (double)(mm * S11 - S1 * S1);
+    const double C22 = (double)(mm * S22 - S2 * S2);
+    const double C33 = (double)(mm * S33 - S3 * S3);
+    const double C12 = (double)(mm * S12 - S1 * S2);
+    const double C13 = (double)(mm * S13 - S1 * S3);
+    const double C23 = (double)(mm * S23 - S2 * S3);
+    const double fm = (double)m;
+    const double mean1 = (double)S1 / fm;
+    const double mean2 = (double)S2 / fm;
+    const double mean3 = (double)S3 / fm;
+    *est = (mean3 - a2 * (mean2 - (double)nnz) - a1 * mean1) / 6.0;
+    const double q = C33 + a2 * a2 * C22 + a1 * a1 * C11 - 2.0 * a2 * C23 - 2.0 * a1 * C13 + 2.0 * a1 * a2 * C12;
+    const double var = m > 1 ? q / (fm * (fm - 1.0)) : std::nan("");
+    *se = std::sqrt((var > 0.0 ? var : (var == var ? 0.0 : var)) / fm) / 6.0;
+}
+
 // Section 5.4 estimate from exact integer sums: ordinary least squares of x3
 // on (1, x1, x2), then T = [mean x3 - a2 (mean x2 - nnz) - a1 mean x1] / 6
 // (tr A = 0, tr A^2 = nnz for a 0/1 symmetric matrix without self-loops).
 // Without control variates T = mean x3 / 6.  The double-precision steps run in
 // exactly the order written.
 void triangle_estimate_host(const int64_t* x, int64_t m, int64_t nnz, int use_cv, double* est,
-                            double* se)
+                            double* se, double* a1_out, double* a2_out)
 {
     typedef __int128 i128;
     i128 S1 = 0, S2 = 0, S3 = 0, S11 = 0, S22 = 0, S33 = 0, S12 = 0, S13 = 0, S23 = 0;
@@ -252,6 +322,8 @@ void triangle_estimate_host(const int64_t* x, int64_t m, int64_t nnz, int use_cv
         a1 = (C13 * C22 - C23 * C12) / det;
         a2 = (C23 * C11 - C13 * C12) / det;
     }
+    if (a1_out) *a1_out = a1;
+    if (a2_out) *a2_out = a2;
     const double mean1 = (double)S1 / fm;
     const double mean2 = (double)S2 / fm;
     const double mean3 = (double)S3 / fm;

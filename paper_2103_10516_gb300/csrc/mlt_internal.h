@@ -228,6 +228,11 @@ int select_levels(const double* V, int n, int cost_model, int m_pilot, int mode,
 void allocate_samples(const int* levels, int L, const double* V, int n, int cost_model, int mode,
                       double target, int m_pilot, int64_t* m_out);
 void triangle_estimate_host(const int64_t* x, int64_t m, int64_t nnz, int use_cv, double* est,
-                            double* se);
+                            double* se, double* a1_out = nullptr, double* a2_out = nullptr);
+void band_samples(const double* c, int lo, int hi, const double* mu, int64_t ld, int64_t nprobes, double* q);
+void level_stats(const double* v, int64_t m, double* mean, double* var);
+void triangle_cv_cheb(double a, double b, double* a1, double* a2);
+void triangle_estimate_fixed_host(const int64_t* x, int64_t m, int64_t nnz, double a1, double a2, double* est,
+                                  double* se);
 
 }  // namespace mlt

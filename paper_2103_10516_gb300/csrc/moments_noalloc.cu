@@ -90,9 +90,13 @@ __global__ void na_init_kernel(double* v0, int64_t d, int ldv, int B, int64_t pr
     }
 }
 
-// One recurrence step for the first `act` columns: a warp per row (one column
-// per lane, ldv/32 passes), out = first ? alpha A v + beta v : 2 (alpha A v + beta v) - prev,
-// with per-CTA partial dots out.out and out.cur written in a fixed order.
+// One recurrence step for the first `act` columns: a warp per row, lane l
+// holding columns l, l + 32, ... (act / 32 rounded up passes, at most
+// kMaxPasses), so each row's bounds and entries are read once per step.
+// out = first ? alpha A v + beta v : 2 (alpha A v + beta v) - prev, with
+// per-CTA partial dots out.out and out.cur written in a fixed order: each
+// lane sums its rows in row order, then the CTA sums its warps in warp order.
+constexpr int kMaxPasses = kMaxProbes / 32;
 __global__ void __launch_bounds__(kThreadsNa) na_step_kernel(
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col, const double* __restrict__ val,
     int64_t d, int ldv, int act, const double* __restrict__ cur, double* prev_out, double alpha, double beta,
@@ -104,26 +108,42 @@ __global__ void __launch_bounds__(kThreadsNa) na_step_kernel(
     const int64_t gw = (int64_t)blockIdx.x * (kThreadsNa / 32) + warp;
     const int64_t nw = (int64_t)gridDim.x * (kThreadsNa / 32);
     const int passes = (act + 31) / 32;
-    for (int ps = 0; ps < passes; ++ps) {
-        const int c = ps * 32 + lane;
-        double s_self = 0.0, s_cross = 0.0;
-        for (int64_t r = gw; r < d; r += nw) {
-            double acc = 0.0;
-            for (int64_t k = rowptr[r]; k < rowptr[r + 1]; ++k) {
-                const double a = val ? val[k] : 1.0;
-                if (c < act) acc = fma(a, cur[(size_t)col[k] * ldv + c], acc);
-            }
-            if (c < act) {
-                const size_t off = (size_t)r * ldv + c;
-                const double xc = cur[off];
-                const double o = first ? alpha * acc + beta * xc : 2.0 * (alpha * acc + beta * xc) - prev_out[off];
-                prev_out[off] = o;
-                s_self = fma(o, o, s_self);
-                s_cross = fma(o, xc, s_cross);
+    double s_self[kMaxPasses], s_cross[kMaxPasses];
+#pragma unroll
+    for (int ps = 0; ps < kMaxPasses; ++ps) s_self[ps] = s_cross[ps] = 0.0;
+    for (int64_t r = gw; r < d; r += nw) {
+        const int64_t k0 = rowptr[r], k1 = rowptr[r + 1];
+        double acc[kMaxPasses];
+#pragma unroll
+        for (int ps = 0; ps < kMaxPasses; ++ps) acc[ps] = 0.0;
+        for (int64_t k = k0; k < k1; ++k) {
+            const double a = val ? val[k] : 1.0;
+            const double* row = cur + (size_t)col[k] * ldv;
+#pragma unroll
+            for (int ps = 0; ps < kMaxPasses; ++ps) {
+                const int c = ps * 32 + lane;
+                if (ps < passes && c < act) acc[ps] = fma(a, row[c], acc[ps]);
             }
         }
-        red[0][warp][lane] = s_self;
-        red[1][warp][lane] = s_cross;
+#pragma unroll
+        for (int ps = 0; ps < kMaxPasses; ++ps) {
+            const int c = ps * 32 + lane;
+            if (ps < passes && c < act) {
+                const size_t off = (size_t)r * ldv + c;
+                const double xc = cur[off];
+                const double o = first ? alpha * acc[ps] + beta * xc : 2.0 * (alpha * acc[ps] + beta * xc) - prev_out[off];
+                prev_out[off] = o;
+                s_self[ps] = fma(o, o, s_self[ps]);
+                s_cross[ps] = fma(o, xc, s_cross[ps]);
+            }
+        }
+    }
+#pragma unroll
+    for (int ps = 0; ps < kMaxPasses; ++ps) {
+        if (ps >= passes) break;   // uniform: passes is a kernel argument
+        const int c = ps * 32 + lane;
+        red[0][warp][lane] = s_self[ps];
+        red[1][warp][lane] = s_cross[ps];
         __syncthreads();
         if (warp == 0) {
             double a0 = 0.0, a1 = 0.0;
@@ -219,7 +239,11 @@ extern "C" int mlt_moments_noalloc(int64_t d, int64_t nnz, const int64_t* rowptr
     if (dev < 0 || dev >= kMaxDevices) return fail(MLT_EINVAL, "mlt_moments_noalloc: device index too large");
     int num_sms = 0;
     MLT_CUDA_TRY(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
-    const int nblk = std::max(1, std::min((int)((d + 7) / 8), 2 * num_sms));
+    // the two vector blocks alone must fit before anything is sized from d
+    if (d > kScratchDoubles / (2 * (int64_t)ldv))
+        return fail(MLT_ERANGE, "mlt_moments_noalloc: d * round_up(nprobes, 32) too large for the 32 MiB scratch "
+                                "array (need 2 d ldv + partials + dots <= 4,194,304 doubles)");
+    const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((d + 7) / 8, 2 * (int64_t)num_sms));
     // layout inside the fixed array (in doubles): V0, V1, partials, dots, metadata
     const int64_t n_v = d * (int64_t)ldv;
     const int64_t n_part = (int64_t)nblk * 2 * ldv;

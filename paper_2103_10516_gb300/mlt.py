@@ -38,7 +38,9 @@ EXPORTS = ["mlt_create_csr", "mlt_destroy", "mlt_matrix_info", "mlt_spectrum_bou
            "mlt_surrogate_get_params", "mlt_surrogate_loss_grad", "mlt_surrogate_train",
            "mlt_surrogate_predict", "mlt_learned_train", "mlt_learned_estimate",
            "mlt_moments_batched", "mlt_autotune", "mlt_moments_noalloc", "mlt_low_traces",
-           "mlt_release_cached", "mlt_poly_apply", "mlt_hutchpp_estimate"]
+           "mlt_release_cached", "mlt_poly_apply", "mlt_hutchpp_estimate", "mlt_pilot_variances",
+           "mlt_select_levels", "mlt_band_samples", "mlt_mlmc_combine", "mlt_triangle_estimate"]
+MLT_TRI_CV = {"none": 0, "fit": 1, "cheb": 2}
 
 
 class MLTError(RuntimeError):
@@ -107,6 +109,12 @@ def lib():
     L.mlt_poly_apply.argtypes = [vp, dbl, dbl, vp, ci, vp, i64, vp, i64, ci, cu, vp]
     L.mlt_hutchpp_estimate.argtypes = [vp, dbl, dbl, vp, ci, u64, i64, ci, ci, ci, vp,
                                        ctypes.POINTER(mlt_hutchpp_result), vp]
+    L.mlt_pilot_variances.argtypes = [vp, ci, vp, i64, i64, vp]
+    L.mlt_select_levels.argtypes = [vp, ci, ci, ci, ci, dbl, ci, vp, vp, ctypes.POINTER(ci)]
+    L.mlt_band_samples.argtypes = [vp, ci, ci, vp, i64, i64, vp]
+    L.mlt_mlmc_combine.argtypes = [ci, vp, vp, vp, ctypes.POINTER(mlt_mlmc_result)]
+    L.mlt_triangle_estimate.argtypes = [vp, i64, i64, ci, dbl, dbl, ctypes.POINTER(dbl), ctypes.POINTER(dbl),
+                                        ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
     L.mlt_profile_start.argtypes = []
     L.mlt_profile_stop.argtypes = [ctypes.POINTER(mlt_kernel_stat), ci, ctypes.POINTER(ci)]
     L.mlt_last_error.argtypes = []
@@ -255,10 +263,68 @@ def mlt_mlmc_default_params():
 def mlt_mlmc_estimate(handle, params):
     r = mlt_mlmc_result()
     _check(lib().mlt_mlmc_estimate(handle, ctypes.byref(params), ctypes.byref(r)))
+    return _result_dict(r)
+
+
+def _result_dict(r):
     L = r.nlevels
     return {"estimate": r.estimate, "stderr": r.std_error, "levels": list(r.levels[:L]),
             "m": list(r.m[:L]), "level_mean": list(r.level_mean[:L]),
             "level_var": list(r.level_var[:L]), "probes": r.probes, "matvecs": r.matvecs}
+
+
+def mlt_pilot_variances(c, mu):
+    """(n+1) x (n+1) table V[lo, hi] of the pilot rows mu (m x ld, host), n = len(c) - 1."""
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    mu = np.ascontiguousarray(np.atleast_2d(mu), dtype=np.float64)
+    n = c.size - 1
+    V = np.zeros((n + 1, n + 1))
+    _check(lib().mlt_pilot_variances(_ptr(c), n, _ptr(mu), mu.shape[1], mu.shape[0], _ptr(V)))
+    return V
+
+
+def mlt_select_levels(V, cost_model="symmetric", m_pilot=0, mode="budget", target=1.0, max_levels=0):
+    """(levels, m) from the variance table V ((n+1) x (n+1), host)."""
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    n = V.shape[0] - 1
+    lv = np.zeros(n + 1, dtype=np.int32)
+    m = np.zeros(n + 1, dtype=np.int64)
+    L = ctypes.c_int()
+    _check(lib().mlt_select_levels(_ptr(V), n, MLT_COST[cost_model] if isinstance(cost_model, str) else cost_model,
+                                   int(m_pilot), MLT_MODE[mode] if isinstance(mode, str) else mode, float(target),
+                                   int(max_levels), _ptr(lv), _ptr(m), ctypes.byref(L)))
+    return [int(v) for v in lv[:L.value]], [int(v) for v in m[:L.value]]
+
+
+def mlt_band_samples(c, lo, hi, mu):
+    """Q_{lo,hi} of every row of mu (host)."""
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    mu = np.ascontiguousarray(np.atleast_2d(mu), dtype=np.float64)
+    q = np.zeros(mu.shape[0])
+    _check(lib().mlt_band_samples(_ptr(c), int(lo), int(hi), _ptr(mu), mu.shape[1], mu.shape[0], _ptr(q)))
+    return q
+
+
+def mlt_mlmc_combine(levels, m, samples):
+    """Eq. multiEstimator from per-level samples concatenated level by level."""
+    lv = np.ascontiguousarray(levels, dtype=np.int32)
+    mm = np.ascontiguousarray(m, dtype=np.int64)
+    smp = np.ascontiguousarray(samples, dtype=np.float64)
+    if smp.size != int(mm.sum()):
+        raise ValueError("mlt_mlmc_combine: %d samples for %d expected" % (smp.size, int(mm.sum())))
+    r = mlt_mlmc_result()
+    _check(lib().mlt_mlmc_combine(lv.size, _ptr(lv), _ptr(mm), _ptr(smp), ctypes.byref(r)))
+    return _result_dict(r)
+
+
+def mlt_triangle_estimate(x, nnz, cv="fit", a=0.0, b=0.0):
+    """(estimate, stderr, a1, a2) from per-probe triangle moments x (nprobes x 3, host int64)."""
+    x = np.ascontiguousarray(x, dtype=np.int64)
+    est, se, a1, a2 = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().mlt_triangle_estimate(_ptr(x), x.shape[0], int(nnz), MLT_TRI_CV[cv] if isinstance(cv, str) else cv,
+                                       float(a), float(b), ctypes.byref(est), ctypes.byref(se), ctypes.byref(a1),
+                                       ctypes.byref(a2)))
+    return est.value, se.value, a1.value, a2.value
 
 
 def mlt_triangle_trace(handle, seed, probe_offset, nprobes, block=256, use_cv=True, x=None,
@@ -552,12 +618,46 @@ def _bind_noalloc(L):
                                       ctypes.c_int, vp, vp, i64, vp]
 
 
+def _noalloc_arg(name, t, dtype, min_len=None, exact_len=None):
+    """Check one tensor argument of mlt_moments_noalloc: the C side receives raw
+    device pointers and cannot see a wrong dtype, a short array or host memory."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError("mlt_moments_noalloc: %s must be a torch tensor" % name)
+    if t.dtype != dtype:
+        raise ValueError("mlt_moments_noalloc: %s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("mlt_moments_noalloc: %s must be contiguous" % name)
+    if exact_len is not None and t.numel() != exact_len:
+        raise ValueError("mlt_moments_noalloc: %s needs %d entries, has %d" % (name, exact_len, t.numel()))
+    if min_len is not None and t.numel() < min_len:
+        raise ValueError("mlt_moments_noalloc: %s needs at least %d entries, has %d" % (name, min_len, t.numel()))
+
+
 def mlt_moments_noalloc(d, nnz, rowptr, col, vals, scale, a, b, seed, probe_offset, degrees, mu,
                         stream=None):
     """All array arguments but `degrees` are CUDA tensors the caller owns; mu is
-    nprobes x ld and is written in place."""
+    nprobes x ld and is written in place.  Raises ValueError, before anything
+    reaches the library, when a tensor has the wrong dtype, is too short, is not
+    contiguous or is not in CUDA memory."""
+    import torch
     deg = np.ascontiguousarray(degrees, dtype=np.int32)
-    _check(lib().mlt_moments_noalloc(int(d), int(nnz), _ptr(rowptr), _ptr(col), _ptr(vals), float(scale),
+    d, nnz = int(d), int(nnz)
+    if d < 1 or nnz < 0:
+        raise ValueError("mlt_moments_noalloc: need d >= 1 and nnz >= 0")
+    _noalloc_arg("rowptr", rowptr, torch.int64, exact_len=d + 1)
+    _noalloc_arg("col", col, torch.int32, min_len=nnz)
+    if vals is not None:
+        _noalloc_arg("vals", vals, torch.float64, min_len=nnz)
+    _noalloc_arg("mu", mu, torch.float64)
+    if mu.dim() != 2 or mu.shape[0] < deg.size:
+        raise ValueError("mlt_moments_noalloc: mu must be 2-D with at least %d rows" % deg.size)
+    if deg.size and mu.shape[1] < int(deg.max()) + 1:
+        raise ValueError("mlt_moments_noalloc: mu needs at least max degree + 1 = %d columns" % (int(deg.max()) + 1))
+    for name, t in (("rowptr", rowptr), ("col", col), ("vals", vals), ("mu", mu)):
+        if t is not None and not t.is_cuda:
+            raise ValueError("mlt_moments_noalloc: %s must be in CUDA memory" % name)
+    _check(lib().mlt_moments_noalloc(d, nnz, _ptr(rowptr), _ptr(col), _ptr(vals), float(scale),
                                      float(a), float(b), int(seed), int(probe_offset), deg.size, _ptr(deg),
                                      _ptr(mu), mu.shape[1], _stream(stream)))
     return mu

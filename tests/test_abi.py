@@ -87,3 +87,40 @@ def test_cheb_coeffs_rejects_bad_input(L):
         with pytest.raises(L.MLTError) as e:
             L.mlt_cheb_coeffs(*args)
         assert e.value.code == L.MLT_EINVAL
+
+
+def test_noalloc_binding_rejects_bad_tensors(L):
+    """mlt_moments_noalloc hands raw device pointers to the library, which cannot
+    see a wrong dtype or a short array: the binding must refuse them first.  With
+    host tensors every dtype and length check still runs (they come before the
+    device check), so each rejection is exercised without a GPU."""
+    import torch
+    d, nnz = 4, 6
+    good = dict(rowptr=torch.tensor([0, 2, 3, 5, 6], dtype=torch.int64),
+                col=torch.tensor([1, 2, 0, 0, 3, 2], dtype=torch.int32),
+                vals=torch.ones(nnz, dtype=torch.float64),
+                mu=torch.zeros((2, 5), dtype=torch.float64))
+    deg = [4, 2]
+    bad_cases = [
+        ("rowptr", torch.tensor([0, 2, 3, 5, 6], dtype=torch.int32), "int64"),
+        ("rowptr", torch.tensor([0, 2, 3, 6], dtype=torch.int64), "entries"),
+        ("col", torch.tensor([1, 2, 0, 0, 3, 2], dtype=torch.int64), "int32"),
+        ("col", torch.tensor([1, 2, 0], dtype=torch.int32), "at least"),
+        ("vals", torch.ones(nnz, dtype=torch.float32), "float64"),
+        ("vals", torch.ones(3, dtype=torch.float64), "at least"),
+        ("mu", torch.zeros((2, 5), dtype=torch.float32), "float64"),
+        ("mu", torch.zeros((1, 5), dtype=torch.float64), "rows"),
+        ("mu", torch.zeros((2, 4), dtype=torch.float64), "columns"),
+        ("mu", torch.zeros((5, 2), dtype=torch.float64).t(), "contiguous"),
+        ("col", [1, 2, 0, 0, 3, 2], "torch tensor"),
+    ]
+    for name, val, msg in bad_cases:
+        args = dict(good)
+        args[name] = val
+        with pytest.raises(ValueError, match=msg):
+            L.mlt_moments_noalloc(d, nnz, args["rowptr"], args["col"], args["vals"], 1.0, -1.0, 1.0, 0, 0,
+                                  deg, args["mu"])
+    # every check passed but the tensors are host memory: refused as well
+    with pytest.raises(ValueError, match="CUDA memory"):
+        L.mlt_moments_noalloc(d, nnz, good["rowptr"], good["col"], good["vals"], 1.0, -1.0, 1.0, 0, 0,
+                              deg, good["mu"])

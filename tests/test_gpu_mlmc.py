@@ -117,3 +117,42 @@ def test_low_cv_mlmc_matches_oracle(L, O):
     aref = O.mlmc_auto(m, "exp", lo, hi, 24, seed=6, m_pilot=12, mode="budget", target=2000.0, low_cv=True)
     assert auto["levels"] == aref["levels"] and auto["m"] == aref["m"]
     assert abs(auto["estimate"] - aref["estimate"]) <= tol
+
+
+def test_pilot_variances_from_gpu_moments_match_oracle(L, O):
+    """The library's pilot variance table (Section 3.2.1), computed from pilot
+    moments of the GPU engine, against the oracle's table from its own moments
+    of the same probes, entry by entry.  A moment error e (|e| <= 1e-10 d) moves
+    a band sample by at most dq = 1e-10 d sum|c|, so a sample variance moves by
+    at most 2 dq (sqrt(V m / (m - 1)) + dq) m / (m - 1)."""
+    m = synth.grid_laplacian_2d(24, shift=0.1)
+    n, mp = 48, 12
+    c = O.cheb_coeffs("log", 0.1, 8.1, n)
+    with L.Matrix(m) as M:
+        mu = M.moments(0.1, 8.1, 2, 0, [n] * mp)
+    V = L.mlt_pilot_variances(c, mu)
+    ref = O.pilot_variances(c, O.moments(m, 0.1, 8.1, 2, 0, [n] * mp))
+    dq = 1e-10 * m.nrows * np.sum(np.abs(c))
+    f = mp / (mp - 1.0)
+    tol = 2.0 * dq * (np.sqrt(ref * f) + dq) * f
+    assert np.all(np.abs(V - ref) <= tol + 1e-300)
+    assert np.all(np.tril(V) == 0.0)
+
+
+@pytest.mark.parametrize("auto", [True, False])
+def test_sharded_path_one_rank_is_mlmc_estimate(L, O, auto):
+    """The sharded driver on one process (no collective) makes the same moment
+    calls as mlt_mlmc_estimate and combines with the same routines, so its
+    estimate equals the library's to the last bit; both match the oracle."""
+    from paper_2103_10516_gb300 import shard
+    m = synth.grid_laplacian_2d(24, shift=0.1)
+    n = 48
+    kw = dict(m_pilot=10, mode="budget", target=3000.0) if auto else dict(levels=[8, 24, 48], m=[60, 20, 6])
+    with L.Matrix(m) as M:
+        lib = M.mlmc("log", 0.1, 8.1, n, seed=2, **kw)
+        sh = shard.mlmc_sharded(shard.library_moments(M.handle, 0.1, 8.1, 2), "log", 0.1, 8.1, n, **kw)
+    for f in ("estimate", "stderr", "levels", "m", "level_mean", "level_var", "probes", "matvecs"):
+        np.testing.assert_array_equal(np.asarray(sh[f]), np.asarray(lib[f]), err_msg=f)   # NaN == NaN
+    ref = O.mlmc_auto(m, "log", 0.1, 8.1, n, seed=2, **kw) if auto else \
+        O.mlmc_fixed(m, "log", 0.1, 8.1, n, kw["levels"], kw["m"], seed=2)
+    assert abs(sh["estimate"] - ref["estimate"]) <= 1e-10 * np.sum(np.abs(ref["coeffs"])) * m.nrows

@@ -79,11 +79,27 @@ def test_rejects_bad_inputs(L):
         assert e.value.code == L.MLT_EINVAL
     g = synth.random_graph(20, 0.3, seed=0)
     with L.Matrix(g) as M:
-        for blk in (64, 128):
+        for blk in (64, 192, 512):
             with pytest.raises(L.MLTError):
                 L.mlt_triangle_trace(M.handle, 0, 0, 10, block=blk)
         with pytest.raises(L.MLTError):
             M.triangles(0, 0, 0)
+
+
+def test_block_128_bit_exact(L, O):
+    """Blocks of 128 probes, as Section 5.4's triangle workload states them,
+    give the oracle's integers and the oracle's estimate bit for bit, and the
+    same results as blocks of 256, over a ragged probe count."""
+    g = synth.rmat_adjacency(12, 16, seed=4)
+    x128 = np.zeros((300, 3), dtype=np.int64)
+    x256 = np.zeros((300, 3), dtype=np.int64)
+    with L.Matrix(g) as G:
+        e128, s128 = L.mlt_triangle_trace(G.handle, 5, 77, 300, block=128, use_cv=True, x=x128)
+        e256, s256 = L.mlt_triangle_trace(G.handle, 5, 77, 300, block=256, use_cv=True, x=x256)
+    xr = O.triangle_moments(g, 5, 77, 300)
+    assert np.array_equal(x128, xr) and np.array_equal(x256, xr)
+    er, sr, _, _ = O.triangle_estimate(xr, g.nnz, True)
+    assert e128 == er and s128 == sr and e256 == er and s256 == sr
 
 
 def test_full_size_rmat20_sampled(L, O):

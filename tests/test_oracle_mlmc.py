@@ -296,3 +296,89 @@ def test_interval_contains_the_spectrum(O):
         lam = np.linalg.eigvalsh(D.T @ D)
         assert a == 0.0 and lam[-1] <= b
         assert abs(b - np.abs(D).sum(axis=1).max() * np.abs(D).sum(axis=0).max()) < 1e-9 * b
+
+
+# ---- pilot variances (Section 3.2.1) ----------------------------------------
+
+def _exhaustive_pilot(O, d=6, n=8, seed=4):
+    """All 2^d Rademacher vectors as the pilot sample of a small symmetric
+    matrix: their moments, the coefficients of exp, and each band's matrix
+    B_{lo,hi} = sum_{j=lo+1..hi} c_j T_j(At) from the eigendecomposition, with
+    T_j(x) = cos(j arccos x) (no recurrence)."""
+    m = synth.random_symmetric(d, 0.6, seed=seed, diag_shift=1.0)
+    lam, Q = np.linalg.eigh(m.to_dense())
+    a, b = float(lam[0]) - 0.2, float(lam[-1]) + 0.3
+    c = O.cheb_coeffs("exp", a, b, n)
+    Z = np.array(list(itertools.product([-1.0, 1.0], repeat=d)))
+    mu = O.moments_z(m, a, b, Z, n)
+    th = np.arccos(np.clip((2 * lam - (a + b)) / (b - a), -1, 1))
+
+    def B(lo, hi):
+        w = sum(c[j] * np.cos(j * th) for j in range(lo + 1, hi + 1))
+        return (Q * w) @ Q.T
+    return c, mu, B, Z.shape[0]
+
+
+def _pilot_pin_error(V, B, N, n):
+    """Largest relative gap between V[lo, hi] and the exact sample variance of
+    z^T B z over all N = 2^d sign vectors: the Hutchinson variance
+    2 (||B||_F^2 - sum_i B_ii^2) (Rademacher z) times N / (N - 1), since the
+    sample variance divides by N - 1.  Entries with lo >= hi must be 0."""
+    worst = 0.0
+    for lo in range(n + 1):
+        for hi in range(n + 1):
+            if lo >= hi:
+                if V[lo, hi] != 0.0:
+                    return float("inf")
+                continue
+            Bm = B(lo, hi)
+            exact = 2.0 * (np.sum(Bm * Bm) - np.sum(np.diag(Bm) ** 2)) * N / (N - 1)
+            worst = max(worst, abs(V[lo, hi] - exact) / max(exact, 1e-300))
+    return worst
+
+
+def test_pilot_variances_exhaustive_closed_form(O):
+    n = 8
+    c, mu, B, N = _exhaustive_pilot(O, n=n)
+    V = O.pilot_variances(c, mu)
+    assert V.shape == (n + 1, n + 1)
+    assert _pilot_pin_error(V, B, N, n) < 1e-9
+
+
+def test_pilot_variance_pin_rejects_planted_mistakes(O):
+    """The closed-form pin is sharp enough to catch the plausible slips of a
+    pilot-variance routine: divisor m instead of m - 1, a band shifted by one
+    term, the transposed table, and a band that starts at its own lower level."""
+    n = 8
+    c, mu, B, N = _exhaustive_pilot(O, n=n)
+    terms = np.asarray(c)[None, :] * mu[:, : n + 1]
+
+    def table(lo_off, hi_off, ddof, transpose=False):
+        V = np.zeros((n + 1, n + 1))
+        for lo in range(n):
+            for hi in range(lo + 1, n + 1):
+                q = terms[:, lo + lo_off: hi + hi_off].sum(axis=1)
+                V[lo, hi] = np.var(q, ddof=ddof)
+        return V.T.copy() if transpose else V
+
+    assert _pilot_pin_error(table(1, 1, 1), B, N, n) < 1e-9        # the correct form
+    for bad in (table(1, 1, 0), table(0, 0, 1), table(2, 1, 1), table(0, 1, 1), table(1, 1, 1, True)):
+        assert _pilot_pin_error(bad, B, N, n) > 1e-3
+
+
+def test_pilot_variances_band_by_band(O):
+    """Each entry equals the sample variance (divisor m - 1) of the pinned band
+    sums Q_{lo,hi} over the pilot rows (every band summed on its own)."""
+    m = synth.grid_laplacian_2d(12, shift=0.1)
+    n = 24
+    c = O.cheb_coeffs("log", 0.1, 8.1, n)
+    mu = O.moments(m, 0.1, 8.1, 9, 40, [n] * 7)
+    V = O.pilot_variances(c, mu)
+    for lo in range(n):
+        for hi in range(lo + 1, n + 1):
+            q = O.band(c, mu, lo, hi)
+            ref = float(np.var(q, ddof=1))
+            assert abs(V[lo, hi] - ref) <= 1e-12 * max(ref, 1e-30) + 1e-28, (lo, hi)
+    assert np.all(np.tril(V) == 0.0)
+    # a single pilot row has no sample variance: the table is all zeros
+    assert np.all(O.pilot_variances(c, mu[:1]) == 0.0)

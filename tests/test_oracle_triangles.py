@@ -70,3 +70,70 @@ def test_control_variate_regression(O):
     assert se <= se0 * math.sqrt(63.0 / 61.0) + 1e-12
     T = O.triangle_count(g)
     assert abs(est - T) < 5 * se
+
+
+def _offdiag_sq(B):
+    return float(np.sum(B * B) - np.sum(np.diag(B) ** 2))
+
+
+@pytest.mark.parametrize("shift", [None, (1.0, 2.5)])
+def test_apriori_cv_coefficients_from_cheb_expansion(O, shift):
+    """a1, a2 of Section 5.4 chosen a priori from x^3 = (3 T_1 + T_3)/4 on the
+    mapped spectrum: A^3 - a2 A^2 - a1 A is (r^3/4) T_3(At) plus a multiple of I,
+    with T_3 evaluated through the eigendecomposition as cos(3 arccos x)."""
+    g = synth.random_graph(30, 0.2, seed=7)
+    A = g.to_dense()
+    lam, Q = np.linalg.eigh(A)
+    if shift is None:      # the Gershgorin interval [-max degree, max degree]
+        a, b = -float(np.max(np.diff(g.rowptr))), float(np.max(np.diff(g.rowptr)))
+    else:                  # an asymmetric interval around the spectrum (c != 0)
+        a, b = float(lam[0]) - shift[0], float(lam[-1]) + shift[1]
+    a1, a2 = O.triangle_cv_cheb(a, b)
+    c, r = 0.5 * (a + b), 0.5 * (b - a)
+    lt = (lam - c) / r
+    T3 = (Q * np.cos(3 * np.arccos(np.clip(lt, -1, 1)))) @ Q.T
+    lhs = A @ A @ A - a2 * (A @ A) - a1 * A - (r ** 3 / 4) * T3
+    const = c ** 3 - 0.75 * c * r * r
+    assert np.max(np.abs(lhs - const * np.eye(30))) < 1e-9 * (r ** 3 + abs(c) ** 3)
+
+
+def test_apriori_cv_exhaustive_signs(O):
+    """Over all 2^d sign vectors the a-priori estimate is the triangle count
+    exactly (no fit, so no bias), and its residual variance is the Hutchinson
+    variance 2 sum_{i != k} B_ik^2 of B = (r^3/4) T_3(At) (a multiple of I adds
+    none); the sample variance over the 2^d vectors has divisor 2^d - 1."""
+    d = 10
+    g = synth.random_graph(d, 0.5, seed=11)
+    A = g.to_dense()
+    Z = np.array(list(itertools.product([-1, 1], repeat=d)), dtype=np.int8)
+    x = O.triangle_moments_z(g, Z)
+    T = O.triangle_count(g)
+    lam, Q = np.linalg.eigh(A)
+    a, b = float(lam[0]) - 0.5, float(lam[-1]) + 0.25
+    a1, a2 = O.triangle_cv_cheb(a, b)
+    est, se = O.triangle_estimate_fixed(x, g.nnz, a1, a2)
+    assert abs(est - T) < 1e-9 * max(T, 1)
+    c, r = 0.5 * (a + b), 0.5 * (b - a)
+    T3 = (Q * np.cos(3 * np.arccos(np.clip((lam - c) / r, -1, 1)))) @ Q.T
+    N = Z.shape[0]
+    pop_var = 2.0 * _offdiag_sq((r ** 3 / 4) * T3)
+    got_pop_var = (se * 6.0) ** 2 * N * (N - 1) / N
+    assert abs(got_pop_var - pop_var) < 1e-8 * pop_var
+    # the plain estimator's spread on the same vectors is larger
+    _, se0, _, _ = O.triangle_estimate(x, g.nnz, use_cv=False)
+    assert se < se0
+
+
+def test_fixed_coefficients_reduce_to_plain_and_regression(O):
+    """With a1 = a2 = 0 the fixed-coefficient form is the plain mean (same
+    variance divisor); with the fitted slopes its estimate is the regression
+    estimate (the variance divisors differ: m - 1 against m - 3)."""
+    g = synth.random_graph(120, 0.08, seed=5)
+    x = O.triangle_moments(g, 0, 0, 64)
+    est0, se0, _, _ = O.triangle_estimate(x, g.nnz, use_cv=False)
+    e, s = O.triangle_estimate_fixed(x, g.nnz, 0.0, 0.0)
+    assert e == est0 and abs(s - se0) <= 1e-15 * se0
+    estr, ser, a1, a2 = O.triangle_estimate(x, g.nnz, use_cv=True)
+    e, s = O.triangle_estimate_fixed(x, g.nnz, a1, a2)
+    assert abs(e - estr) < 1e-12 * abs(estr)
+    assert abs(s - ser * math.sqrt(61.0 / 63.0)) < 1e-6 * ser

@@ -3,8 +3,11 @@ cudaMalloc (inside a stream capture they do not own, in loops that cannot take
 the synchronisation an allocation may cause, or under a host memory pool that
 owns the device memory).  Its output must equal the regular mlt_moments path's
 within the FP64 moment tolerance (1e-10 d), on two calls in a row that share
-the library's fixed scratch array, and inside a CUDA graph capture.  This file
-is collected last on purpose."""
+the library's fixed scratch array, and inside a CUDA graph capture; and it must
+equal the CPU oracle's moments on the same probes within the same tolerance.
+The spectrum interval comes from the host (the oracle's Gershgorin bound), so no
+library call chooses the interval both sides use.  This file is collected last
+on purpose."""
 import numpy as np
 import pytest
 
@@ -31,7 +34,7 @@ def _dev(m):
     return rp, col, val
 
 
-def test_noalloc_matches_regular_path_twice(L):
+def test_noalloc_matches_regular_path_twice(L, O):
     import torch
     calls = [
         (synth.grid_laplacian_2d(32, shift=0.1), 1.0, (0.1, 8.1), 3, 0,
@@ -40,14 +43,16 @@ def test_noalloc_matches_regular_path_twice(L):
          (np.arange(100) % 37).astype(np.int32)),
     ]
     for m, scale, ab, seed, off, deg in calls:
+        a, b = ab if ab else O.interval(m, scale)
         with L.Matrix(m, scale=scale) as M:
-            a, b = ab if ab else M.bounds()
             ref = M.moments(a, b, seed, off, deg)
+        orc = O.moments(m, a, b, seed, off, deg, scale=scale)
         rp, col, val = _dev(m)
         mu = torch.full((deg.size, ref.shape[1] + 3), 5.0, dtype=torch.float64, device="cuda")
         L.mlt_moments_noalloc(m.nrows, m.nnz, rp, col, val, scale, a, b, seed, off, deg, mu)
         got = mu.cpu().numpy()
         assert np.max(np.abs(got[:, :ref.shape[1]] - ref)) <= TOL64 * m.nrows
+        assert np.max(np.abs(got[:, :ref.shape[1]] - orc)) <= TOL64 * m.nrows
         assert np.all(got[:, ref.shape[1]:] == 0.0)
 
 
@@ -67,7 +72,7 @@ def test_noalloc_rejects_oversize_and_bad_input(L):
     assert e.value.code == L.MLT_EINVAL
 
 
-def test_noalloc_inside_graph_capture(L):
+def test_noalloc_inside_graph_capture(L, O):
     """A call captured into a CUDA graph (after one uncaptured call has looked
     up the scratch array) replays to the same moments, twice; captured with a
     column out of range it yields NaN rows instead of an error code."""
@@ -76,6 +81,7 @@ def test_noalloc_inside_graph_capture(L):
     deg = np.array([16] * 30 + [40] * 10, dtype=np.int32)
     with L.Matrix(m) as M:
         ref = M.moments(0.1, 8.1, 7, 50, deg)
+    orc = O.moments(m, 0.1, 8.1, 7, 50, deg)
     rp, col, val = _dev(m)
     warm = torch.zeros((deg.size, ref.shape[1]), dtype=torch.float64, device="cuda")
     L.mlt_moments_noalloc(m.nrows, m.nnz, rp, col, val, 1.0, 0.1, 8.1, 7, 50, deg, warm)
@@ -90,6 +96,7 @@ def test_noalloc_inside_graph_capture(L):
         g.replay()
         torch.cuda.synchronize()
         assert np.max(np.abs(mu.cpu().numpy() - ref)) <= TOL64 * m.nrows
+        assert np.max(np.abs(mu.cpu().numpy() - orc)) <= TOL64 * m.nrows
     bad_col = col.clone()
     bad_col[5] = m.nrows + 3
     g2 = torch.cuda.CUDAGraph()
