@@ -59,6 +59,16 @@ extern "C" {
 #define MLT_DEVICE_PTRS 2u /* rowptr/col/vals are device pointers; they are
                               referenced, not copied, and must outlive the
                               handle                                         */
+#define MLT_REORDER     4u /* the moment engine (mlt_moments and the calls
+                              built on it) runs on a copy of the operator
+                              relabelled by decreasing degree (ties by
+                              increasing id), with each probe entry taken
+                              at its original row id: the moments are those
+                              of the original operator and probes, up to
+                              the order of the floating-point sums.  Pays
+                              on power-law graphs, whose hub rows take most
+                              gathers; square (non-Gram) handles only; the
+                              copy doubles the handle's CSR memory        */
 
 /* ---- functions f of mlt_cheb_coeffs -------------------------------------- */
 #define MLT_FN_LOG   0     /* log x      (log-determinant)                   */
@@ -128,7 +138,8 @@ typedef struct mlt_matrix mlt_matrix;   /* opaque; owns device copies */
  * footnote on Schatten norms).  Host arrays are copied to the device (on
  * `stream`, finished before return); with MLT_DEVICE_PTRS they are used in
  * place.  Errors: MLT_EINVAL on negative sizes, null arrays with nnz > 0,
- * nnz > 2^31-1, rowptr[0] != 0 or rowptr[nrows] != nnz; MLT_ENOMEM; MLT_ECUDA.
+ * nnz > 2^31-1, rowptr[0] != 0 or rowptr[nrows] != nnz, MLT_REORDER with
+ * MLT_GRAM; MLT_ENOMEM; MLT_ECUDA.
  */
 int mlt_create_csr(int64_t nrows, int64_t ncols, int64_t nnz,
                    const int64_t* rowptr, const int32_t* col, const void* vals,

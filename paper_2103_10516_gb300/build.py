@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libmlt.so")
 SOURCES = ["mlt_api.cu", "cheb_kernels.cu", "tri_kernels.cu", "mlp_kernels.cu", "learned.cu", "spectrum.cu",
-           "moments_noalloc.cu", "hutchpp.cu", "mlt_host.cpp"]
+           "moments_noalloc.cu", "hutchpp.cu", "reorder.cu", "mlt_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -43,6 +43,7 @@
 #include "mlt_internal.h"
 #include "rng.cuh"
 
+
 namespace mlt {
 namespace {
 
@@ -51,11 +52,6 @@ constexpr int kSlots = 16;          // steps whose partials are buffered before 
 constexpr int64_t kRowCost = 4;     // units charged per row (the epilogue) on top of its entries
 constexpr int64_t kChunksPerSm = 1024;  // work chunks per SM in the split of an operand
 constexpr int64_t kLongRow = 128;   // rows above max(Uc, this) are cut into segments
-// Resident CTAs per SM the step kernel is compiled for (40 registers, with
-// the running dots in shared memory so that nothing spills): more rows in
-// flight hide more gather latency than the wider budgets of 4 or 5 CTAs buy
-// (measured on the 3D stencil, R-MAT and the 2D grid).
-constexpr int kStepCtasPerSm = 6;
 
 template <typename T> struct Lanes;
 template <> struct Lanes<double> { static constexpr int N = 2; };   // 16-byte vectors
@@ -63,6 +59,52 @@ template <> struct Lanes<float> { static constexpr int N = 4; };
 template <> struct Lanes<df64> { static constexpr int N = 2; };     // 16-byte vectors of pairs
 
 template <typename T, int N> struct alignas(sizeof(T) * N) Pack { T v[N]; };
+
+// Resident CTAs per SM the step kernel is compiled for, the unroll depth of
+// its gather loop, and whether its gathers carry an L2 evict-last policy, per
+// vector type.  More unrolled gathers keep more row reads outstanding but need
+// registers, which lowers the resident CTAs; the evict-last policy keeps the
+// gathered V_k rows in L2 against the streams of V_{k-1}, V_{k+1} and the
+// column indices.  Measured on the scale-22 R-MAT graph (gather-bound) and the
+// 100^3 diffusion operator (streaming): FP32 and FP64 gain from the deeper
+// unroll (FP32 9.5 -> 8.1 ms a step on the graph) and FP32 from the policy
+// (8.1 -> 7.5 ms); the double-float step, heavier in arithmetic, is fastest
+// at six CTAs without either.
+template <int C, int U, bool E> struct TuneOf {
+    static constexpr int kCtas = C, kUnroll = U;
+    static constexpr bool kEvictLast = E;
+};
+template <typename T> struct StepTuning;
+template <> struct StepTuning<float> : TuneOf<5, 8, true> {};
+template <> struct StepTuning<double> : TuneOf<4, 8, false> {};
+template <> struct StepTuning<df64> : TuneOf<6, 4, false> {};
+
+// An L2 access policy that marks lines evict-last (createpolicy, PTX ISA).
+__device__ __forceinline__ uint64_t evict_last_policy()
+{
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// A gathered 16-byte row slice, under the L2 policy `pol` when E.
+template <bool E, typename P>
+__device__ __forceinline__ P ld_gather(const P* p, uint64_t pol)
+{
+    static_assert(sizeof(P) == 16, "16-byte packs");
+    if constexpr (E) {
+        uint4 u;
+        asm volatile("ld.global.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                     : "=r"(u.x), "=r"(u.y), "=r"(u.z), "=r"(u.w)
+                     : "l"(p), "l"(pol));
+        P r;
+        memcpy(&r, &u, 16);
+        return r;
+    } else {
+        (void)pol;
+        return *p;
+    }
+}
 
 // A thread's running dot product.  The kernels keep these in shared memory
 // (one slot per thread, see DotSlots): held in registers beside a row's
@@ -160,6 +202,7 @@ struct StepArgs {
     int B;                 // probes in the group (columns >= B are padding)
     uint64_t seedmix;
     const int64_t* ids;    // global id of each column's probe (direct mode)
+    const int32_t* orig;   // original id of each row (relabelled operator), or null
     double* partials;      // [gridDim.x][2][ldv] for this launch
     // work split of this operand
     int64_t nch, Uc, Ul, nseg;
@@ -201,30 +244,34 @@ struct Lane {
     }
 };
 
-// acc = sum over entries [k0, k1) of a_ij * V[j, c0 .. c0+N).
+
+// acc = sum over entries [k0, k1) of a_ij * V[j, c0 .. c0+N).  Row and entry
+// indices fit in 32 bits (nnz < 2^31 is checked when the handle is made).
 template <typename T, int G>
-__device__ __forceinline__ void row_product(const StepArgs<T>& a, const Lane<T, G>& L, int64_t k0,
-                                            int64_t k1, T (&acc)[Lanes<T>::N])
+__device__ __forceinline__ void row_product(const StepArgs<T>& a, const Lane<T, G>& L, int k0, int k1,
+                                            T (&acc)[Lanes<T>::N], uint64_t pol)
 {
     constexpr int N = Lanes<T>::N;
+    constexpr int kGatherUnroll = StepTuning<T>::kUnroll;
     using P = Pack<T, N>;
 #pragma unroll
     for (int q = 0; q < N; ++q) acc[q] = T(0);
-    for (int64_t base = k0; base < k1; base += G) {
-        const int64_t k = base + L.glane;
+    for (int base = k0; base < k1; base += G) {
+        const int k = base + L.glane;
         int cj = 0;
         T vj = T(0);
         if (k < k1) {
             cj = __ldg(a.col + k);
             vj = a.val ? ldg_val(a.val + k) : T(1);
         }
-        const int cnt = (int)min((int64_t)G, k1 - base);
-#pragma unroll 4
+        const int cnt = min(G, k1 - base);
+#pragma unroll kGatherUnroll
         for (int t = 0; t < cnt; ++t) {
             const int c = __shfl_sync(L.gmask, cj, t, G);
             const T v = shfl_val(L.gmask, vj, t, G);
             if (L.vok) {
-                const P x = *reinterpret_cast<const P*>(a.vgather + (size_t)c * a.ldv + L.c0);
+                const P x = ld_gather<StepTuning<T>::kEvictLast>(
+                    reinterpret_cast<const P*>(a.vgather + (size_t)c * a.ldv + L.c0), pol);
 #pragma unroll
                 for (int q = 0; q < N; ++q) acc[q] = fma(v, x.v[q], acc[q]);
             }
@@ -232,10 +279,28 @@ __device__ __forceinline__ void row_product(const StepArgs<T>& a, const Lane<T, 
     }
 }
 
+// The row's operands of the epilogue, loaded before its gathers (they do not
+// depend on them): V_k at the row and, in a recurrence step, V_{k-1}.
+template <typename T>
+struct RowOperands {
+    Pack<T, Lanes<T>::N> xc, xp;
+};
+
+template <typename T>
+__device__ __forceinline__ RowOperands<T> load_operands(const StepArgs<T>& a, int64_t r, int c0)
+{
+    using P = Pack<T, Lanes<T>::N>;
+    RowOperands<T> o;
+    const size_t off = (size_t)r * a.ldv + c0;
+    if (a.mode != 2) o.xc = *reinterpret_cast<const P*>(a.vcur + off);
+    if (a.mode == 1 || a.mode == 3) o.xp = *reinterpret_cast<const P*>(a.vprev_out + off);
+    return o;
+}
+
 // V_{k+1}[r] from acc = (A V_k)[r], and the fused dot products.
 template <typename T, bool CL>
 __device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0, const T (&acc)[Lanes<T>::N],
-                                         DotSlots<T>& dots)
+                                         const RowOperands<T>& ops, DotSlots<T>& dots)
 {
     constexpr int N = Lanes<T>::N;
     using P = Pack<T, N>;
@@ -247,9 +312,9 @@ __device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0
         *reinterpret_cast<P*>(a.vprev_out + off) = out;
         return;
     }
-    const P xc = *reinterpret_cast<const P*>(a.vcur + off);
+    const P& xc = ops.xc;
     if constexpr (CL) {   // Clenshaw step (mode 3): compiled into its own kernels only
-        const P xp = *reinterpret_cast<const P*>(a.vprev_out + off);
+        const P& xp = ops.xp;
         const P xa = *reinterpret_cast<const P*>(a.addv + off);
 #pragma unroll
         for (int q = 0; q < N; ++q) out.v[q] = a.m1 * (a.alpha * acc[q] + a.beta * xc.v[q]) - xp.v[q] + a.coef * xa.v[q];
@@ -260,7 +325,7 @@ __device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0
 #pragma unroll
         for (int q = 0; q < N; ++q) out.v[q] = a.alpha * acc[q] + a.beta * xc.v[q];
     } else {
-        const P xp = *reinterpret_cast<const P*>(a.vprev_out + off);
+        const P& xp = ops.xp;
 #pragma unroll
         for (int q = 0; q < N; ++q) out.v[q] = T(2) * (a.alpha * acc[q] + a.beta * xc.v[q]) - xp.v[q];
     }
@@ -279,7 +344,7 @@ __device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0
 #pragma unroll
         for (int q = 0; q < N; ++q) {
             if (c0 + q >= a.B) break;
-            const bool neg = probe_negative(a.seedmix, (uint64_t)a.ids[c0 + q], (uint64_t)r);
+            const bool neg = probe_negative(a.seedmix, (uint64_t)a.ids[c0 + q], (uint64_t)(a.orig ? a.orig[r] : r));
             DotAcc<T> s1 = dots[1][q][tid];
             s1.add(neg ? -out.v[q] : out.v[q]);
             dots[1][q][tid] = s1;
@@ -326,38 +391,46 @@ __device__ __forceinline__ void cta_partials(const StepArgs<T>& a, const Lane<T,
 }
 
 template <typename T, int G, bool CL>
-__global__ void __launch_bounds__(kThreads, kStepCtasPerSm) cheb_step_kernel(StepArgs<T> a)
+__global__ void __launch_bounds__(kThreads, StepTuning<T>::kCtas) cheb_step_kernel(StepArgs<T> a)
 {
     constexpr int N = Lanes<T>::N;
     const Lane<T, G> L(a);
     __shared__ DotSlots<T> dots;
     if constexpr (!CL) clear_dots<T>(dots);
+    const uint64_t pol = StepTuning<T>::kEvictLast ? evict_last_policy() : 0;
 
     if (L.active) {
         const int64_t nitems = a.nch + a.nseg;
         for (int64_t it = L.gcls; it < nitems; it += L.ncls) {
             T acc[N];
             if (it < a.nch) {
+                // row and entry indices fit in 32 bits (nnz < 2^31); units may not
                 const int64_t u0 = it * a.Uc, u1 = u0 + a.Uc;
-                int64_t r = __ldg(a.crow + it);
-                int64_t beg = r < a.nrows ? __ldg(a.rowptr + r) : 0;
-                for (; r < a.nrows; ++r) {
-                    const int64_t pr = beg + kRowCost * r;
+                const int nrows = (int)a.nrows;
+                int r = (int)__ldg(a.crow + it);
+                int beg = r < nrows ? (int)__ldg(a.rowptr + r) : 0;
+                int end = r < nrows ? (int)__ldg(a.rowptr + r + 1) : 0;
+                for (; r < nrows; ++r) {
+                    const int64_t pr = (int64_t)beg + kRowCost * r;
                     if (pr >= u1) break;
-                    const int64_t end = __ldg(a.rowptr + r + 1);   // the next row's start
+                    // the row after next's end, one row ahead of its use
+                    const int nxt = r + 2 <= nrows ? (int)__ldg(a.rowptr + r + 2) : end;
                     // rows before u0 belong to the previous chunk; long rows are done by segments
                     if (pr >= u0 && end - beg <= a.Ul) {
-                        row_product<T, G>(a, L, beg, end, acc);
-                        if (L.vok) epilogue<T, CL>(a, r, L.c0, acc, dots);
+                        RowOperands<T> ops;
+                        if (L.vok) ops = load_operands(a, r, L.c0);
+                        row_product<T, G>(a, L, beg, end, acc, pol);
+                        if (L.vok) epilogue<T, CL>(a, r, L.c0, acc, ops, dots);
                     }
                     beg = end;
+                    end = nxt;
                 }
             } else {
                 const int64_t sidx = it - a.nch;
                 const int64_t r = __ldg(a.seg_row + sidx);
-                const int64_t k0 = __ldg(a.seg_k0 + sidx);
-                const int64_t k1 = min(k0 + a.Ul, __ldg(a.rowptr + r + 1));
-                row_product<T, G>(a, L, k0, k1, acc);
+                const int k0 = (int)__ldg(a.seg_k0 + sidx);
+                const int k1 = (int)min((int64_t)k0 + a.Ul, __ldg(a.rowptr + r + 1));
+                row_product<T, G>(a, L, k0, k1, acc, pol);
                 if (L.vok) {
                     Pack<T, N> p;
 #pragma unroll
@@ -386,12 +459,14 @@ __global__ void __launch_bounds__(kThreads) cheb_long_kernel(StepArgs<T> a)
             T acc[N];
 #pragma unroll
             for (int q = 0; q < N; ++q) acc[q] = T(0);
+            const int64_t r = a.long_rows[i];
+            const RowOperands<T> ops = load_operands(a, r, L.c0);
             for (int64_t sidx = a.long_seg0[i]; sidx < a.long_seg0[i + 1]; ++sidx) {
                 const P p = *reinterpret_cast<const P*>(a.segpart + (size_t)sidx * a.ldv + L.c0);
 #pragma unroll
                 for (int q = 0; q < N; ++q) acc[q] += p.v[q];
             }
-            epilogue<T, CL>(a, a.long_rows[i], L.c0, acc, dots);
+            epilogue<T, CL>(a, r, L.c0, acc, ops, dots);
         }
     }
     if (CL || a.mode >= 2) return;
@@ -425,9 +500,11 @@ __global__ void reduce_partials_kernel(const double* __restrict__ part, int max_
     if (lane == 0) dots[(size_t)(ra.step0 + slot) * 2 * B + (size_t)kind * B + c] = s;
 }
 
+// V_0 = z: row i of a relabelled operator holds the probe entry of original
+// row orig[i].
 template <typename T>
 __global__ void init_probes_kernel(T* v0, int64_t d, int ldv, int B, const int64_t* __restrict__ ids,
-                                   uint64_t seedmix)
+                                   uint64_t seedmix, const int32_t* __restrict__ orig)
 {
     const int64_t total = d * (int64_t)ldv;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -435,7 +512,7 @@ __global__ void init_probes_kernel(T* v0, int64_t d, int ldv, int B, const int64
         const int64_t i = e / ldv;
         const int c = (int)(e % ldv);
         T z = T(0);
-        if (c < B) z = probe_negative(seedmix, (uint64_t)ids[c], (uint64_t)i) ? T(-1) : T(1);
+        if (c < B) z = probe_negative(seedmix, (uint64_t)ids[c], (uint64_t)(orig ? orig[i] : i)) ? T(-1) : T(1);
         v0[e] = z;
     }
 }
@@ -565,6 +642,7 @@ void set_split(StepArgs<T>& a, const SpmmPlan& P, T* segpart)
 // State shared by the recurrence steps of one probe group.
 struct GroupCtx {
     bool gram;
+    const int32_t* orig;    // relabelled operator (MLT_REORDER): original row ids, else null
     int64_t d;
     int ldv;
     double alpha, beta;
@@ -582,8 +660,9 @@ int run_steps(mlt_matrix* M, const MomentPlan& plan, GroupCtx& g, int k0, int k1
               T* segpart, cudaStream_t s)
 {
     constexpr int N = Lanes<T>::N;
-    const DevCSR& A = M->A;
+    const DevCSR& A = g.orig ? M->P : M->A;
     const DevCSR& AT = M->AT;
+    SpmmPlan& planA = g.orig ? M->plan_P : M->plan_A;
     const T* valA = vals_of<T>(A);
     const T* valAT = vals_of<T>(AT);
     int rc;
@@ -604,6 +683,7 @@ int run_steps(mlt_matrix* M, const MomentPlan& plan, GroupCtx& g, int k0, int k1
         sa.B = plan.B;
         sa.seedmix = g.seedmix;
         sa.ids = plan.ids_dev;
+        sa.orig = g.orig;
         int nb = 0;
         if (g.gram) {
             StepArgs<T> pa = sa;
@@ -618,7 +698,7 @@ int run_steps(mlt_matrix* M, const MomentPlan& plan, GroupCtx& g, int k0, int k1
         } else {
             sa.rowptr = A.rowptr; sa.col = A.col; sa.val = valA; sa.nrows = A.nrows;
             sa.vgather = cur;
-            set_split(sa, M->plan_A, segpart);
+            set_split(sa, planA, segpart);
         }
         sa.vcur = cur;
         sa.vprev_out = out;
@@ -658,6 +738,7 @@ int run_group(mlt_matrix* M, const MomentPlan& plan, int ks, double a, double b,
 {
     GroupCtx g;
     g.gram = (M->flags & MLT_GRAM) != 0;
+    g.orig = M->perm;
     g.d = plan.dim;
     g.ldv = plan.ldv;
     ks = std::max(0, std::min(ks, plan.K));
@@ -666,7 +747,7 @@ int run_group(mlt_matrix* M, const MomentPlan& plan, int ks, double a, double b,
     const size_t n = (size_t)g.d * g.ldv;
     const size_t wrows = g.gram ? (size_t)M->A.nrows * g.ldv : 0;
     int rc;
-    if ((rc = ensure_spmm_plan(M, M->A, M->plan_A, s))) return rc;
+    if ((rc = ensure_spmm_plan(M, g.orig ? M->P : M->A, g.orig ? M->plan_P : M->plan_A, s))) return rc;
     if (g.gram && (rc = ensure_spmm_plan(M, M->AT, M->plan_AT, s))) return rc;
     if (f32 && (rc = ensure_fp32_values(M, s))) return rc;
     // V buffers: FP32 pair in ws_v (when used), FP64 pair in ws_v (all-FP64) or ws_v2 (mixed)
@@ -685,7 +766,7 @@ int run_group(mlt_matrix* M, const MomentPlan& plan, int ks, double a, double b,
     }
     const size_t tsz = f64 ? sizeof(double) : sizeof(float);
     if (g.gram && (rc = M->ws_w.ensure(wrows * tsz, s))) return rc;
-    const int64_t nseg = std::max(M->plan_A.nseg, g.gram ? M->plan_AT.nseg : (int64_t)0);
+    const int64_t nseg = std::max((g.orig ? M->plan_P : M->plan_A).nseg, g.gram ? M->plan_AT.nseg : (int64_t)0);
     if ((rc = M->ws_seg.ensure((size_t)std::max<int64_t>(nseg, 1) * g.ldv * tsz, s))) return rc;
     g.max_main = 8 * M->num_sms;
     g.max_long = 2 * M->num_sms;
@@ -704,8 +785,8 @@ int run_group(mlt_matrix* M, const MomentPlan& plan, int ks, double a, double b,
     {
         const int nb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, 16LL * M->num_sms);
         ProfScope ps("init_probes", s);
-        if (f32) init_probes_kernel<float><<<std::max(nb, 1), 256, 0, s>>>(Vf[0], g.d, g.ldv, plan.B, plan.ids_dev, g.seedmix);
-        else init_probes_kernel<double><<<std::max(nb, 1), 256, 0, s>>>(Vd[0], g.d, g.ldv, plan.B, plan.ids_dev, g.seedmix);
+        if (f32) init_probes_kernel<float><<<std::max(nb, 1), 256, 0, s>>>(Vf[0], g.d, g.ldv, plan.B, plan.ids_dev, g.seedmix, g.orig);
+        else init_probes_kernel<double><<<std::max(nb, 1), 256, 0, s>>>(Vd[0], g.d, g.ldv, plan.B, plan.ids_dev, g.seedmix, g.orig);
     }
     MLT_CUDA_TRY(cudaGetLastError());
     if (f32) {
@@ -740,18 +821,19 @@ int run_group_df(mlt_matrix* M, const MomentPlan& plan, double a, double b, uint
 {
     GroupCtx g;
     g.gram = (M->flags & MLT_GRAM) != 0;
+    g.orig = M->perm;
     g.d = plan.dim;
     g.ldv = plan.ldv;
     const size_t n = (size_t)g.d * g.ldv;
     const size_t wrows = g.gram ? (size_t)M->A.nrows * g.ldv : 0;
     int rc;
-    if ((rc = ensure_spmm_plan(M, M->A, M->plan_A, s))) return rc;
+    if ((rc = ensure_spmm_plan(M, g.orig ? M->P : M->A, g.orig ? M->plan_P : M->plan_A, s))) return rc;
     if (g.gram && (rc = ensure_spmm_plan(M, M->AT, M->plan_AT, s))) return rc;
     if ((rc = ensure_df_values(M, s))) return rc;
     if ((rc = M->ws_v[0].ensure(n * sizeof(df64), s)) || (rc = M->ws_v[1].ensure(n * sizeof(df64), s))) return rc;
     df64* V[2] = {M->ws_v[0].as<df64>(), M->ws_v[1].as<df64>()};
     if (g.gram && (rc = M->ws_w.ensure(wrows * sizeof(df64), s))) return rc;
-    const int64_t nseg = std::max(M->plan_A.nseg, g.gram ? M->plan_AT.nseg : (int64_t)0);
+    const int64_t nseg = std::max((g.orig ? M->plan_P : M->plan_A).nseg, g.gram ? M->plan_AT.nseg : (int64_t)0);
     if ((rc = M->ws_seg.ensure((size_t)std::max<int64_t>(nseg, 1) * g.ldv * sizeof(df64), s))) return rc;
     g.max_main = 8 * M->num_sms;
     g.max_long = 2 * M->num_sms;
@@ -769,7 +851,7 @@ int run_group_df(mlt_matrix* M, const MomentPlan& plan, double a, double b, uint
     {
         const int nb = (int)std::min<int64_t>(((int64_t)n + 255) / 256, 16LL * M->num_sms);
         ProfScope ps("init_probes", s);
-        init_probes_kernel<df64><<<std::max(nb, 1), 256, 0, s>>>(V[0], g.d, g.ldv, plan.B, plan.ids_dev, g.seedmix);
+        init_probes_kernel<df64><<<std::max(nb, 1), 256, 0, s>>>(V[0], g.d, g.ldv, plan.B, plan.ids_dev, g.seedmix, g.orig);
     }
     MLT_CUDA_TRY(cudaGetLastError());
     if ((rc = run_steps<df64>(M, plan, g, 0, plan.K, V, M->ws_w.as<df64>(), M->ws_seg.as<df64>(), s))) return rc;
@@ -802,6 +884,7 @@ __global__ void scaled_copy_kernel(T* __restrict__ out, const T* __restrict__ x,
 int block_ctx(mlt_matrix* M, int ldv, int cols, int K, double a, double b, GroupCtx& g, cudaStream_t s)
 {
     g.gram = (M->flags & MLT_GRAM) != 0;
+    g.orig = nullptr;   // explicit vector blocks are in original row order
     g.d = g.gram ? M->A.ncols : M->A.nrows;
     g.ldv = ldv;
     int rc;
@@ -1066,6 +1149,7 @@ int ensure_df_values(mlt_matrix* M, cudaStream_t s)
     };
     int rc = conv(M->A, M->own_val_df);
     if (rc) return rc;
+    if (M->perm && (rc = conv(M->P, M->own_p_val_df))) return rc;
     if (M->flags & MLT_GRAM) rc = conv(M->AT, M->own_t_val_df);
     return rc;
 }
@@ -1087,6 +1171,7 @@ int ensure_fp32_values(mlt_matrix* M, cudaStream_t s)
     };
     int rc = conv(M->A, M->own_val32);
     if (rc) return rc;
+    if (M->perm && (rc = conv(M->P, M->own_p_val32))) return rc;
     if (M->flags & MLT_GRAM) rc = conv(M->AT, M->own_t_val32);
     return rc;
 }

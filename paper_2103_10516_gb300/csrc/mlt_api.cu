@@ -383,7 +383,8 @@ static void free_matrix(mlt_matrix* M)
 {
     void* owned[] = {M->own_rowptr, M->own_col, M->own_val, M->own_val32, M->own_t_rowptr,
                      M->own_t_col, M->own_t_val, M->own_t_val32, M->own_val_df, M->own_t_val_df,
-                     M->plan_A.mem, M->plan_AT.mem};
+                     M->own_p_rowptr, M->own_p_col, M->own_p_val, M->own_p_val32, M->own_p_val_df,
+                     M->perm, M->plan_A.mem, M->plan_AT.mem, M->plan_P.mem};
     for (void* p : owned)
         if (p) cudaFreeAsync(p, 0);   // called with the handle's work finished
     mlt::DevBuf* bufs[] = {&M->ws_v[0], &M->ws_v[1], &M->ws_v2[0], &M->ws_v2[1], &M->ws_w, &M->ws_part, &M->ws_dots,
@@ -622,7 +623,8 @@ int mlt_create_csr(int64_t nrows, int64_t ncols, int64_t nnz, const int64_t* row
         if (!std::isfinite(scale)) return fail(MLT_EINVAL, "mlt_create_csr: scale must be finite");
         const bool gram = (flags & MLT_GRAM) != 0;
         if (!gram && nrows != ncols) return fail(MLT_EINVAL, "mlt_create_csr: matrix must be square");
-        if (flags & ~(MLT_GRAM | MLT_DEVICE_PTRS)) return fail(MLT_EINVAL, "mlt_create_csr: unknown flags");
+        if (flags & ~(MLT_GRAM | MLT_DEVICE_PTRS | MLT_REORDER)) return fail(MLT_EINVAL, "mlt_create_csr: unknown flags");
+        if ((flags & MLT_REORDER) && gram) return fail(MLT_EINVAL, "mlt_create_csr: MLT_REORDER needs a square operator, not X^T X");
         const bool dev = (flags & MLT_DEVICE_PTRS) != 0;
         cudaStream_t s = (cudaStream_t)stream;
 
@@ -789,6 +791,7 @@ int mlt_create_csr(int64_t nrows, int64_t ncols, int64_t nnz, const int64_t* row
             }
             if ((rc = cuda_fail(cudaStreamSynchronize(s), "sync"))) return bail(rc);
         }
+        if ((flags & MLT_REORDER) && (rc = build_reorder(M, s))) return bail(rc);
         if ((rc = cuda_fail(cudaStreamSynchronize(s), "mlt_create_csr sync"))) return bail(rc);
         *out = M;
         return MLT_OK;

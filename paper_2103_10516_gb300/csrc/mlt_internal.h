@@ -87,6 +87,8 @@ struct mlt_matrix {
     double scale = 1.0;
     mlt::DevCSR A;     // A itself, or X for a Gram handle
     mlt::DevCSR AT;    // X^T for a Gram handle
+    mlt::DevCSR P;     // MLT_REORDER: A relabelled by decreasing degree (the moment engine's operand)
+    int32_t* perm = nullptr;   // MLT_REORDER: original id of each relabelled row (device), else null
     bool owns = true;
     // owned device allocations (null when referencing caller memory)
     void* own_rowptr = nullptr; void* own_col = nullptr; void* own_val = nullptr;
@@ -95,6 +97,8 @@ struct mlt_matrix {
     void* own_t_val32 = nullptr;
     void* own_val_df = nullptr;
     void* own_t_val_df = nullptr;
+    void* own_p_rowptr = nullptr; void* own_p_col = nullptr; void* own_p_val = nullptr;
+    void* own_p_val32 = nullptr; void* own_p_val_df = nullptr;
     // triangle preparation (inside ws_tri; out_col and pairs inside ws_upcol)
     struct {
         int64_t* out_ptr = nullptr;  // row pointer of the degree-oriented out-lists
@@ -116,7 +120,7 @@ struct mlt_matrix {
     double tri_bound = 0.0;     // sum_(i,j) deg_i deg_j
     int group_width = 0;        // probes per group chosen by mlt_autotune (0: from memory)
     // scratch
-    mlt::SpmmPlan plan_A, plan_AT;
+    mlt::SpmmPlan plan_A, plan_AT, plan_P;
     mlt::DevBuf ws_v[2], ws_v2[2], ws_w, ws_part, ws_dots, ws_misc, ws_out, ws_y, ws_y16, ws_y32, ws_z, ws_x, ws_tri,
         ws_seg, ws_upcol;
     mlt::DevBuf ws_blk[4];      // explicit FP64 vector blocks (polynomial application, Hutch++)
@@ -177,6 +181,8 @@ int poly_apply_block_f32(mlt_matrix* M, double a, double b, const double* c, int
 int moments_block(mlt_matrix* M, double a, double b, double* V0, double* V1, int ldv, int cols, int K,
                   const double** dots_dev, bool df, cudaStream_t s);
 int ensure_spmm_plan(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, cudaStream_t s);
+// MLT_REORDER: build M->P and M->perm (reorder.cu).
+int build_reorder(mlt_matrix* M, cudaStream_t s);
 int spmv_f64(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, const double* x, double* y, cudaStream_t s);
 int lanczos_bounds(mlt_matrix* M, int steps, uint64_t seed, double* lo, double* hi, cudaStream_t s);
 

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libmlt.so")
 
 MLT_OK, MLT_EINVAL, MLT_ENOMEM, MLT_ECUDA, MLT_ERANGE, MLT_ETIMEOUT = 0, -1, -2, -3, -4, -5
 MLT_F64, MLT_F32, MLT_PATTERN = 0, 1, 2
-MLT_GRAM, MLT_DEVICE_PTRS = 1, 2
+MLT_GRAM, MLT_DEVICE_PTRS, MLT_REORDER = 1, 2, 4
 MLT_FN = {"log": 0, "sqrt": 1, "exp": 2, "inv": 3, "pow": 4, "cube": 5}
 MLT_PREC = {"fp64": 0, "fp32": 1, "df64": 3}
 MLT_DIRECT = 1
@@ -360,13 +360,14 @@ def mlt_last_error():
 class Matrix:
     """Owns one mlt_matrix handle built from host CSR arrays (or CUDA tensors)."""
 
-    def __init__(self, csr, gram=False, scale=1.0, vals_dtype=None, stream=None):
+    def __init__(self, csr, gram=False, scale=1.0, vals_dtype=None, stream=None, reorder=False):
         vals = csr.val
         if vals is not None and vals_dtype is not None:
             vals = np.ascontiguousarray(vals, dtype=vals_dtype)
         self._keep = (csr.rowptr, csr.col, vals)
+        flags = (MLT_GRAM if gram else 0) | (MLT_REORDER if reorder else 0)
         self.handle = mlt_create_csr(csr.nrows, csr.ncols, csr.nnz, csr.rowptr, csr.col, vals,
-                                     scale=scale, flags=MLT_GRAM if gram else 0, stream=stream)
+                                     scale=scale, flags=flags, stream=stream)
         self.dim, self.nnz = mlt_matrix_info(self.handle)
 
     def close(self):

@@ -67,6 +67,7 @@ def test_constants_match_header(L):
     assert val("MLT_EINVAL") == L.MLT_EINVAL and val("MLT_ERANGE") == L.MLT_ERANGE
     assert val("MLT_MAX_LEVELS") == L.MLT_MAX_LEVELS and val("MLT_MAX_DEGREE") == L.MLT_MAX_DEGREE
     assert val("MLT_GRAM") == L.MLT_GRAM and val("MLT_DEVICE_PTRS") == L.MLT_DEVICE_PTRS
+    assert val("MLT_REORDER") == L.MLT_REORDER and val("MLT_TRI_CV_CHEB") == L.MLT_TRI_CV["cheb"]
     assert val("MLT_FN_SQRT") == L.MLT_FN["sqrt"] and val("MLT_PREC_FP32") == L.MLT_PREC["fp32"]
     assert val("MLT_NET_NPARAMS") == L.MLT_NET_NPARAMS and val("MLT_NET_HID") == L.MLT_NET_HID
 
