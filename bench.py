@@ -2,14 +2,22 @@
 """Throughput benchmark of the multilevel Chebyshev-Hutchinson engine on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload rmat20_triangles|logdet64|estrada_rmat22|diffusion64_batched|
+                    [--workload estrada_rmat22|rmat20_triangles|logdet64|diffusion64_batched|
                                 nuclear_gram|nuclear_explicit|stencil3d|estrada_learned|level_study|
                                 estrada_hutchpp]
-                    [--precision fp32|fp64|mixed] [--scale S]
+                    [--precision df64|fp64|fp32|mixed] [--scale S] [--no-comparison]
 
 One step is one pass of the whole hot path over one batch of synthetic input:
 
-  rmat20_triangles (default): exact int64 triangle moments of an R-MAT graph
+  estrada_rmat22 (default): Chebyshev moments of the Estrada-index workload,
+      the scale-22 R-MAT adjacency (edge factor 16, seed 1) scaled to spectral
+      radius 10 (a Lanczos bound; interval [-10, 10]), 128 probes to degree
+      128, in double-float pairs (FP64-class; --precision fp64 or fp32 also),
+      on the handle relabelled by degree.  Units: probe-matvecs (64 per probe).
+      Setup also compares, untimed, the learned level (FP32 moments, network
+      trained on 2^14 probes) with plain FP64 MLMC at equal standard error and
+      reports the variance-per-GPU-second gain in config["comparison"].
+  rmat20_triangles: exact int64 triangle moments of an R-MAT graph
       (scale 20, edge factor 16, a=0.57, b=c=0.19, seed 0; symmetric, no
       self-loops or duplicates) for 1024 Rademacher probes in blocks of 128,
       two blocks per launch,
@@ -17,9 +25,6 @@ One step is one pass of the whole hot path over one batch of synthetic input:
   logdet64: multilevel log-det of the 64x64 Dirichlet Laplacian + 0.1 I,
       levels {8, 32, 128} with {256, 64, 16} probes, FP64.  Units: probe-matvecs
       with the doubling evaluation (3072 per step).
-  estrada_rmat22: FP32 Chebyshev moments of the scale-22 R-MAT adjacency
-      scaled to spectral radius 10 (a Lanczos bound; interval [-10, 10]),
-      256 probes to degree 128.  Units: probe-matvecs (64 per probe).
   diffusion64_batched: FP64 log-det level moments of 64 3D diffusion
       operators (10^3 .. 100^3 grids) in one CUDA-graph launch.  Units:
       probe-matvecs summed over the matrices.
@@ -64,8 +69,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-# FP64 (non-tensor) rate of a GB300, nominal: the denominator of the FP64
-# recurrence, which is bound by FP64 arithmetic on this part, not by HBM
+# FP64 (non-tensor) rate of a GB300, nominal: the denominator of FP64
+# recurrence steps (bound by FP64 arithmetic on this part, not by HBM) when the
+# measured rate (mlt_fp64_rate, an FMA loop timed on the device) is unavailable
 FP64_TFLOPS_NOMINAL = 1.25
 
 
@@ -369,47 +375,158 @@ class LogDet64:
         return int(np.sum((deg + 1) // 2))
 
 
+def learned_comparison(mlt, torch, M, sp, base, ntrain, budget, precision="fp32", epochs=40, batch=2048):
+    """The learned coarse level against the plain FP64 multilevel estimator at
+    equal standard error, on the handle M (Estrada index: exp on [-10, 10],
+    n = 128, levels S, P_64 - S, P_128 - P_64 for the learned form).
+
+      1. plain FP64 MLMC, levels and sample counts from a 10-probe pilot under
+         a `budget`-matvec budget: estimate, standard error s_p, GPU time t_p
+         (and the same in FP32, to separate precision from the network);
+      2. the BF16 network trained on `ntrain` probes ((mu_0..mu_15)/d -> P_64/d);
+      3. a pilot of the learned estimator gives its level variances V_k; sample
+         counts m_k = sqrt(V_k / C_k) sum_j sqrt(V_j C_j) / s_p^2 (C = 8, 32, 64
+         recurrence steps) target the standard error s_p.
+    Returns (comparison dict, surrogate, m); the caller times learned estimates
+    with m and calls finish_comparison."""
+    def timed(fn):
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        out = fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1) / 1e3
+    N, L1, COST = 128, 64, (8, 32, 64)
+    plain, t_p = timed(lambda: M.mlmc("exp", -10.0, 10.0, N, seed=3, m_pilot=10, mode="budget", target=budget,
+                                      precision="fp64", stream=sp))
+    plain32, t_p32 = timed(lambda: M.mlmc("exp", -10.0, 10.0, N, seed=3, m_pilot=10, mode="budget", target=budget,
+                                          precision="fp32", stream=sp))
+    S = mlt.Surrogate(5)
+    P = mlt.learned_params("exp", -10.0, 10.0, N, L1, 1, 1, 1, seed=7, probe_offset=base, precision=precision,
+                           stream=sp)
+    loss, t_train = timed(lambda: mlt.mlt_learned_train(M.handle, S.handle, P, ntrain, base, epochs, batch, 2e-3))
+    pil = mlt.learned_params("exp", -10.0, 10.0, N, L1, 512, 128, 32, seed=11, probe_offset=base + (1 << 22),
+                             precision=precision, stream=sp)
+    pilot, t_pil = timed(lambda: mlt.mlt_learned_estimate(M.handle, S.handle, pil))
+    V = [max(v, 1e-300) for v in pilot["level_var"]]
+    s2 = plain["stderr"] ** 2
+    tot = sum(np.sqrt(v * c) for v, c in zip(V, COST))
+    m = [max(2, int(np.ceil(np.sqrt(v / c) * tot / s2))) for v, c in zip(V, COST)]
+    cmp = {"plain_fp64": {"estimate": plain["estimate"], "stderr": plain["stderr"], "gpu_s": round(t_p, 4),
+                          "levels": plain["levels"], "m": plain["m"], "level_var": plain["level_var"],
+                          "budget_matvecs": budget},
+           "plain_fp32": {"estimate": plain32["estimate"], "stderr": plain32["stderr"], "gpu_s": round(t_p32, 4),
+                          "levels": plain32["levels"], "m": plain32["m"]},
+           "learned": {"precision": precision, "train_probes": ntrain, "train_gpu_s": round(t_train, 3),
+                       "train_loss": loss, "pilot_level_var": V, "pilot_gpu_s": round(t_pil, 4)}}
+    return cmp, S, m
+
+
+def finish_comparison(cmp, results, gpu_s, m):
+    """(s^2 t)_plain / (s^2 t)_learned from the learned estimates' standard
+    errors (results: (estimate, stderr) pairs) and their mean GPU time."""
+    if not results:
+        return
+    se = float(np.sqrt(np.mean([e[1] ** 2 for e in results])))
+    lp = cmp["learned"]
+    lp.update({"estimate_first": results[0][0], "stderr": se, "gpu_s": round(gpu_s, 4), "m": m,
+               "estimates": len(results)})
+    pl = cmp["plain_fp64"]
+    cmp["variance_time_gain"] = round((pl["stderr"] ** 2 * pl["gpu_s"]) / (se ** 2 * gpu_s), 3)
+    p32 = cmp["plain_fp32"]
+    cmp["variance_time_gain_vs_plain_fp32"] = round((p32["stderr"] ** 2 * p32["gpu_s"]) / (se ** 2 * gpu_s), 3)
+    cmp["estimates_to_amortise_training"] = round(
+        lp["train_gpu_s"] / max(pl["gpu_s"] * (pl["stderr"] ** 2 / se ** 2) - gpu_s, 1e-9), 1)
+
+
 class EstradaRmat22:
+    """The Estrada-index configuration (R-MAT scale 22, edge factor 16, seed 1,
+    adjacency scaled to spectral radius 10 by a Lanczos bound, exp on [-10, 10],
+    degree 128): Chebyshev moments of 128 probes to degree 128 per step, in
+    double-float pairs by default (FP64-class moments on the FP32 pipes; fp64
+    and fp32 selectable), on the handle relabelled by degree (MLT_REORDER).
+    Setup also runs, untimed, the learned level against plain FP64 MLMC
+    (learned_comparison, network trained on 2^14 probes) and reports the
+    variance-per-GPU-second gain in config["comparison"]."""
     name = "estrada_rmat22"
     unit = "probe-matvecs/s"
-    dtype = "f32"
-    NPROBES = 256
+    NPROBES = 128
     DEG = 128
-    PROBE_SPAN = (1024 + 64) * 256
+    PROBE_SPAN = 1 << 28     # timed (2^20 ids), e2e (2^20) and comparison (from 2^24) ranges
 
-    def __init__(self):
+    def __init__(self, precision=None, compare=True, train_probes=1 << 14):
         from paper_2103_10516_gb300 import synth
+        self.precision = precision or "df64"
+        self.dtype = {"df64": "df64", "fp64": "f64", "fp32": "f32"}[self.precision]
         self.csr = synth.rmat_adjacency(22, 16, seed=1)
         self.d = self.csr.nrows
         self.nnz = self.csr.nnz
         self.scale = None
+        self.compare = compare
+        self.train_probes = train_probes
+        self.cmp = None
 
     def units(self):
         return self.NPROBES * ((self.DEG + 1) // 2)
 
     def config(self):
-        return {"workload": self.name, "graph": "R-MAT scale 22, edge factor 16, seed 1",
-                "d": self.d, "nnz": self.nnz, "probes": self.NPROBES, "degree": self.DEG,
-                "precision": "fp32 vectors, compensated fp32 dots per thread, fp64 after",
-                "interval": [-10.0, 10.0], "scale": self.scale,
-                "group_width": getattr(self, "group_width", None),
-                "l2": "inputs larger than L2 (V 2 x %.0f MB)" % (self.d * self.NPROBES * 4e-6)}
+        prec = {"df64": "double-float vectors and per-thread dots (FP64-class), fp64 after",
+                "fp64": "fp64 throughout",
+                "fp32": "fp32 vectors, compensated fp32 dots per thread, fp64 after"}[self.precision]
+        return {"workload": self.name, "graph": "R-MAT scale 22, edge factor 16, a=0.57 b=c=0.19, seed 1",
+                "d": self.d, "nnz": self.nnz, "probes": self.NPROBES, "degree": self.DEG, "f": "exp",
+                "precision": prec, "interval": [-10.0, 10.0], "scale": self.scale, "relabelled_by_degree": True,
+                "group_width": getattr(self, "group_width", None), "comparison": self.cmp,
+                "l2": "inputs larger than L2 (V blocks 2 x %.0f MB)" % (self.d * self.NPROBES * self._sv() * 1e-6)}
+
+    def _sv(self):
+        return 4 if self.precision == "fp32" else 8
 
     def kernel_bytes(self, launches_per_step):
-        return step_bytes(self.d, self.nnz, 4, 4, self.units(), launches_per_step)
+        return step_bytes(self.d, self.nnz, 4, self._sv(), self.units(), launches_per_step)
+
+    def kernel_flops(self, launches_per_step):
+        n = launches_per_step.get("cheb_step")
+        return {"cheb_step": step_flops(self.d, self.nnz, self.units()) / n} if n else {}
+
+    def gather_bytes(self, launches_per_step):
+        """Bytes of gathered V_k rows per launch (every stored entry reads its
+        column's row slice of the live probes): nnz x s_v per probe-matvec."""
+        n = launches_per_step.get("cheb_step")
+        return self.nnz * self._sv() * self.units() / n if n else None
 
     def setup(self, mlt, torch, rank):
+        sp = torch.cuda.current_stream().cuda_stream
         self.scale = estrada_scale(mlt, self.csr)       # spectral radius 10: spectrum in [-10, 10]
-        self.M = mlt.Matrix(self.csr, scale=self.scale)
+        self.M = mlt.Matrix(self.csr, scale=self.scale, reorder=True)
         # probe-group width by the library's autotuner (untimed setup)
-        self.group_width = mlt.mlt_autotune(self.M.handle, "fp32", 4)
+        self.group_width = mlt.mlt_autotune(self.M.handle, self.precision, 4)
         self.out = torch.empty((self.NPROBES, self.DEG + 1), dtype=torch.float64, device="cuda")
         self.deg = np.full(self.NPROBES, self.DEG, dtype=np.int32)
         self.base = probe_base(rank)
+        if self.compare:
+            cbase = self.base + (1 << 24)
+            self.cmp, S, m = learned_comparison(mlt, torch, self.M, sp, cbase, self.train_probes, 16384)
+            res, t = [], 0.0
+            for i in range(3):
+                P = mlt.learned_params("exp", -10.0, 10.0, 128, 64, *m, seed=13,
+                                       probe_offset=cbase + (1 << 23) + i * sum(m), precision="fp32", stream=sp)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(torch.cuda.current_stream())
+                r = mlt.mlt_learned_estimate(self.M.handle, S.handle, P)
+                e1.record(torch.cuda.current_stream())
+                torch.cuda.synchronize()
+                t += e0.elapsed_time(e1) / 1e3
+                res.append((r["estimate"], r["stderr"]))
+            finish_comparison(self.cmp, res, t / len(res), m)
+            S.close()
 
     def step(self, mlt, stream, i):
-        return mlt.mlt_moments(self.M.handle, -10.0, 10.0, 0, self.base + (i % 1024) * self.NPROBES,
-                               self.deg, precision="fp32", out=self.out, stream=stream)
+        return mlt.mlt_moments(self.M.handle, -10.0, 10.0, 0, self.base + (i % 8192) * self.NPROBES,
+                               self.deg, precision=self.precision, out=self.out, stream=stream)
 
     def e2e_setup(self, torch):
         self.h_rowptr = torch.from_numpy(self.csr.rowptr).pin_memory()
@@ -419,10 +536,10 @@ class EstradaRmat22:
 
     def e2e_step(self, mlt, stream, i):
         h = mlt.mlt_create_csr(self.d, self.d, self.nnz, self.h_rowptr, self.h_col, None,
-                               scale=self.scale, stream=stream)
+                               scale=self.scale, flags=mlt.MLT_REORDER, stream=stream)
         try:
-            mlt.mlt_moments(h, -10.0, 10.0, 0, self.base + (1024 + i) * self.NPROBES, self.deg,
-                            precision="fp32", out=self.h_out, stream=stream)
+            mlt.mlt_moments(h, -10.0, 10.0, 0, self.base + (8192 + i) * self.NPROBES, self.deg,
+                            precision=self.precision, out=self.h_out, stream=stream)
         finally:
             mlt.mlt_destroy(h)
 
@@ -434,6 +551,7 @@ class EstradaRmat22:
         deg = np.full(nprobes, 4, dtype=np.int32)
         oracle.moments(self.csr, -10.0, 10.0, 0, offset, deg, scale=self.scale)
         return nprobes * 4       # the oracle runs direct: one matvec per degree
+
 
 class EstradaHutchpp:
     """Hutch++ (Section 5.3's proposal for the Estrada index) against plain
@@ -995,6 +1113,104 @@ class EstradaLearned:
         sv = 8 if self.precision in ("fp64", "df64") else 4
         return step_bytes(self.d, self.nnz, 4, sv, self.units(), launches_per_step)
 
+    def setup(self, mlt, torch, rank):
+        sp = torch.cuda.current_stream().cuda_stream
+        self.scale = estrada_scale(mlt, self.csr)       # spectral radius 10: spectrum in [-10, 10]
+        self.M = mlt.Matrix(self.csr, scale=self.scale, reorder=True)
+        self.group_width = mlt.mlt_autotune(self.M.handle, self.precision, 4)
+        base = probe_base(rank)
+        self.cmp, self.S, self.m = learned_comparison(mlt, torch, self.M, sp, base, self.ntrain, self.budget,
+                                                      precision=self.precision)
+        self.base = base + (1 << 23)
+        self.results = []
+
+    def step(self, mlt, stream, i):
+        P = mlt.learned_params("exp", -10.0, 10.0, self.N, self.L1, *self.m, seed=13,
+                               probe_offset=self.base + i * sum(self.m), precision=self.precision, stream=stream)
+        r = mlt.mlt_learned_estimate(self.M.handle, self.S.handle, P)
+        self.results.append((r["estimate"], r["stderr"]))
+        return r
+
+    def finish(self, ms_per_step):
+        """Called after the timed steps: the comparison at the measured time."""
+        finish_comparison(self.cmp, self.results, ms_per_step / 1e3, self.m)
+
+    def e2e_setup(self, torch):
+        self.h = (torch.from_numpy(self.csr.rowptr).pin_memory(), torch.from_numpy(self.csr.col).pin_memory(),
+                  torch.from_numpy(self.csr.val).pin_memory())
+        self.h_out = torch.empty((self.NPROBES, self.DEG + 1), dtype=torch.float64).pin_memory()
+        return (sum(t.numel() * t.element_size() for t in self.h), self.h_out.numel() * 8)
+
+    def e2e_step(self, mlt, stream, i):
+        r, c, v = self.h
+        h = mlt.mlt_create_csr(self.d, self.d, self.nnz, r, c, v, stream=stream)
+        try:
+            mlt.mlt_moments(h, self.ab[0], self.ab[1], 0, self.base + (1024 + i) * self.NPROBES, self.deg,
+                            precision=self._prec(mlt), out=self.h_out, stream=stream)
+        finally:
+            mlt.mlt_destroy(h)
+
+    def cpu_sample(self, oracle, nprobes, offset):
+        if not hasattr(self, "ab"):
+            self.ab = [0.1, gershgorin_upper(self.csr)]
+        deg = np.full(nprobes, 8, dtype=np.int32)
+        oracle.moments(self.csr, self.ab[0], self.ab[1], 0, offset, deg)
+        return int(np.sum(deg))                  # direct recurrence: one probe-matvec per degree
+
+
+class EstradaLearned:
+    """The learned coarse level against the plain FP64 multilevel estimator,
+    at equal standard error, on the Estrada index tr exp(A): R-MAT adjacency
+    (edge factor 16, seed 1) scaled to spectral radius 10 (a Lanczos bound),
+    interval [-10, 10], n = 128.
+
+    Setup (untimed, reported in config["comparison"]):
+      1. plain FP64 MLMC with levels and sample counts from a 10-probe pilot
+         under a fixed matvec budget: estimate, standard error s_p, GPU time t_p;
+      2. the BF16 network trained on 2^16 probes ((mu_0..mu_15)/d ->
+         P_64/d), GPU time of training;
+      3. a small pilot of the learned estimator gives the variances V_k of its
+         levels (S, P_64 - S, P_128 - P_64); sample counts m_k follow the
+         optimal allocation m_k = sqrt(V_k / C_k) sum_j sqrt(V_j C_j) / s_p^2
+         (C = 8, 32, 64 recurrence steps) so that its standard error matches s_p.
+    Step (timed): one learned estimate with those m_k, its moments in the
+    --precision given (fp32 by default, or fp64).  The reported ratio is
+    (s^2 t)_plain / (s^2 t)_learned, the variance-per-GPU-second gain."""
+    name = "estrada_learned"
+    unit = "probe-matvecs/s"
+    L1, N = 64, 128
+    COST = (8, 32, 64)
+    PROBE_SPAN = 1 << 28       # training, pilot, timed and e2e ranges below, all inside it
+
+    def __init__(self, scale=None, precision=None):
+        from paper_2103_10516_gb300 import synth
+        self.scale_log2 = scale or 22
+        self.precision = precision or "fp32"
+        self.dtype = "f32+bf16" if self.precision == "fp32" else "f64+bf16"
+        self.csr = synth.rmat_adjacency(self.scale_log2, 16, seed=1)
+        self.d = self.csr.nrows
+        self.nnz = self.csr.nnz
+        self.ntrain = 1 << 16
+        self.budget = 16384
+        self.cmp = None
+        self.m = None
+        self.scale = None
+
+    def units(self):
+        return int(sum(mk * c for mk, c in zip(self.m, self.COST)))
+
+    def config(self):
+        return {"workload": self.name, "graph": "R-MAT scale %d, edge factor 16, seed 1" % self.scale_log2,
+                "d": self.d, "nnz": self.nnz, "f": "exp", "interval": [-10.0, 10.0], "scale": self.scale,
+                "n": self.N,
+                "l1": self.L1, "train_probes": self.ntrain, "precision": self.precision, "m": self.m,
+                "comparison": self.cmp,
+                "l2": "inputs larger than L2 (V blocks of 4 B x d per probe)"}
+
+    def kernel_bytes(self, launches_per_step):
+        sv = 8 if self.precision in ("fp64", "df64") else 4
+        return step_bytes(self.d, self.nnz, 4, sv, self.units(), launches_per_step)
+
     def _timed(self, torch, fn):
         st = torch.cuda.current_stream()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1071,7 +1287,7 @@ class EstradaLearned:
 
     def e2e_step(self, mlt, stream, i):
         h = mlt.mlt_create_csr(self.d, self.d, self.nnz, self.h[0], self.h[1], None, scale=self.scale,
-                               stream=stream)
+                               flags=mlt.MLT_REORDER, stream=stream)
         try:
             P = mlt.learned_params("exp", -10.0, 10.0, self.N, self.L1, *self.m, seed=17,
                                    probe_offset=base_e2e(self.base) + i * sum(self.m), precision=self.precision,
@@ -1317,6 +1533,13 @@ def run_ours(args, dist):
 
     # roofline of the dominant kernel
     peaks, src = load_peaks()
+    fp64_peak, fp64_src = FP64_TFLOPS_NOMINAL, "nominal FP64 rate of GB300"
+    if wl.dtype == "f64":
+        try:
+            fp64_peak = max(mlt.mlt_fp64_rate(1 << 16) for _ in range(3))
+            fp64_src = "measured: register-resident FP64 FMA loop (mlt_fp64_rate), best of 3"
+        except Exception:
+            pass
     kb = wl.kernel_bytes({k: v[0] / args.steps for k, v in stats.items()})
     top = max(stats.items(), key=lambda kv: kv[1][1]) if stats else None
     roof = None
@@ -1333,9 +1556,9 @@ def run_ours(args, dist):
             if wl.dtype == "f64" and hasattr(wl, "kernel_flops") else {}
         if kf.get(name) is not None:
             ach = kf[name] / (avg_ms / 1e3) / 1e12
-            roof = {"bound": "alu", "kernel": name, "achieved": round(ach, 4), "peak": FP64_TFLOPS_NOMINAL,
-                    "unit": "TFLOP/s", "frac": round(ach / FP64_TFLOPS_NOMINAL, 4),
-                    "peak_source": "nominal FP64 rate of GB300", "avg_launch_ms": round(avg_ms, 4),
+            roof = {"bound": "alu", "kernel": name, "achieved": round(ach, 4), "peak": round(fp64_peak, 4),
+                    "unit": "TFLOP/s", "frac": round(ach / fp64_peak, 4),
+                    "peak_source": fp64_src, "avg_launch_ms": round(avg_ms, 4),
                     "algorithmic_flops_per_launch": int(kf[name]),
                     "hbm_gbs_on_algorithmic_bytes": round(byt / (avg_ms / 1e3) / 1e9, 1) if byt else None,
                     "includes": companion if companion in stats else None,
@@ -1349,6 +1572,13 @@ def run_ours(args, dist):
                     "includes": companion if companion in stats else None,
                     "traffic": getattr(wl, "TRAFFIC", {}).get(name),
                     "share_of_step": round(tot / (ms * args.steps), 4)}
+            gb = wl.gather_bytes({k: v[0] / args.steps for k, v in stats.items()}) \
+                if hasattr(wl, "gather_bytes") and name == "cheb_step" else None
+            if gb:
+                # the gathered rows, beside the algorithmic bytes: a row of V_k
+                # is read once per stored entry, mostly from L2
+                roof["gathered_bytes_per_launch"] = int(gb)
+                roof["gather_tbs"] = round(gb / (avg_ms / 1e3) / 1e12, 3)
     launches = int(sum(v[0] for v in stats.values()))
     if not stats and hasattr(wl, "graph_step"):
         # the step is one CUDA graph: its kernels are not timed one by one, so
@@ -1364,8 +1594,8 @@ def run_ours(args, dist):
                     "includes": "every kernel of the graph", "traffic": None, "share_of_step": 1.0}
         else:
             roof = {"bound": "alu", "kernel": "moments_graph (whole step)", "achieved": round(ach, 4),
-                    "peak": FP64_TFLOPS_NOMINAL, "unit": "TFLOP/s", "frac": round(ach / FP64_TFLOPS_NOMINAL, 4),
-                    "peak_source": "nominal FP64 rate of GB300", "avg_launch_ms": round(ms, 4),
+                    "peak": round(fp64_peak, 4), "unit": "TFLOP/s", "frac": round(ach / fp64_peak, 4),
+                    "peak_source": fp64_src, "avg_launch_ms": round(ms, 4),
                     "algorithmic_flops_per_launch": int(fl),
                     "hbm_gbs_on_algorithmic_bytes": round(byt / (ms / 1e3) / 1e9, 1),
                     "includes": "every kernel of the graph", "traffic": None, "share_of_step": 1.0}
@@ -1436,9 +1666,12 @@ def make_workload(args):
             raise SystemExit("--scale applies to the estrada_learned workload only")
         kw["scale"] = args.scale
     if args.precision is not None:
-        if cls not in (NuclearGram, NuclearExplicit, Stencil3D, EstradaLearned, EstradaHutchpp, Diffusion64Batched):
-            raise SystemExit("--precision applies to nuclear_gram, stencil3d, estrada_learned, estrada_hutchpp "
-                             "and diffusion64_batched only")
+        if cls not in (NuclearGram, NuclearExplicit, Stencil3D, EstradaLearned, EstradaHutchpp, Diffusion64Batched,
+                       EstradaRmat22):
+            raise SystemExit("--precision applies to estrada_rmat22, nuclear_gram, stencil3d, estrada_learned, "
+                             "estrada_hutchpp and diffusion64_batched only")
+        if cls is EstradaRmat22 and args.precision not in ("df64", "fp64", "fp32"):
+            raise SystemExit("estrada_rmat22 takes df64, fp64 or fp32")
         if cls is Diffusion64Batched and args.precision not in ("fp64", "df64"):
             raise SystemExit("diffusion64_batched takes fp64 or df64")
         if cls is EstradaHutchpp and args.precision not in ("fp32", "fp64", "df64"):
@@ -1447,6 +1680,8 @@ def make_workload(args):
         if cls is EstradaLearned and args.precision not in ("fp32", "fp64"):
             raise SystemExit("estrada_learned takes fp32 or fp64")
         kw["precision"] = args.precision
+    if cls is EstradaRmat22 and getattr(args, "no_comparison", False):
+        kw["compare"] = False
     return cls(**kw)
 
 
@@ -1456,11 +1691,13 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat20_triangles", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="estrada_rmat22", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64", "df64", "mixed"])
     ap.add_argument("--scale", type=int, default=None, help="R-MAT scale of estrada_learned")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparison", action="store_true",
+                    help="estrada_rmat22: skip the learned-vs-plain comparison in setup")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -500,6 +500,13 @@ int mlt_surrogate_destroy(mlt_surrogate* s);
 /* Copy the FP32 parameter vector in or out (host arrays of MLT_NET_NPARAMS). */
 int mlt_surrogate_set_params(mlt_surrogate* s, const float* params);
 int mlt_surrogate_get_params(mlt_surrogate* s, float* params);
+/* The standardisation mlt_learned_train set (host array of 34 doubles): the
+ * 16 feature means, the 16 feature standard deviations, then the target's
+ * mean and standard deviation; feature k enters the network as
+ * (mu_k/d - mean_k)/std_k and the network's estimate of P_l1 is
+ * d (mean_t + std_t y).  *has_norm is 0 (and the array all zeros) before any
+ * training, when features and target enter unscaled. */
+int mlt_surrogate_get_norm(mlt_surrogate* s, double* norm, int* has_norm);
 /* Mean squared error over n samples and its gradient (host array of
  * MLT_NET_NPARAMS, may be NULL); the parameters are not changed. */
 int mlt_surrogate_loss_grad(mlt_surrogate* s, const float* x, const float* t, int64_t n,
@@ -579,6 +586,18 @@ int mlt_moments_noalloc(int64_t d, int64_t nnz, const int64_t* rowptr, const int
                         const double* vals, double scale, double a, double b, uint64_t seed,
                         int64_t probe_offset, int nprobes, const int32_t* degree, double* mu,
                         int64_t ld_mu, void* stream);
+
+/*
+ * The FP64 arithmetic rate of the current device, in TFLOP/s, measured (the
+ * paper has no counterpart: it is the denominator of the roofline of FP64
+ * moment steps, which this part bounds by FP64 arithmetic, not memory).  One
+ * launch of 8 CTAs per SM x 256 threads, each thread running eight independent
+ * register-resident FMA chains for `iters` steps, timed with CUDA events on
+ * `stream` after a short warm-up launch; 2 flops per FMA.  Allocates (and
+ * frees) a small device array.  Errors: MLT_EINVAL (null tflops, iters
+ * outside [1, 2^30]), MLT_ENOMEM, MLT_ECUDA.
+ */
+int mlt_fp64_rate(int64_t iters, double* tflops, void* stream);
 
 /*
  * Kernel timing (instrumentation; the paper has no counterpart).  Between

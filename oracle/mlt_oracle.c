@@ -20,6 +20,7 @@
  *     triangle count.
  * Dot products are accumulated in long double in row order.
  */
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -54,10 +55,13 @@ void orc_probe(uint64_t seed, uint64_t p, int64_t d, int8_t *z)
 
 /* ---- Chebyshev moments (Section 2.2) ------------------------------------- */
 
-/* y = A x for a CSR matrix; val == NULL means a 0/1 pattern scaled by `scale`. */
+/* y = A x for a CSR matrix; val == NULL means a 0/1 pattern scaled by `scale`.
+ * Each row is summed on its own in entry order, so spreading the rows over
+ * threads (rowpar) changes no result. */
 static void csr_apply(int64_t nrows, const int64_t *rowptr, const int32_t *col,
-                      const double *val, double scale, const double *x, double *y)
+                      const double *val, double scale, const double *x, double *y, int rowpar)
 {
+#pragma omp parallel for schedule(static) if (rowpar)
     for (int64_t i = 0; i < nrows; ++i) {
         long double s = 0.0L;
         for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
@@ -93,6 +97,7 @@ typedef struct {
     double scale;
     int gram;
     double *tmp; /* nrows scratch for the Gram case */
+    int rowpar;  /* spread the rows of each product over threads */
 } orc_op;
 
 static int64_t op_dim(const orc_op *A) { return A->gram ? A->ncols : A->nrows; }
@@ -100,9 +105,9 @@ static int64_t op_dim(const orc_op *A) { return A->gram ? A->ncols : A->nrows; }
 static void op_apply(const orc_op *A, const double *x, double *y)
 {
     if (!A->gram) {
-        csr_apply(A->nrows, A->rowptr, A->col, A->val, A->scale, x, y);
+        csr_apply(A->nrows, A->rowptr, A->col, A->val, A->scale, x, y, A->rowpar);
     } else {
-        csr_apply(A->nrows, A->rowptr, A->col, A->val, A->scale, x, A->tmp);
+        csr_apply(A->nrows, A->rowptr, A->col, A->val, A->scale, x, A->tmp, A->rowpar);
         csr_apply_t(A->nrows, A->ncols, A->rowptr, A->col, A->val, A->scale, A->tmp, y);
     }
 }
@@ -135,6 +140,7 @@ static int moments_one(const orc_op *A, double a, double b, const double *z, int
     mu[0] = (double)dotl(d, z, wcur);
     for (int j = 0; j < deg; ++j) {
         op_apply(A, wcur, aw);
+#pragma omp parallel for schedule(static) if (A->rowpar)
         for (int64_t i = 0; i < d; ++i) {
             double atw = alpha * aw[i] + beta * wcur[i];
             wnext[i] = (j == 0) ? atw : 2.0 * atw - wprev[i];
@@ -150,7 +156,7 @@ static int op_init(orc_op *A, int64_t nrows, int64_t ncols, const int64_t *rowpt
                    const int32_t *col, const double *val, double scale, int gram)
 {
     A->nrows = nrows; A->ncols = ncols; A->rowptr = rowptr; A->col = col;
-    A->val = val; A->scale = scale; A->gram = gram; A->tmp = NULL;
+    A->val = val; A->scale = scale; A->gram = gram; A->tmp = NULL; A->rowpar = 0;
     if (gram) {
         A->tmp = (double *)malloc(sizeof(double) * (size_t)(nrows > 0 ? nrows : 1));
         if (!A->tmp) return -2;
@@ -177,16 +183,22 @@ int orc_moments_z(int64_t nrows, int64_t ncols, const int64_t *rowptr, const int
     return rc;
 }
 
-/* Moments of Rademacher probes with global ids probe_offset + p. */
+/* Moments of Rademacher probes with global ids probe_offset + p.  With fewer
+ * probes than threads (and a plain operator, whose rows are independent
+ * sums) the probes run one after another with each product's rows spread
+ * over the threads; otherwise the probes are spread.  Either way every
+ * number is computed by the same operations in the same order. */
 int orc_moments(int64_t nrows, int64_t ncols, const int64_t *rowptr, const int32_t *col,
                 const double *val, double scale, int gram, double a, double b, uint64_t seed,
                 int64_t probe_offset, int nprobes, const int32_t *deg, double *mu, int64_t ld)
 {
     int rc = 0;
-#pragma omp parallel for schedule(dynamic, 1) reduction(min : rc)
+    const int rowpar = !gram && nprobes < omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) reduction(min : rc) if (!rowpar)
     for (int p = 0; p < nprobes; ++p) {
         orc_op A;
         if (op_init(&A, nrows, ncols, rowptr, col, val, scale, gram)) { rc = -2; continue; }
+        A.rowpar = rowpar;
         int64_t d = op_dim(&A);
         double *z = (double *)malloc(sizeof(double) * (size_t)d);
         if (!z) { free(A.tmp); rc = -2; continue; }

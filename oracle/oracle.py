@@ -423,6 +423,29 @@ def mlmc_auto(m, fn, a, b, n, seed, m_pilot, mode="budget", target=1.0, p=0.0,
     return out
 
 
+def learned_estimate(c, mu, s, m_net, m_1, m_2, l1):
+    """The three-level estimator with a learned coarse level (a project
+    addition; Eq. multiEstimator with the network as its lowest level):
+    E[P_n] = E[S] + E[P_l1 - S] + E[P_n - P_l1].  mu holds the moment rows of
+    m_net, then m_1, then m_2 independent probes (the first two groups to
+    degree l1 at least, the last to n = len(c) - 1); s holds the network's
+    estimate of P_l1 = sum_{j <= l1} c_j mu_j for the first m_net + m_1 probes.
+    Level 1 samples s_i (first group), level 2 P_l1 - s_i (second group),
+    level 3 Q_{l1,n} (third group, absent when l1 = n or m_2 = 0).  Each level
+    reports its sample mean and variance (divisor m - 1); the estimate is the
+    sum of the means and its standard error sqrt(sum var_k / m_k)."""
+    n = len(c) - 1
+    mu = np.atleast_2d(mu)
+    s = np.asarray(s, dtype=np.float64)
+    lv = [s[:m_net], band(c, mu[m_net:m_net + m_1], -1, l1) - s[m_net:m_net + m_1]]
+    if l1 < n and m_2 > 0:
+        lv.append(band(c, mu[m_net + m_1:m_net + m_1 + m_2], l1, n))
+    means = [math.fsum(v.tolist()) / v.size for v in lv]
+    variances = [float(np.var(v, ddof=1)) if v.size > 1 else float("nan") for v in lv]
+    return {"estimate": math.fsum(means), "stderr": math.sqrt(math.fsum(vv / v.size for vv, v in zip(variances, lv))),
+            "level_mean": means, "level_var": variances, "m": [int(v.size) for v in lv]}
+
+
 # ---------------------------------------------------------------------------
 # Hutch++ on the Chebyshev interpolant: the variance reduction Section 5.3
 # suggests for the Estrada index (the method of Meyer, Musco, Musco and

@@ -247,9 +247,13 @@ struct Lane {
 
 // acc = sum over entries [k0, k1) of a_ij * V[j, c0 .. c0+N).  Row and entry
 // indices fit in 32 bits (nnz < 2^31 is checked when the handle is made).
-template <typename T, int G>
-__device__ __forceinline__ void row_product(const StepArgs<T>& a, const Lane<T, G>& L, int k0, int k1,
-                                            T (&acc)[Lanes<T>::N], uint64_t pol)
+// PAT: a 0/1 pattern, every a_ij = 1, so each product is the gathered value
+// itself: acc + x, which equals fma(1, x, acc) bit for bit in every vector
+// type (1 * x is exact, in double-float too) and saves the double-float
+// multiply.
+template <typename T, int G, bool PAT>
+__device__ __forceinline__ void row_product_t(const StepArgs<T>& a, const Lane<T, G>& L, int k0, int k1,
+                                              T (&acc)[Lanes<T>::N], uint64_t pol)
 {
     constexpr int N = Lanes<T>::N;
     constexpr int kGatherUnroll = StepTuning<T>::kUnroll;
@@ -262,21 +266,33 @@ __device__ __forceinline__ void row_product(const StepArgs<T>& a, const Lane<T, 
         T vj = T(0);
         if (k < k1) {
             cj = __ldg(a.col + k);
-            vj = a.val ? ldg_val(a.val + k) : T(1);
+            if constexpr (!PAT) vj = ldg_val(a.val + k);
         }
         const int cnt = min(G, k1 - base);
 #pragma unroll kGatherUnroll
         for (int t = 0; t < cnt; ++t) {
             const int c = __shfl_sync(L.gmask, cj, t, G);
-            const T v = shfl_val(L.gmask, vj, t, G);
+            T v = T(1);
+            if constexpr (!PAT) v = shfl_val(L.gmask, vj, t, G);
             if (L.vok) {
                 const P x = ld_gather<StepTuning<T>::kEvictLast>(
                     reinterpret_cast<const P*>(a.vgather + (size_t)c * a.ldv + L.c0), pol);
 #pragma unroll
-                for (int q = 0; q < N; ++q) acc[q] = fma(v, x.v[q], acc[q]);
+                for (int q = 0; q < N; ++q) {
+                    if constexpr (PAT) acc[q] = acc[q] + x.v[q];
+                    else acc[q] = fma(v, x.v[q], acc[q]);
+                }
             }
         }
     }
+}
+
+template <typename T, int G>
+__device__ __forceinline__ void row_product(const StepArgs<T>& a, const Lane<T, G>& L, int k0, int k1,
+                                            T (&acc)[Lanes<T>::N], uint64_t pol)
+{
+    if (a.val) row_product_t<T, G, false>(a, L, k0, k1, acc, pol);
+    else row_product_t<T, G, true>(a, L, k0, k1, acc, pol);
 }
 
 // The row's operands of the epilogue, loaded before its gathers (they do not

@@ -189,6 +189,14 @@ int mlt_surrogate_get_params(mlt_surrogate* S, float* params)
     return MLT_OK;
 }
 
+int mlt_surrogate_get_norm(mlt_surrogate* S, double* norm, int* has_norm)
+{
+    if (!S || !norm || !has_norm) return fail(MLT_EINVAL, "mlt_surrogate_get_norm: null argument");
+    std::memcpy(norm, S->norm, sizeof(S->norm));
+    *has_norm = S->has_norm ? 1 : 0;
+    return MLT_OK;
+}
+
 int mlt_surrogate_loss_grad(mlt_surrogate* S, const float* x, const float* t, int64_t n, double* loss,
                             float* grad, void* stream)
 {

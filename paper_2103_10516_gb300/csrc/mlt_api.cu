@@ -187,6 +187,25 @@ static int dev_alloc_copy(T** dst, const void* src, size_t count, bool src_dev, 
     return MLT_OK;
 }
 
+// Eight independent FP64 FMA chains per thread, `iters` steps, all in
+// registers: the FP64 pipe's rate with no memory traffic (the denominator of
+// FP64-bound rooflines).  The result is stored so that nothing is elided.
+__global__ void fp64_fma_kernel(double* sink, int64_t iters)
+{
+    double x[8];
+    const double m = 1.0 + 1e-12 * threadIdx.x, c = 1e-9;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = (double)(i + 1);
+    for (int64_t k = 0; k < iters; ++k) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = fma(x[i], m, c);
+    }
+    double t = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t += x[i];
+    sink[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] = t;
+}
+
 __global__ void f32_to_f64_kernel(const float* __restrict__ in, double* __restrict__ out, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -1191,6 +1210,43 @@ int mlt_low_traces(mlt_matrix* m, double a, double b, double* t, int* count, voi
         return low_traces(m, a, b, t, count, (cudaStream_t)stream);
     } catch (...) {
         return fail(MLT_ECUDA, "mlt_low_traces: exception");
+    }
+}
+
+int mlt_fp64_rate(int64_t iters, double* tflops, void* stream)
+{
+    try {
+        if (!tflops || iters < 1 || iters > (1LL << 30)) return fail(MLT_EINVAL, "mlt_fp64_rate: need tflops and 1 <= iters <= 2^30");
+        int dev = 0, sms = 0;
+        MLT_CUDA_TRY(cudaGetDevice(&dev));
+        MLT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        cudaStream_t s = (cudaStream_t)stream;
+        double* sink = nullptr;
+        const int blocks = 8 * sms;
+        if (pool_malloc((void**)&sink, (size_t)blocks * 256 * sizeof(double), s) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(MLT_ENOMEM, "mlt_fp64_rate: device allocation failed");
+        }
+        cudaEvent_t e0, e1;
+        MLT_CUDA_TRY(cudaEventCreate(&e0));
+        MLT_CUDA_TRY(cudaEventCreate(&e1));
+        fp64_fma_kernel<<<blocks, 256, 0, s>>>(sink, 16);     // warm-up
+        MLT_CUDA_TRY(cudaEventRecord(e0, s));
+        fp64_fma_kernel<<<blocks, 256, 0, s>>>(sink, iters);
+        MLT_CUDA_TRY(cudaEventRecord(e1, s));
+        MLT_CUDA_TRY(cudaGetLastError());
+        MLT_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        MLT_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaFreeAsync(sink, s);
+        MLT_CUDA_TRY(cudaStreamSynchronize(s));
+        // 8 chains, one FMA (2 flops) each per iteration
+        *tflops = 2.0 * 8.0 * (double)iters * (double)blocks * 256.0 / ((double)ms * 1e-3) / 1e12;
+        return MLT_OK;
+    } catch (...) {
+        return fail(MLT_ECUDA, "mlt_fp64_rate: exception");
     }
 }
 

@@ -39,7 +39,8 @@ EXPORTS = ["mlt_create_csr", "mlt_destroy", "mlt_matrix_info", "mlt_spectrum_bou
            "mlt_surrogate_predict", "mlt_learned_train", "mlt_learned_estimate",
            "mlt_moments_batched", "mlt_autotune", "mlt_moments_noalloc", "mlt_low_traces",
            "mlt_release_cached", "mlt_poly_apply", "mlt_hutchpp_estimate", "mlt_pilot_variances",
-           "mlt_select_levels", "mlt_band_samples", "mlt_mlmc_combine", "mlt_triangle_estimate"]
+           "mlt_select_levels", "mlt_band_samples", "mlt_mlmc_combine", "mlt_triangle_estimate",
+           "mlt_fp64_rate", "mlt_surrogate_get_norm"]
 MLT_TRI_CV = {"none": 0, "fit": 1, "cheb": 2}
 
 
@@ -115,6 +116,7 @@ def lib():
     L.mlt_mlmc_combine.argtypes = [ci, vp, vp, vp, ctypes.POINTER(mlt_mlmc_result)]
     L.mlt_triangle_estimate.argtypes = [vp, i64, i64, ci, dbl, dbl, ctypes.POINTER(dbl), ctypes.POINTER(dbl),
                                         ctypes.POINTER(dbl), ctypes.POINTER(dbl)]
+    L.mlt_fp64_rate.argtypes = [i64, ctypes.POINTER(dbl), vp]
     L.mlt_profile_start.argtypes = []
     L.mlt_profile_stop.argtypes = [ctypes.POINTER(mlt_kernel_stat), ci, ctypes.POINTER(ci)]
     L.mlt_last_error.argtypes = []
@@ -337,6 +339,13 @@ def mlt_triangle_trace(handle, seed, probe_offset, nprobes, block=256, use_cv=Tr
     return est.value, se.value
 
 
+def mlt_fp64_rate(iters=1 << 16, stream=None):
+    """Measured FP64 FMA rate of the current device (TFLOP/s)."""
+    t = ctypes.c_double()
+    _check(lib().mlt_fp64_rate(int(iters), ctypes.byref(t), _stream(stream)))
+    return t.value
+
+
 def mlt_profile_start():
     _check(lib().mlt_profile_start())
 
@@ -448,6 +457,7 @@ def _bind_learned(L):
     L.mlt_surrogate_loss_grad.argtypes = [vp, vp, vp, i64, ctypes.POINTER(dbl), vp, vp]
     L.mlt_surrogate_train.argtypes = [vp, vp, vp, i64, ci, i64, dbl, ctypes.POINTER(dbl), vp]
     L.mlt_surrogate_predict.argtypes = [vp, vp, i64, vp, vp]
+    L.mlt_surrogate_get_norm.argtypes = [vp, vp, ctypes.POINTER(ci)]
     L.mlt_learned_train.argtypes = [vp, vp, ctypes.POINTER(mlt_learned_params), i64, i64, ci, i64, dbl,
                                     ctypes.POINTER(dbl)]
     L.mlt_learned_estimate.argtypes = [vp, vp, ctypes.POINTER(mlt_learned_params),
@@ -522,6 +532,16 @@ class Surrogate:
         _check(lib().mlt_surrogate_train(self.handle, _ptr(X), _ptr(T), X.shape[0], int(epochs),
                                          int(batch), float(lr), ctypes.byref(loss), _stream(stream)))
         return loss.value
+
+    def get_norm(self):
+        """(feature means (16), feature stds (16), target mean, target std), or
+        None before training set them."""
+        v = np.zeros(2 * MLT_NET_IN + 2)
+        h = ctypes.c_int()
+        _check(lib().mlt_surrogate_get_norm(self.handle, _ptr(v), ctypes.byref(h)))
+        if not h.value:
+            return None
+        return v[:MLT_NET_IN], v[MLT_NET_IN:2 * MLT_NET_IN], float(v[2 * MLT_NET_IN]), float(v[2 * MLT_NET_IN + 1])
 
     def predict(self, X, stream=None):
         X = np.ascontiguousarray(X, dtype=np.float32)

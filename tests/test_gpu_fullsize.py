@@ -10,9 +10,13 @@ max(64, deg/2) * 2^-24 * d, the bound the smaller FP32 tests use up to degree
 stencil and 0.02 on the Gram operator and the scaled R-MAT graph.  Every moment of a spectrum inside
 [a, b] also satisfies |mu_j| <= d.
 
-The sampled probes stay at low degree: the oracle sums in long double, which is
-quad precision in software on aarch64, about 10^8 multiply-adds a few seconds
-there.  The bound above is checked on every moment of every probe."""
+The oracle sums in long double, which is quad precision in software on
+aarch64; with fewer probes than host threads it spreads each product's rows
+over the threads (the same arithmetic), so a few probes per test reach the
+degrees the benchmarks use: degree 64 on the stencil and the Gram operator,
+degree 16 on the scale-22 graph (the moments the learned level consumes).
+FP64 and double-float runs are held to the FP64 tolerance 1e-10 d.  The bound
+|mu_j| <= d (+ tol) is checked on every moment of every probe."""
 import numpy as np
 import pytest
 
@@ -48,9 +52,15 @@ def _check_sampled(O, m, a, b, seed, offset, got, samples, tol, **kw):
         assert err <= tol, (p, dg, err, tol)
 
 
+def _spread(nprobes, k):
+    """k probe indices spread over [0, nprobes): first, last and between, so
+    that several probe groups are sampled."""
+    return sorted(set(int(round(i * (nprobes - 1) / (k - 1))) for i in range(k)))
+
+
 def test_stencil3d_fp32_full_size(L, O):
-    # the 100^3 diffusion operator, 128 probes to degree 128 in FP32; two probes
-    # checked to degree 8 (2 x 8 operator applications of 6.9M entries)
+    # the 100^3 diffusion operator, 128 probes to degree 128 in FP32; four probes
+    # checked to degree 64
     m = synth.diffusion_3d(100, sigma=1.0, shift=0.1, seed=0)
     a, b = 0.1, O.gershgorin(m)[1]
     deg = np.full(128, 128, dtype=np.int32)
@@ -59,13 +69,26 @@ def test_stencil3d_fp32_full_size(L, O):
         got = M.moments(a, b, 0, 4096, deg, precision="fp32")
     tol = _tol32(128, m.nrows)
     _check_all(got, deg, m.nrows, tol)
-    _check_sampled(O, m, a, b, 0, 4096, got, [(0, 8), (127, 8)], tol)
+    _check_sampled(O, m, a, b, 0, 4096, got, [(p, 64) for p in _spread(128, 4)], tol)
+
+
+def test_stencil3d_fp64_full_size(L, O):
+    # the same operator in FP64, 128 probes to degree 64: four probes to degree 64
+    # at the FP64 tolerance
+    m = synth.diffusion_3d(100, sigma=1.0, shift=0.1, seed=0)
+    a, b = 0.1, O.gershgorin(m)[1]
+    deg = np.full(128, 64, dtype=np.int32)
+    with L.Matrix(m) as M:
+        got = M.moments(a, b, 0, 8192, deg, precision="fp64")
+    tol = 1e-10 * m.nrows
+    _check_all(got, deg, m.nrows, tol)
+    _check_sampled(O, m, a, b, 0, 8192, got, [(p, 64) for p in _spread(128, 4)], tol)
 
 
 def test_nuclear_gram_fp32_full_size(L, O):
     # X^T X with X 2^18 x 2^16 (density 1e-4), 512 probes to degree 512 in FP32;
-    # the interval's upper end is ||X||_1 ||X||_inf >= ||X||_2^2; one probe of the
-    # last group checked to degree 32
+    # the interval's upper end is ||X||_1 ||X||_inf >= ||X||_2^2; four probes
+    # from different groups checked to degree 64
     X = synth.sparse_gaussian(1 << 18, 1 << 16, 1e-4, seed=0)
     absv = np.abs(np.asarray(X.val, dtype=np.float64))
     rows = np.repeat(np.arange(X.nrows), np.diff(X.rowptr))
@@ -76,20 +99,39 @@ def test_nuclear_gram_fp32_full_size(L, O):
         got = M.moments(0.0, b, 0, 0, deg, precision="fp32")
     tol = _tol32(512, X.ncols)
     _check_all(got, deg, X.ncols, tol)
-    _check_sampled(O, X, 0.0, b, 0, 0, got, [(511, 32)], tol, gram=True)
+    _check_sampled(O, X, 0.0, b, 0, 0, got, [(p, 64) for p in _spread(512, 4)], tol, gram=True)
 
 
-def test_estrada_rmat22_fp32_full_size(L, O):
+@pytest.fixture(scope="module")
+def rmat22():
+    g = synth.rmat_adjacency(22, 16, seed=1)
+    return g, 10.0 / float(np.max(np.diff(g.rowptr)))
+
+
+def test_estrada_rmat22_fp32_full_size(L, O, rmat22):
     # the R-MAT scale-22 adjacency scaled into [-10, 10] (by its largest degree,
     # a Gershgorin bound), 256 probes to degree 128 in FP32: two probe groups;
-    # one probe of the second group checked to degree 2 (128M entries a step)
-    g = synth.rmat_adjacency(22, 16, seed=1)
-    scale = 10.0 / float(np.max(np.diff(g.rowptr)))
+    # four probes across both groups checked to degree 16
+    g, scale = rmat22
     deg = np.full(256, 128, dtype=np.int32)
     with L.Matrix(g, scale=scale) as M:
         L.mlt_autotune(M.handle, "fp32", 4)
         got = M.moments(-10.0, 10.0, 0, 0, deg, precision="fp32")
     tol = _tol32(128, g.nrows)
     _check_all(got, deg, g.nrows, tol)
-    _check_sampled(O, g, -10.0, 10.0, 0, 0, got, [(255, 2)], tol, scale=scale)
+    _check_sampled(O, g, -10.0, 10.0, 0, 0, got, [(p, 16) for p in _spread(256, 4)], tol, scale=scale)
 
+
+def test_estrada_rmat22_df64_full_size_reordered(L, O, rmat22):
+    # the default benchmark's configuration: the graph relabelled by degree
+    # (MLT_REORDER), double-float moments of 128 probes to degree 128 at the
+    # autotuned group width; four probes checked to degree 16 at the FP64
+    # tolerance
+    g, scale = rmat22
+    deg = np.full(128, 128, dtype=np.int32)
+    with L.Matrix(g, scale=scale, reorder=True) as M:
+        L.mlt_autotune(M.handle, "df64", 4)
+        got = M.moments(-10.0, 10.0, 0, 0, deg, precision="df64")
+    tol = 1e-10 * g.nrows
+    _check_all(got, deg, g.nrows, tol)
+    _check_sampled(O, g, -10.0, 10.0, 0, 0, got, [(p, 16) for p in _spread(128, 4)], tol, scale=scale)

@@ -382,3 +382,49 @@ def test_pilot_variances_band_by_band(O):
     assert np.all(np.tril(V) == 0.0)
     # a single pilot row has no sample variance: the table is all zeros
     assert np.all(O.pilot_variances(c, mu[:1]) == 0.0)
+
+
+# ---- the three-level estimator with a learned coarse level -------------------
+
+def test_learned_levels_exact_under_exhaustive_signs(O):
+    """With every one of the 2^d sign vectors in each of the three groups, the
+    estimate is tr p_n(At) exactly, whatever the network's outputs are (here an
+    arbitrary nonlinear function of the features): the network's mean and the
+    correction's mean cancel sample by sample."""
+    d, n, l1 = 8, 12, 6
+    m = synth.random_symmetric(d, 0.5, seed=3, diag_shift=1.0)
+    lam = np.linalg.eigvalsh(m.to_dense())
+    a, b = float(lam[0]) - 0.3, float(lam[-1]) + 0.2
+    c = O.cheb_coeffs("exp", a, b, n)
+    Z = np.array(list(itertools.product([-1.0, 1.0], repeat=d)))
+    N = Z.shape[0]
+    mu1 = O.moments_z(m, a, b, Z, n)
+    mu = np.vstack([mu1, mu1, mu1])
+    s = np.concatenate([np.sin(3 * mu1[:, 1]) + mu1[:, 2] ** 2] * 2)
+    got = O.learned_estimate(c, mu, s, N, N, N, l1)
+    th = np.arccos((2 * lam - (a + b)) / (b - a))
+    exact = sum(c[j] * np.sum(np.cos(j * th)) for j in range(n + 1))
+    assert abs(got["estimate"] - exact) < 1e-10 * np.sum(np.abs(c)) * d
+    assert got["m"] == [N, N, N]
+
+
+def test_learned_levels_special_cases(O):
+    """S = 0 gives the plain two-level estimator (levels l1, n) plus an exact
+    zero level; S equal to each probe's own P_l1 leaves a correction level of
+    zero samples, and the estimate is the mean of S plus the top band."""
+    m = synth.grid_laplacian_2d(10, shift=0.1)
+    n, l1 = 30, 12
+    c = O.cheb_coeffs("log", 0.1, 8.1, n)
+    m_net, m_1, m_2 = 9, 14, 6
+    deg = [l1] * (m_net + m_1) + [n] * m_2
+    mu = O.moments(m, 0.1, 8.1, 5, 0, deg)
+    zero = O.learned_estimate(c, mu, np.zeros(m_net + m_1), m_net, m_1, m_2, l1)
+    plain = O.mlmc_fixed(m, "log", 0.1, 8.1, n, [l1, n], [m_1, m_2], seed=5, probe_offset=m_net)
+    assert zero["level_mean"][0] == 0.0 and zero["level_var"][0] == 0.0
+    assert abs(zero["estimate"] - plain["estimate"]) < 1e-12 * np.sum(np.abs(c)) * m.nrows
+    own = O.band(c, mu[:m_net + m_1], -1, l1)
+    exact_net = O.learned_estimate(c, mu, own, m_net, m_1, m_2, l1)
+    assert np.all(np.abs(np.asarray(exact_net["level_mean"][1])) < 1e-12 * np.sum(np.abs(c)) * m.nrows)
+    assert exact_net["level_var"][1] < 1e-20 * max(1.0, exact_net["level_var"][0])
+    top = O.band(c, mu[m_net + m_1:], l1, n)
+    assert abs(exact_net["estimate"] - (np.mean(own[:m_net]) + np.mean(top))) < 1e-12 * np.sum(np.abs(c)) * m.nrows

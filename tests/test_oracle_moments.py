@@ -88,3 +88,17 @@ def test_exhaustive_sign_average_is_trace(O):
     th = np.arccos(np.clip(lt, -1, 1))
     for j in range(n + 1):
         assert abs(mu[:, j].mean() - np.sum(np.cos(j * th))) < 1e-11 * d
+
+
+def test_row_parallel_products_change_no_bit(O):
+    """With fewer probes than threads the oracle spreads each product's rows
+    over the threads instead of spreading the probes; each row is still summed
+    alone in entry order, so every moment is the same to the last bit."""
+    import os
+    g = synth.rmat_adjacency(11, 16, seed=6)
+    sc = 0.02
+    a, b = O.interval(g, scale=sc)
+    many = O.moments(g, a, b, 3, 0, [30] * (2 * (os.cpu_count() or 1) + 2), scale=sc)
+    for p in (0, 5):
+        one = O.moments(g, a, b, 3, p, [30], scale=sc)
+        assert np.array_equal(one[0], many[p])
