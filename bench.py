@@ -456,11 +456,12 @@ class EstradaRmat22:
     DEG = 128
     PROBE_SPAN = 1 << 28     # timed (2^20 ids), e2e (2^20) and comparison (from 2^24) ranges
 
-    def __init__(self, precision=None, compare=True, train_probes=1 << 14):
+    def __init__(self, precision=None, compare=True, train_probes=1 << 14, scale=None):
         from paper_2103_10516_gb300 import synth
         self.precision = precision or "df64"
         self.dtype = {"df64": "df64", "fp64": "f64", "fp32": "f32"}[self.precision]
-        self.csr = synth.rmat_adjacency(22, 16, seed=1)
+        self.scale_log2 = scale or 22
+        self.csr = synth.rmat_adjacency(self.scale_log2, 16, seed=1)
         self.d = self.csr.nrows
         self.nnz = self.csr.nnz
         self.scale = None
@@ -475,7 +476,8 @@ class EstradaRmat22:
         prec = {"df64": "double-float vectors and per-thread dots (FP64-class), fp64 after",
                 "fp64": "fp64 throughout",
                 "fp32": "fp32 vectors, compensated fp32 dots per thread, fp64 after"}[self.precision]
-        return {"workload": self.name, "graph": "R-MAT scale 22, edge factor 16, a=0.57 b=c=0.19, seed 1",
+        return {"workload": self.name, "graph": "R-MAT scale %d, edge factor 16, a=0.57 b=c=0.19, seed 1"
+                % self.scale_log2,
                 "d": self.d, "nnz": self.nnz, "probes": self.NPROBES, "degree": self.DEG, "f": "exp",
                 "precision": prec, "interval": [-10.0, 10.0], "scale": self.scale, "relabelled_by_degree": True,
                 "group_width": getattr(self, "group_width", None), "comparison": self.cmp,
@@ -490,6 +492,16 @@ class EstradaRmat22:
     def kernel_flops(self, launches_per_step):
         n = launches_per_step.get("cheb_step")
         return {"cheb_step": step_flops(self.d, self.nnz, self.units()) / n} if n else {}
+
+    @property
+    def TRAFFIC(self):
+        """DRAM bytes per cheb_step launch (dram__bytes_read.sum + dram__bytes_write.sum)
+        from an ncu capture of the default configuration (scale 22, double-float,
+        width 64, relabelled): the mean of three launches; re-taken whenever
+        the kernel changes.  Other configurations have no capture."""
+        if self.precision == "df64" and self.scale_log2 == 22:
+            return {"cheb_step": 29.33e9}
+        return {}
 
     def gather_bytes(self, launches_per_step):
         """Bytes of gathered V_k rows per launch (every stored entry reads its
@@ -1662,8 +1674,8 @@ def make_workload(args):
     cls = WORKLOADS[args.workload]
     kw = {}
     if args.scale is not None:
-        if cls is not EstradaLearned:
-            raise SystemExit("--scale applies to the estrada_learned workload only")
+        if cls not in (EstradaLearned, EstradaRmat22):
+            raise SystemExit("--scale applies to the estrada_learned and estrada_rmat22 workloads only")
         kw["scale"] = args.scale
     if args.precision is not None:
         if cls not in (NuclearGram, NuclearExplicit, Stencil3D, EstradaLearned, EstradaHutchpp, Diffusion64Batched,
@@ -1693,7 +1705,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="estrada_rmat22", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default=None, choices=["fp32", "fp64", "df64", "mixed"])
-    ap.add_argument("--scale", type=int, default=None, help="R-MAT scale of estrada_learned")
+    ap.add_argument("--scale", type=int, default=None, help="R-MAT scale of estrada_learned / estrada_rmat22")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparison", action="store_true",
