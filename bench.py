@@ -1012,7 +1012,9 @@ class Stencil3D:
         self.nnz = self.csr.nnz
         self.precision = precision or "fp32"
         # DRAM bytes per launch (128 live probes) from an ncu capture of the FP32 step
-        self.TRAFFIC = {"fp32": {"cheb_step": 1.5867e9}, "df64": {"cheb_step": 2.1287e9}}.get(self.precision, {})
+        # ncu DRAM bytes per launch of the current build (FP32 only; the
+        # double-float capture predates the current step kernel)
+        self.TRAFFIC = {"fp32": {"cheb_step": 1.5914e9}}.get(self.precision, {})
         self.dtype = {"fp32": "f32", "fp64": "f64", "df64": "df64", "mixed": "f32+f64"}[self.precision]
 
     def _prec(self, mlt):
