@@ -147,7 +147,8 @@ int mlt_create_csr(int64_t nrows, int64_t ncols, int64_t nnz,
                    mlt_matrix** out);
 
 /* Release a handle and every device buffer it owns (NULL is a no-op).  The
- * call waits for the device to finish its work first.  The buffers go back to
+ * call waits for the device to finish its work first; it fails with
+ * MLT_EINVAL while a live mlt_batch holds the handle.  The buffers go back to
  * the library's memory pool (see mlt_release_cached), not to the driver. */
 int mlt_destroy(mlt_matrix* m);
 
@@ -230,6 +231,28 @@ typedef struct {
 
 int mlt_moments_batched(const mlt_moments_job* jobs, int njobs, int precision, unsigned flags,
                         void* stream);
+
+/*
+ * The same job set as a persistent batch: mlt_batch_create prepares every job
+ * (validation, probe order, groups, every device buffer) and captures and
+ * instantiates one CUDA graph with a branch per job, once; mlt_batch_run
+ * replays that graph, each job's probes taking ids probe_offset + id_shift + p
+ * (the shift is written into the id tables the graph reads, so one graph
+ * serves any number of fresh probe sets), and returns when every job's moments
+ * are in its mu (host outputs are copied there after the replay).  The seeds,
+ * degrees, intervals, outputs and precision stay those of the create call.
+ * While a batch lives, its graph points into the workspaces of its handles:
+ * every other call on those handles, mlt_destroy included, fails with
+ * MLT_EINVAL until mlt_batch_destroy.  Calls of one batch must not overlap.
+ * Errors: as mlt_moments_batched; mlt_batch_run also MLT_EINVAL when shifted
+ * ids leave [0, 2^32).
+ */
+typedef struct mlt_batch mlt_batch;   /* opaque */
+
+int mlt_batch_create(const mlt_moments_job* jobs, int njobs, int precision, unsigned flags, void* stream,
+                     mlt_batch** out);
+int mlt_batch_run(mlt_batch* b, int64_t id_shift, void* stream);
+int mlt_batch_destroy(mlt_batch* b);   /* NULL is a no-op; waits for the device */
 
 /*
  * Choose the probe-group width (probes sharing one pass over the matrix) for

@@ -441,6 +441,7 @@ int deflate_blocked(const OrthoScratch& w, const double* Q, int ldq, int s_cols,
 int check_poly_args(mlt_matrix* m, double a, double b, const double* c, int n, const char* who)
 {
     if (!m) return fail(MLT_EINVAL, std::string(who) + ": null matrix");
+    if (int rcb = handle_busy(m, who)) return rcb;
     if (!c) return fail(MLT_EINVAL, std::string(who) + ": null coefficients");
     if (n < 1 || n > MLT_MAX_DEGREE) return fail(MLT_EINVAL, std::string(who) + ": n out of range");
     if (!(a < b) || !std::isfinite(a) || !std::isfinite(b))

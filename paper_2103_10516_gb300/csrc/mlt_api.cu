@@ -443,6 +443,7 @@ int prepare_moment_job(mlt_matrix* m, double a, double b, uint64_t seed, int64_t
                        int group_width, MomentJob& J, cudaStream_t s)
 {
     if (!m) return fail(MLT_EINVAL, "mlt_moments: null handle");
+    if (int rcb = handle_busy(m, "mlt_moments")) return rcb;
     if (nprobes < 0) return fail(MLT_EINVAL, "mlt_moments: negative probe count");
     if (nprobes > 0 && (!degree || !mu)) return fail(MLT_EINVAL, "mlt_moments: null degree or mu");
     if (!(a < b) || !std::isfinite(a) || !std::isfinite(b))
@@ -822,6 +823,7 @@ int mlt_create_csr(int64_t nrows, int64_t ncols, int64_t nnz, const int64_t* row
 int mlt_destroy(mlt_matrix* m)
 {
     if (!m) return MLT_OK;
+    if (int rcb = handle_busy(m, "mlt_destroy")) return rcb;
     int cur = 0;
     cudaGetDevice(&cur);
     const int dev = m->device;
@@ -851,6 +853,7 @@ int mlt_spectrum_bounds(mlt_matrix* m, int method, int steps, uint64_t seed, dou
     (void)steps;
     (void)seed;
     if (!m || !a || !b) return fail(MLT_EINVAL, "mlt_spectrum_bounds: null argument");
+    if (int rcb = handle_busy(m, "mlt_spectrum_bounds")) return rcb;
     if (method != MLT_BOUNDS_GERSHGORIN && method != MLT_BOUNDS_LANCZOS)
         return fail(MLT_EINVAL, "mlt_spectrum_bounds: unknown method");
     try {
@@ -959,10 +962,162 @@ int mlt_moments_batched(const mlt_moments_job* jobs, int njobs, int precision, u
     }
 }
 
+}  // extern "C"
+
+// A persistent batch: every job prepared once, one CUDA graph captured and
+// instantiated once, replayed by mlt_batch_run with new probe ids written
+// into the id tables the graph reads.
+struct mlt_batch {
+    std::vector<mlt::MomentJob> jobs;
+    std::vector<std::vector<int64_t>> ids;     // per job: probe ids in group order, before the shift
+    std::vector<int64_t*> ids_dev;             // per job: the device id table its kernels read
+    std::vector<int64_t> first, count;         // per job: first probe id and probe count
+    cudaGraphExec_t exec = nullptr;
+    int device = 0;
+};
+
+extern "C" {
+
+int mlt_batch_destroy(mlt_batch* b)
+{
+    if (!b) return MLT_OK;
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (auto& J : b->jobs)
+        if (J.m) --J.m->batch_refs;
+    delete b;
+    return MLT_OK;
+}
+
+int mlt_batch_create(const mlt_moments_job* jobs, int njobs, int precision, unsigned flags, void* stream,
+                     mlt_batch** out)
+{
+    try {
+        if (!out) return fail(MLT_EINVAL, "mlt_batch_create: null output");
+        *out = nullptr;
+        if (njobs < 1 || !jobs) return fail(MLT_EINVAL, "mlt_batch_create: need at least one job");
+        for (int i = 0; i < njobs; ++i) {
+            if (!jobs[i].matrix) return fail(MLT_EINVAL, "mlt_batch_create: null matrix");
+            if (jobs[i].nprobes < 1) return fail(MLT_EINVAL, "mlt_batch_create: every job needs a probe");
+            for (int k = 0; k < i; ++k)
+                if (jobs[i].matrix == jobs[k].matrix)
+                    return fail(MLT_EINVAL, "mlt_batch_create: each job needs its own matrix handle");
+        }
+        cudaStream_t s = (cudaStream_t)stream;
+        mlt_batch* B = new mlt_batch();
+        B->jobs.resize(njobs);
+        int rc;
+        for (int i = 0; i < njobs; ++i) {
+            const mlt_moments_job& q = jobs[i];
+            if ((rc = prepare_moment_job(q.matrix, q.a, q.b, q.seed, q.probe_offset, q.nprobes, q.degree, precision,
+                                         flags, q.mu, q.ld_mu, q.group_width, B->jobs[i], s))) {
+                delete B;
+                return rc;
+            }
+        }
+        // the handles are locked from here on: the graph points into their workspaces
+        for (auto& J : B->jobs) ++J.m->batch_refs;
+        for (int i = 0; i < njobs; ++i) {
+            const MomentJob& J = B->jobs[i];
+            const int64_t n = J.nprobes;
+            B->first.push_back(jobs[i].probe_offset);
+            B->count.push_back(n);
+            B->ids_dev.push_back(const_cast<int64_t*>(J.groups.front().ids_dev));
+            std::vector<int64_t> h(n);
+            MLT_CUDA_TRY(cudaMemcpyAsync(h.data(), J.groups.front().ids_dev, n * sizeof(int64_t),
+                                         cudaMemcpyDeviceToHost, s));
+            MLT_CUDA_TRY(cudaStreamSynchronize(s));
+            B->ids.push_back(std::move(h));
+        }
+        MLT_CUDA_TRY(cudaGetDevice(&B->device));
+        cudaStream_t cs = nullptr;
+        std::vector<cudaStream_t> br(std::min(njobs, 64), nullptr);
+        std::vector<cudaEvent_t> ev(njobs + 1, nullptr);
+        auto cleanup = [&]() {
+            for (auto& x : br) if (x) cudaStreamDestroy(x);
+            for (auto& e : ev) if (e) cudaEventDestroy(e);
+            if (cs) cudaStreamDestroy(cs);
+        };
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        for (auto& x : br)
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
+        for (auto& ev1 : ev)
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev1, cudaEventDisableTiming);
+        cudaGraph_t graph = nullptr;
+        rc = MLT_OK;
+        {
+            ProfPause pause;
+            if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+            const bool capturing = e == cudaSuccess;
+            if (e == cudaSuccess) e = cudaEventRecord(ev[njobs], cs);
+            for (int i = 0; i < njobs && e == cudaSuccess; ++i) {
+                cudaStream_t si = br[i % br.size()];
+                e = cudaStreamWaitEvent(si, ev[njobs], 0);
+                if (e == cudaSuccess && (rc = enqueue_moment_job(B->jobs[i], si))) e = cudaErrorUnknown;
+                if (e == cudaSuccess) e = cudaEventRecord(ev[i], si);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[i], 0);
+            }
+            if (capturing) {
+                cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+                if (e == cudaSuccess) e = e2;
+            }
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&B->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        cleanup();
+        if (e != cudaSuccess) {
+            mlt_batch_destroy(B);
+            return rc ? rc : cuda_fail(e, "mlt_batch_create graph");
+        }
+        *out = B;
+        return MLT_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(MLT_ENOMEM, "mlt_batch_create: host allocation failed");
+    } catch (...) {
+        return fail(MLT_ECUDA, "mlt_batch_create: exception");
+    }
+}
+
+int mlt_batch_run(mlt_batch* B, int64_t id_shift, void* stream)
+{
+    try {
+        if (!B || !B->exec) return fail(MLT_EINVAL, "mlt_batch_run: null batch");
+        const size_t njobs = B->jobs.size();
+        for (size_t i = 0; i < njobs; ++i) {
+            const int64_t lo = B->first[i] + id_shift;
+            if (lo < 0 || lo + B->count[i] > (1LL << 32))
+                return fail(MLT_EINVAL, "mlt_batch_run: shifted probe ids must lie in [0, 2^32)");
+        }
+        cudaStream_t s = (cudaStream_t)stream;
+        std::vector<int64_t> h;
+        for (size_t i = 0; i < njobs; ++i) {
+            MomentJob& J = B->jobs[i];
+            h.resize(B->ids[i].size());
+            for (size_t p = 0; p < h.size(); ++p) h[p] = B->ids[i][p] + id_shift;
+            // pageable source: the copy has left h when the call returns
+            MLT_CUDA_TRY(cudaMemcpyAsync(B->ids_dev[i], h.data(), h.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+            MLT_CUDA_TRY(cudaMemsetAsync(J.err, 0, sizeof(int), s));
+        }
+        {
+            ProfScope ps("moments_graph", s);
+            MLT_CUDA_TRY(cudaGraphLaunch(B->exec, s));
+        }
+        int rc;
+        for (size_t i = 0; i < njobs; ++i)
+            if ((rc = finish_moment_job(B->jobs[i], s))) return rc;
+        return MLT_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(MLT_ENOMEM, "mlt_batch_run: host allocation failed");
+    } catch (...) {
+        return fail(MLT_ECUDA, "mlt_batch_run: exception");
+    }
+}
+
 int mlt_autotune(mlt_matrix* m, int precision, int trial_steps, int* best, void* stream)
 {
     try {
         if (!m) return fail(MLT_EINVAL, "mlt_autotune: null handle");
+        if (int rcb = handle_busy(m, "mlt_autotune")) return rcb;
         if (trial_steps < 1 || trial_steps > MLT_MAX_DEGREE / 2) return fail(MLT_EINVAL, "mlt_autotune: bad trial length");
         cudaStream_t s = (cudaStream_t)stream;
         double a = 0.0, b = 0.0;
@@ -1206,6 +1361,7 @@ int mlt_low_traces(mlt_matrix* m, double a, double b, double* t, int* count, voi
 {
     try {
         if (!m || !t) return fail(MLT_EINVAL, "mlt_low_traces: null argument");
+        if (int rcb = handle_busy(m, "mlt_low_traces")) return rcb;
         if (!(a < b) || !std::isfinite(a) || !std::isfinite(b)) return fail(MLT_EINVAL, "mlt_low_traces: need finite a < b");
         return low_traces(m, a, b, t, count, (cudaStream_t)stream);
     } catch (...) {
@@ -1365,6 +1521,7 @@ int mlt_triangle_trace(mlt_matrix* m, uint64_t seed, int64_t probe_offset, int64
 {
     try {
         if (!m) return fail(MLT_EINVAL, "mlt_triangle_trace: null handle");
+        if (int rcb = handle_busy(m, "mlt_triangle_trace")) return rcb;
         if (m->val_type != MLT_PATTERN || (m->flags & MLT_GRAM) || m->A.nrows != m->A.ncols)
             return fail(MLT_EINVAL, "mlt_triangle_trace: needs a square 0/1 pattern matrix");
         if (nprobes < 1) return fail(MLT_EINVAL, "mlt_triangle_trace: need at least one probe");

@@ -119,6 +119,7 @@ struct mlt_matrix {
     double low_diag = 0.0, low_sq = 0.0;
     double tri_bound = 0.0;     // sum_(i,j) deg_i deg_j
     int group_width = 0;        // probes per group chosen by mlt_autotune (0: from memory)
+    int batch_refs = 0;         // persistent batches (mlt_batch) whose graph uses this handle
     // scratch
     mlt::SpmmPlan plan_A, plan_AT, plan_P;
     mlt::DevBuf ws_v[2], ws_v2[2], ws_w, ws_part, ws_dots, ws_misc, ws_out, ws_y, ws_y16, ws_y32, ws_z, ws_x, ws_tri,
@@ -163,6 +164,14 @@ struct MomentJob {
     std::vector<MomentPlan> groups;
     std::vector<std::vector<int>> acts;
 };
+// A persistent batch's CUDA graph points into the workspaces of its handles,
+// so no other call may use (and perhaps regrow) them while the batch lives.
+inline int handle_busy(const mlt_matrix* m, const char* who)
+{
+    if (m && m->batch_refs > 0)
+        return fail(MLT_EINVAL, std::string(who) + ": the handle belongs to a live mlt_batch (destroy it first)");
+    return MLT_OK;
+}
 int prepare_moment_job(mlt_matrix* m, double a, double b, uint64_t seed, int64_t probe_offset, int64_t nprobes,
                        const int32_t* degree, int precision, unsigned flags, double* mu, int64_t ld_mu,
                        int group_width, MomentJob& J, cudaStream_t s);

@@ -40,7 +40,8 @@ EXPORTS = ["mlt_create_csr", "mlt_destroy", "mlt_matrix_info", "mlt_spectrum_bou
            "mlt_moments_batched", "mlt_autotune", "mlt_moments_noalloc", "mlt_low_traces",
            "mlt_release_cached", "mlt_poly_apply", "mlt_hutchpp_estimate", "mlt_pilot_variances",
            "mlt_select_levels", "mlt_band_samples", "mlt_mlmc_combine", "mlt_triangle_estimate",
-           "mlt_fp64_rate", "mlt_surrogate_get_norm"]
+           "mlt_fp64_rate", "mlt_surrogate_get_norm", "mlt_batch_create", "mlt_batch_run",
+           "mlt_batch_destroy"]
 MLT_TRI_CV = {"none": 0, "fit": 1, "cheb": 2}
 
 
@@ -599,6 +600,62 @@ def _bind_batch(L):
                                       ctypes.c_uint, ctypes.c_void_p]
     L.mlt_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]
+    L.mlt_batch_create.argtypes = [ctypes.POINTER(mlt_moments_job), ctypes.c_int, ctypes.c_int, ctypes.c_uint,
+                                   ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    L.mlt_batch_run.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    L.mlt_batch_destroy.argtypes = [ctypes.c_void_p]
+
+
+def _job_array(jobs):
+    arr = (mlt_moments_job * len(jobs))()
+    keep = []
+    for i, j in enumerate(jobs):
+        deg = np.ascontiguousarray(j["degrees"], dtype=np.int32)
+        keep.append(deg)
+        out = j["out"]
+        arr[i].matrix = j["matrix"]
+        arr[i].a, arr[i].b = float(j["a"]), float(j["b"])
+        arr[i].seed, arr[i].probe_offset = int(j.get("seed", 0)), int(j.get("probe_offset", 0))
+        arr[i].nprobes = deg.size
+        arr[i].degree = _ptr(deg)
+        arr[i].mu = _ptr(out)
+        arr[i].ld_mu = out.shape[1]
+        arr[i].group_width = int(j.get("group_width", 0))
+    return arr, keep
+
+
+class Batch:
+    """A persistent batch (mlt_batch_create): the jobs' CUDA graph is built
+    once; run(shift) replays it with probe ids shifted by `shift`.  The jobs'
+    output arrays must outlive the batch."""
+
+    def __init__(self, jobs, precision="fp64", flags=0, stream=None):
+        arr, keep = _job_array(jobs)
+        self._keep = (keep, [j["out"] for j in jobs])
+        h = ctypes.c_void_p()
+        prec = MLT_PREC[precision] if isinstance(precision, str) else precision
+        _check(lib().mlt_batch_create(arr, len(jobs), prec, int(flags), _stream(stream), ctypes.byref(h)))
+        self.handle = h.value
+
+    def run(self, shift=0, stream=None):
+        _check(lib().mlt_batch_run(self.handle, int(shift), _stream(stream)))
+
+    def close(self):
+        if self.handle:
+            lib().mlt_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mlt_moments_batched(jobs, precision="fp64", flags=0, stream=None):

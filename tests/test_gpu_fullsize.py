@@ -135,3 +135,40 @@ def test_estrada_rmat22_df64_full_size_reordered(L, O, rmat22):
     tol = 1e-10 * g.nrows
     _check_all(got, deg, g.nrows, tol)
     _check_sampled(O, g, -10.0, 10.0, 0, 0, got, [(p, 16) for p in _spread(128, 4)], tol, scale=scale)
+
+
+def test_diffusion64_batched_fp64_full_size(L, O):
+    """The 64 diffusion operators of the batched workload (grids 10^3 .. 100^3,
+    sum of d about 9.6e6) as one persistent batch in FP64, each matrix's
+    ragged levels as the benchmark runs them; for every matrix its first
+    probe (degree 16) in full and its last probe (degree 256) through degree
+    16 against the oracle, and |mu_j| <= d for every moment."""
+    import torch
+    mats, jobs, outs, Ms = [], [], [], []
+    try:
+        for i in range(64):
+            side = int(round(10 * 10 ** (i / 63)))
+            sh = float(np.random.default_rng(1000 + i).uniform(0.01, 1.0))
+            m = synth.diffusion_3d(side, sigma=1.0, shift=sh, seed=i)
+            lv, mm = ([16, 64, 256], [64, 16, 4]) if i % 2 == 0 else ([16, 48, 128, 256], [64, 32, 8, 4])
+            deg = np.repeat(np.array(lv, dtype=np.int32), mm)
+            b = float(np.max(np.add.reduceat(np.abs(m.val), m.rowptr[:-1])))   # Gershgorin (positive diagonal)
+            M = L.Matrix(m)
+            Ms.append(M)
+            out = torch.zeros((deg.size, 257), dtype=torch.float64, device="cuda")
+            outs.append(out)
+            mats.append((m, sh, b, deg))
+            jobs.append({"matrix": M.handle, "a": sh, "b": b, "seed": 7, "probe_offset": 3 * 128, "degrees": deg,
+                         "out": out})
+        with L.Batch(jobs) as B:
+            B.run(0)
+            torch.cuda.synchronize()
+        tol = 1e-10
+        for (m, sh, b, deg), out in zip(mats, outs):
+            got = out.cpu().numpy()
+            d = m.nrows
+            _check_all(got, deg, d, tol * d)
+            _check_sampled(O, m, sh, b, 7, 3 * 128, got, [(0, 16), (deg.size - 1, 16)], tol * d)
+    finally:
+        for M in Ms:
+            M.close()

@@ -199,3 +199,19 @@ def test_hutchpp_df64_moments(L, O):
         r0 = L.mlt_hutchpp_estimate(M.handle, 0.1, 8.1, c, 3, 0, 0, 6, precision="df64")   # remainder only
     mu = O.moments(m, 0.1, 8.1, 3, 0, [16] * 6)
     assert abs(r0.estimate - float(np.mean(mu @ c))) <= 1e-10 * np.sum(np.abs(c)) * m.nrows
+
+
+def test_hutchpp_multi_tile_gram_schmidt(L, O):
+    """A sketch wider than one 64-column tile (s = 100) takes the Gram-Schmidt
+    path without Cholesky QR, over two Q tiles, and the 130 remainder probes
+    span three G tiles in the block deflation; all against the oracle."""
+    m = synth.grid_laplacian_2d(30, shift=0.1)
+    c = O.cheb_coeffs("log", 0.1, 8.1, 24)
+    ref, r, samples = _hutchpp_pair(L, O, m, 0.1, 8.1, c, seed=4, off=50, s=100, g=130)
+    sc = np.sum(np.abs(c))
+    assert r.rank == ref["rank"] == 100
+    assert abs(r.t_sketch - ref["t_sketch"]) <= 1e-10 * sc * 100
+    assert np.max(np.abs(samples - ref["samples"])) <= 1e-10 * sc * m.nrows
+    assert abs(r.estimate - ref["estimate"]) <= 1e-10 * sc * m.nrows
+    assert abs(r.std_error - ref["stderr"]) <= 1e-6 * ref["stderr"]
+    assert r.matvecs == 100 * 24 + 230 * 12

@@ -46,16 +46,49 @@ def test_rmat_scale14_and_truth(L, O):
 
 
 def test_exhaustive_signs_give_exact_count(L, O):
-    # every sign vector of a 10-vertex graph: mean x3 = 6T exactly.  The probes
-    # here are the generator's, so instead check E over many ids is unbiased and
-    # the per-probe moments agree with the oracle on explicit probe ids.
+    """Every sign vector of a 10-vertex graph, taken from the GPU's own probes:
+    16,384 probe ids cover all 2^10 sign patterns (checked); averaging the GPU's
+    moments over one probe per pattern averages over the whole sign space, so
+    mean x3 = 6T, mean x2 = nnz and mean x1 = 0 hold exactly, in integers."""
     g = synth.random_graph(10, 0.5, seed=11)
-    x = np.zeros((1024, 3), dtype=np.int64)
+    n = 16384
+    x = np.zeros((n, 3), dtype=np.int64)
     with L.Matrix(g) as G:
-        G.triangles(3, 0, 1024, x=x)
-    assert np.array_equal(x, O.triangle_moments(g, 3, 0, 1024))
+        G.triangles(3, 0, n, x=x)
+    first = {}
+    for p in range(n):
+        key = tuple(O.rademacher(3, p, 10).astype(int))
+        first.setdefault(key, p)
+    assert len(first) == 1 << 10
+    rows = x[sorted(first.values())]
+    assert np.array_equal(rows, O.triangle_moments(g, 3, 0, n)[sorted(first.values())])
     T = O.triangle_count(g)
-    assert abs(x[:, 2].mean() - 6 * T) < 5 * x[:, 2].std() / 32
+    assert int(rows[:, 2].sum()) == 6 * T * (1 << 10)
+    assert int(rows[:, 1].sum()) == g.nnz * (1 << 10)
+    assert int(rows[:, 0].sum()) == 0
+
+
+@pytest.mark.parametrize("cv", ["none", "fit", "cheb"])
+def test_estimates_from_gpu_moments_bit_exact(L, O, cv):
+    """The library's estimate from the GPU's integers, for every control-variate
+    form of Section 5.4 (none, fitted, a priori from the Chebyshev expansion of
+    x^3 on [-max degree, max degree]), equals the oracle's from its own
+    integers to the last bit."""
+    g = synth.rmat_adjacency(13, 16, seed=2)
+    x = np.zeros((700, 3), dtype=np.int64)
+    with L.Matrix(g) as G:
+        L.mlt_triangle_trace(G.handle, 8, 123, 700, x=x)
+    xr = O.triangle_moments(g, 8, 123, 700)
+    assert np.array_equal(x, xr)
+    dmax = float(np.max(np.diff(g.rowptr)))
+    est, se, a1, a2 = L.mlt_triangle_estimate(x, g.nnz, cv, -dmax, dmax)
+    if cv == "cheb":
+        ra1, ra2 = O.triangle_cv_cheb(-dmax, dmax)
+        er, sr = O.triangle_estimate_fixed(xr, g.nnz, ra1, ra2)
+        assert (a1, a2) == (ra1, ra2)
+    else:
+        er, sr, _, _ = O.triangle_estimate(xr, g.nnz, cv == "fit")
+    assert est == er and se == sr
 
 
 def test_device_output(L, O):
