@@ -245,12 +245,26 @@ struct Lane {
 };
 
 
+// Adding a gathered value to a row's running sum (pattern matrices), and
+// closing a batch of such additions.  FP32 and FP64 add directly.  Double-
+// float sums defer their renormalisation to the end of each batch of at most
+// 32 entries (df_add_lazy): the inner loop's arithmetic falls from 11 to 8
+// FP32 operations per value, and the deferred error stays below 2^-38 of the
+// sum.
+template <typename T>
+__device__ __forceinline__ T acc_add(T acc, T x) { return acc + x; }
+template <>
+__device__ __forceinline__ df64 acc_add<df64>(df64 acc, df64 x) { return df_add_lazy(acc, x); }
+template <typename T>
+__device__ __forceinline__ T acc_close(T acc) { return acc; }
+template <>
+__device__ __forceinline__ df64 acc_close<df64>(df64 acc) { return df_norm(acc); }
+
 // acc = sum over entries [k0, k1) of a_ij * V[j, c0 .. c0+N).  Row and entry
 // indices fit in 32 bits (nnz < 2^31 is checked when the handle is made).
 // PAT: a 0/1 pattern, every a_ij = 1, so each product is the gathered value
-// itself: acc + x, which equals fma(1, x, acc) bit for bit in every vector
-// type (1 * x is exact, in double-float too) and saves the double-float
-// multiply.
+// itself, added with acc_add (for FP32 and FP64 that equals fma(1, x, acc)
+// bit for bit; it saves the double-float multiply).
 template <typename T, int G, bool PAT>
 __device__ __forceinline__ void row_product_t(const StepArgs<T>& a, const Lane<T, G>& L, int k0, int k1,
                                               T (&acc)[Lanes<T>::N], uint64_t pol)
@@ -279,10 +293,14 @@ __device__ __forceinline__ void row_product_t(const StepArgs<T>& a, const Lane<T
                     reinterpret_cast<const P*>(a.vgather + (size_t)c * a.ldv + L.c0), pol);
 #pragma unroll
                 for (int q = 0; q < N; ++q) {
-                    if constexpr (PAT) acc[q] = acc[q] + x.v[q];
+                    if constexpr (PAT) acc[q] = acc_add(acc[q], x.v[q]);
                     else acc[q] = fma(v, x.v[q], acc[q]);
                 }
             }
+        }
+        if constexpr (PAT) {
+#pragma unroll
+            for (int q = 0; q < N; ++q) acc[q] = acc_close(acc[q]);
         }
     }
 }

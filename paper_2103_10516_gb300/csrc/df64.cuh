@@ -67,6 +67,21 @@ __device__ __forceinline__ df64 operator*(df64 x, df64 y)
     return df_fast_two_sum(p, e);
 }
 
+// Running-sum addition with a deferred renormalisation: x.hi + y.hi is formed
+// with its exact rounding error (Knuth's two-sum), the error and y.lo go into
+// the low part, and the pair is left unnormalised (8 FP32 operations against
+// 11 for the full sum).  After k such additions the low part carries k
+// roundings of at most 2^-24 of itself, so a caller renormalises (df_norm)
+// every few dozen terms; over 32 terms the deferred error stays below
+// 2^-38 of the sum's magnitude.
+__device__ __forceinline__ df64 df_add_lazy(df64 x, df64 y)
+{
+    const df64 s = df_two_sum(x.hi, y.hi);
+    return df64(s.hi, x.lo + (s.lo + y.lo));
+}
+
+__device__ __forceinline__ df64 df_norm(df64 x) { return df_fast_two_sum(x.hi, x.lo); }
+
 using ::fma;   // the float and double overloads stay visible beside this one
 __device__ __forceinline__ df64 fma(df64 a, df64 b, df64 c) { return a * b + c; }
 
