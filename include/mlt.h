@@ -214,7 +214,9 @@ int mlt_moments(mlt_matrix* m, double a, double b, uint64_t seed,
  * after launch.  Every job must use its own matrix handle.  All device memory
  * is reserved and all inputs are on the device before the graph is captured;
  * the call returns when every job's results are in its mu.  group_width is the
- * number of probes per group (0: the handle's, see mlt_autotune).  Errors as
+ * number of probes per group (0: the handle's, see mlt_autotune; without one,
+ * as many as fit a third of the free device memory, at most 1024, and at most
+ * 64 for operators of 2^20 rows or more with 8-byte vectors).  Errors as
  * mlt_moments, plus MLT_EINVAL for a repeated handle.
  */
 typedef struct {
