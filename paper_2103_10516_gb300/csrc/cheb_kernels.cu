@@ -58,7 +58,47 @@ template <> struct Lanes<double> { static constexpr int N = 2; };   // 16-byte v
 template <> struct Lanes<float> { static constexpr int N = 4; };
 template <> struct Lanes<df64> { static constexpr int N = 2; };     // 16-byte vectors of pairs
 
-template <typename T, int N> struct alignas(sizeof(T) * N) Pack { T v[N]; };
+// A lane's 16-byte slice of a vector row.  Double-float slices hold the high
+// parts of their two entries, then the two low parts, so that a slice loads as
+// two packed FP32 pairs (see the f32x2 operations below).
+template <typename T, int N> struct alignas(sizeof(T) * N) Pack {
+    T v[N];
+    __device__ __forceinline__ T get(int q) const { return v[q]; }
+    __device__ __forceinline__ void set(int q, T x) { v[q] = x; }
+};
+template <> struct alignas(16) Pack<df64, 2> {
+    float h[2], l[2];
+    __device__ __forceinline__ df64 get(int q) const { return df64(h[q], l[q]); }
+    __device__ __forceinline__ void set(int q, df64 x) { h[q] = x.hi; l[q] = x.lo; }
+};
+
+// Entry c of the vector row at v + row_off (row_off = row * ldv, ldv even).
+template <typename T>
+__device__ __forceinline__ void put_entry(T* v, size_t row_off, int c, T x) { v[row_off + c] = x; }
+template <>
+__device__ __forceinline__ void put_entry<df64>(df64* v, size_t row_off, int c, df64 x)
+{
+    float* f = reinterpret_cast<float*>(v + row_off + (c & ~1));
+    f[c & 1] = x.hi;
+    f[2 + (c & 1)] = x.lo;
+}
+
+// Packed FP32 pair arithmetic (two lanes of FP32 in one 64-bit register,
+// round to nearest): GB300 issues each as one instruction for both entries.
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ float lo_half(uint64_t x) { return __uint_as_float((unsigned)x); }
+__device__ __forceinline__ float hi_half(uint64_t x) { return __uint_as_float((unsigned)(x >> 32)); }
 
 // Resident CTAs per SM the step kernel is compiled for, the unroll depth of
 // its gather loop, and whether its gathers carry an L2 evict-last policy, per
@@ -245,20 +285,16 @@ struct Lane {
 };
 
 
-// Adding a gathered value to a row's running sum (pattern matrices), and
-// closing a batch of such additions.  FP32 and FP64 add directly.  Double-
-// float sums defer their renormalisation to the end of each batch of at most
-// 32 entries (df_add_lazy): the inner loop's arithmetic falls from 11 to 8
-// FP32 operations per value, and the deferred error stays below 2^-38 of the
-// sum.
+// Adding a gathered value to a row's running sum (FP32 and FP64 pattern
+// matrices), and closing a batch of such additions.  Double-float pattern sums
+// take row_sum_df2 below: they defer their renormalisation to the end of each
+// batch of at most 32 entries (df_add_lazy, then df_norm), which cuts the
+// arithmetic from 11 to 8 FP32 operations per value; the deferred error stays
+// below 2^-38 of the sum.
 template <typename T>
 __device__ __forceinline__ T acc_add(T acc, T x) { return acc + x; }
-template <>
-__device__ __forceinline__ df64 acc_add<df64>(df64 acc, df64 x) { return df_add_lazy(acc, x); }
 template <typename T>
 __device__ __forceinline__ T acc_close(T acc) { return acc; }
-template <>
-__device__ __forceinline__ df64 acc_close<df64>(df64 acc) { return df_norm(acc); }
 
 // acc = sum over entries [k0, k1) of a_ij * V[j, c0 .. c0+N).  Row and entry
 // indices fit in 32 bits (nnz < 2^31 is checked when the handle is made).
@@ -293,8 +329,8 @@ __device__ __forceinline__ void row_product_t(const StepArgs<T>& a, const Lane<T
                     reinterpret_cast<const P*>(a.vgather + (size_t)c * a.ldv + L.c0), pol);
 #pragma unroll
                 for (int q = 0; q < N; ++q) {
-                    if constexpr (PAT) acc[q] = acc_add(acc[q], x.v[q]);
-                    else acc[q] = fma(v, x.v[q], acc[q]);
+                    if constexpr (PAT) acc[q] = acc_add(acc[q], x.get(q));
+                    else acc[q] = fma(v, x.get(q), acc[q]);
                 }
             }
         }
@@ -305,11 +341,50 @@ __device__ __forceinline__ void row_product_t(const StepArgs<T>& a, const Lane<T
     }
 }
 
+// row_product_t for a double-float pattern matrix on packed FP32 pairs: the
+// lane's two entries advance together through the operations of df_add_lazy
+// and, at the end of each batch, df_norm, in the same order and rounding, so
+// the sums are the same bit for bit at half the arithmetic instructions.  A
+// slice loads as (high parts, low parts), the two packed operands.
+template <int G>
+__device__ __forceinline__ void row_sum_df2(const StepArgs<df64>& a, const Lane<df64, G>& L, int k0, int k1,
+                                            df64 (&acc)[2])
+{
+    constexpr int kGatherUnroll = StepTuning<df64>::kUnroll;
+    uint64_t H = 0, Lo = 0;
+    for (int base = k0; base < k1; base += G) {
+        const int k = base + L.glane;
+        const int cj = k < k1 ? __ldg(a.col + k) : 0;
+        const int cnt = min(G, k1 - base);
+#pragma unroll kGatherUnroll
+        for (int t = 0; t < cnt; ++t) {
+            const int c = __shfl_sync(L.gmask, cj, t, G);
+            if (L.vok) {
+                const ulonglong2 x = *reinterpret_cast<const ulonglong2*>(a.vgather + (size_t)c * a.ldv + L.c0);
+                const uint64_t s = add2(H, x.x);
+                const uint64_t bb = sub2(s, H);
+                const uint64_t e = add2(sub2(H, sub2(s, bb)), sub2(x.x, bb));
+                Lo = add2(Lo, add2(e, x.y));
+                H = s;
+            }
+        }
+        const uint64_t s = add2(H, Lo);
+        Lo = sub2(Lo, sub2(s, H));
+        H = s;
+    }
+    acc[0] = df64(lo_half(H), lo_half(Lo));
+    acc[1] = df64(hi_half(H), hi_half(Lo));
+}
+
 template <typename T, int G>
 __device__ __forceinline__ void row_product(const StepArgs<T>& a, const Lane<T, G>& L, int k0, int k1,
                                             T (&acc)[Lanes<T>::N], uint64_t pol)
 {
-    if (a.val) row_product_t<T, G, false>(a, L, k0, k1, acc, pol);
+    if (a.val) {
+        row_product_t<T, G, false>(a, L, k0, k1, acc, pol);
+        return;
+    }
+    if constexpr (std::is_same<T, df64>::value) row_sum_df2<G>(a, L, k0, k1, acc);
     else row_product_t<T, G, true>(a, L, k0, k1, acc, pol);
 }
 
@@ -342,7 +417,7 @@ __device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0
     P out;
     if (a.mode == 2) {
 #pragma unroll
-        for (int q = 0; q < N; ++q) out.v[q] = acc[q];
+        for (int q = 0; q < N; ++q) out.set(q, acc[q]);
         *reinterpret_cast<P*>(a.vprev_out + off) = out;
         return;
     }
@@ -351,17 +426,18 @@ __device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0
         const P& xp = ops.xp;
         const P xa = *reinterpret_cast<const P*>(a.addv + off);
 #pragma unroll
-        for (int q = 0; q < N; ++q) out.v[q] = a.m1 * (a.alpha * acc[q] + a.beta * xc.v[q]) - xp.v[q] + a.coef * xa.v[q];
+        for (int q = 0; q < N; ++q)
+            out.set(q, a.m1 * (a.alpha * acc[q] + a.beta * xc.get(q)) - xp.get(q) + a.coef * xa.get(q));
         *reinterpret_cast<P*>(a.vprev_out + off) = out;
         return;
     }
     if (a.mode == 0) {
 #pragma unroll
-        for (int q = 0; q < N; ++q) out.v[q] = a.alpha * acc[q] + a.beta * xc.v[q];
+        for (int q = 0; q < N; ++q) out.set(q, a.alpha * acc[q] + a.beta * xc.get(q));
     } else {
         const P& xp = ops.xp;
 #pragma unroll
-        for (int q = 0; q < N; ++q) out.v[q] = T(2) * (a.alpha * acc[q] + a.beta * xc.v[q]) - xp.v[q];
+        for (int q = 0; q < N; ++q) out.set(q, T(2) * (a.alpha * acc[q] + a.beta * xc.get(q)) - xp.get(q));
     }
     *reinterpret_cast<P*>(a.vprev_out + off) = out;
     const int tid = threadIdx.x;
@@ -369,8 +445,9 @@ __device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0
 #pragma unroll
         for (int q = 0; q < N; ++q) {
             DotAcc<T> s0 = dots[0][q][tid], s1 = dots[1][q][tid];
-            s0.add_prod(out.v[q], out.v[q]);
-            s1.add_prod(out.v[q], xc.v[q]);
+            const T o = out.get(q);
+            s0.add_prod(o, o);
+            s1.add_prod(o, xc.get(q));
             dots[0][q][tid] = s0;
             dots[1][q][tid] = s1;
         }
@@ -380,7 +457,7 @@ __device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0
             if (c0 + q >= a.B) break;
             const bool neg = probe_negative(a.seedmix, (uint64_t)a.ids[c0 + q], (uint64_t)(a.orig ? a.orig[r] : r));
             DotAcc<T> s1 = dots[1][q][tid];
-            s1.add(neg ? -out.v[q] : out.v[q]);
+            s1.add(neg ? -out.get(q) : out.get(q));
             dots[1][q][tid] = s1;
         }
     }
@@ -468,7 +545,7 @@ __global__ void __launch_bounds__(kThreads, StepTuning<T>::kCtas) cheb_step_kern
                 if (L.vok) {
                     Pack<T, N> p;
 #pragma unroll
-                    for (int q = 0; q < N; ++q) p.v[q] = acc[q];
+                    for (int q = 0; q < N; ++q) p.set(q, acc[q]);
                     *reinterpret_cast<Pack<T, N>*>(a.segpart + (size_t)sidx * a.ldv + L.c0) = p;
                 }
             }
@@ -498,7 +575,7 @@ __global__ void __launch_bounds__(kThreads) cheb_long_kernel(StepArgs<T> a)
             for (int64_t sidx = a.long_seg0[i]; sidx < a.long_seg0[i + 1]; ++sidx) {
                 const P p = *reinterpret_cast<const P*>(a.segpart + (size_t)sidx * a.ldv + L.c0);
 #pragma unroll
-                for (int q = 0; q < N; ++q) acc[q] += p.v[q];
+                for (int q = 0; q < N; ++q) acc[q] += p.get(q);
             }
             epilogue<T, CL>(a, r, L.c0, acc, ops, dots);
         }
@@ -547,7 +624,7 @@ __global__ void init_probes_kernel(T* v0, int64_t d, int ldv, int B, const int64
         const int c = (int)(e % ldv);
         T z = T(0);
         if (c < B) z = probe_negative(seedmix, (uint64_t)ids[c], (uint64_t)(orig ? orig[i] : i)) ? T(-1) : T(1);
-        v0[e] = z;
+        put_entry(v0, (size_t)(e - c), c, z);
     }
 }
 
@@ -899,10 +976,24 @@ int run_group_df(mlt_matrix* M, const MomentPlan& plan, double a, double b, uint
     return MLT_OK;
 }
 
-__global__ void to_df_kernel(const double* __restrict__ in, df64* __restrict__ out, int64_t n)
+// Matrix values as double-float pairs, entry by entry (values are read one
+// entry at a time, not as vector slices).
+__global__ void to_df_values_kernel(const double* __restrict__ in, df64* __restrict__ out, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = df64(in[i]);
+}
+
+// In place: the n (even) doubles at v become n double-float entries in the
+// slice layout of Pack<df64, 2>; one thread per pair reads both before writing.
+__global__ void to_df_kernel(double* v, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n / 2;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 x = reinterpret_cast<const double2*>(v)[i];
+        const df64 p(x.x), q(x.y);
+        reinterpret_cast<float4*>(v)[i] = make_float4(p.hi, q.hi, p.lo, q.lo);
+    }
 }
 
 // out[i] = coef * x[i] over n elements (x null: zeros).
@@ -1046,10 +1137,11 @@ int moments_block(mlt_matrix* M, double a, double b, double* V0, double* V1, int
         if ((rc = ensure_df_values(M, s))) return rc;
         const int64_t n = g.d * (int64_t)ldv;
         const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 16LL * M->num_sms));
+        if (ldv & 1) return MLT_EINVAL;
         df64* W0 = reinterpret_cast<df64*>(V0);
         {
             ProfScope ps("to_df", s);
-            to_df_kernel<<<nb, 256, 0, s>>>(V0, W0, n);
+            to_df_kernel<<<nb, 256, 0, s>>>(V0, n);
         }
         MLT_CUDA_TRY(cudaGetLastError());
         df64* V[2] = {W0, reinterpret_cast<df64*>(V1)};
@@ -1175,7 +1267,7 @@ int ensure_df_values(mlt_matrix* M, cudaStream_t s)
         if (e != cudaSuccess) return fail(MLT_ENOMEM, "device allocation (double-float values) failed");
         const int nb = (int)std::min<int64_t>((C.nnz + 255) / 256, 16LL * M->num_sms);
         ProfScope ps("to_df", s);
-        to_df_kernel<<<std::max(nb, 1), 256, 0, s>>>(C.val64, p, C.nnz);
+        to_df_values_kernel<<<std::max(nb, 1), 256, 0, s>>>(C.val64, p, C.nnz);
         MLT_CUDA_TRY(cudaGetLastError());
         own = p;
         C.valdf = p;
