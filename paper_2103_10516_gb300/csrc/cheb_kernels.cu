@@ -52,6 +52,7 @@ constexpr int kSlots = 16;          // steps whose partials are buffered before 
 constexpr int64_t kRowCost = 4;     // units charged per row (the epilogue) on top of its entries
 constexpr int64_t kChunksPerSm = 1024;  // work chunks per SM in the split of an operand
 constexpr int64_t kLongRow = 128;   // rows above max(Uc, this) are cut into segments
+constexpr int32_t kSegWindow = 16384;    // column window of the segment dealing order
 
 template <typename T> struct Lanes;
 template <> struct Lanes<double> { static constexpr int N = 2; };   // 16-byte vectors
@@ -83,41 +84,31 @@ __device__ __forceinline__ void put_entry<df64>(df64* v, size_t row_off, int c, 
     f[2 + (c & 1)] = x.lo;
 }
 
-// Packed FP32 pair arithmetic (two lanes of FP32 in one 64-bit register,
-// round to nearest): GB300 issues each as one instruction for both entries.
-__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b)
-{
-    uint64_t d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b)
-{
-    uint64_t d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ float lo_half(uint64_t x) { return __uint_as_float((unsigned)x); }
-__device__ __forceinline__ float hi_half(uint64_t x) { return __uint_as_float((unsigned)(x >> 32)); }
 
 // Resident CTAs per SM the step kernel is compiled for, the unroll depth of
-// its gather loop, and whether its gathers carry an L2 evict-last policy, per
-// vector type.  More unrolled gathers keep more row reads outstanding but need
-// registers, which lowers the resident CTAs; the evict-last policy keeps the
-// gathered V_k rows in L2 against the streams of V_{k-1}, V_{k+1} and the
-// column indices.  Measured on the scale-22 R-MAT graph (gather-bound) and the
-// 100^3 diffusion operator (streaming): FP32 and FP64 gain from the deeper
-// unroll (FP32 9.5 -> 8.1 ms a step on the graph) and FP32 from the policy
-// (8.1 -> 7.5 ms); the double-float step, heavier in arithmetic, is fastest
-// at six CTAs without either.
-template <int C, int U, bool E> struct TuneOf {
+// its gather loop, whether its gathers carry an L2 evict-last policy, and
+// whether long-row segments are dealt out in column-window order (see
+// ensure_spmm_plan), per vector type.  More unrolled gathers keep more row
+// reads outstanding but need registers, which lowers the resident CTAs; the
+// evict-last policy keeps the gathered V_k rows in L2 against the streams of
+// V_{k-1}, V_{k+1} and the column indices.  Measured on the scale-22 R-MAT
+// graph (gather-bound) and the 100^3 diffusion operator (streaming): FP32 and
+// FP64 gain from the deeper unroll (FP32 9.5 -> 8.1 ms a step on the graph)
+// and FP32 from the policy (8.1 -> 7.5 ms).  The double-float step on packed
+// pairs (row_sum_df2, epilogue_df2) needs few enough registers for eight
+// unrolled gathers at five CTAs: 8.4 -> 7.2 ms on the graph, against 8.3 at
+// six CTAs and unroll 8 and 8.1 at five and unroll 12 (3% slower on the
+// streaming operator).  The column-window order takes FP32 and double-float
+// steps on the graph 3-4% lower and the FP64 step, bound by FP64 arithmetic,
+// 2% higher.
+template <int C, int U, bool E, bool W> struct TuneOf {
     static constexpr int kCtas = C, kUnroll = U;
-    static constexpr bool kEvictLast = E;
+    static constexpr bool kEvictLast = E, kWindowSegs = W;
 };
 template <typename T> struct StepTuning;
-template <> struct StepTuning<float> : TuneOf<5, 8, true> {};
-template <> struct StepTuning<double> : TuneOf<4, 8, false> {};
-template <> struct StepTuning<df64> : TuneOf<6, 4, false> {};
+template <> struct StepTuning<float> : TuneOf<5, 8, true, true> {};
+template <> struct StepTuning<double> : TuneOf<4, 8, false, false> {};
+template <> struct StepTuning<df64> : TuneOf<5, 8, false, true> {};
 
 // An L2 access policy that marks lines evict-last (createpolicy, PTX ISA).
 __device__ __forceinline__ uint64_t evict_last_policy()
@@ -252,6 +243,7 @@ struct StepArgs {
     const int64_t* seg_k0;
     const int32_t* long_rows;
     const int64_t* long_seg0;
+    const int32_t* seg_order;   // dealing order of the segments, or null (segment order)
     T* segpart;            // [nseg][ldv] partial products of long-row segments
 };
 
@@ -406,6 +398,37 @@ __device__ __forceinline__ RowOperands<T> load_operands(const StepArgs<T>& a, in
     return o;
 }
 
+// The recurrence update and the V.V, V.V_k dot products of epilogue (below)
+// for double-float vectors, on packed pairs: the lane's two entries go through
+// the df64 operations of the generic code side by side.  A recurrence step
+// folds its factor 2 into alpha and beta (doubling is exact), so
+// out = (2 alpha) acc + (2 beta) xc - xp equals 2 (alpha acc + beta xc) - xp.
+__device__ __forceinline__ void epilogue_df2(const StepArgs<df64>& a, size_t off, const df64 (&acc)[2],
+                                             const RowOperands<df64>& ops, DotSlots<df64>& dots)
+{
+    df2 xc;
+    memcpy(&xc, &ops.xc, sizeof(df2));
+    df2 al = df2_of(a.alpha, a.alpha), be = df2_of(a.beta, a.beta);
+    if (a.mode != 0) {
+        al = df2_twice(al);
+        be = df2_twice(be);
+    }
+    df2 out = al * df2_of(acc[0], acc[1]) + be * xc;
+    if (a.mode != 0) {
+        df2 xp;
+        memcpy(&xp, &ops.xp, sizeof(df2));
+        out = out + (-xp);
+    }
+    *reinterpret_cast<ulonglong2*>(a.vprev_out + off) = make_ulonglong2(out.h, out.l);
+    const int tid = threadIdx.x;
+    const df2 s0 = out * out + df2_of(dots[0][0][tid].s, dots[0][1][tid].s);
+    dots[0][0][tid].s = df2_first(s0);
+    dots[0][1][tid].s = df2_second(s0);
+    const df2 s1 = out * xc + df2_of(dots[1][0][tid].s, dots[1][1][tid].s);
+    dots[1][0][tid].s = df2_first(s1);
+    dots[1][1][tid].s = df2_second(s1);
+}
+
 // V_{k+1}[r] from acc = (A V_k)[r], and the fused dot products.
 template <typename T, bool CL>
 __device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0, const T (&acc)[Lanes<T>::N],
@@ -430,6 +453,12 @@ __device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0
             out.set(q, a.m1 * (a.alpha * acc[q] + a.beta * xc.get(q)) - xp.get(q) + a.coef * xa.get(q));
         *reinterpret_cast<P*>(a.vprev_out + off) = out;
         return;
+    }
+    if constexpr (std::is_same<T, df64>::value) {
+        if (!a.direct) {
+            epilogue_df2(a, off, acc, ops, dots);
+            return;
+        }
     }
     if (a.mode == 0) {
 #pragma unroll
@@ -537,7 +566,7 @@ __global__ void __launch_bounds__(kThreads, StepTuning<T>::kCtas) cheb_step_kern
                     end = nxt;
                 }
             } else {
-                const int64_t sidx = it - a.nch;
+                const int64_t sidx = a.seg_order ? (int64_t)__ldg(a.seg_order + (it - a.nch)) : it - a.nch;
                 const int64_t r = __ldg(a.seg_row + sidx);
                 const int k0 = (int)__ldg(a.seg_k0 + sidx);
                 const int k1 = (int)min((int64_t)k0 + a.Ul, __ldg(a.rowptr + r + 1));
@@ -747,6 +776,7 @@ void set_split(StepArgs<T>& a, const SpmmPlan& P, T* segpart)
     a.seg_k0 = P.seg_k0;
     a.long_rows = P.long_rows;
     a.long_seg0 = P.long_seg0;
+    a.seg_order = StepTuning<T>::kWindowSegs ? P.seg_order : nullptr;
     a.segpart = segpart;
 }
 
@@ -1155,10 +1185,26 @@ int moments_block(mlt_matrix* M, double a, double b, double* V0, double* V1, int
     return MLT_OK;
 }
 
+// The first column of each segment.
+__global__ void seg_first_col_kernel(const int32_t* __restrict__ col, const int64_t* __restrict__ k0, int64_t n,
+                                     int32_t* __restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = col[k0[i]];
+}
+
 // Build the fixed work split of one CSR operand (once per matrix): chunk size
 // Uc from the unit count so that there are a few dozen chunks per SM, the row
 // holding the first unit of every chunk, and the segment table of rows longer
 // than Uc.  Computed on the host from a copy of rowptr.
+//
+// Segments are dealt out in the order of their first column, in windows of
+// kSegWindow columns (row order within a window).  A row's columns are sorted,
+// so the segments in flight at any moment gather from one narrow band of
+// columns, and a vector row that several long rows share is read from L2
+// rather than DRAM by all but the first.  The order only decides when a
+// segment runs; its partial product, and the order in which a row's segments
+// are added, do not change.
 int ensure_spmm_plan(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, cudaStream_t s)
 {
     if (P.ready) return MLT_OK;
@@ -1198,7 +1244,7 @@ int ensure_spmm_plan(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, cudaStream_t s
     long_seg0.push_back((int64_t)seg_row.size());
     const int64_t nseg = (int64_t)seg_row.size();
     const int nlong = (int)long_rows.size();
-    const size_t bytes = nch * sizeof(int64_t) + nseg * (sizeof(int64_t) + sizeof(int32_t)) +
+    const size_t bytes = nch * sizeof(int64_t) + nseg * (sizeof(int64_t) + 2 * sizeof(int32_t)) +
                          (nlong + 1) * sizeof(int64_t) + nlong * sizeof(int32_t) + 64;
     char* mem = nullptr;
     if (pool_malloc((void**)&mem, bytes, s) != cudaSuccess) {
@@ -1211,6 +1257,7 @@ int ensure_spmm_plan(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, cudaStream_t s
     P.long_seg0 = P.seg_k0 + nseg;
     P.seg_row = reinterpret_cast<int32_t*>(P.long_seg0 + nlong + 1);
     P.long_rows = P.seg_row + nseg;
+    P.seg_order = P.long_rows + nlong;
     MLT_CUDA_TRY(cudaMemcpyAsync(P.crow, crow.data(), nch * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     if (nseg) {
         MLT_CUDA_TRY(cudaMemcpyAsync(P.seg_k0, seg_k0.data(), nseg * sizeof(int64_t), cudaMemcpyHostToDevice, s));
@@ -1221,6 +1268,19 @@ int ensure_spmm_plan(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, cudaStream_t s
     if (nlong)
         MLT_CUDA_TRY(cudaMemcpyAsync(P.long_rows, long_rows.data(), nlong * sizeof(int32_t),
                                      cudaMemcpyHostToDevice, s));
+    if (nseg) {
+        std::vector<int32_t> first(nseg), order(nseg);
+        const int nb = (int)std::min<int64_t>((nseg + 255) / 256, 16LL * M->num_sms);
+        seg_first_col_kernel<<<nb, 256, 0, s>>>(C.col, P.seg_k0, nseg, P.seg_order);
+        MLT_CUDA_TRY(cudaGetLastError());
+        MLT_CUDA_TRY(cudaMemcpyAsync(first.data(), P.seg_order, nseg * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        MLT_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int64_t i = 0; i < nseg; ++i) order[i] = (int32_t)i;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+            return first[x] / kSegWindow < first[y] / kSegWindow;
+        });
+        MLT_CUDA_TRY(cudaMemcpyAsync(P.seg_order, order.data(), nseg * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    }
     MLT_CUDA_TRY(cudaStreamSynchronize(s));
     P.nch = nch;
     P.Uc = Uc;

@@ -14,6 +14,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 namespace mlt {
 
 struct __align__(8) df64 {
@@ -86,5 +88,80 @@ using ::fma;   // the float and double overloads stay visible beside this one
 __device__ __forceinline__ df64 fma(df64 a, df64 b, df64 c) { return a * b + c; }
 
 __device__ __forceinline__ double df_to_double(df64 x) { return (double)x.hi + (double)x.lo; }
+
+// Packed FP32 pairs: two FP32 values in one 64-bit register (the first in the
+// low half), operated on by one f32x2 instruction, round to nearest.  GB300
+// issues each of these once for both values.
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t neg2(uint64_t a) { return a ^ 0x8000000080000000ull; }
+__device__ __forceinline__ uint64_t pack2(float a, float b)
+{
+    return (uint64_t)__float_as_uint(a) | ((uint64_t)__float_as_uint(b) << 32);
+}
+__device__ __forceinline__ float lo_half(uint64_t x) { return __uint_as_float((unsigned)x); }
+__device__ __forceinline__ float hi_half(uint64_t x) { return __uint_as_float((unsigned)(x >> 32)); }
+
+// Two double-float numbers side by side: h holds their high parts, l their
+// low parts.  Each operation below is the df64 operation of the same name
+// applied to both numbers, step for step with the same roundings, so its
+// results are those of two scalar calls bit for bit.
+struct df2 {
+    uint64_t h, l;
+};
+
+__device__ __forceinline__ df2 df2_of(df64 x0, df64 x1) { return df2{pack2(x0.hi, x1.hi), pack2(x0.lo, x1.lo)}; }
+__device__ __forceinline__ df64 df2_first(df2 x) { return df64(lo_half(x.h), lo_half(x.l)); }
+__device__ __forceinline__ df64 df2_second(df2 x) { return df64(hi_half(x.h), hi_half(x.l)); }
+
+__device__ __forceinline__ df2 df2_fast_two_sum(uint64_t a, uint64_t b)
+{
+    const uint64_t s = add2(a, b);
+    return df2{s, sub2(b, sub2(s, a))};
+}
+
+__device__ __forceinline__ df2 operator+(df2 x, df2 y)
+{
+    const uint64_t s = add2(x.h, y.h);
+    const uint64_t bb = sub2(s, x.h);
+    const uint64_t e = add2(sub2(x.h, sub2(s, bb)), sub2(y.h, bb));
+    return df2_fast_two_sum(s, add2(e, add2(x.l, y.l)));
+}
+
+__device__ __forceinline__ df2 operator-(df2 x) { return df2{neg2(x.h), neg2(x.l)}; }
+
+__device__ __forceinline__ df2 operator*(df2 x, df2 y)
+{
+    const uint64_t p = mul2(x.h, y.h);
+    uint64_t e = fma2(x.h, y.h, neg2(p));
+    e = fma2(x.h, y.l, e);
+    e = fma2(x.l, y.h, e);
+    return df2_fast_two_sum(p, e);
+}
+
+// 2x, exactly (both parts doubled).
+__device__ __forceinline__ df2 df2_twice(df2 x) { return df2{add2(x.h, x.h), add2(x.l, x.l)}; }
 
 }  // namespace mlt

@@ -74,6 +74,7 @@ struct SpmmPlan {
     int64_t* long_seg0 = nullptr;  // first segment of each long row (nlong + 1)
     int32_t* seg_row = nullptr;    // row of each segment
     int32_t* long_rows = nullptr;  // the long rows
+    int32_t* seg_order = nullptr;  // segments in the order they are dealt out (see ensure_spmm_plan)
     void* mem = nullptr;           // one device allocation holding all of the above
 };
 
