@@ -137,6 +137,23 @@ __device__ __forceinline__ P ld_gather(const P* p, uint64_t pol)
     }
 }
 
+// The same 16-byte load as two 64-bit words (the operands of packed pair
+// arithmetic).
+template <bool E>
+__device__ __forceinline__ ulonglong2 ld_gather2(const void* p, uint64_t pol)
+{
+    if constexpr (E) {
+        ulonglong2 u;
+        asm volatile("ld.global.L2::cache_hint.v2.u64 {%0,%1}, [%2], %3;"
+                     : "=l"(u.x), "=l"(u.y)
+                     : "l"(p), "l"(pol));
+        return u;
+    } else {
+        (void)pol;
+        return *reinterpret_cast<const ulonglong2*>(p);
+    }
+}
+
 // A thread's running dot product.  The kernels keep these in shared memory
 // (one slot per thread, see DotSlots): held in registers beside a row's
 // gathers they pushed the step kernel past the six-CTA register budget, and
@@ -277,31 +294,113 @@ struct Lane {
 };
 
 
-// Adding a gathered value to a row's running sum (FP32 and FP64 pattern
-// matrices), and closing a batch of such additions.  Double-float pattern sums
-// take row_sum_df2 below: they defer their renormalisation to the end of each
-// batch of at most 32 entries (df_add_lazy, then df_norm), which cuts the
-// arithmetic from 11 to 8 FP32 operations per value; the deferred error stays
-// below 2^-38 of the sum.
-template <typename T>
-__device__ __forceinline__ T acc_add(T acc, T x) { return acc + x; }
-template <typename T>
-__device__ __forceinline__ T acc_close(T acc) { return acc; }
+// Running sums of one row over the lane's N columns: add() takes one gathered
+// row slice (and the entry's value, for valued matrices), close() ends a batch
+// of at most G entries, out() gives the N sums.  Three forms:
+//  - SumScalar: any vector type, acc = fma(a_ij, x, acc) for valued matrices
+//    and acc + x for patterns (every a_ij = 1; for FP32 and FP64 that equals
+//    fma(1, x, acc) bit for bit);
+//  - SumF2, FP32 patterns: the four sums as two packed pairs, each packed add
+//    the scalar add on both halves, so the sums are the same bit for bit (on
+//    valued matrices the packed form, with a_ij broadcast into a pair,
+//    measured slower);
+//  - SumDf2, double-float patterns: the two sums as packed pairs of high and
+//    low parts, added as df_add_lazy does (the rounding error of the high
+//    parts into the low parts, left unnormalised) and renormalised as df_norm
+//    does at the end of each batch.  That cuts the arithmetic from 11 to 8
+//    FP32 operations per value, each packed instruction doing two, and the
+//    deferred error stays below 2^-38 of the sum.  A double-float slice loads
+//    as (high parts, low parts), the two packed operands.
+template <typename T, bool PAT>
+struct SumScalar {
+    static constexpr int N = Lanes<T>::N;
+    using P = Pack<T, N>;
+    T s[N];
+    __device__ __forceinline__ void init()
+    {
+#pragma unroll
+        for (int q = 0; q < N; ++q) s[q] = T(0);
+    }
+    template <bool E>
+    __device__ __forceinline__ void add(const T* p, T v, uint64_t pol)
+    {
+        const P x = ld_gather<E>(reinterpret_cast<const P*>(p), pol);
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            if constexpr (PAT) s[q] = s[q] + x.get(q);
+            else s[q] = fma(v, x.get(q), s[q]);
+        }
+    }
+    __device__ __forceinline__ void close() {}
+    __device__ __forceinline__ void out(T (&acc)[N]) const
+    {
+#pragma unroll
+        for (int q = 0; q < N; ++q) acc[q] = s[q];
+    }
+};
 
-// acc = sum over entries [k0, k1) of a_ij * V[j, c0 .. c0+N).  Row and entry
-// indices fit in 32 bits (nnz < 2^31 is checked when the handle is made).
-// PAT: a 0/1 pattern, every a_ij = 1, so each product is the gathered value
-// itself, added with acc_add (for FP32 and FP64 that equals fma(1, x, acc)
-// bit for bit; it saves the double-float multiply).
+struct SumF2 {
+    uint64_t A0, A1;
+    __device__ __forceinline__ void init() { A0 = A1 = 0; }
+    template <bool E>
+    __device__ __forceinline__ void add(const float* p, float, uint64_t pol)
+    {
+        const ulonglong2 x = ld_gather2<E>(p, pol);
+        A0 = add2(A0, x.x);
+        A1 = add2(A1, x.y);
+    }
+    __device__ __forceinline__ void close() {}
+    __device__ __forceinline__ void out(float (&acc)[4]) const
+    {
+        acc[0] = lo_half(A0);
+        acc[1] = hi_half(A0);
+        acc[2] = lo_half(A1);
+        acc[3] = hi_half(A1);
+    }
+};
+
+struct SumDf2 {
+    uint64_t H, Lo;
+    __device__ __forceinline__ void init() { H = Lo = 0; }
+    template <bool E>
+    __device__ __forceinline__ void add(const df64* p, df64, uint64_t pol)
+    {
+        const ulonglong2 x = ld_gather2<E>(p, pol);
+        const uint64_t s = add2(H, x.x);
+        const uint64_t bb = sub2(s, H);
+        const uint64_t e = add2(sub2(H, sub2(s, bb)), sub2(x.x, bb));
+        Lo = add2(Lo, add2(e, x.y));
+        H = s;
+    }
+    __device__ __forceinline__ void close()
+    {
+        const uint64_t s = add2(H, Lo);
+        Lo = sub2(Lo, sub2(s, H));
+        H = s;
+    }
+    __device__ __forceinline__ void out(df64 (&acc)[2]) const
+    {
+        acc[0] = df64(lo_half(H), lo_half(Lo));
+        acc[1] = df64(hi_half(H), hi_half(Lo));
+    }
+};
+
+template <typename T, bool PAT> struct SumOf { using type = SumScalar<T, PAT>; };
+template <> struct SumOf<float, true> { using type = SumF2; };
+template <> struct SumOf<df64, true> { using type = SumDf2; };
+
+// acc = sum over entries [k0, k1) of a_ij * V[j, c0 .. c0+N), the column
+// indices (and values) loaded G at a time from the row's first entry.  Row
+// and entry indices fit in 32 bits (nnz < 2^31 is checked when the handle is
+// made).
 template <typename T, int G, bool PAT>
 __device__ __forceinline__ void row_product_t(const StepArgs<T>& a, const Lane<T, G>& L, int k0, int k1,
                                               T (&acc)[Lanes<T>::N], uint64_t pol)
 {
-    constexpr int N = Lanes<T>::N;
     constexpr int kGatherUnroll = StepTuning<T>::kUnroll;
-    using P = Pack<T, N>;
-#pragma unroll
-    for (int q = 0; q < N; ++q) acc[q] = T(0);
+    constexpr bool E = StepTuning<T>::kEvictLast;
+    typename SumOf<T, PAT>::type S;
+    S.init();
     for (int base = k0; base < k1; base += G) {
         const int k = base + L.glane;
         int cj = 0;
@@ -316,67 +415,18 @@ __device__ __forceinline__ void row_product_t(const StepArgs<T>& a, const Lane<T
             const int c = __shfl_sync(L.gmask, cj, t, G);
             T v = T(1);
             if constexpr (!PAT) v = shfl_val(L.gmask, vj, t, G);
-            if (L.vok) {
-                const P x = ld_gather<StepTuning<T>::kEvictLast>(
-                    reinterpret_cast<const P*>(a.vgather + (size_t)c * a.ldv + L.c0), pol);
-#pragma unroll
-                for (int q = 0; q < N; ++q) {
-                    if constexpr (PAT) acc[q] = acc_add(acc[q], x.get(q));
-                    else acc[q] = fma(v, x.get(q), acc[q]);
-                }
-            }
+            if (L.vok) S.template add<E>(a.vgather + (size_t)c * a.ldv + L.c0, v, pol);
         }
-        if constexpr (PAT) {
-#pragma unroll
-            for (int q = 0; q < N; ++q) acc[q] = acc_close(acc[q]);
-        }
+        S.close();
     }
-}
-
-// row_product_t for a double-float pattern matrix on packed FP32 pairs: the
-// lane's two entries advance together through the operations of df_add_lazy
-// and, at the end of each batch, df_norm, in the same order and rounding, so
-// the sums are the same bit for bit at half the arithmetic instructions.  A
-// slice loads as (high parts, low parts), the two packed operands.
-template <int G>
-__device__ __forceinline__ void row_sum_df2(const StepArgs<df64>& a, const Lane<df64, G>& L, int k0, int k1,
-                                            df64 (&acc)[2])
-{
-    constexpr int kGatherUnroll = StepTuning<df64>::kUnroll;
-    uint64_t H = 0, Lo = 0;
-    for (int base = k0; base < k1; base += G) {
-        const int k = base + L.glane;
-        const int cj = k < k1 ? __ldg(a.col + k) : 0;
-        const int cnt = min(G, k1 - base);
-#pragma unroll kGatherUnroll
-        for (int t = 0; t < cnt; ++t) {
-            const int c = __shfl_sync(L.gmask, cj, t, G);
-            if (L.vok) {
-                const ulonglong2 x = *reinterpret_cast<const ulonglong2*>(a.vgather + (size_t)c * a.ldv + L.c0);
-                const uint64_t s = add2(H, x.x);
-                const uint64_t bb = sub2(s, H);
-                const uint64_t e = add2(sub2(H, sub2(s, bb)), sub2(x.x, bb));
-                Lo = add2(Lo, add2(e, x.y));
-                H = s;
-            }
-        }
-        const uint64_t s = add2(H, Lo);
-        Lo = sub2(Lo, sub2(s, H));
-        H = s;
-    }
-    acc[0] = df64(lo_half(H), lo_half(Lo));
-    acc[1] = df64(hi_half(H), hi_half(Lo));
+    S.out(acc);
 }
 
 template <typename T, int G>
 __device__ __forceinline__ void row_product(const StepArgs<T>& a, const Lane<T, G>& L, int k0, int k1,
                                             T (&acc)[Lanes<T>::N], uint64_t pol)
 {
-    if (a.val) {
-        row_product_t<T, G, false>(a, L, k0, k1, acc, pol);
-        return;
-    }
-    if constexpr (std::is_same<T, df64>::value) row_sum_df2<G>(a, L, k0, k1, acc);
+    if (a.val) row_product_t<T, G, false>(a, L, k0, k1, acc, pol);
     else row_product_t<T, G, true>(a, L, k0, k1, acc, pol);
 }
 
