@@ -193,11 +193,42 @@ template <> struct DotAcc<df64> {
     __device__ __forceinline__ double value() const { return df_to_double(s); }
 };
 
-// The CTA's running dots: [0] V_{k+1}.V_{k+1} (unused in direct mode), [1]
-// V_{k+1}.V_k or z.V_{k+1}; slot [q][tid] for the thread's column c0 + q, so a
-// warp's accesses are consecutive.
+// The CTA's running dots: kind [0] V_{k+1}.V_{k+1} (unused in direct mode),
+// [1] V_{k+1}.V_k or z.V_{k+1}, for the thread's columns c0 + q.  Each thread
+// only touches its own slots, and a warp's accesses are consecutive.
 template <typename T>
-using DotSlots = DotAcc<T>[2][Lanes<T>::N][kThreads];
+struct DotSlots {
+    DotAcc<T> d[2][Lanes<T>::N][kThreads];
+    __device__ __forceinline__ DotAcc<T> load(int kind, int q, int t) const { return d[kind][q][t]; }
+    __device__ __forceinline__ void store(int kind, int q, int t, DotAcc<T> x) { d[kind][q][t] = x; }
+};
+// FP32: the Kahan sums of columns (c0, c0 + 1) and (c0 + 2, c0 + 3) as packed
+// pairs, (sums, compensations), so that epilogue_f2 updates two columns with
+// each packed instruction.
+template <>
+struct DotSlots<float> {
+    ulonglong2 d[2][2][kThreads];
+    __device__ __forceinline__ DotAcc<float> load(int kind, int q, int t) const
+    {
+        const ulonglong2 v = d[kind][q >> 1][t];
+        DotAcc<float> x;
+        x.s = (q & 1) ? hi_half(v.x) : lo_half(v.x);
+        x.c = (q & 1) ? hi_half(v.y) : lo_half(v.y);
+        return x;
+    }
+    __device__ __forceinline__ void store(int kind, int q, int t, DotAcc<float> x)
+    {
+        ulonglong2 v = d[kind][q >> 1][t];
+        if (q & 1) {
+            v.x = pack2(lo_half(v.x), x.s);
+            v.y = pack2(lo_half(v.y), x.c);
+        } else {
+            v.x = pack2(x.s, hi_half(v.x));
+            v.y = pack2(x.c, hi_half(v.y));
+        }
+        d[kind][q >> 1][t] = v;
+    }
+};
 
 // A matrix value through the read-only cache.
 template <typename T>
@@ -471,12 +502,52 @@ __device__ __forceinline__ void epilogue_df2(const StepArgs<df64>& a, size_t off
     }
     *reinterpret_cast<ulonglong2*>(a.vprev_out + off) = make_ulonglong2(out.h, out.l);
     const int tid = threadIdx.x;
-    const df2 s0 = out * out + df2_of(dots[0][0][tid].s, dots[0][1][tid].s);
-    dots[0][0][tid].s = df2_first(s0);
-    dots[0][1][tid].s = df2_second(s0);
-    const df2 s1 = out * xc + df2_of(dots[1][0][tid].s, dots[1][1][tid].s);
-    dots[1][0][tid].s = df2_first(s1);
-    dots[1][1][tid].s = df2_second(s1);
+    const df2 s0 = out * out + df2_of(dots.d[0][0][tid].s, dots.d[0][1][tid].s);
+    dots.d[0][0][tid].s = df2_first(s0);
+    dots.d[0][1][tid].s = df2_second(s0);
+    const df2 s1 = out * xc + df2_of(dots.d[1][0][tid].s, dots.d[1][1][tid].s);
+    dots.d[1][0][tid].s = df2_first(s1);
+    dots.d[1][1][tid].s = df2_second(s1);
+}
+
+// A packed Kahan step on two columns: sc = (sums, compensations) takes the
+// products a * b, each as DotAcc<float>::add_prod does.
+__device__ __forceinline__ void kahan_prod2(ulonglong2& sc, uint64_t a, uint64_t b)
+{
+    ulonglong2 v = sc;
+    const uint64_t y = fma2(a, b, neg2(v.y));
+    const uint64_t t = add2(v.x, y);
+    v.y = sub2(sub2(t, v.x), y);
+    v.x = t;
+    sc = v;
+}
+
+// The recurrence update and the V.V, V.V_k dot products of epilogue (below)
+// for FP32 vectors, on packed pairs: out = alpha' acc + beta' xc (- xp), the
+// product beta' xc rounded and alpha' acc fused into the sum, with the factor
+// 2 of a recurrence step folded into alpha' and beta' (doubling is exact).
+__device__ __forceinline__ void epilogue_f2(const StepArgs<float>& a, size_t off, const float (&acc)[4],
+                                            const RowOperands<float>& ops, DotSlots<float>& dots)
+{
+    ulonglong2 xc;
+    memcpy(&xc, &ops.xc, sizeof(xc));
+    const float al = a.mode != 0 ? 2.0f * a.alpha : a.alpha;
+    const float be = a.mode != 0 ? 2.0f * a.beta : a.beta;
+    const uint64_t al2 = pack2(al, al), be2 = pack2(be, be);
+    uint64_t o0 = fma2(al2, pack2(acc[0], acc[1]), mul2(be2, xc.x));
+    uint64_t o1 = fma2(al2, pack2(acc[2], acc[3]), mul2(be2, xc.y));
+    if (a.mode != 0) {
+        ulonglong2 xp;
+        memcpy(&xp, &ops.xp, sizeof(xp));
+        o0 = sub2(o0, xp.x);
+        o1 = sub2(o1, xp.y);
+    }
+    *reinterpret_cast<ulonglong2*>(a.vprev_out + off) = make_ulonglong2(o0, o1);
+    const int tid = threadIdx.x;
+    kahan_prod2(dots.d[0][0][tid], o0, o0);
+    kahan_prod2(dots.d[0][1][tid], o1, o1);
+    kahan_prod2(dots.d[1][0][tid], o0, xc.x);
+    kahan_prod2(dots.d[1][1][tid], o1, xc.y);
 }
 
 // V_{k+1}[r] from acc = (A V_k)[r], and the fused dot products.
@@ -510,6 +581,12 @@ __device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0
             return;
         }
     }
+    if constexpr (std::is_same<T, float>::value) {
+        if (!a.direct) {
+            epilogue_f2(a, off, acc, ops, dots);
+            return;
+        }
+    }
     if (a.mode == 0) {
 #pragma unroll
         for (int q = 0; q < N; ++q) out.set(q, a.alpha * acc[q] + a.beta * xc.get(q));
@@ -523,21 +600,21 @@ __device__ __forceinline__ void epilogue(const StepArgs<T>& a, int64_t r, int c0
     if (!a.direct) {
 #pragma unroll
         for (int q = 0; q < N; ++q) {
-            DotAcc<T> s0 = dots[0][q][tid], s1 = dots[1][q][tid];
+            DotAcc<T> s0 = dots.load(0, q, tid), s1 = dots.load(1, q, tid);
             const T o = out.get(q);
             s0.add_prod(o, o);
             s1.add_prod(o, xc.get(q));
-            dots[0][q][tid] = s0;
-            dots[1][q][tid] = s1;
+            dots.store(0, q, tid, s0);
+            dots.store(1, q, tid, s1);
         }
     } else {
 #pragma unroll
         for (int q = 0; q < N; ++q) {
             if (c0 + q >= a.B) break;
             const bool neg = probe_negative(a.seedmix, (uint64_t)a.ids[c0 + q], (uint64_t)(a.orig ? a.orig[r] : r));
-            DotAcc<T> s1 = dots[1][q][tid];
+            DotAcc<T> s1 = dots.load(1, q, tid);
             s1.add(neg ? -out.get(q) : out.get(q));
-            dots[1][q][tid] = s1;
+            dots.store(1, q, tid, s1);
         }
     }
 }
@@ -548,8 +625,10 @@ __device__ __forceinline__ void clear_dots(DotSlots<T>& dots)
 {
 #pragma unroll
     for (int q = 0; q < Lanes<T>::N; ++q) {
-        dots[0][q][threadIdx.x].clear();
-        dots[1][q][threadIdx.x].clear();
+        DotAcc<T> z;
+        z.clear();
+        dots.store(0, q, threadIdx.x, z);
+        dots.store(1, q, threadIdx.x, z);
     }
 }
 
@@ -572,8 +651,8 @@ __device__ __forceinline__ void cta_partials(const StepArgs<T>& a, const Lane<T,
             const long long gglob = g0 + g;
             if (gglob >= L.ncls * a.nchunks || (int)(gglob % a.nchunks) != ch) continue;
             const int t = g * G + gl;
-            s0 += dots[0][q][t].value();
-            s1 += dots[1][q][t].value();
+            s0 += dots.load(0, q, t).value();
+            s1 += dots.load(1, q, t).value();
         }
         part[c] = s0;
         part[a.ldv + c] = s1;
