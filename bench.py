@@ -1041,10 +1041,9 @@ class Stencil3D:
         self.d = self.csr.nrows
         self.nnz = self.csr.nnz
         self.precision = precision or "fp32"
-        # DRAM bytes per launch (128 live probes) from an ncu capture of the FP32 step
-        # ncu DRAM bytes per launch of the current build (FP32 only; the
-        # double-float capture predates the current step kernel)
-        self.TRAFFIC = {"fp32": {"cheb_step": 1.5914e9}}.get(self.precision, {})
+        # DRAM bytes per launch (128 live probes) from an ncu capture of the
+        # step kernel as built; none until the current kernel is captured
+        self.TRAFFIC = {}
         self.dtype = {"fp32": "f32", "fp64": "f64", "df64": "df64", "mixed": "f32+f64"}[self.precision]
 
     def _prec(self, mlt):
