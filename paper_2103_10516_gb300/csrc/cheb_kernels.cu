@@ -110,7 +110,10 @@ __device__ __forceinline__ void put_entry<df64>(df64* v, size_t row_off, int c, 
 // step on the 100^3 diffusion operator (7 entries a row) from 0.569 to
 // 0.516 ms and the Gram operator's X^T step from 0.201 to 0.182 ms, left FP32
 // on the graph unchanged (6.18 -> 6.14 ms), and slowed the double-float and
-// FP64 steps by 2-9%.
+// FP64 steps by 2-9%.  They apply to groups of at least unroll-depth lanes:
+// a narrower group (few live probes) takes at most G entries a batch, and a
+// block of mostly idle slots cost the learned estimator's FP32 moments, whose
+// last steps run 1-2 live probes, 16% of their time.
 template <int C, int U, bool E, bool W, bool PR> struct TuneOf {
     static constexpr int kCtas = C, kUnroll = U;
     static constexpr bool kEvictLast = E, kWindowSegs = W, kPredicated = PR;
@@ -451,10 +454,11 @@ __device__ __forceinline__ void row_product_t(const StepArgs<T>& a, const Lane<T
             if constexpr (!PAT) vj = ldg_val(a.val + k);
         }
         const int cnt = min(G, k1 - base);
-        if constexpr (StepTuning<T>::kPredicated) {
+        if constexpr (StepTuning<T>::kPredicated && G >= kGatherUnroll) {
             // blocks of kGatherUnroll predicated slots: every gather of a block
             // is issued before the first of them is consumed, also in the
-            // last, partial block
+            // last, partial block (groups narrower than a block, which take
+            // at most G entries a batch, keep the plain loop)
             for (int t0 = 0; t0 < cnt; t0 += kGatherUnroll) {
 #pragma unroll
                 for (int u = 0; u < kGatherUnroll; ++u) {
@@ -1354,12 +1358,14 @@ __global__ void seg_first_col_kernel(const int32_t* __restrict__ col, const int6
 // than Uc.  Computed on the host from a copy of rowptr.
 //
 // Segments are dealt out in the order of their first column, in windows of
-// kSegWindow columns (row order within a window).  A row's columns are sorted,
-// so the segments in flight at any moment gather from one narrow band of
+// kSegWindow columns (row order within a window).  Where a row's columns are
+// sorted, the segments in flight at any moment gather from one narrow band of
 // columns, and a vector row that several long rows share is read from L2
-// rather than DRAM by all but the first.  The order only decides when a
-// segment runs; its partial product, and the order in which a row's segments
-// are added, do not change.
+// rather than DRAM by all but the first.  (The relabelled operator keeps each
+// row's entries in their original order, so there the bands are wider; the
+// order still measured 3-4% faster for FP32 and double-float steps on the
+// scale-22 graph.)  The order only decides when a segment runs; its partial
+// product, and the order in which a row's segments are added, do not change.
 int ensure_spmm_plan(mlt_matrix* M, const DevCSR& C, SpmmPlan& P, cudaStream_t s)
 {
     if (P.ready) return MLT_OK;
