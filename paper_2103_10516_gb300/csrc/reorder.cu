@@ -16,6 +16,8 @@
 // copy; everything else keeps the original arrays.
 #include <cuda_runtime.h>
 
+#include <cub/cub.cuh>
+
 #include <algorithm>
 #include <vector>
 
@@ -23,6 +25,27 @@
 
 namespace mlt {
 namespace {
+
+// key[i] = ~deg_i, so that an ascending sort puts larger degrees first; id[i] = i.
+__global__ void degree_keys_kernel(const int64_t* __restrict__ rp, int64_t n, uint32_t* __restrict__ key,
+                                   int32_t* __restrict__ id)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        key[i] = ~(uint32_t)(rp[i + 1] - rp[i]);
+        id[i] = (int32_t)i;
+    }
+}
+
+// pdeg[j] = degree of row perm[j]; inv[perm[j]] = j.
+__global__ void permuted_degrees_kernel(const int64_t* __restrict__ rp, const int32_t* __restrict__ perm, int64_t n,
+                                        int64_t* __restrict__ pdeg, int32_t* __restrict__ inv)
+{
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t o = perm[j];
+        pdeg[j] = rp[o + 1] - rp[o];
+        inv[o] = (int32_t)j;
+    }
+}
 
 // Row j of the relabelled matrix is row perm[j] of the original, with every
 // column c renamed inv[c].  One warp per row (entries in their original order).
@@ -46,27 +69,17 @@ __global__ void relabel_rows_kernel(const int64_t* __restrict__ rp, const int32_
 
 }  // namespace
 
+// All on the device, in stream order: the stable radix sort of the keys ~deg
+// gives perm (decreasing degree, equal degrees in increasing id), a prefix
+// sum of the permuted degrees gives the relabelled row pointers, and one
+// warp per row copies and renames the entries.
 int build_reorder(mlt_matrix* M, cudaStream_t s)
 {
     const DevCSR& A = M->A;
     const int64_t n = A.nrows, nnz = A.nnz;
-    std::vector<int64_t> rp(n + 1);
-    MLT_CUDA_TRY(cudaMemcpyAsync(rp.data(), A.rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    MLT_CUDA_TRY(cudaStreamSynchronize(s));
-    // counting sort by degree, descending; equal degrees keep increasing ids
-    int64_t maxdeg = 0;
-    for (int64_t i = 0; i < n; ++i) maxdeg = std::max(maxdeg, rp[i + 1] - rp[i]);
-    std::vector<int64_t> start(maxdeg + 2, 0);
-    for (int64_t i = 0; i < n; ++i) ++start[maxdeg - (rp[i + 1] - rp[i]) + 1];
-    for (int64_t b = 0; b <= maxdeg; ++b) start[b + 1] += start[b];
-    std::vector<int32_t> perm(std::max<int64_t>(n, 1)), inv(std::max<int64_t>(n, 1));
-    for (int64_t i = 0; i < n; ++i) perm[start[maxdeg - (rp[i + 1] - rp[i])]++] = (int32_t)i;
-    std::vector<int64_t> prp(n + 1);
-    prp[0] = 0;
-    for (int64_t j = 0; j < n; ++j) {
-        inv[perm[j]] = (int32_t)j;
-        prp[j + 1] = prp[j] + (rp[perm[j] + 1] - rp[perm[j]]);
-    }
+    if (n >= (int64_t(1) << 31)) return fail(MLT_EINVAL, "relabelling needs fewer than 2^31 rows");
+    const int nn = (int)n;
+    std::vector<void*> scratch;
     auto alloc = [&](void** p, size_t bytes) -> int {
         if (pool_malloc(p, std::max<size_t>(bytes, 16), s) != cudaSuccess) {
             cudaGetLastError();
@@ -74,8 +87,13 @@ int build_reorder(mlt_matrix* M, cudaStream_t s)
         }
         return MLT_OK;
     };
-    int rc;
-    void *d_prp = nullptr, *d_pcol = nullptr, *d_pval = nullptr, *d_perm = nullptr, *d_inv = nullptr;
+    auto release = [&]() {
+        for (void* p : scratch) cudaFreeAsync(p, s);
+        scratch.clear();
+    };
+    int rc = MLT_OK;
+    void *d_prp = nullptr, *d_pcol = nullptr, *d_pval = nullptr, *d_perm = nullptr;
+    void *d_inv = nullptr, *d_key = nullptr, *d_key2 = nullptr, *d_id = nullptr, *d_pdeg = nullptr, *d_tmp = nullptr;
     if ((rc = alloc(&d_prp, (n + 1) * sizeof(int64_t)))) return rc;
     M->own_p_rowptr = d_prp;
     if ((rc = alloc(&d_pcol, nnz * sizeof(int32_t)))) return rc;
@@ -86,19 +104,66 @@ int build_reorder(mlt_matrix* M, cudaStream_t s)
     }
     if ((rc = alloc(&d_perm, n * sizeof(int32_t)))) return rc;
     M->perm = static_cast<int32_t*>(d_perm);
-    if ((rc = alloc(&d_inv, n * sizeof(int32_t)))) return rc;
-    MLT_CUDA_TRY(cudaMemcpyAsync(d_prp, prp.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-    MLT_CUDA_TRY(cudaMemcpyAsync(d_perm, perm.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    MLT_CUDA_TRY(cudaMemcpyAsync(d_inv, inv.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-    if (n > 0) {
-        const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((n * 32 + 255) / 256, 16LL * M->num_sms));
-        ProfScope ps("relabel_rows", s);
-        relabel_rows_kernel<<<nb, 256, 0, s>>>(A.rowptr, A.col, A.val64, static_cast<int64_t*>(d_prp),
-                                               M->perm, static_cast<int32_t*>(d_inv), static_cast<int32_t*>(d_pcol),
-                                               static_cast<double*>(d_pval), n);
-        MLT_CUDA_TRY(cudaGetLastError());
+    // scratch, freed (stream-ordered) before returning
+    auto alloc_scratch = [&](void** p, size_t bytes) -> int {
+        const int r = alloc(p, bytes);
+        if (r == MLT_OK) scratch.push_back(*p);
+        return r;
+    };
+    if ((rc = alloc_scratch(&d_inv, n * sizeof(int32_t))) || (rc = alloc_scratch(&d_key, n * sizeof(uint32_t))) ||
+        (rc = alloc_scratch(&d_key2, n * sizeof(uint32_t))) || (rc = alloc_scratch(&d_id, n * sizeof(int32_t))) ||
+        (rc = alloc_scratch(&d_pdeg, n * sizeof(int64_t)))) {
+        release();
+        return rc;
     }
-    cudaFreeAsync(d_inv, s);
+    size_t sort_bytes = 0, scan_bytes = 0;
+    cudaError_t e = cub::DeviceRadixSort::SortPairs(nullptr, sort_bytes, static_cast<uint32_t*>(d_key),
+                                                    static_cast<uint32_t*>(d_key2), static_cast<int32_t*>(d_id),
+                                                    static_cast<int32_t*>(d_perm), nn, 0, 32, s);
+    if (e == cudaSuccess)
+        e = cub::DeviceScan::InclusiveSum(nullptr, scan_bytes, static_cast<int64_t*>(d_pdeg),
+                                          static_cast<int64_t*>(d_prp) + 1, nn, s);
+    if (e != cudaSuccess) {
+        release();
+        return fail(MLT_ECUDA, "relabelling: cub sizing failed");
+    }
+    const size_t tmp_bytes = std::max(sort_bytes, scan_bytes);
+    if ((rc = alloc_scratch(&d_tmp, tmp_bytes))) {
+        release();
+        return rc;
+    }
+    if (n > 0) {
+        const int nb = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 16LL * M->num_sms));
+        ProfScope ps("relabel", s);
+        degree_keys_kernel<<<nb, 256, 0, s>>>(A.rowptr, n, static_cast<uint32_t*>(d_key), static_cast<int32_t*>(d_id));
+        size_t b = tmp_bytes;
+        e = cub::DeviceRadixSort::SortPairs(d_tmp, b, static_cast<uint32_t*>(d_key), static_cast<uint32_t*>(d_key2),
+                                            static_cast<int32_t*>(d_id), static_cast<int32_t*>(d_perm), nn, 0, 32, s);
+        if (e == cudaSuccess) {
+            permuted_degrees_kernel<<<nb, 256, 0, s>>>(A.rowptr, static_cast<int32_t*>(d_perm), n,
+                                                       static_cast<int64_t*>(d_pdeg), static_cast<int32_t*>(d_inv));
+            e = cudaMemsetAsync(d_prp, 0, sizeof(int64_t), s);
+        }
+        if (e == cudaSuccess) {
+            b = tmp_bytes;
+            e = cub::DeviceScan::InclusiveSum(d_tmp, b, static_cast<int64_t*>(d_pdeg), static_cast<int64_t*>(d_prp) + 1,
+                                              nn, s);
+        }
+        if (e == cudaSuccess) {
+            const int nbr = (int)std::max<int64_t>(1, std::min<int64_t>((n * 32 + 255) / 256, 16LL * M->num_sms));
+            relabel_rows_kernel<<<nbr, 256, 0, s>>>(A.rowptr, A.col, A.val64, static_cast<int64_t*>(d_prp), M->perm,
+                                                    static_cast<int32_t*>(d_inv), static_cast<int32_t*>(d_pcol),
+                                                    static_cast<double*>(d_pval), n);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+            release();
+            return fail(MLT_ECUDA, "relabelling kernels failed");
+        }
+    } else {
+        MLT_CUDA_TRY(cudaMemsetAsync(d_prp, 0, sizeof(int64_t), s));
+    }
+    release();
     M->P.nrows = n;
     M->P.ncols = n;
     M->P.nnz = nnz;
