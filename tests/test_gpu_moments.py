@@ -300,3 +300,75 @@ def test_df64_mlmc_matches_oracle(L, O):
     with L.Matrix(m) as M:
         got = M.mlmc("log", 0.1, 8.1, 128, seed=0, levels=[8, 32, 128], m=[256, 64, 16], precision="df64")
     assert abs(got["estimate"] - ref["estimate"]) <= 1e-10 * np.sum(np.abs(ref["coeffs"])) * m.nrows
+
+
+def test_direct_mode_fp32_and_df64(L, O):
+    # direct mode reads and writes single columns of the dot slots (FP32 slots
+    # hold column pairs packed); ragged degrees retire probes step by step
+    m = synth.grid_laplacian_2d(20, shift=0.1)
+    deg = np.array([0, 1, 2, 3, 17, 40, 41, 5, 6] * 5, dtype=np.int32)
+    ref = O.moments(m, 0.1, 8.1, 7, 100, deg)
+    with L.Matrix(m) as M:
+        f32 = M.moments(0.1, 8.1, 7, 100, deg, precision="fp32", flags=L.MLT_DIRECT)
+        df = M.moments(0.1, 8.1, 7, 100, deg, precision="df64", flags=L.MLT_DIRECT)
+    assert np.max(np.abs(f32 - ref)) <= 64 * 2.0 ** -24 * m.nrows
+    assert np.max(np.abs(df - ref)) <= TOL64 * m.nrows
+
+
+@pytest.mark.parametrize("nprobes", [1, 3, 9, 33, 64, 129])
+@pytest.mark.parametrize("pattern", [False, True])
+def test_fp32_group_widths_short_and_long_rows(L, O, nprobes, pattern):
+    # FP32 lane groups of 1 to 32 lanes (1 to 129 live probes): groups of at
+    # least eight lanes gather in predicated blocks of eight, narrower ones in
+    # the plain loop.  Rows of 0 to 13 entries (not multiples of the block)
+    # plus three hub rows longer than a work chunk, cut into segments.
+    rng = np.random.default_rng(nprobes + 1000 * pattern)
+    d = 400
+    rows, cols = [], []
+    for i in range(d):
+        k = int(rng.integers(0, 7))
+        for j in rng.choice(d, size=k, replace=False):
+            if j != i:
+                rows += [i, j]
+                cols += [j, i]
+    for h in (3, 150, 397):
+        for j in range(d):
+            if j != h:
+                rows += [h, j]
+                cols += [j, h]
+    key = np.unique(np.array(rows, dtype=np.int64) * d + np.array(cols, dtype=np.int64))
+    r, c = key // d, key % d
+    rowptr = np.zeros(d + 1, dtype=np.int64)
+    np.cumsum(np.bincount(r, minlength=d), out=rowptr[1:])
+    val = None if pattern else rng.uniform(0.5, 1.5, size=key.size)
+    if val is not None:   # symmetric values
+        vm = {}
+        for t in range(key.size):
+            a_, b_ = int(r[t]), int(c[t])
+            vm.setdefault((min(a_, b_), max(a_, b_)), val[t])
+            val[t] = vm[(min(a_, b_), max(a_, b_))]
+    m = synth.CSR(d, d, rowptr, c.astype(np.int32), val)
+    sc = 1.0 / 400.0
+    a, b = O.interval(m, scale=sc)
+    deg = rng.integers(0, 40, size=nprobes).astype(np.int32)
+    deg[0] = 39
+    with L.Matrix(m, scale=sc) as M:
+        got = M.moments(a, b, 5, 17, deg, precision="fp32")
+    ref = O.moments(m, a, b, 5, 17, deg, scale=sc)
+    assert np.max(np.abs(got - ref)) <= 64 * 2.0 ** -24 * d
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 64 * 2.0 ** -24), ("df64", TOL64)])
+def test_relabelled_graph_window_ordered_segments(L, O, precision, tol):
+    # a power-law graph relabelled by degree, with hub rows cut into segments
+    # that are dealt out in column-window order; the order must not change the
+    # moments beyond rounding
+    g = synth.rmat_adjacency(12, 16, seed=7)
+    sc = 10.0 / float(np.max(np.diff(g.rowptr)))
+    deg = np.array([33, 20, 7, 2] * 10, dtype=np.int32)
+    with L.Matrix(g, scale=sc, reorder=True) as M:
+        got = M.moments(-10.0, 10.0, 9, 4, deg, precision=precision)
+        again = M.moments(-10.0, 10.0, 9, 4, deg, precision=precision)
+    ref = O.moments(g, -10.0, 10.0, 9, 4, deg, scale=sc)
+    assert np.array_equal(got, again)
+    assert np.max(np.abs(got - ref)) <= tol * g.nrows
