@@ -85,10 +85,11 @@ __device__ __forceinline__ void put_entry<df64>(df64* v, size_t row_off, int c, 
 }
 
 
-// Resident CTAs per SM the step kernel is compiled for, the unroll depth of
-// its gather loop, whether its gathers carry an L2 evict-last policy, and
-// whether long-row segments are dealt out in column-window order (see
-// ensure_spmm_plan), per vector type.  More unrolled gathers keep more row
+// Per vector type: the resident CTAs per SM the step kernel is compiled for
+// (C), the unroll depth of its gather loop (U), whether its gathers carry an
+// L2 evict-last policy (E), whether long-row segments are dealt out in
+// column-window order (W, see ensure_spmm_plan), predicated gather blocks (PR)
+// and the column-index prefetch on pattern matrices (PF).  More unrolled gathers keep more row
 // reads outstanding but need registers, which lowers the resident CTAs; the
 // evict-last policy keeps the gathered V_k rows in L2 against the streams of
 // V_{k-1}, V_{k+1} and the column indices.  Measured on the scale-22 R-MAT
@@ -102,8 +103,8 @@ __device__ __forceinline__ void put_entry<df64>(df64* v, size_t row_off, int c, 
 // steps on the graph 3-4% lower and the FP64 step, bound by FP64 arithmetic,
 // 2% higher.
 //
-// The last parameter shapes the gather loop for rows whose length is not a
-// multiple of the unroll depth: predicated (PR) gathers go in blocks of
+// PR shapes the gather loop for rows whose length is not a multiple of the
+// unroll depth: predicated gathers go in blocks of
 // unroll-depth slots, each slot switched off past the row's end, so that a
 // short row's gathers are all in flight together; without PR the compiler's
 // remainder loop takes them one at a time.  Predicated blocks took the FP32
