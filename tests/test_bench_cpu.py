@@ -51,3 +51,23 @@ def test_reference_arm_two_ranks():
     lines = _lines(r.stdout)
     assert len(lines) == 1          # rank 0 alone prints
     _check_line(lines[0], 2)
+
+
+def test_roofline_byte_and_flop_models():
+    # the per-launch algorithmic bytes of the recurrence step (survey 8(d)):
+    # the matrix once (4 bytes a stored entry for a pattern, 8 (d + 1) of row
+    # pointers) and, per live probe, V_k and V_{k-1} read and V_{k+1} written.
+    # The default Estrada step (R-MAT scale 22, 128 probes to degree 128 in
+    # double-float, two 64-probe groups of 64 launches) gives the 6.99 GB the
+    # bench line reports; an FP64 step costs 2 flops a stored entry and 8 a
+    # vector entry per probe-matvec.
+    sys.path.insert(0, ROOT)
+    import bench
+    d, nnz = 1 << 22, 128_307_214
+    got = bench.step_bytes(d, nnz, 4, 8, 128 * 64, {"cheb_step": 128})["cheb_step"]
+    assert got == 4 * nnz + 8 * (d + 1) + 3 * d * 8 * 64 == 6_989_234_240
+    # probes that retire early lower the average live width per launch
+    got2 = bench.step_bytes(1000, 7000, 8, 8, 10 * 3 + 2 * 5, {"cheb_step": 5})["cheb_step"]
+    assert got2 == 7000 * 8 + 8 * 1001 + 3 * 1000 * 8 * (40 / 5)
+    assert bench.step_bytes(d, nnz, 4, 8, 10, {}) == {}
+    assert bench.step_flops(4096, 20_224, 3) == 3 * (2 * 20_224 + 8 * 4096)
