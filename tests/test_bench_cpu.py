@@ -71,3 +71,22 @@ def test_roofline_byte_and_flop_models():
     assert got2 == 7000 * 8 + 8 * 1001 + 3 * 1000 * 8 * (40 / 5)
     assert bench.step_bytes(d, nnz, 4, 8, 10, {}) == {}
     assert bench.step_flops(4096, 20_224, 3) == 3 * (2 * 20_224 + 8 * 4096)
+
+
+def test_learned_comparison_figure_of_merit():
+    # the metric's comparison: at equal standard error the GPU time an
+    # estimator needs scales with its variance, so the figure of merit is
+    # (s^2 t)_plain / (s^2 t)_learned.  Hand example: plain FP64 s = 6, t = 5 s;
+    # plain FP32 s = 6, t = 1 s; learned estimates with s = 3 and 5 (pooled
+    # s^2 = 17) in 2 s each.  Training 9 s is repaid after 9 / (5 * 36/17 - 2)
+    # estimates.
+    sys.path.insert(0, ROOT)
+    import bench
+    cmp = {"plain_fp64": {"stderr": 6.0, "gpu_s": 5.0}, "plain_fp32": {"stderr": 6.0, "gpu_s": 1.0},
+           "learned": {"train_gpu_s": 9.0}}
+    bench.finish_comparison(cmp, [(10.0, 3.0), (11.0, 5.0)], 2.0, [7, 2])
+    assert abs(cmp["learned"]["stderr"] ** 2 - 17.0) < 1e-12
+    assert cmp["variance_time_gain"] == round(36 * 5 / (17 * 2), 3)
+    assert cmp["variance_time_gain_vs_plain_fp32"] == round(36 * 1 / (17 * 2), 3)
+    assert cmp["estimates_to_amortise_training"] == round(9 / (5 * 36 / 17 - 2), 1)
+    assert cmp["learned"]["estimate_first"] == 10.0 and cmp["learned"]["estimates"] == 2
